@@ -1,0 +1,133 @@
+"""Pins of the oracle's V-cycle, full multigrid, PCG and L2 error (Algorithms 1-2, Section 4.2)."""
+
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import assembly, fe, multigrid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fmg_iterations_paper.txt")
+
+
+def _paper_counts():
+    out = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        tok = line.split()
+        d, L = int(tok[0]), int(tok[1])
+        for k, v in enumerate(tok[2:], start=1):
+            if v != "-":
+                out[(d, L, k)] = int(v)
+    return out
+
+
+def _vcycle_matrix(H):
+    N = H.levels[H.L].N
+    B = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        B[:, i] = H.vcycle(H.L, e)
+    return B
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 1, 3), (2, 2, 3), (3, 2, 2)])
+def test_symmetric_vcycle_is_spd_and_contracting(d, k, L):
+    """Reverse-order post-smoothing makes B symmetric positive definite with eig(BA) in (0, 1]."""
+    H = multigrid.Hierarchy(d, k, L, symmetric=True)
+    B = _vcycle_matrix(H)
+    A = H.A[L].toarray()
+    assert np.abs(B - B.T).max() <= 1e-13 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    ev = np.linalg.eigvals(B @ A).real
+    assert ev.min() > 0.5 and ev.max() < 1 + 1e-10
+
+
+def test_forward_forward_vcycle_is_not_symmetric():
+    H = multigrid.Hierarchy(2, 2, 3, symmetric=False)
+    B = _vcycle_matrix(H)
+    assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("d,k", [(2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6), (2, 7), (3, 1), (3, 2)])
+def test_fmg_iteration_counts_against_paper(d, k):
+    """Algorithm 2 with f = 1 at L = 4: never more V-cycles than the paper prints
+    (Tables 1/2), and at most 3 for k >= 3 (Section 2.2)."""
+    paper = _paper_counts()[(d, 4, k)]
+    it = multigrid.fmg_iterations(d, k, 4, lambda X: np.ones(len(X)))
+    assert 1 <= it <= paper
+    if k >= 3:
+        assert it <= 3
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fmg_iterations_independent_of_level(k):
+    """Section 2.2: the count is independent of the mesh level (2D, L = 3..6), up to
+    one step for the lowest order, which the paper says saturates more slowly."""
+    its = [multigrid.fmg_iterations(2, k, L, lambda X: np.ones(len(X))) for L in (3, 4, 5, 6)]
+    assert max(its) - min(its) <= 1
+    if k >= 2:
+        assert its[-1] <= its[0]
+
+
+@pytest.mark.parametrize("d,k,L,sm,om", [(2, 2, 4, "multiplicative", 1.0), (2, 3, 3, "additive", 0.35),
+                                         (3, 2, 3, "multiplicative", 1.0), (3, 1, 3, "additive", 0.175)])
+def test_pcg_converges_to_direct_solution(d, k, L, sm, om):
+    H = multigrid.Hierarchy(d, k, L, smoother=sm, omega=om)
+    b = np.random.default_rng(5).uniform(-1, 1, H.levels[L].N)
+    x, it, rel = multigrid.pcg(H.A[L], b, H.precondition, rtol=1e-10, max_it=60)
+    assert rel <= 1e-10 and it < 30
+    xd = spla.spsolve(H.A[L].tocsc(), b)
+    assert np.abs(x - xd).max() <= 1e-8 * np.abs(xd).max()
+
+
+def test_pcg_breaks_down_or_stalls_with_literal_additive_damping_in_3d():
+    """omega = 0.7 with lambda_max(sum P_j) = 8 makes the 3D additive V-cycle indefinite."""
+    H = multigrid.Hierarchy(3, 2, 3, smoother="additive", omega=0.7)
+    b = np.random.default_rng(6).uniform(-1, 1, H.levels[3].N)
+    try:
+        _, it, rel = multigrid.pcg(H.A[3], b, H.precondition, rtol=1e-10, max_it=40)
+    except FloatingPointError:
+        return
+    assert rel > 1e-10
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 2, 3), (3, 2, 2)])
+def test_pcg_recovers_polynomial_solution_in_Vh(d, k, L):
+    H = multigrid.Hierarchy(d, k, L)
+    lv = H.levels[L]
+    u = lambda X: np.prod(X * (1 - X), axis=1)
+
+    def f(X):
+        s = np.zeros(len(X))
+        for t in range(d):
+            s += 2 * np.prod(np.delete(X * (1 - X), t, axis=1), axis=1)
+        return s
+    x, it, rel = multigrid.pcg(H.A[L], assembly.load_vector(lv, f), H.precondition, rtol=1e-12)
+    np.testing.assert_allclose(x, assembly.interpolate(lv, u), atol=1e-11)
+    assert multigrid.l2_error(lv, x, u) < 1e-12
+
+
+@pytest.mark.parametrize("d,k,levels", [(2, 1, (3, 4, 5)), (2, 2, (2, 3, 4)), (2, 3, (2, 3)), (3, 1, (2, 3))])
+def test_l2_error_converges_with_order_k_plus_1(d, k, levels):
+    """u = prod sin(pi x_t), f = d pi^2 u: ||u_h - u|| = O(h^(k+1)) (Section 4.2 test problem)."""
+    u = lambda X: np.prod(np.sin(np.pi * X), axis=1)
+    f = lambda X: d * np.pi ** 2 * u(X)
+    errs = []
+    for L in levels:
+        lv = fe.Level(d, k, L)
+        A = assembly.stiffness(lv)
+        x = spla.spsolve(A.tocsc(), assembly.load_vector(lv, f))
+        errs.append(multigrid.l2_error(lv, x, u))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - (k + 1)) < 0.25), rates
+
+
+def test_l2_error_of_exact_interpolant_of_constant_zero():
+    lv = fe.Level(2, 2, 2)
+    assert multigrid.l2_error(lv, np.zeros(lv.N), lambda X: np.zeros(len(X))) == 0.0
+    # ||1||_{L2} over the unit square, with u_h = 0: exactly 1
+    assert abs(multigrid.l2_error(lv, np.zeros(lv.N), lambda X: np.ones(len(X))) - 1.0) < 1e-14
