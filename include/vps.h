@@ -1,0 +1,194 @@
+/*
+ * vps.h -- C ABI of the GB300 vertex-patch multigrid library.
+ *
+ * The library solves the Poisson problem -Laplace u = f on (0,1)^d,
+ * u = 0 on the boundary (d = 2, 3; Section 2, Eq. 2.1), discretised with
+ * continuous Q_k Lagrange elements on Gauss-Lobatto support points on the
+ * uniform mesh with 2^level cells per direction (Section 2, Eq. 2.2-2.4).
+ * Its hot path is the geometric multigrid V-cycle (Algorithm 1) with a
+ * vertex-patch Schwarz smoother (Section 2.2, Algorithm 3) whose local
+ * solves use fast diagonalisation (Section 2.4, Eq. 2.13-2.15), the
+ * matrix-free operator (Section 2.3) and the grid transfers (Section 2.1),
+ * inside a preconditioned conjugate-gradient solver.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value: VPS_OK (0) or a negative VPS_E* code; no call aborts the
+ *   process.  vps_last_error() returns a message for the last failure.
+ * Handle: created by vps_create, owns the level hierarchy, the 1D tables
+ *   and all workspaces (device memory allocated at creation).  A handle is
+ *   used by one host thread at a time; all its work is issued on the CUDA
+ *   stream given to vps_create, asynchronously unless stated otherwise.
+ * Device vectors: every vector argument is a caller-owned DEVICE pointer
+ *   (e.g. a PyTorch tensor's data_ptr()), valid for the stream of the
+ *   handle.  They must not alias each other unless a call says so.
+ * Working precision: VPS_FP64 handles store level vectors as double,
+ *   VPS_FP32 handles as float ("void*" arguments below are of that type).
+ *   vps_solve always takes double vectors: with VPS_FP32 the V-cycle runs
+ *   in float inside a double-precision CG (mixed precision, Section 4.2).
+ * Level layout: a vector of level l holds all n1 = k 2^l + 1 nodes per
+ *   direction including the boundary, lexicographic with dimension 0
+ *   fastest, rows padded to `row_pitch` elements (vps_level_layout); entry
+ *   (i0,i1[,i2]) sits at i0 + row_pitch*(i1 + n1*i2).  Boundary nodes and
+ *   padding are ignored on input and written as 0 on output.
+ * Compact layout: interior nodes only, (n1-2)^d entries, lexicographic with
+ *   dimension 0 fastest.  This is the ordering of the paper's DoF layout
+ *   (Section 3.1.2) with the Dirichlet nodes eliminated.
+ */
+#ifndef VPS_H
+#define VPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vps_context* vps_handle;
+
+/* status codes */
+#define VPS_OK          0
+#define VPS_EINVAL     -1  /* bad argument (dimension, degree, level, pointer, damping, ...) */
+#define VPS_ENOMEM     -2  /* device allocation failed */
+#define VPS_ECUDA      -3  /* a CUDA runtime call or kernel launch failed */
+#define VPS_ENOCONV    -4  /* CG reached max_it without meeting the tolerance */
+#define VPS_EBREAKDOWN -5  /* CG breakdown: p^T A p <= 0 or a non-finite scalar */
+#define VPS_ETIMEOUT   -6  /* a bounded device-side wait expired */
+
+/* precision */
+#define VPS_FP64 0         /* everything in double */
+#define VPS_FP32 1         /* float level vectors and V-cycle; double outer CG */
+
+/* smoother */
+#define VPS_MULTIPLICATIVE 0  /* 2^d-colour multiplicative Schwarz, Algorithm 3 */
+#define VPS_ADDITIVE       1  /* damped additive Schwarz over the same patches */
+
+#define VPS_MAX_DEGREE 7
+
+/*
+ * vps_create -- build the hierarchy for Q_degree on 2^level cells per direction.
+ *   dim 2 or 3; degree 1..7; level >= 1 with at most 2^31 nodes per level
+ *   vector; precision VPS_FP64 or VPS_FP32; smoother VPS_MULTIPLICATIVE or
+ *   VPS_ADDITIVE; damping > 0 (used by the additive smoother; the
+ *   multiplicative one is undamped as in Algorithm 3); n_pre, n_post >= 0
+ *   smoothing steps per level in the V-cycle (Algorithm 1 uses 1 and 1).
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream; CUDA graphs
+ *   are only used on non-default streams).  On success *out receives the
+ *   handle.  Allocates all device memory; synchronous.
+ *   Errors: VPS_EINVAL (checked before any CUDA call), VPS_ENOMEM, VPS_ECUDA.
+ */
+int vps_create(int dim, int degree, int level, int precision, int smoother,
+               double damping, int n_pre, int n_post, void* cuda_stream,
+               vps_handle* out);
+
+/* vps_destroy -- synchronise the stream and free everything. NULL is a no-op. */
+int vps_destroy(vps_handle h);
+
+/*
+ * vps_sizes -- problem sizes of the finest level: interior DoFs, number of
+ * vertex patches (2^level - 1)^d, and device bytes held by the handle.
+ * Any output pointer may be NULL.
+ */
+int vps_sizes(vps_handle h, int64_t* n_interior, int64_t* n_patches,
+              size_t* device_bytes);
+
+/* vps_level_layout -- n1 (nodes per direction), row pitch and total
+ * elements of a level-layout vector of `level` (1..finest). */
+int vps_level_layout(vps_handle h, int level, int64_t* n1, int64_t* row_pitch,
+                     int64_t* total_elems);
+
+/* vps_pack / vps_unpack -- compact <-> level layout of `level`, working
+ * precision.  pack writes 0 to boundary and padding entries. */
+int vps_pack(vps_handle h, int level, const void* compact, void* level_vec);
+int vps_unpack(vps_handle h, int level, const void* level_vec, void* compact);
+
+/*
+ * vps_smooth -- n_steps smoothing steps S_l(x, b) on `level` (level layout,
+ * working precision), in place on x.  Multiplicative: one step visits the
+ * 2^d colours in increasing order; every colour is one fused kernel that
+ * gathers each patch's closure, forms the local residual
+ * r_j = R_j b - Abar_j Rbar_j x (Section 2.2) and adds A_j^{-1} r_j by fast
+ * diagonalisation (Eq. 2.13/2.14).  Additive: x += damping *
+ * sum_j R_j^T A_j^{-1} R_j (b - A x).  Requires level >= 2 (level 1 holds a
+ * single patch: use vps_vcycle).  b and x must not alias.
+ */
+int vps_smooth(vps_handle h, int level, const void* b, void* x, int n_steps);
+
+/* vps_smooth_colour -- one multiplicative colour pass (0 <= colour < 2^d) on
+ * `level` (>= 1), in place on x.  Used to test single launches. */
+int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* x);
+
+/* vps_apply -- y = A_level x (Eq. 2.3, matrix-free), working precision,
+ * level layout.  x and y must not alias. */
+int vps_apply(vps_handle h, int level, const void* x, void* y);
+
+/* vps_restrict -- r_coarse = (I^up)^T r_fine from level `fine_level` to
+ * fine_level-1 (Section 2.1: restriction is the transpose of prolongation). */
+int vps_restrict(vps_handle h, int fine_level, const void* r_fine, void* r_coarse);
+
+/* vps_prolongate_add -- x_fine += I^up x_coarse (interpolation of the coarse
+ * finite element function at the fine support points, Section 2.1). */
+int vps_prolongate_add(vps_handle h, int fine_level, const void* x_coarse, void* x_fine);
+
+/*
+ * vps_vcycle -- x = Vcycle_L(A_L, 0, b) on the finest level (Algorithm 1),
+ * level layout, working precision.  n_pre / n_post smoothing steps per
+ * level; the multiplicative post-smoother visits the colours in reverse
+ * order so that the cycle is a symmetric preconditioner; the coarsest
+ * level (level 1, one vertex patch) is solved exactly by one patch solve.
+ */
+int vps_vcycle(vps_handle h, const void* b, void* x);
+
+/*
+ * vps_solve -- CG on the finest level, preconditioned by one V-cycle per
+ * iteration, x0 = 0, until ||b - A x||_2 <= rtol ||b||_2 (beta in the
+ * flexible Polak-Ribiere form).  b, x: compact DOUBLE device vectors.
+ * iters / rel_res (host pointers, may be NULL) receive the iteration count
+ * and final relative residual.  Synchronises the stream once per iteration
+ * to read the residual norm.  Errors: VPS_ENOCONV, VPS_EBREAKDOWN, ...
+ */
+int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
+              int* iters, double* rel_res);
+
+/*
+ * vps_solve_host -- as vps_solve, but b and x are HOST pointers (compact,
+ * double).  Copies b to the device, solves, copies x back; synchronous.
+ */
+int vps_solve_host(vps_handle h, const double* b_host, double* x_host, double rtol,
+                   int max_it, int* iters, double* rel_res);
+
+/*
+ * vps_assemble_rhs_sines -- load vector b_i = int f phi_i (Eq. 2.4) on the
+ * finest level for f(x) = sum_m coef[m] prod_t sin(pi freq[m*dim+t] x_t),
+ * with (k+2)-point Gauss quadrature per cell and direction.  coef, freq:
+ * HOST arrays of n_modes (n_modes*dim) entries; b: compact DOUBLE device
+ * vector.
+ */
+int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef,
+                           const int* freq, double* b);
+
+/*
+ * vps_l2_error_sine -- ||u_h - u||_{L2} for u = prod_t sin(pi x_t) and the
+ * finite element function u_h with compact DOUBLE device coefficients x,
+ * by (k+2)^d Gauss points per cell.  *err (host) receives the value.
+ * Synchronous.
+ */
+int vps_l2_error_sine(vps_handle h, const double* x, double* err);
+
+/* vps_set_graphs -- 1: capture the V-cycle in a CUDA graph on first use and
+ * replay it (default on non-default streams); 0: launch kernels directly. */
+int vps_set_graphs(vps_handle h, int enable);
+
+/* vps_last_error -- message of the last failure on h (h = NULL: the last
+ * failure of vps_create on this thread).  Valid until the next call. */
+const char* vps_last_error(vps_handle h);
+
+/* vps_status_string -- name of a status code. */
+const char* vps_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VPS_H */

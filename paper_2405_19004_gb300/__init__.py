@@ -1,0 +1,234 @@
+"""GB300 vertex-patch multigrid for Q_k Poisson problems -- Python binding.
+
+A thin ctypes binding over the C ABI of ``libvps.so`` (``include/vps.h``):
+the functions below carry the same names as the C entry points and only
+marshal arguments; every numerical step runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.
+
+There is no CPU path: importing works without a GPU (so the library can be
+inspected), but every call that computes needs the compiled library and a
+CUDA device, and raises ``VpsError`` otherwise.
+"""
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libvps.so")
+
+VPS_OK = 0
+VPS_EINVAL = -1
+VPS_ENOMEM = -2
+VPS_ECUDA = -3
+VPS_ENOCONV = -4
+VPS_EBREAKDOWN = -5
+VPS_ETIMEOUT = -6
+VPS_FP64 = 0
+VPS_FP32 = 1
+VPS_MULTIPLICATIVE = 0
+VPS_ADDITIVE = 1
+VPS_MAX_DEGREE = 7
+
+# C signatures: name -> (restype, argtypes)
+_i, _d, _p, _i64p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "vps_create": (_i, [_i, _i, _i, _i, _i, _d, _i, _i, _p, ctypes.POINTER(_p)]),
+    "vps_destroy": (_i, [_p]),
+    "vps_sizes": (_i, [_p, _i64p, _i64p, ctypes.POINTER(ctypes.c_size_t)]),
+    "vps_level_layout": (_i, [_p, _i, _i64p, _i64p, _i64p]),
+    "vps_pack": (_i, [_p, _i, _p, _p]),
+    "vps_unpack": (_i, [_p, _i, _p, _p]),
+    "vps_smooth": (_i, [_p, _i, _p, _p, _i]),
+    "vps_smooth_colour": (_i, [_p, _i, _i, _p, _p]),
+    "vps_apply": (_i, [_p, _i, _p, _p]),
+    "vps_restrict": (_i, [_p, _i, _p, _p]),
+    "vps_prolongate_add": (_i, [_p, _i, _p, _p]),
+    "vps_vcycle": (_i, [_p, _p, _p]),
+    "vps_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "vps_solve_host": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "vps_assemble_rhs_sines": (_i, [_p, _i, _p, _p, _p]),
+    "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
+    "vps_set_graphs": (_i, [_p, _i]),
+    "vps_last_error": (ctypes.c_char_p, [_p]),
+    "vps_status_string": (ctypes.c_char_p, [_i]),
+}
+
+_lib = None
+
+
+class VpsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_status_name(code)} ({code}): {msg}")
+        self.code = code
+
+
+def _status_name(code):
+    names = {0: "VPS_OK", -1: "VPS_EINVAL", -2: "VPS_ENOMEM", -3: "VPS_ECUDA",
+             -4: "VPS_ENOCONV", -5: "VPS_EBREAKDOWN", -6: "VPS_ETIMEOUT"}
+    return names.get(code, "VPS_UNKNOWN")
+
+
+def lib():
+    """The loaded library (raises VpsError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise VpsError(VPS_ECUDA, f"{LIB_PATH} missing: run __graft_entry__.build() first "
+                                      "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(rc, handle=None):
+    if rc != VPS_OK:
+        msg = lib().vps_last_error(handle)
+        raise VpsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Poisson:
+    """One level hierarchy of -Laplace u = f on (0,1)^dim with Q_degree elements.
+
+    Owns a ``vps_handle``; all its work runs on ``self.stream`` (a torch CUDA
+    stream).  Each method makes the stream wait for the caller's current
+    stream before the call and the current stream wait for it afterwards.
+    """
+
+    def __init__(self, dim, degree, level, precision=VPS_FP64, smoother=VPS_MULTIPLICATIVE,
+                 damping=1.0, n_pre=1, n_post=1, stream=None, graphs=True):
+        import torch
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise VpsError(VPS_ECUDA, "no CUDA device (there is no CPU fallback)")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.dim, self.degree, self.level = dim, degree, level
+        self.precision, self.smoother = precision, smoother
+        h = ctypes.c_void_p()
+        rc = lib().vps_create(dim, degree, level, precision, smoother, float(damping), n_pre, n_post,
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != VPS_OK:
+            raise VpsError(rc, lib().vps_last_error(None).decode())
+        self.h = h
+        if not graphs:
+            _check(lib().vps_set_graphs(self.h, 0), self.h)
+        self.dtype = torch.float64 if precision == VPS_FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- ordering with torch's current stream
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _leave(self):
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
+    def _call(self, fn, *args):
+        self._enter()
+        try:
+            return _check(fn(self.h, *args), self.h)
+        finally:
+            self._leave()
+
+    # --- sizes and layouts
+    def sizes(self):
+        n, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib().vps_sizes(self.h, ctypes.byref(n), ctypes.byref(p), ctypes.byref(b)), self.h)
+        return n.value, p.value, b.value
+
+    def layout(self, level=None):
+        level = self.level if level is None else level
+        n1, px, tot = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().vps_level_layout(self.h, level, ctypes.byref(n1), ctypes.byref(px),
+                                      ctypes.byref(tot)), self.h)
+        return n1.value, px.value, tot.value
+
+    def empty_level(self, level=None, dtype=None):
+        n1, px, tot = self.layout(level)
+        return self.torch.zeros(tot, dtype=dtype or self.dtype, device="cuda")
+
+    def n_interior(self, level=None):
+        n1, _, _ = self.layout(level)
+        return (n1 - 2) ** self.dim
+
+    # --- entry points (same names as the C ABI)
+    def vps_pack(self, level, compact, lev):
+        self._call(lib().vps_pack, level, _ptr(compact), _ptr(lev))
+
+    def vps_unpack(self, level, lev, compact):
+        self._call(lib().vps_unpack, level, _ptr(lev), _ptr(compact))
+
+    def vps_smooth(self, level, b, x, n_steps=1):
+        self._call(lib().vps_smooth, level, _ptr(b), _ptr(x), n_steps)
+
+    def vps_smooth_colour(self, level, colour, b, x):
+        self._call(lib().vps_smooth_colour, level, colour, _ptr(b), _ptr(x))
+
+    def vps_apply(self, level, x, y):
+        self._call(lib().vps_apply, level, _ptr(x), _ptr(y))
+
+    def vps_restrict(self, fine_level, rf, rc):
+        self._call(lib().vps_restrict, fine_level, _ptr(rf), _ptr(rc))
+
+    def vps_prolongate_add(self, fine_level, xc, xf):
+        self._call(lib().vps_prolongate_add, fine_level, _ptr(xc), _ptr(xf))
+
+    def vps_vcycle(self, b, x):
+        self._call(lib().vps_vcycle, _ptr(b), _ptr(x))
+
+    def vps_solve(self, b, x, rtol=1e-10, max_it=100):
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._call(lib().vps_solve, _ptr(b), _ptr(x), float(rtol), int(max_it), ctypes.byref(it),
+                   ctypes.byref(rel))
+        return it.value, rel.value
+
+    def vps_solve_host(self, b_host, x_host, rtol=1e-10, max_it=100):
+        """b_host, x_host: CPU float64 tensors (pinned for full-speed copies)."""
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._call(lib().vps_solve_host, _ptr(b_host), _ptr(x_host), float(rtol), int(max_it),
+                   ctypes.byref(it), ctypes.byref(rel))
+        return it.value, rel.value
+
+    def vps_assemble_rhs_sines(self, coef, freq, b):
+        import numpy as np
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        freq = np.ascontiguousarray(freq, dtype=np.int32)
+        self._call(lib().vps_assemble_rhs_sines, len(coef), coef.ctypes.data_as(ctypes.c_void_p),
+                   freq.ctypes.data_as(ctypes.c_void_p), _ptr(b))
+
+    def vps_l2_error_sine(self, x):
+        err = ctypes.c_double()
+        self._call(lib().vps_l2_error_sine, _ptr(x), ctypes.byref(err))
+        return err.value
+
+    def vps_set_graphs(self, enable):
+        _check(lib().vps_set_graphs(self.h, int(bool(enable))), self.h)
+
+    # --- conveniences on compact vectors
+    def to_level(self, compact, level=None):
+        level = self.level if level is None else level
+        lev = self.empty_level(level)
+        self.vps_pack(level, compact.to(device="cuda", dtype=self.dtype).contiguous(), lev)
+        return lev
+
+    def to_compact(self, lev, level=None):
+        level = self.level if level is None else level
+        out = self.torch.empty(self.n_interior(level), dtype=lev.dtype, device="cuda")
+        self.vps_unpack(level, lev, out)
+        return out

@@ -1,0 +1,699 @@
+// C ABI of libvps: handle lifecycle, the V-cycle driver (Algorithm 1), the
+// preconditioned CG driver and the helpers declared in include/vps.h.
+//
+// Everything numerical runs in the kernels of kernels_dk.cu and ops.cu; this
+// file only validates arguments, owns device memory, sequences launches on
+// the handle's stream and, on non-default streams, captures the V-cycle
+// into a CUDA graph that is replayed on every later call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "vps.h"
+#include "vps_internal.h"
+
+namespace vps {
+void register_kernels_d2_k1(KernelSet*);
+void register_kernels_d2_k2(KernelSet*);
+void register_kernels_d2_k3(KernelSet*);
+void register_kernels_d2_k4(KernelSet*);
+void register_kernels_d2_k5(KernelSet*);
+void register_kernels_d2_k6(KernelSet*);
+void register_kernels_d2_k7(KernelSet*);
+void register_kernels_d3_k1(KernelSet*);
+void register_kernels_d3_k2(KernelSet*);
+void register_kernels_d3_k3(KernelSet*);
+void register_kernels_d3_k4(KernelSet*);
+void register_kernels_d3_k5(KernelSet*);
+void register_kernels_d3_k6(KernelSet*);
+void register_kernels_d3_k7(KernelSet*);
+}  // namespace vps
+
+using namespace vps;
+
+namespace {
+
+constexpr int kMaxLevels = 24;
+constexpr int kMaxDevices = 64;
+
+std::mutex g_mutex;
+bool g_registered = false;
+bool g_uploaded[kMaxDevices][2][kMaxK];
+thread_local std::string g_create_error;
+
+void register_all() {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_registered) return;
+  register_kernels_d2_k1(kernel_registry(2, 1));
+  register_kernels_d2_k2(kernel_registry(2, 2));
+  register_kernels_d2_k3(kernel_registry(2, 3));
+  register_kernels_d2_k4(kernel_registry(2, 4));
+  register_kernels_d2_k5(kernel_registry(2, 5));
+  register_kernels_d2_k6(kernel_registry(2, 6));
+  register_kernels_d2_k7(kernel_registry(2, 7));
+  register_kernels_d3_k1(kernel_registry(3, 1));
+  register_kernels_d3_k2(kernel_registry(3, 2));
+  register_kernels_d3_k3(kernel_registry(3, 3));
+  register_kernels_d3_k4(kernel_registry(3, 4));
+  register_kernels_d3_k5(kernel_registry(3, 5));
+  register_kernels_d3_k6(kernel_registry(3, 6));
+  register_kernels_d3_k7(kernel_registry(3, 7));
+  g_registered = true;
+}
+
+}  // namespace
+
+struct vps_context {
+  int dim = 0, k = 0, L = 0, prec = 0, smoother = 0;
+  double damping = 1.0;
+  int n_pre = 1, n_post = 1;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool use_graphs = false;
+  std::string err;
+  HostTables tab;
+  KernelSet* ks = nullptr;
+  LevelGeom geom[kMaxLevels + 1];
+  size_t esz = 8;                       // bytes per working-precision element
+  void* bv[kMaxLevels + 1] = {};        // per-level right-hand sides (working precision)
+  void* xv[kMaxLevels + 1] = {};        // per-level iterates
+  void* rv[kMaxLevels + 1] = {};        // per-level residuals
+  void* inv_lam = nullptr;              // 1/(sum of eigenvalues), working precision, m^d
+  // CG state, FP64, finest level layout
+  double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cz = nullptr,
+         *czn = nullptr, *cAp = nullptr;
+  double* partial = nullptr;            // 2 * kDotBlocks
+  double* dots = nullptr;               // scratch scalars for norms
+  CgScalars* sc = nullptr;
+  CgScalars* host_sc = nullptr;         // pinned
+  double* host_dots = nullptr;          // pinned
+  double* comp_b = nullptr;             // compact FP64 staging for vps_solve_host
+  double* comp_x = nullptr;
+  double* rhs_buf = nullptr;            // 1D load vectors for vps_assemble_rhs_sines
+  size_t rhs_cap = 0;
+  double* l2_tab = nullptr;             // basis table for the L2 error
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // captured preconditioner graph (input r = cr, output czn)
+  cudaGraphExec_t prec_graph = nullptr;
+};
+
+namespace {
+
+int fail(vps_context* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define VPS_CK(h, expr)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? VPS_ENOMEM : VPS_ECUDA, "%s: %s", \
+                  #expr, cudaGetErrorString(e_));                                        \
+  } while (0)
+
+int dalloc(vps_context* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, e == cudaErrorMemoryAllocation ? VPS_ENOMEM : VPS_ECUDA,
+                "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  e = cudaMemset(*p, 0, bytes);
+  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return VPS_OK;
+}
+
+int set_device(vps_context* h) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) {
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail(h, VPS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  }
+  return VPS_OK;
+}
+
+int check_level(vps_context* h, int level, int lo) {
+  if (level < lo || level > h->L)
+    return fail(h, VPS_EINVAL, "level %d outside %d..%d", level, lo, h->L);
+  return VPS_OK;
+}
+
+// ------------------------------------------------------------ smoothing
+template <typename T>
+const KernelFns<T>& fns(vps_context* h);
+template <>
+const KernelFns<float>& fns<float>(vps_context* h) { return h->ks->f; }
+template <>
+const KernelFns<double>& fns<double>(vps_context* h) { return h->ks->d; }
+
+template <typename T>
+int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
+  const LevelGeom& g = h->geom[l];
+  const int nc = 1 << h->dim;
+  const T* il = static_cast<const T*>(h->inv_lam);
+  if (h->smoother == VPS_ADDITIVE) {
+    T* r = static_cast<T*>(h->rv[l]);
+    VPS_CK(h, fns<T>(h).apply(g, x, b, r, h->stream));
+    for (int c = 0; c < nc; ++c)
+      VPS_CK(h, fns<T>(h).smooth_add(g, make_colour(g, c), r, x, il, (T)h->damping, h->stream));
+  } else {
+    for (int i = 0; i < nc; ++i) {
+      const int c = forward ? i : nc - 1 - i;
+      VPS_CK(h, fns<T>(h).smooth_mult(g, make_colour(g, c), b, x, il, h->stream));
+    }
+  }
+  return VPS_OK;
+}
+
+// x_L = Vcycle_L(A_L, 0, b_L) (Algorithm 1) in working precision T.
+template <typename T>
+int vcycle_core(vps_context* h, const T* bL, T* xL) {
+  const KernelFns<T>& F = fns<T>(h);
+  const T* b[kMaxLevels + 1];
+  T* x[kMaxLevels + 1];
+  for (int l = 1; l <= h->L; ++l) {
+    b[l] = static_cast<const T*>(h->bv[l]);
+    x[l] = static_cast<T*>(h->xv[l]);
+  }
+  b[h->L] = bL;
+  x[h->L] = xL;
+  for (int l = h->L; l >= 2; --l) {
+    const LevelGeom& g = h->geom[l];
+    VPS_CK(h, cudaMemsetAsync(x[l], 0, g.total * sizeof(T), h->stream));
+    for (int s = 0; s < h->n_pre; ++s) {
+      int rc = smooth_step<T>(h, l, b[l], x[l], true);
+      if (rc) return rc;
+    }
+    T* r = static_cast<T*>(h->rv[l]);
+    VPS_CK(h, F.apply(g, x[l], b[l], r, h->stream));
+    VPS_CK(h, F.restrict_(g, h->geom[l - 1], r, static_cast<T*>(h->bv[l - 1]), h->stream));
+  }
+  // coarsest level: one vertex patch holds every interior DoF; one patch
+  // solve from zero is the exact coarse solve
+  {
+    const LevelGeom& g = h->geom[1];
+    VPS_CK(h, cudaMemsetAsync(x[1], 0, g.total * sizeof(T), h->stream));
+    VPS_CK(h, F.smooth_mult(g, make_colour(g, 0), b[1], x[1],
+                            static_cast<const T*>(h->inv_lam), h->stream));
+  }
+  for (int l = 2; l <= h->L; ++l) {
+    VPS_CK(h, F.prolong_add(h->geom[l], h->geom[l - 1], x[l - 1], x[l], h->stream));
+    for (int s = 0; s < h->n_post; ++s) {
+      int rc = smooth_step<T>(h, l, b[l], x[l], false);
+      if (rc) return rc;
+    }
+  }
+  return VPS_OK;
+}
+
+// z = B r for the CG: FP64 V-cycle, or cast -> FP32 V-cycle -> cast.
+int precondition_direct(vps_context* h) {
+  const LevelGeom& g = h->geom[h->L];
+  if (h->prec == VPS_FP64) return vcycle_core<double>(h, h->cr, h->czn);
+  VPS_CK(h, launch_cast_d2f(h->cr, static_cast<float*>(h->bv[h->L]), g.total, h->stream));
+  int rc = vcycle_core<float>(h, static_cast<const float*>(h->bv[h->L]),
+                              static_cast<float*>(h->xv[h->L]));
+  if (rc) return rc;
+  VPS_CK(h, launch_cast_f2d(static_cast<const float*>(h->xv[h->L]), h->czn, g.total, h->stream));
+  return VPS_OK;
+}
+
+int precondition(vps_context* h) {
+  if (!h->use_graphs) return precondition_direct(h);
+  if (!h->prec_graph) {
+    cudaGraph_t graph = nullptr;
+    VPS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = precondition_direct(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(h, VPS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->prec_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->prec_graph = nullptr;
+      return fail(h, VPS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  VPS_CK(h, cudaGraphLaunch(h->prec_graph, h->stream));
+  return VPS_OK;
+}
+
+int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_res) {
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t n = g.total;
+  // ||b||
+  VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  const double nb = std::sqrt(h->host_dots[0]);
+  VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  if (!(nb > 0.0)) {
+    if (!std::isfinite(nb)) return fail(h, VPS_EBREAKDOWN, "right-hand side is not finite");
+    return VPS_OK;
+  }
+  VPS_CK(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+  int rc = precondition(h);
+  if (rc) return rc;
+  VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+  double rel = 1.0;
+  for (int it = 1; it <= max_it; ++it) {
+    VPS_CK(h, h->ks->d.apply(g, h->cp, nullptr, h->cAp, h->stream));
+    VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
+    VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
+    VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
+    VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                              h->stream));
+    VPS_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->host_sc->flag) {
+      if (iters) *iters = it;
+      return fail(h, VPS_EBREAKDOWN, "CG breakdown at iteration %d (p^T A p = %g)", it,
+                  h->host_sc->pAp);
+    }
+    rel = std::sqrt(h->host_sc->rr) / nb;
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = rel;
+    if (!std::isfinite(rel))
+      return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
+    if (rel <= rtol) return VPS_OK;
+    if (it == max_it) break;
+    rc = precondition(h);
+    if (rc) return rc;
+    VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
+    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream));
+  }
+  return fail(h, VPS_ENOCONV, "CG did not reach %g in %d iterations (%g)", rtol, max_it, rel);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vps_status_string(int s) {
+  switch (s) {
+    case VPS_OK: return "VPS_OK";
+    case VPS_EINVAL: return "VPS_EINVAL";
+    case VPS_ENOMEM: return "VPS_ENOMEM";
+    case VPS_ECUDA: return "VPS_ECUDA";
+    case VPS_ENOCONV: return "VPS_ENOCONV";
+    case VPS_EBREAKDOWN: return "VPS_EBREAKDOWN";
+    case VPS_ETIMEOUT: return "VPS_ETIMEOUT";
+    default: return "unknown status";
+  }
+}
+
+const char* vps_last_error(vps_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int vps_create(int dim, int degree, int level, int precision, int smoother, double damping,
+               int n_pre, int n_post, void* cuda_stream, vps_handle* out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, VPS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(nullptr, VPS_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+  if (degree < 1 || degree > VPS_MAX_DEGREE)
+    return fail(nullptr, VPS_EINVAL, "degree must be 1..%d (got %d)", VPS_MAX_DEGREE, degree);
+  if (level < 1 || level > kMaxLevels) return fail(nullptr, VPS_EINVAL, "level must be >= 1");
+  if (precision != VPS_FP64 && precision != VPS_FP32)
+    return fail(nullptr, VPS_EINVAL, "precision must be VPS_FP64 or VPS_FP32");
+  if (smoother != VPS_MULTIPLICATIVE && smoother != VPS_ADDITIVE)
+    return fail(nullptr, VPS_EINVAL, "smoother must be VPS_MULTIPLICATIVE or VPS_ADDITIVE");
+  if (!(damping > 0.0) || !std::isfinite(damping))
+    return fail(nullptr, VPS_EINVAL, "damping must be positive and finite");
+  if (n_pre < 0 || n_post < 0 || n_pre > 64 || n_post > 64)
+    return fail(nullptr, VPS_EINVAL, "n_pre/n_post must be 0..64");
+  {
+    const LevelGeom g = make_geom(dim, degree, level);
+    if ((double)g.total > 2147483647.0)
+      return fail(nullptr, VPS_EINVAL, "level %d too large: %lld elements per vector", level,
+                  (long long)g.total);
+  }
+  register_all();
+  vps_context* h = new vps_context();
+  h->dim = dim; h->k = degree; h->L = level; h->prec = precision; h->smoother = smoother;
+  h->damping = damping; h->n_pre = n_pre; h->n_post = n_post;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->use_graphs = h->stream != nullptr;
+  h->esz = precision == VPS_FP64 ? sizeof(double) : sizeof(float);
+  char ebuf[256];
+  if (!build_tables(degree, &h->tab, ebuf, sizeof(ebuf))) {
+    delete h;
+    return fail(nullptr, VPS_EINVAL, "%s", ebuf);
+  }
+  h->ks = kernel_registry(dim, degree);
+  if (!h->ks || !h->ks->present) {
+    delete h;
+    return fail(nullptr, VPS_EINVAL, "no kernels for dim %d degree %d", dim, degree);
+  }
+  auto bail = [&](int rc) {
+    g_create_error = h->err;
+    vps_destroy(h);
+    return rc;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return bail(VPS_ECUDA);
+  }
+  if (h->device < 0 || h->device >= kMaxDevices) {
+    h->err = "device index out of range";
+    return bail(VPS_ECUDA);
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    bool& up = g_uploaded[h->device][dim - 2][degree - 1];
+    if (!up) {
+      e = h->ks->upload(h->tab);
+      if (e != cudaSuccess) {
+        h->err = std::string("constant upload: ") + cudaGetErrorString(e);
+        return bail(VPS_ECUDA);
+      }
+      up = true;
+    }
+  }
+  int rc;
+  for (int l = 1; l <= level; ++l) {
+    h->geom[l] = make_geom(dim, degree, l);
+    const size_t vb = (size_t)h->geom[l].total * h->esz;
+    if ((rc = dalloc(h, &h->bv[l], vb)) || (rc = dalloc(h, &h->xv[l], vb)) ||
+        (rc = dalloc(h, &h->rv[l], vb)))
+      return bail(rc);
+  }
+  // 1/(lambda_i + lambda_j [+ lambda_l]) in reference units
+  {
+    const int m = h->tab.m;
+    const int md = dim == 3 ? m * m * m : m * m;
+    std::vector<double> il(md);
+    for (int a = 0; a < md; ++a) {
+      const int i0 = a % m, i1 = (a / m) % m, i2 = a / (m * m);
+      double s = h->tab.lam[i0] + h->tab.lam[i1] + (dim == 3 ? h->tab.lam[i2] : 0.0);
+      il[a] = 1.0 / s;
+    }
+    if ((rc = dalloc(h, &h->inv_lam, md * h->esz))) return bail(rc);
+    if (precision == VPS_FP64) {
+      e = cudaMemcpy(h->inv_lam, il.data(), md * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> f(il.begin(), il.end());
+      e = cudaMemcpy(h->inv_lam, f.data(), md * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+      h->err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+      return bail(VPS_ECUDA);
+    }
+  }
+  const LevelGeom& gf = h->geom[level];
+  const size_t db = (size_t)gf.total * sizeof(double);
+  const int64_t ni = gf.n1 - 2;
+  const size_t cbytes = (size_t)(dim == 3 ? ni * ni * ni : ni * ni) * sizeof(double);
+  void* p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cb = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cx = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cr = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cp = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cz = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->czn = (double*)p;
+  if ((rc = dalloc(h, &p, db))) return bail(rc); h->cAp = (double*)p;
+  if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_b = (double*)p;
+  if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_x = (double*)p;
+  if ((rc = dalloc(h, &p, 2 * kDotBlocks * sizeof(double)))) return bail(rc); h->partial = (double*)p;
+  if ((rc = dalloc(h, &p, 8 * sizeof(double)))) return bail(rc); h->dots = (double*)p;
+  if ((rc = dalloc(h, &p, sizeof(CgScalars)))) return bail(rc); h->sc = (CgScalars*)p;
+  if ((rc = dalloc(h, &p, 256 * sizeof(double)))) return bail(rc); h->l2_tab = (double*)p;
+  e = cudaMallocHost(&p, sizeof(CgScalars));
+  if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
+  h->host_sc = (CgScalars*)p;
+  e = cudaMallocHost(&p, 8 * sizeof(double));
+  if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
+  h->host_dots = (double*)p;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    h->err = std::string("create: ") + cudaGetErrorString(e);
+    return bail(VPS_ECUDA);
+  }
+  *out = h;
+  return VPS_OK;
+}
+
+int vps_destroy(vps_handle h) {
+  if (!h) return VPS_OK;
+  if (h->device >= 0) cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->prec_graph) cudaGraphExecDestroy(h->prec_graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->host_sc) cudaFreeHost(h->host_sc);
+  if (h->host_dots) cudaFreeHost(h->host_dots);
+  delete h;
+  return VPS_OK;
+}
+
+int vps_sizes(vps_handle h, int64_t* n_interior, int64_t* n_patches, size_t* device_bytes) {
+  if (!h) return VPS_EINVAL;
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t ni = g.n1 - 2, nv = g.ncell - 1;
+  if (n_interior) *n_interior = h->dim == 3 ? ni * ni * ni : ni * ni;
+  if (n_patches) *n_patches = h->dim == 3 ? nv * nv * nv : nv * nv;
+  if (device_bytes) *device_bytes = h->bytes;
+  return VPS_OK;
+}
+
+int vps_level_layout(vps_handle h, int level, int64_t* n1, int64_t* row_pitch, int64_t* total) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  const LevelGeom& g = h->geom[level];
+  if (n1) *n1 = g.n1;
+  if (row_pitch) *row_pitch = g.px;
+  if (total) *total = g.total;
+  return VPS_OK;
+}
+
+int vps_pack(vps_handle h, int level, const void* compact, void* lev) {
+  if (!h || !compact || !lev) return h ? fail(h, VPS_EINVAL, "NULL vector") : VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (int rc = set_device(h)) return rc;
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, launch_pack<double>(h->geom[level], (const double*)compact, (double*)lev, h->stream));
+  else
+    VPS_CK(h, launch_pack<float>(h->geom[level], (const float*)compact, (float*)lev, h->stream));
+  return VPS_OK;
+}
+
+int vps_unpack(vps_handle h, int level, const void* lev, void* compact) {
+  if (!h || !compact || !lev) return h ? fail(h, VPS_EINVAL, "NULL vector") : VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (int rc = set_device(h)) return rc;
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, launch_unpack<double>(h->geom[level], (const double*)lev, (double*)compact, h->stream));
+  else
+    VPS_CK(h, launch_unpack<float>(h->geom[level], (const float*)lev, (float*)compact, h->stream));
+  return VPS_OK;
+}
+
+int vps_smooth(vps_handle h, int level, const void* b, void* x, int n_steps) {
+  if (!h) return VPS_EINVAL;
+  if (!b || !x || b == x) return fail(h, VPS_EINVAL, "b and x must be distinct non-NULL vectors");
+  if (n_steps < 0) return fail(h, VPS_EINVAL, "n_steps < 0");
+  if (int rc = check_level(h, level, 2)) return rc;
+  if (int rc = set_device(h)) return rc;
+  for (int s = 0; s < n_steps; ++s) {
+    int rc = h->prec == VPS_FP64
+                 ? smooth_step<double>(h, level, (const double*)b, (double*)x, true)
+                 : smooth_step<float>(h, level, (const float*)b, (float*)x, true);
+    if (rc) return rc;
+  }
+  return VPS_OK;
+}
+
+int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* x) {
+  if (!h) return VPS_EINVAL;
+  if (!b || !x || b == x) return fail(h, VPS_EINVAL, "b and x must be distinct non-NULL vectors");
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (colour < 0 || colour >= (1 << h->dim)) return fail(h, VPS_EINVAL, "colour out of range");
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[level];
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, h->ks->d.smooth_mult(g, make_colour(g, colour), (const double*)b, (double*)x,
+                                   (const double*)h->inv_lam, h->stream));
+  else
+    VPS_CK(h, h->ks->f.smooth_mult(g, make_colour(g, colour), (const float*)b, (float*)x,
+                                   (const float*)h->inv_lam, h->stream));
+  return VPS_OK;
+}
+
+int vps_apply(vps_handle h, int level, const void* x, void* y) {
+  if (!h) return VPS_EINVAL;
+  if (!x || !y || x == y) return fail(h, VPS_EINVAL, "x and y must be distinct non-NULL vectors");
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[level];
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, h->ks->d.apply(g, (const double*)x, nullptr, (double*)y, h->stream));
+  else
+    VPS_CK(h, h->ks->f.apply(g, (const float*)x, nullptr, (float*)y, h->stream));
+  return VPS_OK;
+}
+
+int vps_restrict(vps_handle h, int fine_level, const void* rf, void* rc_) {
+  if (!h) return VPS_EINVAL;
+  if (!rf || !rc_ || rf == rc_) return fail(h, VPS_EINVAL, "bad vectors");
+  if (int rc = check_level(h, fine_level, 2)) return rc;
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom &f = h->geom[fine_level], &c = h->geom[fine_level - 1];
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, h->ks->d.restrict_(f, c, (const double*)rf, (double*)rc_, h->stream));
+  else
+    VPS_CK(h, h->ks->f.restrict_(f, c, (const float*)rf, (float*)rc_, h->stream));
+  return VPS_OK;
+}
+
+int vps_prolongate_add(vps_handle h, int fine_level, const void* xc, void* xf) {
+  if (!h) return VPS_EINVAL;
+  if (!xc || !xf || xc == xf) return fail(h, VPS_EINVAL, "bad vectors");
+  if (int rc = check_level(h, fine_level, 2)) return rc;
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom &f = h->geom[fine_level], &c = h->geom[fine_level - 1];
+  if (h->prec == VPS_FP64)
+    VPS_CK(h, h->ks->d.prolong_add(f, c, (const double*)xc, (double*)xf, h->stream));
+  else
+    VPS_CK(h, h->ks->f.prolong_add(f, c, (const float*)xc, (float*)xf, h->stream));
+  return VPS_OK;
+}
+
+int vps_vcycle(vps_handle h, const void* b, void* x) {
+  if (!h) return VPS_EINVAL;
+  if (!b || !x || b == x) return fail(h, VPS_EINVAL, "b and x must be distinct non-NULL vectors");
+  if (int rc = set_device(h)) return rc;
+  return h->prec == VPS_FP64 ? vcycle_core<double>(h, (const double*)b, (double*)x)
+                             : vcycle_core<float>(h, (const float*)b, (float*)x);
+}
+
+int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it, int* iters,
+              double* rel_res) {
+  if (!h) return VPS_EINVAL;
+  if (!b || !x) return fail(h, VPS_EINVAL, "NULL vector");
+  if (!(rtol > 0.0) || max_it < 1) return fail(h, VPS_EINVAL, "need rtol > 0 and max_it >= 1");
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[h->L];
+  VPS_CK(h, launch_pack<double>(g, b, h->cb, h->stream));
+  int rc = cg_solve(h, rtol, max_it, iters, rel_res);
+  cudaError_t e = launch_unpack<double>(g, h->cx, x, h->stream);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "unpack: %s", cudaGetErrorString(e));
+  return VPS_OK;
+}
+
+int vps_solve_host(vps_handle h, const double* b_host, double* x_host, double rtol, int max_it,
+                   int* iters, double* rel_res) {
+  if (!h) return VPS_EINVAL;
+  if (!b_host || !x_host) return fail(h, VPS_EINVAL, "NULL vector");
+  if (int rc = set_device(h)) return rc;
+  const int64_t ni = h->geom[h->L].n1 - 2;
+  const size_t nbytes = (size_t)(h->dim == 3 ? ni * ni * ni : ni * ni) * sizeof(double);
+  VPS_CK(h, cudaMemcpyAsync(h->comp_b, b_host, nbytes, cudaMemcpyHostToDevice, h->stream));
+  int rc = vps_solve(h, h->comp_b, h->comp_x, rtol, max_it, iters, rel_res);
+  VPS_CK(h, cudaMemcpyAsync(x_host, h->comp_x, nbytes, cudaMemcpyDeviceToHost, h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef, const int* freq,
+                           double* b) {
+  if (!h) return VPS_EINVAL;
+  if (n_modes < 1 || n_modes > 4096 || !coef || !freq || !b)
+    return fail(h, VPS_EINVAL, "bad sine-mode arguments");
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[h->L];
+  const int k = h->k, ni = g.n1 - 2, q = k + 2;
+  double xq[16], wq[16], val[kMaxK + 1];
+  gauss_rule(q, xq, wq);
+  // b1d[(mode*dim + t)*ni + j] = int sin(pi f x) phi_{j+1}(x) dx (times coef for t = 0)
+  std::vector<double> b1d((size_t)n_modes * h->dim * ni, 0.0);
+  std::vector<double> full(g.n1);
+  for (int md = 0; md < n_modes; ++md)
+    for (int t = 0; t < h->dim; ++t) {
+      const double f = freq[md * h->dim + t];
+      std::fill(full.begin(), full.end(), 0.0);
+      for (int c = 0; c < g.ncell; ++c)
+        for (int qq = 0; qq < q; ++qq) {
+          const double x = (c + xq[qq]) * g.h;
+          const double fv = std::sin(M_PI * f * x) * wq[qq] * g.h;
+          lagrange_eval(k, h->tab.z, xq[qq], val);
+          for (int i = 0; i <= k; ++i) full[k * c + i] += fv * val[i];
+        }
+      const double s = t == 0 ? coef[md] : 1.0;
+      for (int j = 0; j < ni; ++j) b1d[((size_t)md * h->dim + t) * ni + j] = s * full[j + 1];
+    }
+  const size_t need = b1d.size() * sizeof(double);
+  if (need > h->rhs_cap) {
+    if (h->rhs_buf) cudaFree(h->rhs_buf);
+    h->rhs_buf = nullptr;
+    h->rhs_cap = 0;
+    cudaError_t e = cudaMalloc(&h->rhs_buf, need);
+    if (e != cudaSuccess) return fail(h, VPS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    h->rhs_cap = need;
+  }
+  VPS_CK(h, cudaMemcpyAsync(h->rhs_buf, b1d.data(), need, cudaMemcpyHostToDevice, h->stream));
+  VPS_CK(h, launch_rhs_tensor(g, n_modes, h->rhs_buf, b, h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  return VPS_OK;
+}
+
+int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
+  if (!h) return VPS_EINVAL;
+  if (!x || !err) return fail(h, VPS_EINVAL, "NULL pointer");
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[h->L];
+  const int k = h->k, q = k + 2, nl = k + 1;
+  double xq[16], wq[16], val[kMaxK + 1];
+  gauss_rule(q, xq, wq);
+  std::vector<double> tab(nl * q + 2 * q);
+  for (int qq = 0; qq < q; ++qq) {
+    lagrange_eval(k, h->tab.z, xq[qq], val);
+    for (int a = 0; a <= k; ++a) tab[a * q + qq] = val[a];
+  }
+  for (int qq = 0; qq < q; ++qq) {
+    tab[nl * q + qq] = xq[qq];
+    tab[nl * q + q + qq] = wq[qq];
+  }
+  VPS_CK(h, cudaMemcpyAsync(h->l2_tab, tab.data(), tab.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, h->stream));
+  VPS_CK(h, launch_pack<double>(g, x, h->cx, h->stream));
+  VPS_CK(h, launch_l2_error_sine(g, h->cx, h->l2_tab, q, h->partial, h->dots, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  *err = std::sqrt(h->host_dots[0]);
+  return VPS_OK;
+}
+
+int vps_set_graphs(vps_handle h, int enable) {
+  if (!h) return VPS_EINVAL;
+  if (enable && !h->stream) return fail(h, VPS_EINVAL, "CUDA graphs need a non-default stream");
+  h->use_graphs = enable != 0;
+  return VPS_OK;
+}
+
+}  // extern "C"

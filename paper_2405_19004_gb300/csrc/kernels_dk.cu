@@ -1,0 +1,973 @@
+// Hot-path kernels for one (dimension, degree) pair.
+//
+// This file is compiled once per pair with -DVPS_DIM=<2|3> -DVPS_K=<1..7>;
+// each object registers its entry points in the library's kernel registry.
+// Every 1D matrix lives in this unit's __constant__ memory and is indexed
+// with compile-time offsets only (all contraction loops are unrolled), so
+// the multiply-adds take their matrix operand straight from the constant
+// bank and shared memory only carries tensor data.
+//
+// Kernels
+//  * smooth_mult  -- one colour of the multiplicative vertex-patch smoother
+//                    (Algorithm 3, the "Fused" kernel of Section 3.1.3): per
+//                    patch, gather the closure x and interior b, local
+//                    residual r = b - Abar x by sum factorisation with the
+//                    reuse of Section 3.1.1, local solve by fast
+//                    diagonalisation (Eq. 2.13/2.14), interior update.
+//  * smooth_add   -- one colour of the additive smoother from a global
+//                    residual (fast diagonalisation only).
+//  * apply        -- y = A x or r = b - A x: the operator as a Kronecker sum
+//                    of banded global 1D matrices (Section 2.3, Cartesian
+//                    mesh), evaluated on output tiles without atomics.
+//  * prolong_add / restrict_ -- tensor-product interpolation and its
+//                    transpose (Section 2.1), per coarse-cell tile.
+//
+// Shared-memory layouts.  A contraction stage reads a tensor whose slowest
+// index is the contracted one, in[c][L], and writes out[L][o]: the output's
+// slowest index is then the next direction to contract, so directions
+// rotate z -> y -> x without transposes.  With P patches per block the
+// patch index is the fastest index ([c][L][p]); P is a power of two, so
+// for both 4- and 8-byte words every warp access is free of bank conflicts
+// (the odd extents 2k+1 and 2k-1 keep the strided writes conflict free).
+#include <cstdio>
+
+#include "vps_internal.h"
+
+#ifndef VPS_DIM
+#error "compile with -DVPS_DIM=2|3"
+#endif
+#ifndef VPS_K
+#error "compile with -DVPS_K=1..7"
+#endif
+
+namespace vps {
+namespace {
+
+constexpr int DIM = VPS_DIM;
+constexpr int K = VPS_K;
+constexpr int n = 2 * K + 1;   // patch closure nodes per direction
+constexpr int m = 2 * K - 1;   // patch interior nodes per direction
+constexpr int nl = K + 1;      // nodes per cell and direction
+
+template <typename T>
+struct DevTab {
+  T Ap[m * n];
+  T Mp[m * n];
+  T S[m * m];
+  T Kb[K * n];
+  T Mb[K * n];
+  T P1[n * nl];
+};
+
+template <typename T>
+__constant__ DevTab<T> c_tab;
+
+// ---------------------------------------------------------------- config
+template <typename T>
+struct SmoothCfg {
+  // patches per block (power of two) and threads per block
+  static constexpr int P = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 8 : K == 3 ? 4 : K <= 5 ? 2 : 1)
+                                    : (K <= 3 ? 32 : 16);
+  static constexpr int lines0 = DIM == 3 ? n * n : n;
+  static constexpr int NT0 = ((P * lines0 + 31) / 32) * 32;
+  static constexpr int NT = NT0 > 256 ? 256 : NT0;
+  static constexpr int NB = 128 / (int)sizeof(T);  // word-banks per wavefront
+  // patch-major stride of the first stage's output, chosen so that the
+  // next stage (patch index fastest) hits P distinct bank groups
+  static constexpr int size0 = DIM == 3 ? n * n * m : n * m;
+  static constexpr int S0 = P == 1 ? size0
+                                   : size0 + ((((NB / P) - size0) % NB) + NB) % NB;
+  // stage-1 outputs: U and W in 3D, the residual R in 2D
+  static constexpr int sizeU = DIM == 3 ? n * m * m : m * m;
+  static constexpr int nU = DIM == 3 ? 2 : 1;
+  static constexpr int md = DIM == 3 ? m * m * m : m * m;
+  static constexpr size_t smem_mult = sizeof(T) * (size_t)(2 * P * S0 + nU * P * sizeU);
+  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md);
+};
+
+__device__ __forceinline__ int64_t closure_origin(int64_t gp, const ColourGeom& cg, int64_t px,
+                                                  int64_t pz) {
+  const int64_t i0 = gp % cg.cnt[0];
+  const int64_t r = gp / cg.cnt[0];
+  const int64_t i1 = r % cg.cnt[1];
+  const int64_t i2 = r / cg.cnt[1];
+  const int64_t o0 = (int64_t)K * (cg.par[0] + 2 * i0);
+  const int64_t o1 = (int64_t)K * (cg.par[1] + 2 * i1);
+  const int64_t o2 = DIM == 3 ? (int64_t)K * (cg.par[2] + 2 * i2) : 0;
+  return o0 + o1 * px + o2 * pz;
+}
+
+// One fast-diagonalisation contraction over interleaved tensors.
+// MODE 0: out = S^T in, MODE 1: out = (S^T in) * inv_lam, MODE 2: out = S in.
+template <typename T, int P, int NT, int MODE>
+__device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict__ out,
+                                         const T* __restrict__ inv_lam) {
+  constexpr int NL = DIM == 3 ? m * m : m;
+  const DevTab<T>& tb = c_tab<T>;
+  for (int t = threadIdx.x; t < P * NL; t += NT) {
+    const int p = t % P, L = t / P;
+    T v[m];
+#pragma unroll
+    for (int c = 0; c < m; ++c) v[c] = in[(c * NL + L) * P + p];
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) acc = fma(MODE == 2 ? tb.S[o * m + c] : tb.S[c * m + o], v[c], acc);
+      if (MODE == 1) acc *= __ldg(inv_lam + L * m + o);
+      out[(L * m + o) * P + p] = acc;
+    }
+  }
+}
+
+// Back-transformation S (x) S (x) S of the scaled coefficients in X0 and the
+// final update of the interior: x_I += scale * u.
+template <typename T, int P, int NT>
+__device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restrict__ x,
+                                                       int64_t pbase, const ColourGeom& cg,
+                                                       int64_t px, int64_t pz, T scale) {
+  constexpr int NL = DIM == 3 ? m * m : m;
+  const DevTab<T>& tb = c_tab<T>;
+  const T* last_in;
+  if constexpr (DIM == 3) {
+    fd_stage<T, P, NT, 2>(X0, X1, nullptr);
+    __syncthreads();
+    fd_stage<T, P, NT, 2>(X1, X0, nullptr);
+    __syncthreads();
+    last_in = X0;
+  } else {
+    fd_stage<T, P, NT, 2>(X0, X1, nullptr);
+    __syncthreads();
+    last_in = X1;
+  }
+  for (int t = threadIdx.x; t < P * NL; t += NT) {
+    const int p = t % P, L = t / P;
+    const int64_t gp = pbase + p;
+    if (gp >= cg.npatch) continue;
+    T v[m];
+#pragma unroll
+    for (int c = 0; c < m; ++c) v[c] = last_in[(c * NL + L) * P + p];
+    int64_t row;
+    if constexpr (DIM == 3) {
+      const int zz = L / m, yy = L % m;
+      row = closure_origin(gp, cg, px, pz) + (zz + 1) * pz + (yy + 1) * px + 1;
+    } else {
+      row = closure_origin(gp, cg, px, pz) + (L + 1) * px + 1;
+    }
+    T* dst = x + row;
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) acc = fma(tb.S[o * m + c], v[c], acc);
+      dst[o] = fma(scale, acc, dst[o]);
+    }
+  }
+}
+
+// ------------------------------------------------------- multiplicative
+template <typename T>
+__global__ void __launch_bounds__(SmoothCfg<T>::NT)
+smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
+                   int64_t px, int64_t pz, ColourGeom cg, T bscale) {
+  using C = SmoothCfg<T>;
+  constexpr int P = C::P, NT = C::NT, S0 = C::S0;
+  const DevTab<T>& tb = c_tab<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tM = reinterpret_cast<T*>(smem_raw);
+  T* tA = tM + P * S0;
+  const int64_t pbase = (int64_t)blockIdx.x * P;
+
+  if constexpr (DIM == 3) {
+    T* U = tA + P * S0;
+    T* W = U + P * C::sizeU;
+    // Stage 0: lines along z read straight from global memory into
+    // registers; tM = M x, tA = A x along z (interior output rows only).
+    for (int t = threadIdx.x; t < P * n * n; t += NT) {
+      const int p = t / (n * n), L = t % (n * n);
+      const int yy = L / n, xx = L % n;
+      const int64_t gp = pbase + p;
+      T v[n];
+      if (gp < cg.npatch) {
+        const T* src = x + closure_origin(gp, cg, px, pz) + yy * px + xx;
+#pragma unroll
+        for (int c = 0; c < n; ++c) v[c] = src[c * pz];
+      } else {
+#pragma unroll
+        for (int c = 0; c < n; ++c) v[c] = T(0);
+      }
+      T* dM = tM + p * S0 + L * m;
+      T* dA = tA + p * S0 + L * m;
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        T am = T(0), aa = T(0);
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          am = fma(tb.Mp[o * n + c], v[c], am);
+          aa = fma(tb.Ap[o * n + c], v[c], aa);
+        }
+        dM[o] = am;
+        dA[o] = aa;
+      }
+    }
+    __syncthreads();
+    // Stage 1: along y.  U = M (M x), W = A (M x) + M (A x)  (the inner sum
+    // M x along z is shared by two terms, Section 3.1.1).
+    constexpr int NL1 = n * m;
+    for (int t = threadIdx.x; t < P * NL1; t += NT) {
+      const int p = t % P, L = t / P;
+      const T* sM = tM + p * S0 + L;
+      const T* sA = tA + p * S0 + L;
+      T vm[n], va[n];
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        vm[c] = sM[c * NL1];
+        va[c] = sA[c * NL1];
+      }
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        T u = T(0), w = T(0);
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          u = fma(tb.Mp[o * n + c], vm[c], u);
+          w = fma(tb.Ap[o * n + c], vm[c], w);
+          w = fma(tb.Mp[o * n + c], va[c], w);
+        }
+        U[(L * m + o) * P + p] = u;
+        W[(L * m + o) * P + p] = w;
+      }
+    }
+    __syncthreads();
+    // Stage 2: along x.  r = bscale * b - (A U + M W) on the interior.
+    constexpr int NL2 = m * m;
+    T* R = tM;
+    for (int t = threadIdx.x; t < P * NL2; t += NT) {
+      const int p = t % P, L = t / P;
+      const int zz = L / m, yy = L % m;
+      const int64_t gp = pbase + p;
+      T vu[n], vw[n], bv[m];
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        vu[c] = U[(c * NL2 + L) * P + p];
+        vw[c] = W[(c * NL2 + L) * P + p];
+      }
+      if (gp < cg.npatch) {
+        const T* src = b + closure_origin(gp, cg, px, pz) + (zz + 1) * pz + (yy + 1) * px + 1;
+#pragma unroll
+        for (int o = 0; o < m; ++o) bv[o] = bscale * src[o];
+      } else {
+#pragma unroll
+        for (int o = 0; o < m; ++o) bv[o] = T(0);
+      }
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        T acc = bv[o];
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          acc = fma(-tb.Ap[o * n + c], vu[c], acc);
+          acc = fma(-tb.Mp[o * n + c], vw[c], acc);
+        }
+        R[(L * m + o) * P + p] = acc;
+      }
+    }
+    __syncthreads();
+    // Fast diagonalisation: S^T along z, y, x (scaled), then S back.
+    fd_stage<T, P, NT, 0>(tM, tA, nullptr);
+    __syncthreads();
+    fd_stage<T, P, NT, 0>(tA, tM, nullptr);
+    __syncthreads();
+    fd_stage<T, P, NT, 1>(tM, tA, inv_lam);
+    __syncthreads();
+    fd_backward_and_update<T, P, NT>(tA, tM, x, pbase, cg, px, pz, T(1));
+  } else {
+    // 2D.  Stage 0: lines along y from global; tM = M x, tA = A x along y.
+    for (int t = threadIdx.x; t < P * n; t += NT) {
+      const int p = t / n, L = t % n;
+      const int64_t gp = pbase + p;
+      T v[n];
+      if (gp < cg.npatch) {
+        const T* src = x + closure_origin(gp, cg, px, pz) + L;
+#pragma unroll
+        for (int c = 0; c < n; ++c) v[c] = src[c * px];
+      } else {
+#pragma unroll
+        for (int c = 0; c < n; ++c) v[c] = T(0);
+      }
+      T* dM = tM + p * S0 + L * m;
+      T* dA = tA + p * S0 + L * m;
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        T am = T(0), aa = T(0);
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          am = fma(tb.Mp[o * n + c], v[c], am);
+          aa = fma(tb.Ap[o * n + c], v[c], aa);
+        }
+        dM[o] = am;
+        dA[o] = aa;
+      }
+    }
+    __syncthreads();
+    // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior; the
+    // result goes to an interleaved buffer placed after tA.
+    T* R = tA + P * S0;
+    for (int t = threadIdx.x; t < P * m; t += NT) {
+      const int p = t % P, L = t / P;
+      const int64_t gp = pbase + p;
+      const T* sM = tM + p * S0 + L;
+      const T* sA = tA + p * S0 + L;
+      T vm[n], va[n], bv[m];
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        vm[c] = sM[c * m];
+        va[c] = sA[c * m];
+      }
+      if (gp < cg.npatch) {
+        const T* src = b + closure_origin(gp, cg, px, pz) + (L + 1) * px + 1;
+#pragma unroll
+        for (int o = 0; o < m; ++o) bv[o] = bscale * src[o];
+      } else {
+#pragma unroll
+        for (int o = 0; o < m; ++o) bv[o] = T(0);
+      }
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        T acc = bv[o];
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          acc = fma(-tb.Ap[o * n + c], vm[c], acc);
+          acc = fma(-tb.Mp[o * n + c], va[c], acc);
+        }
+        R[(L * m + o) * P + p] = acc;
+      }
+    }
+    __syncthreads();
+    T* X0 = R;
+    T* X1 = tM;  // tM/tA are free now; P*S0 >= P*m*m
+    fd_stage<T, P, NT, 0>(X0, X1, nullptr);
+    __syncthreads();
+    fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
+    __syncthreads();
+    fd_backward_and_update<T, P, NT>(X0, X1, x, pbase, cg, px, pz, T(1));
+  }
+}
+
+// ------------------------------------------------------------- additive
+// x_I += scale * A_ref^-1 r_I for every patch of one colour.
+template <typename T>
+__global__ void __launch_bounds__(SmoothCfg<T>::NT)
+smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv_lam,
+                  int64_t px, int64_t pz, ColourGeom cg, T scale) {
+  using C = SmoothCfg<T>;
+  constexpr int P = C::P, NT = C::NT, MD = C::md;
+  const DevTab<T>& tb = c_tab<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X0 = reinterpret_cast<T*>(smem_raw);
+  T* X1 = X0 + P * MD;
+  const int64_t pbase = (int64_t)blockIdx.x * P;
+  constexpr int NL = DIM == 3 ? m * m : m;
+  // first S^T contraction reads the interior residual lines from global
+  for (int t = threadIdx.x; t < P * NL; t += NT) {
+    const int p = t % P, L = t / P;
+    const int64_t gp = pbase + p;
+    T v[m];
+    if (gp < cg.npatch) {
+      const T* src;
+      if constexpr (DIM == 3) {
+        const int yy = L / m, xx = L % m;
+        src = r + closure_origin(gp, cg, px, pz) + pz + (yy + 1) * px + 1 + xx;
+#pragma unroll
+        for (int c = 0; c < m; ++c) v[c] = src[c * pz];
+      } else {
+        src = r + closure_origin(gp, cg, px, pz) + px + 1 + L;
+#pragma unroll
+        for (int c = 0; c < m; ++c) v[c] = src[c * px];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < m; ++c) v[c] = T(0);
+    }
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) acc = fma(tb.S[c * m + o], v[c], acc);
+      X1[(L * m + o) * P + p] = acc;
+    }
+  }
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    fd_stage<T, P, NT, 0>(X1, X0, nullptr);
+    __syncthreads();
+    fd_stage<T, P, NT, 1>(X0, X1, inv_lam);
+    __syncthreads();
+    fd_backward_and_update<T, P, NT>(X1, X0, x, pbase, cg, px, pz, scale);
+  } else {
+    fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
+    __syncthreads();
+    fd_backward_and_update<T, P, NT>(X0, X1, x, pbase, cg, px, pz, scale);
+  }
+}
+
+// ------------------------------------------------------------- operator
+// y = A x on an output tile of TN = K*CT nodes per direction.  The first
+// contraction (along the slowest direction) reads its lines of 2K+1 nodes
+// straight from global memory; the halo of K nodes per side is only needed
+// in the directions contracted later.  A = sum of Kronecker products of the
+// banded global 1D matrices (Section 2.3): z -> M, K; y -> M M, K M + M K;
+// x -> K (M M) + M (K M + M K).
+struct ApplyCfg {
+  static constexpr int CT = DIM == 3 ? (K == 1 ? 8 : K == 2 ? 4 : K == 3 ? 3 : K <= 5 ? 2 : 1)
+                                     : (32 + K - 1) / K;
+  static constexpr int TN = K * CT;
+  static constexpr int BN = TN + 2 * K;
+  static constexpr int RB = BN | 1;    // odd row stride
+  static constexpr int NT = 256;
+  // 3D: stage-A outputs [TN][BN][RB] x2, stage-B outputs [TN][TN][RB] x2
+  // 2D: stage-A outputs [TN][RB] x2
+  static constexpr int a_sz = DIM == 3 ? TN * BN * RB : TN * RB;
+  static constexpr int b_sz = DIM == 3 ? TN * TN * RB : 0;
+  template <typename T>
+  static constexpr size_t smem() { return sizeof(T) * (size_t)(2 * a_sz + 2 * b_sz); }
+};
+
+// out[q] = sum over the band of node position q of B[q][j] * v[q + j]
+// (q = 0: vertex node, all 2K+1 entries; else the K+1 entries of its cell).
+#define VPS_BAND_LOOP(q, j) \
+  _Pragma("unroll") for (int j = 0; j <= 2 * K; ++j) if (q == 0 || (j >= K - q && j <= 2 * K - q))
+
+template <typename T>
+__global__ void __launch_bounds__(ApplyCfg::NT)
+apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
+             int64_t px, int64_t pz, T scale) {
+  using C = ApplyCfg;
+  constexpr int TN = C::TN, BN = C::BN, RB = C::RB, CT = C::CT, NT = C::NT;
+  const DevTab<T>& tb = c_tab<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tm = reinterpret_cast<T*>(smem_raw);
+  T* tk = tm + C::a_sz;
+  const int x0 = blockIdx.x * TN, y0 = blockIdx.y * TN;
+  if constexpr (DIM == 3) {
+    const int z0 = blockIdx.z * TN;
+    T* mm = tk + C::a_sz;
+    T* ww = mm + C::b_sz;
+    // stage A: along z from global; units (y, x) over the halo box, z segment
+    for (int u = threadIdx.x; u < BN * BN * CT; u += NT) {
+      const int xx = u % BN, yy = (u / BN) % BN, cz = u / (BN * BN);
+      const int gx = x0 - K + xx, gy = y0 - K + yy, gz0 = z0 + cz * K - K;
+      T v[2 * K + 1];
+      const bool inxy = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+#pragma unroll
+      for (int i = 0; i <= 2 * K; ++i) {
+        const int gz = gz0 + i;
+        v[i] = (inxy && gz >= 0 && gz < n1) ? x[(int64_t)gz * pz + (int64_t)gy * px + gx] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        T am = T(0), ak = T(0);
+        VPS_BAND_LOOP(q, j) {
+          am = fma(tb.Mb[q * n + j], v[q + j], am);
+          ak = fma(tb.Kb[q * n + j], v[q + j], ak);
+        }
+        tm[((cz * K + q) * BN + yy) * RB + xx] = am;
+        tk[((cz * K + q) * BN + yy) * RB + xx] = ak;
+      }
+    }
+    __syncthreads();
+    // stage B: along y; units (z, y segment, x over the halo)
+    for (int u = threadIdx.x; u < TN * CT * BN; u += NT) {
+      const int xx = u % BN, cy = (u / BN) % CT, Z = u / (BN * CT);
+      T vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+      for (int i = 0; i <= 2 * K; ++i) {
+        vm[i] = tm[(Z * BN + cy * K + i) * RB + xx];
+        vk[i] = tk[(Z * BN + cy * K + i) * RB + xx];
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        T a = T(0), bb = T(0);
+        VPS_BAND_LOOP(q, j) {
+          a = fma(tb.Mb[q * n + j], vm[q + j], a);
+          bb = fma(tb.Kb[q * n + j], vm[q + j], bb);
+          bb = fma(tb.Mb[q * n + j], vk[q + j], bb);
+        }
+        mm[(Z * TN + cy * K + q) * RB + xx] = a;
+        ww[(Z * TN + cy * K + q) * RB + xx] = bb;
+      }
+    }
+    __syncthreads();
+    // stage C: along x; units (y fastest, z, x segment); write the tile
+    for (int u = threadIdx.x; u < TN * TN * CT; u += NT) {
+      const int Y = u % TN, Z = (u / TN) % TN, cx = u / (TN * TN);
+      const int gy = y0 + Y, gz = z0 + Z;
+      if (gy >= n1 || gz >= n1) continue;
+      T vm[2 * K + 1], vw[2 * K + 1];
+#pragma unroll
+      for (int i = 0; i <= 2 * K; ++i) {
+        vm[i] = mm[(Z * TN + Y) * RB + cx * K + i];
+        vw[i] = ww[(Z * TN + Y) * RB + cx * K + i];
+      }
+      const bool inner_yz = gy >= 1 && gy <= n1 - 2 && gz >= 1 && gz <= n1 - 2;
+      const int64_t rowi = (int64_t)gz * pz + (int64_t)gy * px;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const int gx = x0 + cx * K + q;
+        if (gx >= n1) continue;
+        T acc = T(0);
+        VPS_BAND_LOOP(q, j) {
+          acc = fma(tb.Kb[q * n + j], vm[q + j], acc);
+          acc = fma(tb.Mb[q * n + j], vw[q + j], acc);
+        }
+        T out = T(0);
+        if (inner_yz && gx >= 1 && gx <= n1 - 2)
+          out = bvec ? bvec[rowi + gx] - scale * acc : scale * acc;
+        y[rowi + gx] = out;
+      }
+    }
+  } else {
+    // stage A (2D): along y from global; units (x over the halo, y segment)
+    for (int u = threadIdx.x; u < BN * CT; u += NT) {
+      const int xx = u % BN, cy = u / BN;
+      const int gx = x0 - K + xx, gy0 = y0 + cy * K - K;
+      T v[2 * K + 1];
+#pragma unroll
+      for (int i = 0; i <= 2 * K; ++i) {
+        const int gy = gy0 + i;
+        v[i] = (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) ? x[(int64_t)gy * px + gx] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        T am = T(0), ak = T(0);
+        VPS_BAND_LOOP(q, j) {
+          am = fma(tb.Mb[q * n + j], v[q + j], am);
+          ak = fma(tb.Kb[q * n + j], v[q + j], ak);
+        }
+        tm[(cy * K + q) * RB + xx] = am;
+        tk[(cy * K + q) * RB + xx] = ak;
+      }
+    }
+    __syncthreads();
+    // stage B: along x; y = K0 (M1 x) + M0 (K1 x)
+    for (int u = threadIdx.x; u < TN * CT; u += NT) {
+      const int Y = u % TN, cx = u / TN;
+      const int gy = y0 + Y;
+      if (gy >= n1) continue;
+      T vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+      for (int i = 0; i <= 2 * K; ++i) {
+        vm[i] = tm[Y * RB + cx * K + i];
+        vk[i] = tk[Y * RB + cx * K + i];
+      }
+      const int64_t rowi = (int64_t)gy * px;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const int gx = x0 + cx * K + q;
+        if (gx >= n1) continue;
+        T acc = T(0);
+        VPS_BAND_LOOP(q, j) {
+          acc = fma(tb.Kb[q * n + j], vm[q + j], acc);
+          acc = fma(tb.Mb[q * n + j], vk[q + j], acc);
+        }
+        T out = T(0);
+        if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2)
+          out = bvec ? bvec[rowi + gx] - scale * acc : scale * acc;
+        y[rowi + gx] = out;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ transfers
+// Tiles of CC coarse cells per direction; the first contraction (slowest
+// direction) reads from global memory.
+struct TransferCfg {
+  static constexpr int CC = DIM == 3 ? (K <= 1 ? 8 : K <= 2 ? 4 : K <= 4 ? 2 : 1)
+                                     : (K <= 2 ? 16 : 8);
+  static constexpr int CB = K * CC + 1;   // coarse nodes of the tile (prolongation input)
+  static constexpr int CBp = CB | 1;
+  static constexpr int FB = 2 * K * CC;   // owned fine nodes (prolongation output)
+  static constexpr int RFB = 2 * K * CC + 2 * K + 1;  // fine nodes read (restriction)
+  static constexpr int RFBp = RFB | 1;
+  static constexpr int CN = K * CC;       // owned coarse nodes (restriction output)
+  static constexpr int NT = 256;
+  template <typename T>
+  static constexpr size_t smem_prolong() {
+    return sizeof(T) * (size_t)(DIM == 3 ? FB * CB * CBp + FB * FB * CBp : FB * CBp);
+  }
+  template <typename T>
+  static constexpr size_t smem_restrict() {
+    return sizeof(T) * (size_t)(DIM == 3 ? CN * RFB * RFBp + CN * CN * RFBp : CN * RFBp);
+  }
+};
+
+// x_fine += P x_coarse.  Fine node 2K*C + s (s < 2K) of coarse cell C is
+// sum_i P1[s][i] x_c[K*C + i] per direction; each block owns the fine nodes
+// of its coarse cells (half-open), so no two blocks write the same node.
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_t pxc,
+                   int64_t pzc, int n1f, int64_t pxf, int64_t pzf) {
+  using C = TransferCfg;
+  constexpr int CB = C::CB, CBp = C::CBp, FB = C::FB, CC = C::CC, NT = C::NT;
+  const DevTab<T>& tb = c_tab<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t1 = reinterpret_cast<T*>(smem_raw);
+  const int cx0 = blockIdx.x * CC, cy0 = blockIdx.y * CC;
+  if constexpr (DIM == 3) {
+    const int cz0 = blockIdx.z * CC;
+    T* t2 = t1 + FB * CB * CBp;
+    // along z from global: units (coarse y, coarse x) x coarse cell z
+    for (int u = threadIdx.x; u < CB * CB * CC; u += NT) {
+      const int xx = u % CB, yy = (u / CB) % CB, cz = u / (CB * CB);
+      const int gx = K * cx0 + xx, gy = K * cy0 + yy;
+      T v[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) {
+        const int gz = K * (cz0 + cz) + i;
+        v[i] = (gx < n1c && gy < n1c && gz < n1c) ? xc[(int64_t)gz * pzc + (int64_t)gy * pxc + gx]
+                                                  : T(0);
+      }
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        t1[((2 * K * cz + s) * CB + yy) * CBp + xx] = acc;
+      }
+    }
+    __syncthreads();
+    // along y: units (fine z, coarse cell y, coarse x)
+    for (int u = threadIdx.x; u < FB * CC * CB; u += NT) {
+      const int xx = u % CB, cy = (u / CB) % CC, Z = u / (CB * CC);
+      T v[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) v[i] = t1[(Z * CB + K * cy + i) * CBp + xx];
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        t2[(Z * FB + 2 * K * cy + s) * CBp + xx] = acc;
+      }
+    }
+    __syncthreads();
+    // along x: units (fine y fastest, fine z, coarse cell x); accumulate
+    for (int u = threadIdx.x; u < FB * FB * CC; u += NT) {
+      const int Y = u % FB, Z = (u / FB) % FB, cx = u / (FB * FB);
+      const int gy = 2 * K * cy0 + Y, gz = 2 * K * cz0 + Z;
+      if (gy < 1 || gy > n1f - 2 || gz < 1 || gz > n1f - 2) continue;
+      T v[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) v[i] = t2[(Z * FB + Y) * CBp + K * cx + i];
+      T* dst = xf + (int64_t)gz * pzf + (int64_t)gy * pxf;
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) {
+        const int gx = 2 * K * (cx0 + cx) + s;
+        if (gx < 1 || gx > n1f - 2) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        dst[gx] += acc;
+      }
+    }
+  } else {
+    // along y from global: units (coarse x) x coarse cell y
+    for (int u = threadIdx.x; u < CB * CC; u += NT) {
+      const int xx = u % CB, cy = u / CB;
+      const int gx = K * cx0 + xx;
+      T v[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) {
+        const int gy = K * (cy0 + cy) + i;
+        v[i] = (gx < n1c && gy < n1c) ? xc[(int64_t)gy * pxc + gx] : T(0);
+      }
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        t1[(2 * K * cy + s) * CBp + xx] = acc;
+      }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < FB * CC; u += NT) {
+      const int Y = u % FB, cx = u / FB;
+      const int gy = 2 * K * cy0 + Y;
+      if (gy < 1 || gy > n1f - 2) continue;
+      T v[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) v[i] = t1[Y * CBp + K * cx + i];
+      T* dst = xf + (int64_t)gy * pxf;
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) {
+        const int gx = 2 * K * (cx0 + cx) + s;
+        if (gx < 1 || gx > n1f - 2) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        dst[gx] += acc;
+      }
+    }
+  }
+  (void)pzc;
+  (void)pzf;
+}
+
+// Restriction r_c = P^T r_f per direction: coarse node K*C + i gathers the
+// fine nodes of coarse cell C with weights P1[s][i]; a coarse vertex (i = 0)
+// also gathers cell C-1 with weights P1[s][K] (the shared fine node once).
+// v holds the 4K+1 fine values of cells C-1 and C.
+template <typename T>
+__device__ __forceinline__ void restrict_1d(const T (&v)[4 * K + 1], T (&out)[K]) {
+  const DevTab<T>& tb = c_tab<T>;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s <= 2 * K; ++s) acc = fma(tb.P1[s * nl + i], v[2 * K + s], acc);
+    if (i == 0) {
+#pragma unroll
+      for (int s = 0; s < 2 * K; ++s) acc = fma(tb.P1[s * nl + K], v[s], acc);
+    }
+    out[i] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+restrict_kernel(const T* __restrict__ rf, T* __restrict__ rc, int n1c, int64_t pxc, int64_t pzc,
+                int n1f, int64_t pxf, int64_t pzf) {
+  using C = TransferCfg;
+  constexpr int RFB = C::RFB, RFBp = C::RFBp, CN = C::CN, CC = C::CC, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t1 = reinterpret_cast<T*>(smem_raw);
+  const int C0x = blockIdx.x * CC, C0y = blockIdx.y * CC;
+  const int fx0 = 2 * K * (C0x - 1), fy0 = 2 * K * (C0y - 1);
+  if constexpr (DIM == 3) {
+    const int C0z = blockIdx.z * CC;
+    T* t2 = t1 + CN * RFB * RFBp;
+    // along z from global: units (fine y, fine x) x coarse cell z
+    for (int u = threadIdx.x; u < RFB * RFB * CC; u += NT) {
+      const int xx = u % RFB, yy = (u / RFB) % RFB, cz = u / (RFB * RFB);
+      const int gx = fx0 + xx, gy = fy0 + yy, gz0 = 2 * K * (C0z + cz - 1);
+      const bool inxy = gx >= 0 && gx < n1f && gy >= 0 && gy < n1f;
+      T v[4 * K + 1], o[K];
+#pragma unroll
+      for (int i = 0; i <= 4 * K; ++i) {
+        const int gz = gz0 + i;
+        v[i] = (inxy && gz >= 0 && gz < n1f) ? rf[(int64_t)gz * pzf + (int64_t)gy * pxf + gx] : T(0);
+      }
+      restrict_1d<T>(v, o);
+#pragma unroll
+      for (int i = 0; i < K; ++i) t1[((K * cz + i) * RFB + yy) * RFBp + xx] = o[i];
+    }
+    __syncthreads();
+    // along y: units (coarse z, coarse cell y, fine x)
+    for (int u = threadIdx.x; u < CN * CC * RFB; u += NT) {
+      const int xx = u % RFB, cy = (u / RFB) % CC, Z = u / (RFB * CC);
+      T v[4 * K + 1], o[K];
+#pragma unroll
+      for (int i = 0; i <= 4 * K; ++i) v[i] = t1[(Z * RFB + 2 * K * cy + i) * RFBp + xx];
+      restrict_1d<T>(v, o);
+#pragma unroll
+      for (int i = 0; i < K; ++i) t2[(Z * CN + K * cy + i) * RFBp + xx] = o[i];
+    }
+    __syncthreads();
+    // along x: units (coarse y fastest, coarse z, coarse cell x); write
+    for (int u = threadIdx.x; u < CN * CN * CC; u += NT) {
+      const int Y = u % CN, Z = (u / CN) % CN, cx = u / (CN * CN);
+      const int gy = K * C0y + Y, gz = K * C0z + Z;
+      if (gy >= n1c || gz >= n1c) continue;
+      T v[4 * K + 1], o[K];
+#pragma unroll
+      for (int i = 0; i <= 4 * K; ++i) v[i] = t2[(Z * CN + Y) * RFBp + 2 * K * cx + i];
+      restrict_1d<T>(v, o);
+      const bool inner_yz = gy >= 1 && gy <= n1c - 2 && gz >= 1 && gz <= n1c - 2;
+      T* dst = rc + (int64_t)gz * pzc + (int64_t)gy * pxc;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int gx = K * (C0x + cx) + i;
+        if (gx >= n1c) continue;
+        dst[gx] = (inner_yz && gx >= 1 && gx <= n1c - 2) ? o[i] : T(0);
+      }
+    }
+  } else {
+    for (int u = threadIdx.x; u < RFB * CC; u += NT) {
+      const int xx = u % RFB, cy = u / RFB;
+      const int gx = fx0 + xx, gy0 = 2 * K * (C0y + cy - 1);
+      T v[4 * K + 1], o[K];
+#pragma unroll
+      for (int i = 0; i <= 4 * K; ++i) {
+        const int gy = gy0 + i;
+        v[i] = (gx >= 0 && gx < n1f && gy >= 0 && gy < n1f) ? rf[(int64_t)gy * pxf + gx] : T(0);
+      }
+      restrict_1d<T>(v, o);
+#pragma unroll
+      for (int i = 0; i < K; ++i) t1[(K * cy + i) * RFBp + xx] = o[i];
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < CN * CC; u += NT) {
+      const int Y = u % CN, cx = u / CN;
+      const int gy = K * C0y + Y;
+      if (gy >= n1c) continue;
+      T v[4 * K + 1], o[K];
+#pragma unroll
+      for (int i = 0; i <= 4 * K; ++i) v[i] = t1[Y * RFBp + 2 * K * cx + i];
+      restrict_1d<T>(v, o);
+      T* dst = rc + (int64_t)gy * pxc;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int gx = K * (C0x + cx) + i;
+        if (gx >= n1c) continue;
+        dst[gx] = (gy >= 1 && gy <= n1c - 2 && gx >= 1 && gx <= n1c - 2) ? o[i] : T(0);
+      }
+    }
+  }
+  (void)pzc;
+}
+
+// The upper boundary layer of a coarse vector (index n1c-1 in any
+// direction) is owned by no restriction tile; this zeroes it.
+template <typename T>
+__global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, int64_t pz) {
+  const int64_t nface = DIM == 3 ? (int64_t)n1 * n1 : n1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < DIM * nface;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(e / nface);
+    const int64_t r = e % nface;
+    const int a = (int)(r % n1), c = DIM == 3 ? (int)(r / n1) : 0;
+    int64_t idx;
+    if (f == 0) idx = (int64_t)c * pz + (int64_t)a * px + (n1 - 1);
+    else if (f == 1) idx = (int64_t)c * pz + (int64_t)(n1 - 1) * px + a;
+    else idx = (int64_t)(n1 - 1) * pz + (int64_t)c * px + a;
+    v[idx] = T(0);
+  }
+}
+
+// ------------------------------------------------------------ launchers
+template <typename T>
+cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
+                               const T* inv_lam, cudaStream_t s) {
+  using C = SmoothCfg<T>;
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + C::P - 1) / C::P;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  smooth_mult_kernel<T><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, g.px, g.pz, cg,
+                                                                     bscale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
+                              const T* inv_lam, T scale, cudaStream_t s) {
+  using C = SmoothCfg<T>;
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + C::P - 1) / C::P;
+  const T sc = DIM == 3 ? T(scale / g.h) : scale;
+  smooth_add_kernel<T><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, g.px, g.pz, cg, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
+  using C = ApplyCfg;
+  const unsigned t = (unsigned)((g.n1 + C::TN - 1) / C::TN);
+  dim3 grid(t, t, DIM == 3 ? t : 1);
+  const T scale = DIM == 3 ? T(g.h) : T(1);
+  apply_kernel<T><<<grid, C::NT, C::smem<T>(), s>>>(x, b, y, g.n1, g.px, g.pz, scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prolong_launch(const LevelGeom& f, const LevelGeom& c, const T* xc, T* xf,
+                           cudaStream_t s) {
+  using C = TransferCfg;
+  const unsigned t = (unsigned)((c.ncell + C::CC - 1) / C::CC);
+  dim3 grid(t, t, DIM == 3 ? t : 1);
+  prolong_add_kernel<T><<<grid, C::NT, C::smem_prolong<T>(), s>>>(xc, xf, c.n1, c.px, c.pz, f.n1,
+                                                                   f.px, f.pz);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf, T* rc,
+                            cudaStream_t s) {
+  using C = TransferCfg;
+  const unsigned t = (unsigned)((c.ncell + C::CC - 1) / C::CC);
+  dim3 grid(t, t, DIM == 3 ? t : 1);
+  restrict_kernel<T><<<grid, C::NT, C::smem_restrict<T>(), s>>>(rf, rc, c.n1, c.px, c.pz, f.n1,
+                                                                 f.px, f.pz);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(rc, c.n1, c.px, c.pz);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_smem_limits() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(smooth_mult_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SmoothCfg<T>::smem_mult);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(smooth_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SmoothCfg<T>::smem_add);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ApplyCfg::smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(prolong_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TransferCfg::smem_prolong<T>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(restrict_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TransferCfg::smem_restrict<T>());
+}
+
+template <typename T>
+void fill_tab(const HostTables& h, DevTab<T>* d) {
+  for (int i = 0; i < m * n; ++i) {
+    d->Ap[i] = (T)h.Ap[i];
+    d->Mp[i] = (T)h.Mp[i];
+  }
+  for (int i = 0; i < m * m; ++i) d->S[i] = (T)h.S[i];
+  for (int i = 0; i < K * n; ++i) {
+    d->Kb[i] = (T)h.Kb[i];
+    d->Mb[i] = (T)h.Mb[i];
+  }
+  for (int i = 0; i < n * nl; ++i) d->P1[i] = (T)h.P1[i];
+}
+
+cudaError_t upload(const HostTables& h) {
+  if (h.k != K) return cudaErrorInvalidValue;
+  DevTab<float> tf;
+  DevTab<double> td;
+  fill_tab(h, &tf);
+  fill_tab(h, &td);
+  cudaError_t e = cudaMemcpyToSymbol(c_tab<float>, &tf, sizeof(tf));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_tab<double>, &td, sizeof(td));
+  if (e != cudaSuccess) return e;
+  e = set_smem_limits<float>();
+  if (e != cudaSuccess) return e;
+  return set_smem_limits<double>();
+}
+
+}  // namespace
+
+#define VPS_CAT2(a, b, c) a##b##_k##c
+#define VPS_CAT(a, b, c) VPS_CAT2(a, b, c)
+void VPS_CAT(register_kernels_d, VPS_DIM, VPS_K)(KernelSet* ks) {
+  ks->present = true;
+  ks->upload = upload;
+  ks->f.smooth_mult = smooth_mult_launch<float>;
+  ks->f.smooth_add = smooth_add_launch<float>;
+  ks->f.apply = apply_launch<float>;
+  ks->f.prolong_add = prolong_launch<float>;
+  ks->f.restrict_ = restrict_launch<float>;
+  ks->d.smooth_mult = smooth_mult_launch<double>;
+  ks->d.smooth_add = smooth_add_launch<double>;
+  ks->d.apply = apply_launch<double>;
+  ks->d.prolong_add = prolong_launch<double>;
+  ks->d.restrict_ = restrict_launch<double>;
+}
+
+}  // namespace vps

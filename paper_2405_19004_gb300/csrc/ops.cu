@@ -1,0 +1,340 @@
+// Vector kernels of the solver: layout conversion, deterministic
+// reductions, the CG updates, the separable load vector and the L2 error.
+//
+// The paper runs these "vector operations" through a library vector class
+// (Section 3, building blocks); here they are plain kernels.  Reductions use
+// a fixed grid and fixed trees, so a result does not depend on scheduling:
+// the same inputs give bit-identical scalars on every run.
+#include <cmath>
+
+#include "vps_internal.h"
+
+namespace vps {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int per_thread = 1) {
+  int64_t g = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  if (g < 1) g = 1;
+  if (g > 4 * 152 * 8) g = 4 * 152 * 8;
+  return (unsigned)g;
+}
+
+template <typename T>
+__global__ void pack_kernel(const T* __restrict__ comp, T* __restrict__ lev, int dim, int n1,
+                            int64_t px, int64_t pz, int64_t total) {
+  const int ni = n1 - 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = e % px;
+    const int64_t i1 = (e / px) % n1;
+    const int64_t i2 = dim == 3 ? e / pz : 1;
+    T v = T(0);
+    if (i0 >= 1 && i0 <= ni && i1 >= 1 && i1 <= ni && i2 >= 1 && i2 <= ni)
+      v = comp[(i0 - 1) + (int64_t)ni * ((i1 - 1) + (int64_t)ni * (dim == 3 ? i2 - 1 : 0))];
+    lev[e] = v;
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(const T* __restrict__ lev, T* __restrict__ comp, int dim, int n1,
+                              int64_t px, int64_t pz, int64_t ncomp) {
+  const int ni = n1 - 2;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncomp;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j0 = c % ni;
+    const int64_t j1 = (c / ni) % ni;
+    const int64_t j2 = dim == 3 ? c / ((int64_t)ni * ni) : 0;
+    comp[c] = lev[(j0 + 1) + (j1 + 1) * px + (dim == 3 ? (j2 + 1) * pz : 0)];
+  }
+}
+
+template <typename T>
+__global__ void zero_kernel(T* __restrict__ p, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = T(0);
+}
+
+// Fixed-order block reduction of NV values per thread.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  for (int j = 0; j < NV; ++j) sh[j * kThreads + threadIdx.x] = v[j];
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int j = 0; j < NV; ++j) sh[j * kThreads + threadIdx.x] += sh[j * kThreads + threadIdx.x + s];
+    __syncthreads();
+  }
+  for (int j = 0; j < NV; ++j) v[j] = sh[j * kThreads];
+}
+
+// partial[j * kDotBlocks + block] = sum over this block's fixed subset.
+__global__ void __launch_bounds__(kThreads)
+dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                   const double* __restrict__ c, const double* __restrict__ e, int64_t n,
+                   double* __restrict__ partial) {
+  __shared__ double sh[2 * kThreads];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)kDotBlocks * kThreads) {
+    v[0] = fma(a[i], b[i], v[0]);
+    if (c) v[1] = fma(c[i], e[i], v[1]);
+  }
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = v[0];
+    partial[kDotBlocks + blockIdx.x] = v[1];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+dot_final_kernel(const double* __restrict__ partial, double* __restrict__ out, int nprod) {
+  __shared__ double sh[2 * kThreads];
+  double v[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) {
+    v[0] += partial[i];
+    v[1] += partial[kDotBlocks + i];
+  }
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    out[0] = v[0];
+    if (nprod > 1) out[1] = v[1];
+  }
+}
+
+__global__ void cg_alpha_kernel(CgScalars* sc) {
+  const double pAp = sc->pAp;
+  if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(sc->rz)) {
+    sc->flag = 1;
+    sc->alpha = 0.0;
+  } else {
+    sc->alpha = sc->rz / pAp;
+  }
+}
+
+__global__ void cg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
+                                    const double* __restrict__ p, const double* __restrict__ Ap,
+                                    const CgScalars* __restrict__ sc, int64_t n) {
+  const double alpha = sc->alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, Ap[i], r[i]);
+  }
+}
+
+__global__ void cg_beta_kernel(CgScalars* sc) {
+  const double rz = sc->rz;
+  if (!(rz != 0.0) || !isfinite(sc->rzn) || !isfinite(sc->rzo)) {
+    sc->flag = 1;
+    sc->beta = 0.0;
+  } else {
+    sc->beta = (sc->rzn - sc->rzo) / rz;
+  }
+  sc->rz = sc->rzn;
+}
+
+__global__ void cg_update_p_kernel(double* __restrict__ p, double* __restrict__ z,
+                                   const double* __restrict__ zn, const CgScalars* __restrict__ sc,
+                                   int64_t n) {
+  const double beta = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = zn[i];
+    p[i] = fma(beta, p[i], v);
+    z[i] = v;
+  }
+}
+
+__global__ void cg_init_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i];
+}
+
+__global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void cast_f2d_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* __restrict__ y, const T* __restrict__ x, T a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// b[c] = sum_m prod_t b1d[(mode*dim + t)*ni + j_t]
+__global__ void rhs_tensor_kernel(const double* __restrict__ b1d, double* __restrict__ b, int dim,
+                                  int ni, int n_modes, int64_t ncomp) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncomp;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j[3];
+    j[0] = c % ni;
+    j[1] = (c / ni) % ni;
+    j[2] = dim == 3 ? c / ((int64_t)ni * ni) : 0;
+    double s = 0.0;
+    for (int md = 0; md < n_modes; ++md) {
+      double p = 1.0;
+      for (int t = 0; t < dim; ++t) p *= b1d[(int64_t)(md * dim + t) * ni + j[t]];
+      s += p;
+    }
+    b[c] = s;
+  }
+}
+
+// Squared L2 error contributions: one thread per (cell, Gauss point).
+// tab: [ (k+1)*q basis values V[a][qq] | q points | q weights ] (FP64).
+__global__ void __launch_bounds__(kThreads)
+l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, int dim, int k,
+                  int q, int ncell, int64_t px, int64_t pz, double h, double* __restrict__ partial) {
+  __shared__ double sh[2 * kThreads];
+  const int nl = k + 1;
+  const double* V = tab;
+  const double* xq = tab + nl * q;
+  const double* wq = xq + q;
+  const int64_t qd = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q;
+  const int64_t cells = dim == 3 ? (int64_t)ncell * ncell * ncell : (int64_t)ncell * ncell;
+  const int64_t work = cells * qd;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < work;
+       e += (int64_t)kDotBlocks * kThreads) {
+    const int64_t cell = e / qd;
+    const int64_t qi = e % qd;
+    int qa[3] = {(int)(qi % q), (int)((qi / q) % q), dim == 3 ? (int)(qi / ((int64_t)q * q)) : 0};
+    int64_t ca[3] = {cell % ncell, (cell / ncell) % ncell, dim == 3 ? cell / ((int64_t)ncell * ncell) : 0};
+    double uh = 0.0;
+    const int na = dim == 3 ? nl * nl * nl : nl * nl;
+    for (int a = 0; a < na; ++a) {
+      const int a0 = a % nl, a1 = (a / nl) % nl, a2 = a / (nl * nl);
+      double phi = V[a0 * q + qa[0]] * V[a1 * q + qa[1]];
+      int64_t idx = (k * ca[0] + a0) + (k * ca[1] + a1) * px;
+      if (dim == 3) {
+        phi *= V[a2 * q + qa[2]];
+        idx += (k * ca[2] + a2) * pz;
+      }
+      uh = fma(phi, x[idx], uh);
+    }
+    double u = 1.0, w = 1.0;
+    for (int t = 0; t < dim; ++t) {
+      u *= sin(M_PI * (ca[t] + xq[qa[t]]) * h);
+      w *= wq[qa[t]] * h;
+    }
+    const double d = uh - u;
+    acc[0] = fma(w * d, d, acc[0]);
+  }
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = acc[0];
+    partial[kDotBlocks + blockIdx.x] = 0.0;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s) {
+  pack_kernel<T><<<grid_for(g.total, 4), kThreads, 0, s>>>(compact, lev, g.dim, g.n1, g.px, g.pz,
+                                                            g.total);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStream_t s) {
+  const int64_t ni = g.n1 - 2;
+  const int64_t nc = g.dim == 3 ? ni * ni * ni : ni * ni;
+  unpack_kernel<T><<<grid_for(nc, 4), kThreads, 0, s>>>(lev, compact, g.dim, g.n1, g.px, g.pz, nc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s) {
+  zero_kernel<T><<<grid_for(n, 4), kThreads, 0, s>>>(p, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
+                        int64_t n, double* partial, double* out, cudaStream_t s) {
+  dot_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
+  dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, c ? 2 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* partial, double* out,
+                        cudaStream_t s) {
+  return launch_dot2(a, b, nullptr, nullptr, n, partial, out, s);
+}
+
+cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
+                                CgScalars* sc, int64_t n, cudaStream_t s) {
+  cg_alpha_kernel<<<1, 1, 0, s>>>(sc);
+  cg_update_xr_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(x, r, p, Ap, sc, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
+                               cudaStream_t s) {
+  cg_beta_kernel<<<1, 1, 0, s>>>(sc);
+  cg_update_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, sc, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s) {
+  (void)sc;
+  cg_init_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  cast_d2f_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s) {
+  cast_f2d_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s) {
+  axpy_kernel<T><<<grid_for(n, 4), kThreads, 0, s>>>(y, x, a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_tensor(const LevelGeom& g, int n_modes, const double* b1d, double* b,
+                              cudaStream_t s) {
+  const int64_t ni = g.n1 - 2;
+  const int64_t nc = g.dim == 3 ? ni * ni * ni : ni * ni;
+  rhs_tensor_kernel<<<grid_for(nc, 4), kThreads, 0, s>>>(b1d, b, g.dim, (int)ni, n_modes, nc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l2_error_sine(const LevelGeom& g, const double* xlev, const double* tab, int q,
+                                 double* partial, double* out, cudaStream_t s) {
+  l2_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(xlev, tab, g.dim, g.k, q, g.ncell, g.px, g.pz,
+                                                     g.h, partial);
+  dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, 1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pack<float>(const LevelGeom&, const float*, float*, cudaStream_t);
+template cudaError_t launch_pack<double>(const LevelGeom&, const double*, double*, cudaStream_t);
+template cudaError_t launch_unpack<float>(const LevelGeom&, const float*, float*, cudaStream_t);
+template cudaError_t launch_unpack<double>(const LevelGeom&, const double*, double*, cudaStream_t);
+template cudaError_t launch_zero<float>(float*, int64_t, cudaStream_t);
+template cudaError_t launch_zero<double>(double*, int64_t, cudaStream_t);
+template cudaError_t launch_axpy_inplace<float>(float*, const float*, float, int64_t, cudaStream_t);
+template cudaError_t launch_axpy_inplace<double>(double*, const double*, double, int64_t,
+                                                 cudaStream_t);
+
+}  // namespace vps

@@ -1,0 +1,152 @@
+// Internal declarations shared by the translation units of libvps.
+//
+// Host-side 1D tables (computed once per degree in setup.cpp, FP64), the
+// geometry of a level vector, and the per-(dim, degree) kernel entry points
+// that every instantiation unit (kernels_dk.cu compiled with VPS_DIM and
+// VPS_K) registers at load time.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vps {
+
+constexpr int kMaxK = 7;
+
+// 1D tables of Q_k in reference units (cell size 1), FP64.
+//  Ap, Mp : interior rows (1..2k-1) of the stiffness / mass matrices of the
+//           two-cell patch closure (2k+1 nodes), row-major m x n
+//           (Section 2.4: the patch operator is a Kronecker sum of these).
+//  S, lam : generalised eigenpairs of the interior blocks,
+//           A_I S = M_I S diag(lam), S^T M_I S = I (Eq. 2.15); S row-major,
+//           column j = eigenvector j.
+//  Kb, Mb : rows of the global 1D stiffness / mass matrices as bands:
+//           node o with q = o mod k couples to o-k+j, j = 0..2k, coefficient
+//           Kb[q*(2k+1)+j]  (Section 2.3, Cartesian cells).
+//  P1     : interpolation of the k+1 coarse basis functions of one coarse
+//           cell at its 2k+1 fine support points, row-major (2k+1) x (k+1)
+//           (Section 2.1).
+struct HostTables {
+  int k = 0;
+  int n = 0, m = 0;
+  double z[kMaxK + 1];                       // GLL nodes on [0,1]
+  double Khat[(kMaxK + 1) * (kMaxK + 1)];    // reference element stiffness
+  double Mhat[(kMaxK + 1) * (kMaxK + 1)];    // reference element mass
+  double Ap[(2 * kMaxK - 1) * (2 * kMaxK + 1)];
+  double Mp[(2 * kMaxK - 1) * (2 * kMaxK + 1)];
+  double S[(2 * kMaxK - 1) * (2 * kMaxK - 1)];
+  double lam[2 * kMaxK - 1];
+  double Kb[kMaxK * (2 * kMaxK + 1)];
+  double Mb[kMaxK * (2 * kMaxK + 1)];
+  double P1[(2 * kMaxK + 1) * (kMaxK + 1)];
+};
+
+// Computes every table for degree k (1..kMaxK). Returns false on failure.
+bool build_tables(int k, HostTables* t, char* err, size_t errlen);
+
+// Gauss-Legendre rule on [0,1] with q points (q <= 16).
+void gauss_rule(int q, double* x, double* w);
+
+// Lagrange basis of the GLL nodes z (k+1 of them) at point x.
+void lagrange_eval(int k, const double* z, double x, double* val);
+
+// Geometry of one level vector.
+struct LevelGeom {
+  int dim = 0, k = 0, level = 0;
+  int n1 = 0;          // nodes per direction incl. boundary
+  int ncell = 0;       // cells per direction
+  int64_t px = 0;      // row pitch (elements)
+  int64_t pz = 0;      // plane pitch (elements), 3D; = px * n1
+  int64_t total = 0;   // elements in the buffer
+  double h = 0.0;
+};
+
+LevelGeom make_geom(int dim, int k, int level);
+
+// Patches of one colour on one level.
+struct ColourGeom {
+  int cnt[3] = {1, 1, 1};     // patches per direction
+  int par[3] = {0, 0, 0};     // vertex parity per direction
+  int64_t npatch = 0;
+};
+
+ColourGeom make_colour(const LevelGeom& g, int colour);
+
+template <typename T>
+struct KernelFns {
+  // one multiplicative colour pass: x += R^T A_j^-1 (R b - Abar Rbar x)
+  cudaError_t (*smooth_mult)(const LevelGeom&, const ColourGeom&, const T* b, T* x,
+                             const T* inv_lam, cudaStream_t) = nullptr;
+  // one additive colour pass from a precomputed residual: x += scale R^T A_ref^-1 R r
+  cudaError_t (*smooth_add)(const LevelGeom&, const ColourGeom&, const T* r, T* x,
+                            const T* inv_lam, T scale, cudaStream_t) = nullptr;
+  // y = A x  (b == nullptr)  or  y = b - A x  (residual)
+  cudaError_t (*apply)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
+  // x_fine += P x_coarse
+  cudaError_t (*prolong_add)(const LevelGeom& fine, const LevelGeom& coarse, const T* xc, T* xf,
+                             cudaStream_t) = nullptr;
+  // r_coarse = P^T r_fine
+  cudaError_t (*restrict_)(const LevelGeom& fine, const LevelGeom& coarse, const T* rf, T* rc,
+                           cudaStream_t) = nullptr;
+};
+
+struct KernelSet {
+  bool present = false;
+  // copies the degree's tables into this unit's constant memory on the
+  // current device (synchronous)
+  cudaError_t (*upload)(const HostTables&) = nullptr;
+  KernelFns<float> f;
+  KernelFns<double> d;
+};
+
+// Registry indexed [dim-2][k-1]; filled by static initialisers of the
+// instantiation units.
+KernelSet* kernel_registry(int dim, int k);
+
+// --- generic vector kernels (ops.cu) ------------------------------------
+template <typename T>
+cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s);
+
+// Deterministic dot products over a whole level buffer: partial sums per
+// block into `partial` (kDotBlocks doubles per product), then one block
+// reduces them in a fixed order into out[0..nprod).
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
+                        int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* partial,
+                        double* out, cudaStream_t s);
+
+// CG scalar updates (all scalars live in device memory, see api.cu).
+struct CgScalars {
+  double rz;      // r_i . z_i
+  double pAp;     // p . A p
+  double alpha;
+  double rr;      // r . r after the update
+  double rzn;     // r_{i+1} . z_{i+1}
+  double rzo;     // r_{i+1} . z_i
+  double beta;
+  int flag;       // 1: breakdown detected on the device
+};
+cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
+                                CgScalars* sc, int64_t n, cudaStream_t s);
+cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
+                               cudaStream_t s);
+cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s);
+cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
+cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s);
+
+// b (compact, double) = sum_m coef_m prod_t b1d[m][t][node_t]  with b1d on device
+cudaError_t launch_rhs_tensor(const LevelGeom& g, int n_modes, const double* b1d, double* b,
+                              cudaStream_t s);
+// per-cell squared L2 error contributions of u_h - prod sin(pi x) -> partial sums
+cudaError_t launch_l2_error_sine(const LevelGeom& g, const double* xlev, const double* tab,
+                                 int q, double* partial, double* out, cudaStream_t s);
+
+}  // namespace vps
