@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the vertex-patch multigrid solver on one GB300 (or N replicas).
+
+Workload (one "step"): a V-cycle-preconditioned CG solve to a relative
+residual of 1e-10 of the 3D Poisson problem with Q4 elements on 32^3 cells
+(129^3 nodes, 2,048,383 interior DoFs), seeded random right-hand side in
+[-1, 1], colour-multiplicative vertex-patch smoother (1 pre / 1 post step),
+FP32 V-cycle inside FP64 CG.  The step runs every row of the hot path:
+fused patch smoother, matrix-free operator, transfers, V-cycle (captured as
+a CUDA graph) and CG.
+
+Printed (rank 0, one JSON line): value = interior DoFs solved per second
+over all ranks; e2e = the same through the host-buffer entry point
+(vps_solve_host, host<->device copies included); roofline of the dominant
+kernel (the finest-level FP32 smoother colour pass); the time to 1e-10 of
+the FP32-multigrid and FP64 solves; the oracle's CPU throughput.
+
+N > 1 (torchrun): every rank solves its own independent problem (replicas,
+weak scaling; the path has no data exchange between problems).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "smoother DoF/s & % FP32/FP64 peak; time-to-1e-10 residual FP32-MG vs FP64; p50/p99"
+D, K, L = 3, 4, 5
+RTOL = 1e-10
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak of GB300 (nominal, dense)
+FP64_PEAK_TFLOPS = 1.25
+CPU_SAMPLE_LEVEL = 3           # oracle sample: same problem family at level 3
+CPU_SAMPLE_REPEATS = 10
+
+
+def smoother_flops_per_patch(d, k):
+    """Dense sum-factorised flops of one fused patch update (FMA = 2 flops).
+
+    Local residual with interior output rows, then fast diagonalisation:
+    3D: 4mn^3 + 6m^2n^2 + 4m^3n + 12m^4 + 4m^3;  2D: 4mn^2 + 4m^2n + 8m^3 + 4m^2.
+    """
+    n, m = 2 * k + 1, 2 * k - 1
+    if d == 3:
+        return 4 * m * n ** 3 + 6 * m * m * n * n + 4 * m ** 3 * n + 12 * m ** 4 + 4 * m ** 3
+    return 4 * m * n * n + 4 * m * m * n + 8 * m ** 3 + 4 * m * m
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the FP64 / additive side measurements")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--repeats", type=int, default=CPU_SAMPLE_REPEATS, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- oracle
+def cpu_worker(repeats):
+    """Times the oracle PCG solve (FP64, multiplicative V-cycle) on the host."""
+    import numpy as np  # noqa: F401
+    from oracle import multigrid
+    from synthetic import uniform_vector
+    H = multigrid.Hierarchy(D, K, CPU_SAMPLE_LEVEL)
+    N = H.levels[CPU_SAMPLE_LEVEL].N
+    b = uniform_vector(N, 1)
+    times, its = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        _, it, rel = multigrid.pcg(H.A[CPU_SAMPLE_LEVEL], b, H.precondition, RTOL, 100)
+        times.append(time.perf_counter() - t0)
+        its.append(it)
+    print(json.dumps({"n": N, "times": times, "iters": its, "rel": rel}))
+
+
+def run_cpu_sample(repeats):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                          "--repeats", str(repeats)], capture_output=True, text=True, env=env,
+                         cwd=ROOT, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_desc(n, repeats):
+    return (f"oracle FP64 PCG (multiplicative V-cycle, 1/1 smoothing) of the same 3D Q4 problem at "
+            f"level {CPU_SAMPLE_LEVEL} ({n} DoFs; the workload is level {L}), {repeats} solves, "
+            f"setup excluded, BLAS threads 1")
+
+
+def config(extra=None):
+    c = {"workload": f"3D Poisson, Q{K}, 2^{L} cells/dir (129^3 nodes, 2048383 interior DoFs), "
+                     f"random RHS U[-1,1] seed 1, V-cycle-preconditioned CG to {RTOL:g}",
+         "dim": D, "degree": K, "level": L, "smoother": "multiplicative (8 colours), 1 pre / 1 post",
+         "precision": "FP32 V-cycle, FP64 CG", "l2": "flushed between timed steps (256 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W, Kst = args.warmup, args.steps
+    res = run_cpu_sample(W + Kst)
+    t = res["times"][W:]
+    n = res["n"]
+    value = n / statistics.mean(t)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s",
+            "n_gpus": args.gpus, "steps": Kst, "warmup": W,
+            "ms_per_step": 1e3 * statistics.mean(t), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample": f"level {CPU_SAMPLE_LEVEL} ({n} DoFs)"}),
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc(n, Kst)},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if self.uuid:
+            mine = [r for r in rows if len(r) > 1 and self.uuid in r[1]]
+            rows = mine or rows
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                mx = float(r[3])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.repeats)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    # the oracle's host sample runs first, in a fresh process, before any CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_sample(CPU_SAMPLE_REPEATS)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2405_19004_gb300 as vps
+    from synthetic import uniform_vector
+
+    P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
+    N = P.n_interior()
+    b = torch.as_tensor(uniform_vector(N, 1 + rank), device="cuda")
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = P.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    its = []
+    for _ in range(args.warmup):
+        it, rel = P.vps_solve(b, x, RTOL, 100)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    launches0 = P.vps_kernel_launches()
+    barrier()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        stream.wait_stream(torch.cuda.current_stream())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rel = P.vps_solve(b, x, RTOL, 100)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        its.append(it)
+    barrier()
+    launches = P.vps_kernel_launches() - launches0
+    clocks = sampler.stop()
+    t_step = statistics.mean(times)
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * N / t_step
+
+    # end to end through the host-buffer entry point (copies inside)
+    bh = torch.as_tensor(uniform_vector(N, 1 + rank)).pin_memory()
+    xh = torch.zeros(N, dtype=torch.float64).pin_memory()
+    P.vps_solve_host(bh, xh, RTOL, 100)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.vps_solve_host(bh, xh, RTOL, 100)
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = statistics.mean(e2e_t)
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+
+    # dominant kernel: finest-level FP32 smoother colour passes, CUDA events on the
+    # library's stream around each launch (same kernel and data sizes as in the solve)
+    lib = vps.lib()
+    import ctypes
+    bs = P.to_level(b.float())
+    xs = P.empty_level()
+    torch.cuda.synchronize()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    n_rep = 20
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(8 * n_rep)]
+    for c in range(8):  # warm-up
+        vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+    for r in range(n_rep):
+        for c in range(8):
+            a, z = evs[r * 8 + c]
+            a.record(stream)
+            vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+            z.record(stream)
+    torch.cuda.synchronize()
+    launch_ms = [a.elapsed_time(z) for a, z in evs]
+    t_launch = statistics.mean(launch_ms) / 1e3
+    n_patches = (2 ** L - 1) ** 3
+    flops_per_launch = smoother_flops_per_patch(D, K) * n_patches / 8.0
+    achieved = flops_per_launch / t_launch / 1e12
+    t_smooth_step = 8 * t_launch
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # FP64 V-cycle solve (time to 1e-10 in double precision)
+        P64 = vps.Poisson(D, K, L, precision=vps.VPS_FP64)
+        x64 = torch.zeros_like(b)
+        P64.vps_solve(b, x64, RTOL, 100)
+        t64 = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it64, rel64 = P64.vps_solve(b, x64, RTOL, 100)
+            t64.append(time.perf_counter() - t0)
+        # FP64 smoother step for the FP64 fraction of peak
+        bs64 = P64.to_level(b)
+        xs64 = P64.empty_level()
+        P64.vps_smooth(L, bs64, xs64, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(P64.stream)
+        for _ in range(3):
+            vps._check(lib.vps_smooth(P64.h, L, ptr(bs64), ptr(xs64), 1), P64.h)
+        e1.record(P64.stream)
+        torch.cuda.synchronize()
+        t64_step = e0.elapsed_time(e1) / 3e3
+        f64 = smoother_flops_per_patch(D, K) * n_patches / t64_step / 1e12
+        dx = (x64 - x).abs().max().item() / x64.abs().max().item()
+        extras = {
+            "time_to_1e-10_s": {"fp32_mg": t_step, "fp64": min(t64), "speedup": min(t64) / t_step},
+            "iterations": {"fp32_mg": its[-1], "fp64": it64},
+            "fp32_vs_fp64_solution_rel_maxdiff": dx,
+            "smoother_fp64": {"dof_per_s": N / t64_step, "tflops": f64,
+                              "frac_of_fp64_peak": f64 / FP64_PEAK_TFLOPS,
+                              "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"},
+        }
+        P64.close()
+        # additive smoother: damping 0.7 taken literally, and 0.7 of the stability limit
+        add = {}
+        for om in (0.7, 0.7 * 2 / 8):
+            Pa = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_ADDITIVE, damping=om)
+            xa = torch.zeros_like(b)
+            try:
+                Pa.vps_solve(b, xa, RTOL, 200)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ita, rela = Pa.vps_solve(b, xa, RTOL, 200)
+                add[f"omega_{om:g}"] = {"status": "converged", "iterations": ita,
+                                        "time_s": time.perf_counter() - t0}
+            except vps.VpsError as e:
+                add[f"omega_{om:g}"] = {"status": str(e).split(":")[0]}
+            Pa.close()
+        extras["additive_fp32_mg"] = add
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+        "iterations": its[-1], "rel_residual": rel,
+        "smoother_fp32": {"dof_per_s": N / t_smooth_step, "tflops": achieved,
+                          "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS},
+        "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "avg_launch_us": 1e6 * t_launch, "flops_per_launch": flops_per_launch},
+        "e2e": {"value": world * N / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        cpu_v = cpu["n"] / statistics.mean(cpu["times"])
+        line["cpu_baseline"] = {"value": cpu_v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                                "sample": sample_desc(cpu["n"], len(cpu["times"]))}
+    line.update(extras)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

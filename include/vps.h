@@ -176,6 +176,11 @@ int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef,
  */
 int vps_l2_error_sine(vps_handle h, const double* x, double* err);
 
+/* vps_kernel_launches -- number of kernels the handle has launched since
+ * creation (direct launches plus, for every replay of a captured graph, the
+ * kernels the graph holds).  Instrumentation for benchmarks. */
+int vps_kernel_launches(vps_handle h, int64_t* count);
+
 /* vps_set_graphs -- 1: capture the V-cycle in a CUDA graph on first use and
  * replay it (default on non-default streams); 0: launch kernels directly. */
 int vps_set_graphs(vps_handle h, int enable);

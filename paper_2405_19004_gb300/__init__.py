@@ -49,6 +49,7 @@ SIGNATURES = {
     "vps_assemble_rhs_sines": (_i, [_p, _i, _p, _p, _p]),
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
     "vps_set_graphs": (_i, [_p, _i]),
+    "vps_kernel_launches": (_i, [_p, _i64p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -216,6 +217,11 @@ class Poisson:
         err = ctypes.c_double()
         self._call(lib().vps_l2_error_sine, _ptr(x), ctypes.byref(err))
         return err.value
+
+    def vps_kernel_launches(self):
+        c = ctypes.c_int64()
+        _check(lib().vps_kernel_launches(self.h, ctypes.byref(c)), self.h)
+        return c.value
 
     def vps_set_graphs(self, enable):
         _check(lib().vps_set_graphs(self.h, int(bool(enable))), self.h)

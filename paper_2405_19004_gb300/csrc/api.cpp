@@ -100,6 +100,8 @@ struct vps_context {
   std::vector<void*> allocs;
   // captured preconditioner graph (input r = cr, output czn)
   cudaGraphExec_t prec_graph = nullptr;
+  int64_t graph_kernels = 0;            // kernel nodes in prec_graph
+  int64_t kernels = 0;                  // kernels launched by this handle
 };
 
 namespace {
@@ -145,6 +147,14 @@ int set_device(vps_context* h) {
   }
   return VPS_OK;
 }
+
+// Adds the kernels launched during an entry point to the handle's tally.
+struct LaunchTally {
+  vps_context* h;
+  int64_t start;
+  explicit LaunchTally(vps_context* hh) : h(hh), start(launch_counter()) {}
+  ~LaunchTally() { h->kernels += launch_counter() - start; }
+};
 
 int check_level(vps_context* h, int level, int lo) {
   if (level < lo || level > h->L)
@@ -237,7 +247,10 @@ int precondition(vps_context* h) {
   if (!h->prec_graph) {
     cudaGraph_t graph = nullptr;
     VPS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launch_counter();
     int rc = precondition_direct(h);
+    h->graph_kernels = launch_counter() - before;
+    launch_counter() = before;  // captured, not launched
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -252,6 +265,7 @@ int precondition(vps_context* h) {
     }
   }
   VPS_CK(h, cudaGraphLaunch(h->prec_graph, h->stream));
+  launch_counter() += h->graph_kernels;
   return VPS_OK;
 }
 
@@ -494,6 +508,7 @@ int vps_pack(vps_handle h, int level, const void* compact, void* lev) {
   if (!h || !compact || !lev) return h ? fail(h, VPS_EINVAL, "NULL vector") : VPS_EINVAL;
   if (int rc = check_level(h, level, 1)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   if (h->prec == VPS_FP64)
     VPS_CK(h, launch_pack<double>(h->geom[level], (const double*)compact, (double*)lev, h->stream));
   else
@@ -505,6 +520,7 @@ int vps_unpack(vps_handle h, int level, const void* lev, void* compact) {
   if (!h || !compact || !lev) return h ? fail(h, VPS_EINVAL, "NULL vector") : VPS_EINVAL;
   if (int rc = check_level(h, level, 1)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   if (h->prec == VPS_FP64)
     VPS_CK(h, launch_unpack<double>(h->geom[level], (const double*)lev, (double*)compact, h->stream));
   else
@@ -518,6 +534,7 @@ int vps_smooth(vps_handle h, int level, const void* b, void* x, int n_steps) {
   if (n_steps < 0) return fail(h, VPS_EINVAL, "n_steps < 0");
   if (int rc = check_level(h, level, 2)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   for (int s = 0; s < n_steps; ++s) {
     int rc = h->prec == VPS_FP64
                  ? smooth_step<double>(h, level, (const double*)b, (double*)x, true)
@@ -533,6 +550,7 @@ int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* 
   if (int rc = check_level(h, level, 1)) return rc;
   if (colour < 0 || colour >= (1 << h->dim)) return fail(h, VPS_EINVAL, "colour out of range");
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom& g = h->geom[level];
   if (h->prec == VPS_FP64)
     VPS_CK(h, h->ks->d.smooth_mult(g, make_colour(g, colour), (const double*)b, (double*)x,
@@ -548,6 +566,7 @@ int vps_apply(vps_handle h, int level, const void* x, void* y) {
   if (!x || !y || x == y) return fail(h, VPS_EINVAL, "x and y must be distinct non-NULL vectors");
   if (int rc = check_level(h, level, 1)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom& g = h->geom[level];
   if (h->prec == VPS_FP64)
     VPS_CK(h, h->ks->d.apply(g, (const double*)x, nullptr, (double*)y, h->stream));
@@ -561,6 +580,7 @@ int vps_restrict(vps_handle h, int fine_level, const void* rf, void* rc_) {
   if (!rf || !rc_ || rf == rc_) return fail(h, VPS_EINVAL, "bad vectors");
   if (int rc = check_level(h, fine_level, 2)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom &f = h->geom[fine_level], &c = h->geom[fine_level - 1];
   if (h->prec == VPS_FP64)
     VPS_CK(h, h->ks->d.restrict_(f, c, (const double*)rf, (double*)rc_, h->stream));
@@ -574,6 +594,7 @@ int vps_prolongate_add(vps_handle h, int fine_level, const void* xc, void* xf) {
   if (!xc || !xf || xc == xf) return fail(h, VPS_EINVAL, "bad vectors");
   if (int rc = check_level(h, fine_level, 2)) return rc;
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom &f = h->geom[fine_level], &c = h->geom[fine_level - 1];
   if (h->prec == VPS_FP64)
     VPS_CK(h, h->ks->d.prolong_add(f, c, (const double*)xc, (double*)xf, h->stream));
@@ -586,6 +607,7 @@ int vps_vcycle(vps_handle h, const void* b, void* x) {
   if (!h) return VPS_EINVAL;
   if (!b || !x || b == x) return fail(h, VPS_EINVAL, "b and x must be distinct non-NULL vectors");
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   return h->prec == VPS_FP64 ? vcycle_core<double>(h, (const double*)b, (double*)x)
                              : vcycle_core<float>(h, (const float*)b, (float*)x);
 }
@@ -596,6 +618,7 @@ int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
   if (!b || !x) return fail(h, VPS_EINVAL, "NULL vector");
   if (!(rtol > 0.0) || max_it < 1) return fail(h, VPS_EINVAL, "need rtol > 0 and max_it >= 1");
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom& g = h->geom[h->L];
   VPS_CK(h, launch_pack<double>(g, b, h->cb, h->stream));
   int rc = cg_solve(h, rtol, max_it, iters, rel_res);
@@ -625,6 +648,7 @@ int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef, const 
   if (n_modes < 1 || n_modes > 4096 || !coef || !freq || !b)
     return fail(h, VPS_EINVAL, "bad sine-mode arguments");
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom& g = h->geom[h->L];
   const int k = h->k, ni = g.n1 - 2, q = k + 2;
   double xq[16], wq[16], val[kMaxK + 1];
@@ -665,6 +689,7 @@ int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
   if (!h) return VPS_EINVAL;
   if (!x || !err) return fail(h, VPS_EINVAL, "NULL pointer");
   if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
   const LevelGeom& g = h->geom[h->L];
   const int k = h->k, q = k + 2, nl = k + 1;
   double xq[16], wq[16], val[kMaxK + 1];
@@ -686,6 +711,12 @@ int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
                             h->stream));
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   *err = std::sqrt(h->host_dots[0]);
+  return VPS_OK;
+}
+
+int vps_kernel_launches(vps_handle h, int64_t* count) {
+  if (!h || !count) return VPS_EINVAL;
+  *count = h->kernels;
   return VPS_OK;
 }
 

@@ -852,6 +852,7 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
   smooth_mult_kernel<T><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, g.px, g.pz, cg,
                                                                      bscale);
   return cudaGetLastError();
@@ -864,6 +865,7 @@ cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T*
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T sc = DIM == 3 ? T(scale / g.h) : scale;
+  VPS_COUNT_LAUNCH();
   smooth_add_kernel<T><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, g.px, g.pz, cg, sc);
   return cudaGetLastError();
 }
@@ -874,6 +876,7 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
   const unsigned t = (unsigned)((g.n1 + C::TN - 1) / C::TN);
   dim3 grid(t, t, DIM == 3 ? t : 1);
   const T scale = DIM == 3 ? T(g.h) : T(1);
+  VPS_COUNT_LAUNCH();
   apply_kernel<T><<<grid, C::NT, C::smem<T>(), s>>>(x, b, y, g.n1, g.px, g.pz, scale);
   return cudaGetLastError();
 }
@@ -884,6 +887,7 @@ cudaError_t prolong_launch(const LevelGeom& f, const LevelGeom& c, const T* xc, 
   using C = TransferCfg;
   const unsigned t = (unsigned)((c.ncell + C::CC - 1) / C::CC);
   dim3 grid(t, t, DIM == 3 ? t : 1);
+  VPS_COUNT_LAUNCH();
   prolong_add_kernel<T><<<grid, C::NT, C::smem_prolong<T>(), s>>>(xc, xf, c.n1, c.px, c.pz, f.n1,
                                                                    f.px, f.pz);
   return cudaGetLastError();
@@ -895,10 +899,12 @@ cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf,
   using C = TransferCfg;
   const unsigned t = (unsigned)((c.ncell + C::CC - 1) / C::CC);
   dim3 grid(t, t, DIM == 3 ? t : 1);
+  VPS_COUNT_LAUNCH();
   restrict_kernel<T><<<grid, C::NT, C::smem_restrict<T>(), s>>>(rf, rc, c.n1, c.px, c.pz, f.n1,
                                                                  f.px, f.pz);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
   zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(rc, c.n1, c.px, c.pz);
   return cudaGetLastError();
 }

@@ -244,6 +244,7 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
 
 template <typename T>
 cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   pack_kernel<T><<<grid_for(g.total, 4), kThreads, 0, s>>>(compact, lev, g.dim, g.n1, g.px, g.pz,
                                                             g.total);
   return cudaGetLastError();
@@ -253,19 +254,23 @@ template <typename T>
 cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStream_t s) {
   const int64_t ni = g.n1 - 2;
   const int64_t nc = g.dim == 3 ? ni * ni * ni : ni * ni;
+  VPS_COUNT_LAUNCH();
   unpack_kernel<T><<<grid_for(nc, 4), kThreads, 0, s>>>(lev, compact, g.dim, g.n1, g.px, g.pz, nc);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   zero_kernel<T><<<grid_for(n, 4), kThreads, 0, s>>>(p, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
                         int64_t n, double* partial, double* out, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   dot_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
+  VPS_COUNT_LAUNCH();
   dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, c ? 2 : 1);
   return cudaGetLastError();
 }
@@ -277,36 +282,44 @@ cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* par
 
 cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
                                 CgScalars* sc, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   cg_alpha_kernel<<<1, 1, 0, s>>>(sc);
+  VPS_COUNT_LAUNCH();
   cg_update_xr_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(x, r, p, Ap, sc, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
                                cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   cg_beta_kernel<<<1, 1, 0, s>>>(sc);
+  VPS_COUNT_LAUNCH();
   cg_update_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, sc, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s) {
   (void)sc;
+  VPS_COUNT_LAUNCH();
   cg_init_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   cast_d2f_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   cast_f2d_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   axpy_kernel<T><<<grid_for(n, 4), kThreads, 0, s>>>(y, x, a, n);
   return cudaGetLastError();
 }
@@ -315,14 +328,17 @@ cudaError_t launch_rhs_tensor(const LevelGeom& g, int n_modes, const double* b1d
                               cudaStream_t s) {
   const int64_t ni = g.n1 - 2;
   const int64_t nc = g.dim == 3 ? ni * ni * ni : ni * ni;
+  VPS_COUNT_LAUNCH();
   rhs_tensor_kernel<<<grid_for(nc, 4), kThreads, 0, s>>>(b1d, b, g.dim, (int)ni, n_modes, nc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_l2_error_sine(const LevelGeom& g, const double* xlev, const double* tab, int q,
                                  double* partial, double* out, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
   l2_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(xlev, tab, g.dim, g.k, q, g.ncell, g.px, g.pz,
                                                      g.h, partial);
+  VPS_COUNT_LAUNCH();
   dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, 1);
   return cudaGetLastError();
 }

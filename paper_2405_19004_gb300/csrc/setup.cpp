@@ -287,6 +287,11 @@ ColourGeom make_colour(const LevelGeom& g, int colour) {
   return c;
 }
 
+int64_t& launch_counter() {
+  static thread_local int64_t count = 0;
+  return count;
+}
+
 static KernelSet g_registry[2][kMaxK];
 
 KernelSet* kernel_registry(int dim, int k) {

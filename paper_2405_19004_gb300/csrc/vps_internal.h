@@ -73,6 +73,11 @@ struct ColourGeom {
 
 ColourGeom make_colour(const LevelGeom& g, int colour);
 
+// Number of kernels this thread has launched through the library (every
+// launch site increments it); used to report launches per call.
+int64_t& launch_counter();
+#define VPS_COUNT_LAUNCH() (++::vps::launch_counter())
+
 template <typename T>
 struct KernelFns {
   // one multiplicative colour pass: x += R^T A_j^-1 (R b - Abar Rbar x)
