@@ -185,8 +185,37 @@ int vps_kernel_launches(vps_handle h, int64_t* count);
  * replay it (default on non-default streams); 0: launch kernels directly. */
 int vps_set_graphs(vps_handle h, int enable);
 
+/*
+ * vps_smooth_additive_static -- one additive smoothing step on `level`
+ * (2..), in place on x, WITHOUT a handle and without allocating memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- e.g. an application whose framework reserves
+ * nearly all device memory for its own pool at start-up, a latency-bound
+ * loop that cannot afford the synchronisation of cudaMalloc/cudaFree, or a
+ * deployment with a fixed, audited device-memory budget.
+ *   Computes x += damping * sum_j R_j^T A_j^{-1} R_j (b - A x), the step of
+ *   vps_smooth on a VPS_ADDITIVE handle with the same damping.
+ *   dim, degree, level, precision, damping: as for vps_create; b, x: device
+ *   vectors in the level layout of `level` (float for VPS_FP32, double for
+ *   VPS_FP64), caller-owned, distinct.  cuda_stream: the stream to run on.
+ *   Scratch: the residual and the eigenvalue table live in one static device
+ *   array of 32 MiB inside the library; a level whose residual needs more
+ *   than 32 MiB - 32 KiB (for example 3D Q4 on more than 2^5 cells per
+ *   direction) is rejected with VPS_EINVAL and a message.  The array stays
+ *   allocated on every GPU that loaded the library until the process exits.
+ *   The first call on a device (with that device current) looks up the
+ *   array's device address and uploads the degree's constant tables; make
+ *   that first call before any stream capture begins.  Every call shares
+ *   the array and overwrites it: calls whose work overlaps on one GPU race,
+ *   so issue them in one stream or order them.  Errors: VPS_EINVAL,
+ *   VPS_ECUDA; message via vps_last_error(NULL).
+ */
+int vps_smooth_additive_static(int dim, int degree, int level, int precision, double damping,
+                               const void* b, void* x, void* cuda_stream);
+
 /* vps_last_error -- message of the last failure on h (h = NULL: the last
- * failure of vps_create on this thread).  Valid until the next call. */
+ * failure of vps_create or vps_smooth_additive_static on this thread).
+ * Valid until the next call. */
 const char* vps_last_error(vps_handle h);
 
 /* vps_status_string -- name of a status code. */

@@ -50,6 +50,7 @@ SIGNATURES = {
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
     "vps_set_graphs": (_i, [_p, _i]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
+    "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -93,6 +94,19 @@ def _check(rc, handle=None):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def vps_smooth_additive_static(dim, degree, level, precision, damping, b, x, stream):
+    """One additive smoothing step without a handle and without allocating.
+
+    b, x: CUDA tensors in the level layout of ``level`` (float32 for VPS_FP32,
+    float64 for VPS_FP64); stream: a torch CUDA stream the call runs on.  The
+    step's scratch lives in a fixed 32 MiB device array inside the library
+    (larger levels are rejected); calls that overlap on one GPU race on it.
+    """
+    rc = lib().vps_smooth_additive_static(dim, degree, level, precision, float(damping), _ptr(b),
+                                          _ptr(x), ctypes.c_void_p(stream.cuda_stream))
+    return _check(rc, None)
 
 
 class Poisson:

@@ -67,6 +67,13 @@ void register_all() {
 
 }  // namespace
 
+namespace vps {
+// Fills the kernel registry (idempotent); used by entry points without a handle.
+void ensure_registered() { register_all(); }
+// Sets the message vps_last_error(NULL) returns on this thread.
+void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace vps
+
 struct vps_context {
   int dim = 0, k = 0, L = 0, prec = 0, smoother = 0;
   double damping = 1.0;

@@ -105,9 +105,10 @@ struct KernelSet {
   KernelFns<double> d;
 };
 
-// Registry indexed [dim-2][k-1]; filled by static initialisers of the
-// instantiation units.
+// Registry indexed [dim-2][k-1]; filled by ensure_registered().
 KernelSet* kernel_registry(int dim, int k);
+void ensure_registered();
+void set_thread_error(const char* msg);
 
 // --- generic vector kernels (ops.cu) ------------------------------------
 template <typename T>
