@@ -135,8 +135,8 @@ int vps_prolongate_add(vps_handle h, int fine_level, const void* x_coarse, void*
  * vps_vcycle -- x = Vcycle_L(A_L, 0, b) on the finest level (Algorithm 1),
  * level layout, working precision.  n_pre / n_post smoothing steps per
  * level; the multiplicative post-smoother visits the colours in reverse
- * order so that the cycle is a symmetric preconditioner; the coarsest
- * level (level 1, one vertex patch) is solved exactly by one patch solve.
+ * order so that the cycle is a symmetric preconditioner; the coarsest level
+ * (vps_set_coarse_level) is solved exactly.
  */
 int vps_vcycle(vps_handle h, const void* b, void* x);
 
@@ -175,6 +175,21 @@ int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef,
  * Synchronous.
  */
 int vps_l2_error_sine(vps_handle h, const double* x, double* err);
+
+/*
+ * vps_set_coarse_level -- choose the coarsest level of the V-cycle, solved
+ * exactly (Algorithm 1's coarse grid solver).  On the uniform Cartesian mesh
+ * the operator of a whole level is a Kronecker sum of 1D stiffness and mass
+ * matrices (Eq. 2.11/2.12), so the exact solve is a global fast
+ * diagonalisation (Eq. 2.13-2.15 with the level's 1D eigenpairs).
+ * level: 1..finest (level 1 holds a single vertex patch; the finest level
+ * makes the V-cycle an exact solver), or 0 for the default chosen at
+ * creation: the finest level below the top with at most 32 interior nodes
+ * per direction.  At most 255 interior nodes per direction.  Synchronises
+ * the stream and allocates the level's tables.  Errors: VPS_EINVAL.
+ */
+int vps_set_coarse_level(vps_handle h, int level);
+int vps_get_coarse_level(vps_handle h, int* level);
 
 /* vps_kernel_launches -- number of kernels the handle has launched since
  * creation (direct launches plus, for every replay of a captured graph, the

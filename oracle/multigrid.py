@@ -2,7 +2,8 @@
 
 * V-cycle: Algorithm 1 (pre-smooth, residual, restrict with the transpose of
   the prolongation, recurse from a zero initial guess, prolongate-add,
-  post-smooth).  The coarse problem is solved exactly.  The paper closes the
+  post-smooth).  The coarse problem is solved exactly (dense LU) on a
+  chosen coarsest level (default 1).  The paper closes the
   recursion "on level 0" with one smoother step; the mesh M_0 has no interior
   vertex, so the reading used here is that the coarsest level is level 1,
   whose single vertex patch covers every interior DoF -- one patch solve is
@@ -27,18 +28,22 @@ class Hierarchy:
     """Levels 1..L of one problem (d, k): A_l, I^up_l, patch solvers."""
 
     def __init__(self, d, k, L, smoother="multiplicative", omega=1.0,
-                 n_pre=1, n_post=1, symmetric=True):
-        if L < 1:
-            raise ValueError("L >= 1")
+                 n_pre=1, n_post=1, symmetric=True, coarse_level=1):
+        """coarse_level: the level solved exactly (Algorithm 1's coarse grid
+        solver); 1 recurses as deep as the mesh allows."""
+        if L < 1 or not 1 <= coarse_level <= L:
+            raise ValueError("need 1 <= coarse_level <= L")
         self.d, self.k, self.L = d, k, L
+        self.coarse = coarse_level
         self.smoother, self.omega = smoother, omega
         self.n_pre, self.n_post, self.symmetric = n_pre, n_post, symmetric
-        self.levels = {l: fe.Level(d, k, l) for l in range(1, L + 1)}
-        self.A = {l: assembly.stiffness(self.levels[l]) for l in range(1, L + 1)}
-        self.P = {l: assembly.prolongation(self.levels[l]) for l in range(2, L + 1)}
+        lo = coarse_level
+        self.levels = {l: fe.Level(d, k, l) for l in range(lo, L + 1)}
+        self.A = {l: assembly.stiffness(self.levels[l]) for l in range(lo, L + 1)}
+        self.P = {l: assembly.prolongation(self.levels[l]) for l in range(lo + 1, L + 1)}
         self.ps = {l: smoothers.PatchSolver(self.levels[l], self.A[l])
-                   for l in range(2, L + 1)}
-        self.coarse_lu = sla.lu_factor(self.A[1].toarray())
+                   for l in range(max(2, lo + 1), L + 1)}
+        self.coarse_lu = sla.lu_factor(self.A[lo].toarray())
 
     def smooth(self, l, x, b, forward=True):
         if self.smoother == "additive":
@@ -49,7 +54,7 @@ class Hierarchy:
 
     def vcycle(self, l, b, x=None):
         """x_l = Vcycle_l(A_l, x, b) (Algorithm 1); x defaults to 0."""
-        if l == 1:
+        if l == self.coarse:
             return sla.lu_solve(self.coarse_lu, b)
         x = np.zeros_like(b) if x is None else np.array(x, dtype=np.float64)
         for _ in range(self.n_pre):

@@ -50,6 +50,8 @@ SIGNATURES = {
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
     "vps_set_graphs": (_i, [_p, _i]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
+    "vps_set_coarse_level": (_i, [_p, _i]),
+    "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
@@ -118,7 +120,7 @@ class Poisson:
     """
 
     def __init__(self, dim, degree, level, precision=VPS_FP64, smoother=VPS_MULTIPLICATIVE,
-                 damping=1.0, n_pre=1, n_post=1, stream=None, graphs=True):
+                 damping=1.0, n_pre=1, n_post=1, stream=None, graphs=True, coarse_level=0):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -134,6 +136,8 @@ class Poisson:
         self.h = h
         if not graphs:
             _check(lib().vps_set_graphs(self.h, 0), self.h)
+        if coarse_level:
+            _check(lib().vps_set_coarse_level(self.h, int(coarse_level)), self.h)
         self.dtype = torch.float64 if precision == VPS_FP64 else torch.float32
 
     def close(self):
@@ -231,6 +235,14 @@ class Poisson:
         err = ctypes.c_double()
         self._call(lib().vps_l2_error_sine, _ptr(x), ctypes.byref(err))
         return err.value
+
+    def vps_set_coarse_level(self, level):
+        self._call(lib().vps_set_coarse_level, int(level))
+
+    def vps_get_coarse_level(self):
+        c = ctypes.c_int()
+        _check(lib().vps_get_coarse_level(self.h, ctypes.byref(c)), self.h)
+        return c.value
 
     def vps_kernel_launches(self):
         c = ctypes.c_int64()

@@ -109,6 +109,13 @@ struct vps_context {
   cudaGraphExec_t prec_graph = nullptr;
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
+  // exact coarse solve on level `coarse` by global fast diagonalisation
+  int coarse = 1;
+  int gni = 0;                          // interior nodes per direction on that level
+  void* gS = nullptr;                   // S (gni x gni), working precision
+  void* ginv = nullptr;                 // h^(2-d) / (sum of eigenvalues), gni^d
+  void* gt1 = nullptr;                  // two gni^d work tensors
+  void* gt2 = nullptr;
 };
 
 namespace {
@@ -196,6 +203,87 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   return VPS_OK;
 }
 
+// x = A_l^{-1} b on the coarse level by global fast diagonalisation: S^T
+// along z, y, x (the last pass scaled by 1/(sum of eigenvalues)), then S back.
+template <typename T>
+int coarse_solve(vps_context* h, const T* b, T* x) {
+  const LevelGeom& g = h->geom[h->coarse];
+  const int ni = h->gni, d = h->dim, px = (int)g.px, pz = (int)g.pz;
+  const T* S = static_cast<const T*>(h->gS);
+  const T* inv = static_cast<const T*>(h->ginv);
+  T* t1 = static_cast<T*>(h->gt1);
+  T* t2 = static_cast<T*>(h->gt2);
+  cudaStream_t st = h->stream;
+  VPS_CK(h, cudaMemsetAsync(x, 0, g.total * sizeof(T), st));
+  if (d == 3) {
+    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(0, t1, t2, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(1, t2, t1, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, t2, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, S, inv, ni, d, false, true, px, pz, st));
+  } else {
+    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(1, t1, t2, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, S, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, S, inv, ni, d, false, true, px, pz, st));
+  }
+  return VPS_OK;
+}
+
+// Automatic coarsest level: the finest level below L with at most 32
+// interior nodes per direction (level 1 if none).
+int auto_coarse_level(int k, int L) {
+  int best = 1;
+  for (int l = 1; l < L; ++l)
+    if (k * (1 << l) - 1 <= 32) best = l;
+  return best;
+}
+
+// Builds the global fast-diagonalisation data of level lc (allocates).
+int setup_coarse(vps_context* h, int lc) {
+  std::vector<double> S, lam;
+  char ebuf[256];
+  if (!build_global_fd(h->k, lc, &S, &lam, ebuf, sizeof(ebuf)))
+    return fail(h, VPS_EINVAL, "coarse level %d: %s", lc, ebuf);
+  const int ni = (int)lam.size(), d = h->dim;
+  const size_t nd = (size_t)ni * ni * (d == 3 ? ni : 1);
+  const double hs = std::pow(h->geom[lc].h, 2 - d);  // A^{-1} = h^(2-d) A_ref^{-1}
+  std::vector<double> inv(nd);
+  for (size_t a = 0; a < nd; ++a) {
+    const size_t i0 = a % ni, i1 = (a / ni) % ni, i2 = a / ((size_t)ni * ni);
+    inv[a] = hs / (lam[i0] + lam[i1] + (d == 3 ? lam[i2] : 0.0));
+  }
+  for (void* p : {h->gS, h->ginv, h->gt1, h->gt2})
+    if (p) {
+      cudaFree(p);
+      for (auto& q : h->allocs)
+        if (q == p) q = nullptr;
+    }
+  h->gS = h->ginv = h->gt1 = h->gt2 = nullptr;
+  int rc;
+  if ((rc = dalloc(h, &h->gS, (size_t)ni * ni * h->esz)) || (rc = dalloc(h, &h->ginv, nd * h->esz)) ||
+      (rc = dalloc(h, &h->gt1, nd * h->esz)) || (rc = dalloc(h, &h->gt2, nd * h->esz)))
+    return rc;
+  cudaError_t e;
+  if (h->prec == VPS_FP64) {
+    e = cudaMemcpy(h->gS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->ginv, inv.data(), nd * sizeof(double), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> Sf(S.begin(), S.end()), invf(inv.begin(), inv.end());
+    e = cudaMemcpy(h->gS, Sf.data(), Sf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->ginv, invf.data(), nd * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "coarse tables: %s", cudaGetErrorString(e));
+  h->coarse = lc;
+  h->gni = ni;
+  if (h->prec_graph) {
+    cudaGraphExecDestroy(h->prec_graph);
+    h->prec_graph = nullptr;
+  }
+  return VPS_OK;
+}
+
 // x_L = Vcycle_L(A_L, 0, b_L) (Algorithm 1) in working precision T.
 template <typename T>
 int vcycle_core(vps_context* h, const T* bL, T* xL) {
@@ -208,7 +296,8 @@ int vcycle_core(vps_context* h, const T* bL, T* xL) {
   }
   b[h->L] = bL;
   x[h->L] = xL;
-  for (int l = h->L; l >= 2; --l) {
+  const int lc = h->coarse;
+  for (int l = h->L; l > lc; --l) {
     const LevelGeom& g = h->geom[l];
     VPS_CK(h, cudaMemsetAsync(x[l], 0, g.total * sizeof(T), h->stream));
     for (int s = 0; s < h->n_pre; ++s) {
@@ -219,15 +308,12 @@ int vcycle_core(vps_context* h, const T* bL, T* xL) {
     VPS_CK(h, F.apply(g, x[l], b[l], r, h->stream));
     VPS_CK(h, F.restrict_(g, h->geom[l - 1], r, static_cast<T*>(h->bv[l - 1]), h->stream));
   }
-  // coarsest level: one vertex patch holds every interior DoF; one patch
-  // solve from zero is the exact coarse solve
+  // coarsest level: exact solve (Algorithm 1's coarse grid solver)
   {
-    const LevelGeom& g = h->geom[1];
-    VPS_CK(h, cudaMemsetAsync(x[1], 0, g.total * sizeof(T), h->stream));
-    VPS_CK(h, F.smooth_mult(g, make_colour(g, 0), b[1], x[1],
-                            static_cast<const T*>(h->inv_lam), h->stream));
+    int rc = coarse_solve<T>(h, b[lc], x[lc]);
+    if (rc) return rc;
   }
-  for (int l = 2; l <= h->L; ++l) {
+  for (int l = lc + 1; l <= h->L; ++l) {
     VPS_CK(h, F.prolong_add(h->geom[l], h->geom[l - 1], x[l - 1], x[l], h->stream));
     for (int s = 0; s < h->n_post; ++s) {
       int rc = smooth_step<T>(h, l, b[l], x[l], false);
@@ -463,6 +549,7 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   if ((rc = dalloc(h, &p, 8 * sizeof(double)))) return bail(rc); h->dots = (double*)p;
   if ((rc = dalloc(h, &p, sizeof(CgScalars)))) return bail(rc); h->sc = (CgScalars*)p;
   if ((rc = dalloc(h, &p, 256 * sizeof(double)))) return bail(rc); h->l2_tab = (double*)p;
+  if ((rc = setup_coarse(h, auto_coarse_level(degree, level)))) return bail(rc);
   e = cudaMallocHost(&p, sizeof(CgScalars));
   if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
   h->host_sc = (CgScalars*)p;
@@ -718,6 +805,23 @@ int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
                             h->stream));
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   *err = std::sqrt(h->host_dots[0]);
+  return VPS_OK;
+}
+
+int vps_set_coarse_level(vps_handle h, int level) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = set_device(h)) return rc;
+  if (level == 0) level = auto_coarse_level(h->k, h->L);
+  if (level < 1 || level > h->L)
+    return fail(h, VPS_EINVAL, "coarse level %d outside 1..%d", level, h->L);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return fail(h, VPS_ECUDA, "stream synchronisation failed");
+  return setup_coarse(h, level);
+}
+
+int vps_get_coarse_level(vps_handle h, int* level) {
+  if (!h || !level) return VPS_EINVAL;
+  *level = h->coarse;
   return VPS_OK;
 }
 

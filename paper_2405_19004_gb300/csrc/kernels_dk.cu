@@ -71,6 +71,12 @@ struct SmoothCfg {
   static constexpr int lines0 = DIM == 3 ? n * n : n;
   static constexpr int NT0 = ((P * lines0 + 31) / 32) * 32;
   static constexpr int NT = NT0 > 256 ? 256 : NT0;
+  // blocks per SM the register allocation is sized for: about 40 registers
+  // per thread for FP32 and 64 for FP64 up to k = 4; the k >= 5 stages hold
+  // 2(2k+1) + 2(2k-1) values per thread and get 80 / 128
+  static constexpr int RESIDENT = K >= 5 ? (sizeof(T) == 4 ? 768 : 512)
+                                         : (sizeof(T) == 4 ? 1536 : 1024);
+  static constexpr int MINB = RESIDENT / NT > 8 ? 8 : (RESIDENT / NT < 1 ? 1 : RESIDENT / NT);
   static constexpr int NB = 128 / (int)sizeof(T);  // word-banks per wavefront
   // patch-major stride of the first stage's output, chosen so that the
   // next stage (patch index fastest) hits P distinct bank groups
@@ -81,20 +87,50 @@ struct SmoothCfg {
   static constexpr int sizeU = DIM == 3 ? n * m * m : m * m;
   static constexpr int nU = DIM == 3 ? 2 : 1;
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
-  static constexpr size_t smem_mult = sizeof(T) * (size_t)(2 * P * S0 + nU * P * sizeU);
-  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md);
+  // tM, tA | U, W (3D) or R (2D) | b interior | x interior   (elements)
+  static constexpr size_t elems_mult = (size_t)2 * P * S0 + (size_t)nU * P * sizeU + 2 * P * md;
+  static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
+  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md) + sizeof(int) * P;
 };
 
-__device__ __forceinline__ int64_t closure_origin(int64_t gp, const ColourGeom& cg, int64_t px,
-                                                  int64_t pz) {
-  const int64_t i0 = gp % cg.cnt[0];
-  const int64_t r = gp / cg.cnt[0];
-  const int64_t i1 = r % cg.cnt[1];
-  const int64_t i2 = r / cg.cnt[1];
-  const int64_t o0 = (int64_t)K * (cg.par[0] + 2 * i0);
-  const int64_t o1 = (int64_t)K * (cg.par[1] + 2 * i1);
-  const int64_t o2 = DIM == 3 ? (int64_t)K * (cg.par[2] + 2 * i2) : 0;
+// Offset of the first closure node of patch gp of a colour (int: every
+// level vector holds fewer than 2^31 elements).
+__device__ __forceinline__ int closure_origin(int gp, const ColourGeom& cg, int px, int pz) {
+  const int i0 = gp % cg.cnt[0];
+  const int r = gp / cg.cnt[0];
+  const int i1 = r % cg.cnt[1];
+  const int i2 = r / cg.cnt[1];
+  const int o0 = K * (cg.par[0] + 2 * i0);
+  const int o1 = K * (cg.par[1] + 2 * i1);
+  const int o2 = DIM == 3 ? K * (cg.par[2] + 2 * i2) : 0;
   return o0 + o1 * px + o2 * pz;
+}
+
+// Origins of the block's P patches (-1: beyond the colour), computed once.
+template <int P>
+__device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, int px, int pz) {
+  if (threadIdx.x < P) {
+    const int64_t gp = (int64_t)blockIdx.x * P + threadIdx.x;
+    s_org[threadIdx.x] = gp < cg.npatch ? closure_origin((int)gp, cg, px, pz) : -1;
+  }
+}
+
+// Interior values (m^d per patch) of a level vector into the interleaved
+// layout [z][y][x][p], multiplied by `scale`.  Rows are read contiguously.
+template <typename T, int P, int NT>
+__device__ __forceinline__ void load_interior(const T* __restrict__ src, const int* s_org, T* dst,
+                                              int px, int pz, T scale) {
+  constexpr int MD = DIM == 3 ? m * m * m : m * m;
+  for (int e = threadIdx.x; e < P * MD; e += NT) {
+    const int o = e % m, rest = e / m;             // x fastest
+    const int yy = rest % m;
+    const int zz = DIM == 3 ? (rest / m) % m : 0;
+    const int p = DIM == 3 ? rest / (m * m) : rest / m;
+    const int org = s_org[p];
+    T v = T(0);
+    if (org >= 0) v = scale * src[org + (DIM == 3 ? (zz + 1) * pz : 0) + (yy + 1) * px + 1 + o];
+    dst[((DIM == 3 ? (zz * m + yy) * m : yy * m) + o) * P + p] = v;
+  }
 }
 
 // One fast-diagonalisation contraction over interleaved tensors.
@@ -121,11 +157,12 @@ __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict
 }
 
 // Back-transformation S (x) S (x) S of the scaled coefficients in X0 and the
-// final update of the interior: x_I += scale * u.
+// final update of the interior: x_I = base_I + scale * u, where base_I is
+// the interior of x staged in shared memory (xs != nullptr) or read from x.
 template <typename T, int P, int NT>
 __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restrict__ x,
-                                                       int64_t pbase, const ColourGeom& cg,
-                                                       int64_t px, int64_t pz, T scale) {
+                                                       const T* xs, const int* s_org, int px,
+                                                       int pz, T scale) {
   constexpr int NL = DIM == 3 ? m * m : m;
   const DevTab<T>& tb = c_tab<T>;
   const T* last_in;
@@ -142,17 +179,17 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
   }
   for (int t = threadIdx.x; t < P * NL; t += NT) {
     const int p = t % P, L = t / P;
-    const int64_t gp = pbase + p;
-    if (gp >= cg.npatch) continue;
+    const int org = s_org[p];
+    if (org < 0) continue;
     T v[m];
 #pragma unroll
     for (int c = 0; c < m; ++c) v[c] = last_in[(c * NL + L) * P + p];
-    int64_t row;
+    int row;
     if constexpr (DIM == 3) {
       const int zz = L / m, yy = L % m;
-      row = closure_origin(gp, cg, px, pz) + (zz + 1) * pz + (yy + 1) * px + 1;
+      row = org + (zz + 1) * pz + (yy + 1) * px + 1;
     } else {
-      row = closure_origin(gp, cg, px, pz) + (L + 1) * px + 1;
+      row = org + (L + 1) * px + 1;
     }
     T* dst = x + row;
 #pragma unroll
@@ -160,41 +197,52 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
       T acc = T(0);
 #pragma unroll
       for (int c = 0; c < m; ++c) acc = fma(tb.S[o * m + c], v[c], acc);
-      dst[o] = fma(scale, acc, dst[o]);
+      const T base = xs ? xs[(L * m + o) * P + p] : dst[o];
+      dst[o] = fma(scale, acc, base);
     }
   }
 }
 
 // ------------------------------------------------------- multiplicative
 template <typename T>
-__global__ void __launch_bounds__(SmoothCfg<T>::NT)
+__global__ void __launch_bounds__(SmoothCfg<T>::NT, SmoothCfg<T>::MINB)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
-                   int64_t px, int64_t pz, ColourGeom cg, T bscale) {
+                   int px, int pz, ColourGeom cg, T bscale) {
   using C = SmoothCfg<T>;
-  constexpr int P = C::P, NT = C::NT, S0 = C::S0;
+  constexpr int P = C::P, NT = C::NT, S0 = C::S0, MD = C::md;
   const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tM = reinterpret_cast<T*>(smem_raw);
   T* tA = tM + P * S0;
-  const int64_t pbase = (int64_t)blockIdx.x * P;
+  T* U = tA + P * S0;                       // 3D: U, W; 2D: R
+  T* bI = U + C::nU * P * C::sizeU;         // interior of b, interleaved [z][y][x][p]
+  T* xI = bI + P * MD;                      // interior of x, interleaved
+  int* s_org = reinterpret_cast<int*>(xI + P * MD);
+  load_origins<P>(s_org, cg, px, pz);
+  __syncthreads();
+  load_interior<T, P, NT>(b, s_org, bI, px, pz, bscale);
 
   if constexpr (DIM == 3) {
-    T* U = tA + P * S0;
     T* W = U + P * C::sizeU;
     // Stage 0: lines along z read straight from global memory into
     // registers; tM = M x, tA = A x along z (interior output rows only).
+    // The interior values of x are kept for the final update.
     for (int t = threadIdx.x; t < P * n * n; t += NT) {
       const int p = t / (n * n), L = t % (n * n);
       const int yy = L / n, xx = L % n;
-      const int64_t gp = pbase + p;
+      const int org = s_org[p];
       T v[n];
-      if (gp < cg.npatch) {
-        const T* src = x + closure_origin(gp, cg, px, pz) + yy * px + xx;
+      if (org >= 0) {
+        const T* src = x + org + yy * px + xx;
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c] = src[c * pz];
       } else {
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c] = T(0);
+      }
+      if (yy >= 1 && yy <= m && xx >= 1 && xx <= m) {
+#pragma unroll
+        for (int c = 1; c <= m; ++c) xI[(((c - 1) * m + yy - 1) * m + xx - 1) * P + p] = v[c];
       }
       T* dM = tM + p * S0 + L * m;
       T* dA = tA + p * S0 + L * m;
@@ -243,25 +291,15 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     T* R = tM;
     for (int t = threadIdx.x; t < P * NL2; t += NT) {
       const int p = t % P, L = t / P;
-      const int zz = L / m, yy = L % m;
-      const int64_t gp = pbase + p;
-      T vu[n], vw[n], bv[m];
+      T vu[n], vw[n];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
         vu[c] = U[(c * NL2 + L) * P + p];
         vw[c] = W[(c * NL2 + L) * P + p];
       }
-      if (gp < cg.npatch) {
-        const T* src = b + closure_origin(gp, cg, px, pz) + (zz + 1) * pz + (yy + 1) * px + 1;
-#pragma unroll
-        for (int o = 0; o < m; ++o) bv[o] = bscale * src[o];
-      } else {
-#pragma unroll
-        for (int o = 0; o < m; ++o) bv[o] = T(0);
-      }
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = bv[o];
+        T acc = bI[(L * m + o) * P + p];
 #pragma unroll
         for (int c = 0; c < n; ++c) {
           acc = fma(-tb.Ap[o * n + c], vu[c], acc);
@@ -278,20 +316,24 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     __syncthreads();
     fd_stage<T, P, NT, 1>(tM, tA, inv_lam);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(tA, tM, x, pbase, cg, px, pz, T(1));
+    fd_backward_and_update<T, P, NT>(tA, tM, x, xI, s_org, px, pz, T(1));
   } else {
     // 2D.  Stage 0: lines along y from global; tM = M x, tA = A x along y.
     for (int t = threadIdx.x; t < P * n; t += NT) {
       const int p = t / n, L = t % n;
-      const int64_t gp = pbase + p;
+      const int org = s_org[p];
       T v[n];
-      if (gp < cg.npatch) {
-        const T* src = x + closure_origin(gp, cg, px, pz) + L;
+      if (org >= 0) {
+        const T* src = x + org + L;
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c] = src[c * px];
       } else {
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c] = T(0);
+      }
+      if (L >= 1 && L <= m) {
+#pragma unroll
+        for (int c = 1; c <= m; ++c) xI[((c - 1) * m + L - 1) * P + p] = v[c];
       }
       T* dM = tM + p * S0 + L * m;
       T* dA = tA + p * S0 + L * m;
@@ -308,31 +350,21 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
     }
     __syncthreads();
-    // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior; the
-    // result goes to an interleaved buffer placed after tA.
-    T* R = tA + P * S0;
+    // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior.
+    T* R = U;
     for (int t = threadIdx.x; t < P * m; t += NT) {
       const int p = t % P, L = t / P;
-      const int64_t gp = pbase + p;
       const T* sM = tM + p * S0 + L;
       const T* sA = tA + p * S0 + L;
-      T vm[n], va[n], bv[m];
+      T vm[n], va[n];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
         vm[c] = sM[c * m];
         va[c] = sA[c * m];
       }
-      if (gp < cg.npatch) {
-        const T* src = b + closure_origin(gp, cg, px, pz) + (L + 1) * px + 1;
-#pragma unroll
-        for (int o = 0; o < m; ++o) bv[o] = bscale * src[o];
-      } else {
-#pragma unroll
-        for (int o = 0; o < m; ++o) bv[o] = T(0);
-      }
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = bv[o];
+        T acc = bI[(L * m + o) * P + p];
 #pragma unroll
         for (int c = 0; c < n; ++c) {
           acc = fma(-tb.Ap[o * n + c], vm[c], acc);
@@ -348,7 +380,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     __syncthreads();
     fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X0, X1, x, pbase, cg, px, pz, T(1));
+    fd_backward_and_update<T, P, NT>(X0, X1, x, xI, s_org, px, pz, T(1));
   }
 }
 
@@ -357,29 +389,30 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
 template <typename T>
 __global__ void __launch_bounds__(SmoothCfg<T>::NT)
 smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv_lam,
-                  int64_t px, int64_t pz, ColourGeom cg, T scale) {
+                  int px, int pz, ColourGeom cg, T scale) {
   using C = SmoothCfg<T>;
   constexpr int P = C::P, NT = C::NT, MD = C::md;
   const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X0 = reinterpret_cast<T*>(smem_raw);
   T* X1 = X0 + P * MD;
-  const int64_t pbase = (int64_t)blockIdx.x * P;
+  int* s_org = reinterpret_cast<int*>(X1 + P * MD);
+  load_origins<P>(s_org, cg, px, pz);
+  __syncthreads();
   constexpr int NL = DIM == 3 ? m * m : m;
   // first S^T contraction reads the interior residual lines from global
   for (int t = threadIdx.x; t < P * NL; t += NT) {
     const int p = t % P, L = t / P;
-    const int64_t gp = pbase + p;
+    const int org = s_org[p];
     T v[m];
-    if (gp < cg.npatch) {
-      const T* src;
+    if (org >= 0) {
       if constexpr (DIM == 3) {
         const int yy = L / m, xx = L % m;
-        src = r + closure_origin(gp, cg, px, pz) + pz + (yy + 1) * px + 1 + xx;
+        const T* src = r + org + pz + (yy + 1) * px + 1 + xx;
 #pragma unroll
         for (int c = 0; c < m; ++c) v[c] = src[c * pz];
       } else {
-        src = r + closure_origin(gp, cg, px, pz) + px + 1 + L;
+        const T* src = r + org + px + 1 + L;
 #pragma unroll
         for (int c = 0; c < m; ++c) v[c] = src[c * px];
       }
@@ -401,11 +434,11 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
     __syncthreads();
     fd_stage<T, P, NT, 1>(X0, X1, inv_lam);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X1, X0, x, pbase, cg, px, pz, scale);
+    fd_backward_and_update<T, P, NT>(X1, X0, x, nullptr, s_org, px, pz, scale);
   } else {
     fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X0, X1, x, pbase, cg, px, pz, scale);
+    fd_backward_and_update<T, P, NT>(X0, X1, x, nullptr, s_org, px, pz, scale);
   }
 }
 
@@ -417,8 +450,9 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
 // banded global 1D matrices (Section 2.3): z -> M, K; y -> M M, K M + M K;
 // x -> K (M M) + M (K M + M K).
 struct ApplyCfg {
-  static constexpr int CT = DIM == 3 ? (K == 1 ? 8 : K == 2 ? 4 : K == 3 ? 3 : K <= 5 ? 2 : 1)
-                                     : (32 + K - 1) / K;
+  // cells per tile: a power of two (see Apply3Cfg)
+  static constexpr int CT = DIM == 3 ? (K == 1 ? 8 : K == 2 ? 4 : K <= 5 ? 2 : 1)
+                                     : (K == 1 ? 32 : K == 2 ? 16 : K == 3 ? 16 : 8);
   static constexpr int TN = K * CT;
   static constexpr int BN = TN + 2 * K;
   static constexpr int RB = BN | 1;    // odd row stride
@@ -573,6 +607,128 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
           out = bvec ? bvec[rowi + gx] - scale * acc : scale * acc;
         y[rowi + gx] = out;
       }
+    }
+  }
+}
+
+// 3D operator on wide x-y tiles marching in z.  A block owns TX x TY output
+// columns (x, y) and a range of ZR planes.  For every plane it contracts z
+// (lines of the band read from global memory, cached in L1 across planes)
+// over the tile plus a halo of K in x and y, then y over the tile plus the x
+// halo, then x; the z-contraction planes are double-buffered so each plane
+// costs two barriers.  Halo recomputation: ((T+2K)/T)^2 in the z stage and
+// (T+2K)/T in the y stage, against ((T+2K)/T)^2 and (T+2K)/T with T = K*CT
+// small for cubic tiles.
+struct Apply3Cfg {
+  // cells per tile in x and y: a power of two, so that tiles of TX nodes
+  // cover the nodes 0 .. n1-2 = k 2^l - 1 exactly (no ragged tiles)
+  static constexpr int CX = K == 1 ? 32 : (K == 2 ? 16 : 8);
+  static constexpr int TX = K * CX;
+  static constexpr int BX = TX + 2 * K;
+  static constexpr int RB = BX | 1;
+  static constexpr int ZC = K >= 4 ? 2 : (K == 1 ? 8 : 4);  // cells per block in z
+  static constexpr int ZR = ZC * K;                          // planes per block
+  // threads: one y-stage unit each (BX * CX units), so that stage is one
+  // round; the z and x stages then take about K+2 and one round
+  static constexpr int UB = BX * CX;
+  static constexpr int NT0 = ((UB + 31) / 32) * 32;
+  static constexpr int NT = NT0 > 1024 ? ((UB / 2 + 31) / 32) * 32 : (NT0 < 256 ? 256 : NT0);
+  static constexpr int MINB = (NT <= 512 && K <= 5) ? 2 : 1;
+  template <typename T>
+  static constexpr size_t smem() { return sizeof(T) * (size_t)(4 * BX * RB + 2 * TX * RB); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
+apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
+              int px, int pz, T scale) {
+  using C = Apply3Cfg;
+  constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
+  const DevTab<T>& tb = c_tab<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* zbuf = reinterpret_cast<T*>(smem_raw);  // [2][2][BX][RB]: (m, k) x double buffer
+  T* MM = zbuf + 4 * BX * RB;                // [TX][RB]
+  T* WW = MM + TX * RB;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  const int z0 = blockIdx.z * C::ZR;         // a multiple of K
+  int buf = 0;
+  for (int cz = 0; cz < C::ZC; ++cz) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int z = z0 + cz * K + q;
+      if (z >= n1 - 1) break;  // uniform in the block; plane n1-1 is zeroed elsewhere
+      T* mZ = zbuf + (2 * buf) * BX * RB;
+      T* kZ = mZ + BX * RB;
+      // z contraction of plane z over the halo'd tile
+      for (int u = threadIdx.x; u < BX * BX; u += NT) {
+        const int xx = u % BX, yy = u / BX;
+        const int gx = x0 - K + xx, gy = y0 - K + yy;
+        T am = T(0), ak = T(0);
+        if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
+          const T* col = x + gy * px + gx;
+          VPS_BAND_LOOP(q, j) {
+            const int gz = z - K + j;
+            const T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
+            am = fma(tb.Mb[q * n + j], v, am);
+            ak = fma(tb.Kb[q * n + j], v, ak);
+          }
+        }
+        mZ[yy * RB + xx] = am;
+        kZ[yy * RB + xx] = ak;
+      }
+      __syncthreads();
+      // y contraction: units (x over the halo, cell segment in y)
+      for (int u = threadIdx.x; u < BX * CX; u += NT) {
+        const int xx = u % BX, cy = u / BX;
+        T vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = mZ[(cy * K + i) * RB + xx];
+          vk[i] = kZ[(cy * K + i) * RB + xx];
+        }
+#pragma unroll
+        for (int qy = 0; qy < K; ++qy) {
+          T a = T(0), bb = T(0);
+          VPS_BAND_LOOP(qy, j) {
+            a = fma(tb.Mb[qy * n + j], vm[qy + j], a);
+            bb = fma(tb.Kb[qy * n + j], vm[qy + j], bb);
+            bb = fma(tb.Mb[qy * n + j], vk[qy + j], bb);
+          }
+          MM[(cy * K + qy) * RB + xx] = a;
+          WW[(cy * K + qy) * RB + xx] = bb;
+        }
+      }
+      __syncthreads();
+      // x contraction and store: units (y fastest, cell segment in x)
+      const bool inner_z = z >= 1 && z <= n1 - 2;
+      for (int u = threadIdx.x; u < TX * CX; u += NT) {
+        const int Y = u % TX, cx = u / TX;
+        const int gy = y0 + Y;
+        if (gy >= n1) continue;
+        T vm[2 * K + 1], vw[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = MM[Y * RB + cx * K + i];
+          vw[i] = WW[Y * RB + cx * K + i];
+        }
+        const bool inner_yz = inner_z && gy >= 1 && gy <= n1 - 2;
+        const int rowi = z * pz + gy * px;
+#pragma unroll
+        for (int qx = 0; qx < K; ++qx) {
+          const int gx = x0 + cx * K + qx;
+          if (gx >= n1) continue;
+          T acc = T(0);
+          VPS_BAND_LOOP(qx, j) {
+            acc = fma(tb.Kb[qx * n + j], vm[qx + j], acc);
+            acc = fma(tb.Mb[qx * n + j], vw[qx + j], acc);
+          }
+          T out = T(0);
+          if (inner_yz && gx >= 1 && gx <= n1 - 2)
+            out = bvec ? bvec[rowi + gx] - scale * acc : scale * acc;
+          y[rowi + gx] = out;
+        }
+      }
+      buf ^= 1;
     }
   }
 }
@@ -853,8 +1009,8 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_mult_kernel<T><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, g.px, g.pz, cg,
-                                                                     bscale);
+  smooth_mult_kernel<T><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, (int)g.px,
+                                                                     (int)g.pz, cg, bscale);
   return cudaGetLastError();
 }
 
@@ -866,18 +1022,33 @@ cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T*
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T sc = DIM == 3 ? T(scale / g.h) : scale;
   VPS_COUNT_LAUNCH();
-  smooth_add_kernel<T><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, g.px, g.pz, cg, sc);
+  smooth_add_kernel<T><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, (int)g.px,
+                                                                   (int)g.pz, cg, sc);
   return cudaGetLastError();
 }
 
+// Tiles cover the nodes 0 .. n1-2 of every direction; the upper boundary
+// layer (index n1-1) is zeroed by a second, small kernel.
 template <typename T>
 cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
-  using C = ApplyCfg;
-  const unsigned t = (unsigned)((g.n1 + C::TN - 1) / C::TN);
-  dim3 grid(t, t, DIM == 3 ? t : 1);
-  const T scale = DIM == 3 ? T(g.h) : T(1);
+  const int span = g.n1 - 1;
+  if constexpr (DIM == 3) {
+    using C3 = Apply3Cfg;
+    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
+    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    VPS_COUNT_LAUNCH();
+    apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
+                                                                   (int)g.pz, T(g.h));
+  } else {
+    using C = ApplyCfg;
+    const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
+    VPS_COUNT_LAUNCH();
+    apply_kernel<T><<<dim3(t, t, 1), C::NT, C::smem<T>(), s>>>(x, b, y, g.n1, g.px, g.pz, T(1));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   VPS_COUNT_LAUNCH();
-  apply_kernel<T><<<grid, C::NT, C::smem<T>(), s>>>(x, b, y, g.n1, g.px, g.pz, scale);
+  zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
   return cudaGetLastError();
 }
 
@@ -921,6 +1092,11 @@ cudaError_t set_smem_limits() {
   e = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ApplyCfg::smem<T>());
   if (e != cudaSuccess) return e;
+  if constexpr (DIM == 3) {
+    e = cudaFuncSetAttribute(apply3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Apply3Cfg::smem<T>());
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(prolong_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)TransferCfg::smem_prolong<T>());
   if (e != cudaSuccess) return e;

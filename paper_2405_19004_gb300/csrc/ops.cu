@@ -240,7 +240,63 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
   }
 }
 
+template <typename T, int MODE>
+__global__ void fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                      const T* __restrict__ S, const T* __restrict__ inv, int ni,
+                                      int dim, int in_lev, int out_lev, int px, int pz) {
+  const int NL = dim == 3 ? ni * ni : ni;
+  const int total = NL * ni;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int o = e % ni, L = e / ni;
+    // L splits into (slow, fast) = (a, b) of the two remaining indices
+    const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
+    T acc = T(0);
+    for (int c = 0; c < ni; ++c) {
+      T v;
+      if (in_lev)
+        v = dim == 3 ? in[(c + 1) * pz + (a + 1) * px + bb + 1] : in[(c + 1) * px + bb + 1];
+      else
+        v = in[c * NL + L];
+      const T w = MODE == 2 ? S[o * ni + c] : S[c * ni + o];
+      acc = fma(w, v, acc);
+    }
+    if (MODE == 1) acc *= inv[L * ni + o];
+    if (out_lev) {
+      if (dim == 3) out[(a + 1) * pz + (bb + 1) * px + o + 1] = acc;
+      else out[(L + 1) * px + o + 1] = acc;
+    } else {
+      out[L * ni + o] = acc;
+    }
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* S, const T* inv, int ni,
+                                  int dim, bool in_lev, bool out_lev, int px, int pz,
+                                  cudaStream_t s) {
+  const int64_t total = (int64_t)ni * ni * (dim == 3 ? ni : 1);
+  const unsigned grid = grid_for(total);
+  VPS_COUNT_LAUNCH();
+  if (mode == 0)
+    fd_global_pass_kernel<T, 0><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
+                                                          px, pz);
+  else if (mode == 1)
+    fd_global_pass_kernel<T, 1><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
+                                                          px, pz);
+  else
+    fd_global_pass_kernel<T, 2><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
+                                                          px, pz);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fd_global_pass<float>(int, const float*, float*, const float*,
+                                                  const float*, int, int, bool, bool, int, int,
+                                                  cudaStream_t);
+template cudaError_t launch_fd_global_pass<double>(int, const double*, double*, const double*,
+                                                   const double*, int, int, bool, bool, int, int,
+                                                   cudaStream_t);
 
 template <typename T>
 cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s) {

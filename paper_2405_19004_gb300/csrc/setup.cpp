@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "vps_internal.h"
 
@@ -258,6 +259,79 @@ bool build_tables(int k, HostTables* T, char* err, size_t errlen) {
     double xi = 0.5 * (fc + T->z[j]);
     lagrange_eval(k, T->z, xi, val);
     for (int i = 0; i <= k; ++i) T->P1[s * nl + i] = val[i];
+  }
+  return true;
+}
+
+bool build_global_fd(int k, int level, std::vector<double>* S, std::vector<double>* lam, char* err,
+                     size_t errlen) {
+  const int ncell = 1 << level, n1 = k * ncell + 1, ni = n1 - 2, nl = k + 1;
+  if (ni < 1 || ni > kMaxGlobalFd) {
+    std::snprintf(err, errlen, "global fast diagonalisation needs 1..%d interior nodes (got %d)",
+                  kMaxGlobalFd, ni);
+    return false;
+  }
+  HostTables t;
+  if (!build_tables(k, &t, err, errlen)) return false;
+  // global 1D matrices of the level in reference units (cell size 1), interior block
+  std::vector<double> Kg((size_t)n1 * n1, 0.0), Mg((size_t)n1 * n1, 0.0);
+  for (int c = 0; c < ncell; ++c)
+    for (int i = 0; i < nl; ++i)
+      for (int j = 0; j < nl; ++j) {
+        Kg[(size_t)(c * k + i) * n1 + c * k + j] += t.Khat[i * nl + j];
+        Mg[(size_t)(c * k + i) * n1 + c * k + j] += t.Mhat[i * nl + j];
+      }
+  std::vector<double> A((size_t)ni * ni), M((size_t)ni * ni), L((size_t)ni * ni),
+      tmp((size_t)ni * ni), C((size_t)ni * ni), Q((size_t)ni * ni);
+  for (int i = 0; i < ni; ++i)
+    for (int j = 0; j < ni; ++j) {
+      A[(size_t)i * ni + j] = Kg[(size_t)(i + 1) * n1 + j + 1];
+      M[(size_t)i * ni + j] = Mg[(size_t)(i + 1) * n1 + j + 1];
+    }
+  if (!cholesky(ni, M.data(), L.data())) {
+    std::snprintf(err, errlen, "global mass matrix not positive definite");
+    return false;
+  }
+  for (int col = 0; col < ni; ++col)
+    for (int i = 0; i < ni; ++i) {
+      double sacc = A[(size_t)i * ni + col];
+      for (int q = 0; q < i; ++q) sacc -= L[(size_t)i * ni + q] * tmp[(size_t)q * ni + col];
+      tmp[(size_t)i * ni + col] = sacc / L[(size_t)i * ni + i];
+    }
+  for (int row = 0; row < ni; ++row)
+    for (int i = 0; i < ni; ++i) {
+      double sacc = tmp[(size_t)row * ni + i];
+      for (int q = 0; q < i; ++q) sacc -= L[(size_t)i * ni + q] * C[(size_t)row * ni + q];
+      C[(size_t)row * ni + i] = sacc / L[(size_t)i * ni + i];
+    }
+  for (int i = 0; i < ni; ++i)
+    for (int j = i + 1; j < ni; ++j)
+      C[(size_t)i * ni + j] = C[(size_t)j * ni + i] =
+          0.5 * (C[(size_t)i * ni + j] + C[(size_t)j * ni + i]);
+  lam->assign(ni, 0.0);
+  S->assign((size_t)ni * ni, 0.0);
+  jacobi_eigen(ni, C.data(), Q.data(), lam->data());
+  for (int col = 0; col < ni; ++col)
+    for (int i = ni - 1; i >= 0; --i) {
+      double sacc = Q[(size_t)i * ni + col];
+      for (int q = i + 1; q < ni; ++q) sacc -= L[(size_t)q * ni + i] * (*S)[(size_t)q * ni + col];
+      (*S)[(size_t)i * ni + col] = sacc / L[(size_t)i * ni + i];
+    }
+  // self-check S^T M S = I
+  double worst = 0.0;
+  for (int i = 0; i < ni; ++i)
+    for (int j = 0; j < ni; ++j) {
+      double v = 0.0;
+      for (int a = 0; a < ni; ++a) {
+        double ma = 0.0;
+        for (int b2 = 0; b2 < ni; ++b2) ma += M[(size_t)a * ni + b2] * (*S)[(size_t)b2 * ni + j];
+        v += (*S)[(size_t)a * ni + i] * ma;
+      }
+      worst = std::fmax(worst, std::fabs(v - (i == j)));
+    }
+  if (!(worst < 1e-9) || !((*lam)[0] > 0.0)) {
+    std::snprintf(err, errlen, "global eigen-decomposition self-check failed (%.3g)", worst);
+    return false;
   }
   return true;
 }

@@ -8,6 +8,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace vps {
@@ -44,6 +45,15 @@ struct HostTables {
 
 // Computes every table for degree k (1..kMaxK). Returns false on failure.
 bool build_tables(int k, HostTables* t, char* err, size_t errlen);
+
+// Generalised eigenpairs of the global interior 1D stiffness and mass
+// matrices of a whole level (reference cell size 1): K S = M S diag(lam),
+// S^T M S = I, S row-major ni x ni (ni = k 2^level - 1 <= kMaxGlobalFd).
+// The level operator is a Kronecker sum of these (Eq. 2.11/2.12 for the
+// whole mesh), so the same fast diagonalisation inverts it exactly.
+constexpr int kMaxGlobalFd = 255;
+bool build_global_fd(int k, int level, std::vector<double>* S, std::vector<double>* lam,
+                     char* err, size_t errlen);
 
 // Gauss-Legendre rule on [0,1] with q points (q <= 16).
 void gauss_rule(int q, double* x, double* w);
@@ -147,6 +157,15 @@ cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s
 cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s);
+
+// One pass of the global fast diagonalisation of a level (runtime ni):
+// out[L][o] = sum_c W(c, o) in[c][L] with W = S (MODE 0: S^T, MODE 1: S^T
+// then * inv[L*ni+o], MODE 2: S).  in_lev / out_lev: read / write the
+// interior of a level-layout vector instead of a compact tensor.
+template <typename T>
+cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* S, const T* inv, int ni,
+                                  int dim, bool in_lev, bool out_lev, int px, int pz,
+                                  cudaStream_t s);
 
 // b (compact, double) = sum_m coef_m prod_t b1d[m][t][node_t]  with b1d on device
 cudaError_t launch_rhs_tensor(const LevelGeom& g, int n_modes, const double* b1d, double* b,

@@ -106,17 +106,39 @@ def test_transfers_match_oracle(d, k, l, prec):
     assert rr[n1c - 1] == 0.0 and rr[pxc * (n1c - 1) + 1] == 0.0
 
 
+@pytest.mark.parametrize("coarse", [1, 0])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("d,k,L,sm,om", [(2, 2, 4, 0, 1.0), (2, 3, 3, 1, 0.35), (3, 2, 3, 0, 1.0),
-                                         (3, 3, 2, 1, 0.175), (2, 1, 4, 0, 1.0)])
-def test_vcycle_matches_oracle(d, k, L, sm, om, prec):
-    H = multigrid.Hierarchy(d, k, L, smoother="additive" if sm else "multiplicative", omega=om)
+                                         (3, 3, 2, 1, 0.175), (2, 1, 5, 0, 1.0), (3, 1, 4, 0, 1.0)])
+def test_vcycle_matches_oracle(d, k, L, sm, om, prec, coarse):
     P = _poisson(d, k, L, prec, sm, om)
+    if coarse:
+        P.vps_set_coarse_level(coarse)
+    H = multigrid.Hierarchy(d, k, L, smoother="additive" if sm else "multiplicative", omega=om,
+                            coarse_level=P.vps_get_coarse_level())
     b = as_prec(normal_vector(H.levels[L].N, 9), prec)
     x = P.empty_level(L)
     P.vps_vcycle(to_dev(P, b, L), x)
     tol = 1e-11 if prec == 0 else 1e-5
     assert rel_err(to_host(P, x, L), H.vcycle(L, b)) <= tol
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 3, 4), (3, 2, 3), (2, 7, 2), (3, 5, 2)])
+def test_coarse_level_equal_to_finest_makes_the_vcycle_exact(d, k, L):
+    """Global fast diagonalisation of a whole level is its exact inverse."""
+    import scipy.sparse.linalg as spla
+    lv, A, _ = oracle_level(d, k, L)
+    P = _poisson(d, k, L, 0)
+    P.vps_set_coarse_level(L)
+    b = normal_vector(lv.N, 15)
+    x = P.empty_level(L)
+    P.vps_vcycle(to_dev(P, b, L), x)
+    assert rel_err(to_host(P, x, L), spla.spsolve(A.tocsc(), b)) <= 1e-11
+
+
+def test_default_coarse_level_rule():
+    for d, k, L, want in [(3, 4, 5, 3), (2, 2, 4, 3), (3, 1, 6, 5), (3, 7, 4, 2), (2, 5, 1, 1)]:
+        assert _poisson(d, k, L, 1).vps_get_coarse_level() == want
 
 
 @pytest.mark.parametrize("d,k", [(2, 2), (3, 3), (2, 7)])
@@ -135,11 +157,12 @@ def test_level_one_vcycle_is_exact_solve(d, k):
                                          (3, 3, 3, 0, 1.0)])
 def test_solve_matches_oracle(d, k, L, sm, om, prec):
     import torch
-    H = multigrid.Hierarchy(d, k, L, smoother="additive" if sm else "multiplicative", omega=om)
+    P = _poisson(d, k, L, prec, sm, om)
+    H = multigrid.Hierarchy(d, k, L, smoother="additive" if sm else "multiplicative", omega=om,
+                            coarse_level=P.vps_get_coarse_level())
     A = H.A[L]
     b = uniform_vector(H.levels[L].N, 11)
     xo, ito, relo = multigrid.pcg(A, b, H.precondition, rtol=1e-10, max_it=100)
-    P = _poisson(d, k, L, prec, sm, om)
     bt = torch.as_tensor(b, device="cuda")
     xt = torch.zeros_like(bt)
     it, rel = P.vps_solve(bt, xt, 1e-10, 100)
