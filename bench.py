@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64 / additive side measurements")
+    p.add_argument("--tune-cache", default=None,
+                   help="autotuner cache file (reused when it holds this workload)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--repeats", type=int, default=CPU_SAMPLE_REPEATS, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -207,6 +209,9 @@ def main():
     from synthetic import uniform_vector
 
     P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
+    P.vps_autotune(args.tune_cache)  # timed trials on this GPU, before the timed region
+    tuned = {"coarse_level": P.vps_get_coarse_level(),
+             "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)]}
     N = P.n_interior()
     b = torch.as_tensor(uniform_vector(N, 1 + rank), device="cuda")
     x = torch.zeros_like(b)
@@ -301,6 +306,7 @@ def main():
     if not args.no_extras and rank == 0:
         # FP64 V-cycle solve (time to 1e-10 in double precision)
         P64 = vps.Poisson(D, K, L, precision=vps.VPS_FP64)
+        P64.vps_autotune(args.tune_cache)
         x64 = torch.zeros_like(b)
         P64.vps_solve(b, x64, RTOL, 100)
         t64 = []
@@ -357,7 +363,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+        "data": "synthetic",
+        "config": config({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                          "autotuned": tuned}),
         "iterations": its[-1], "rel_residual": rel,
         "smoother_fp32": {"dof_per_s": N / t_smooth_step, "tflops": achieved,
                           "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS},

@@ -191,6 +191,22 @@ int vps_l2_error_sine(vps_handle h, const double* x, double* err);
 int vps_set_coarse_level(vps_handle h, int level);
 int vps_get_coarse_level(vps_handle h, int* level);
 
+/*
+ * vps_autotune -- choose, by timed trials on this handle's own buffers, the
+ * smoother variant of every level (patches per thread block, the tuning
+ * axis of Section 3.1.2) and the coarsest level (vps_set_coarse_level) that
+ * give the fastest CG solve.  cache_path (may be NULL): a JSON file keyed by
+ * (dim, degree, precision, smoother, level, smoothing steps); an entry found
+ * there is applied without timing (*from_cache = 1), otherwise the result is
+ * written to it.  Synchronous; runs solves on the handle's stream.
+ */
+int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
+
+/* vps_set_smooth_variant / vps_get_smooth_variant -- the smoother variant
+ * (0..2) of `level` (0: every level), and its patches per thread block. */
+int vps_set_smooth_variant(vps_handle h, int level, int variant);
+int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_per_block);
+
 /* vps_kernel_launches -- number of kernels the handle has launched since
  * creation (direct launches plus, for every replay of a captured graph, the
  * kernels the graph holds).  Instrumentation for benchmarks. */

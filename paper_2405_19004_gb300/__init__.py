@@ -51,6 +51,9 @@ SIGNATURES = {
     "vps_set_graphs": (_i, [_p, _i]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
     "vps_set_coarse_level": (_i, [_p, _i]),
+    "vps_autotune": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i)]),
+    "vps_set_smooth_variant": (_i, [_p, _i, _i]),
+    "vps_get_smooth_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
@@ -235,6 +238,23 @@ class Poisson:
         err = ctypes.c_double()
         self._call(lib().vps_l2_error_sine, _ptr(x), ctypes.byref(err))
         return err.value
+
+    def vps_autotune(self, cache_path=None):
+        """Tune smoother variants and the coarsest level; returns True if the
+        settings came from the cache file."""
+        fc = ctypes.c_int()
+        path = cache_path.encode() if cache_path else None
+        self._call(lib().vps_autotune, path, ctypes.byref(fc))
+        return bool(fc.value)
+
+    def vps_set_smooth_variant(self, level, variant):
+        self._call(lib().vps_set_smooth_variant, int(level), int(variant))
+
+    def vps_get_smooth_variant(self, level):
+        v, p = ctypes.c_int(), ctypes.c_int()
+        _check(lib().vps_get_smooth_variant(self.h, int(level), ctypes.byref(v), ctypes.byref(p)),
+               self.h)
+        return v.value, p.value
 
     def vps_set_coarse_level(self, level):
         self._call(lib().vps_set_coarse_level, int(level))

@@ -109,6 +109,7 @@ struct vps_context {
   cudaGraphExec_t prec_graph = nullptr;
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
+  int smooth_var[kMaxLevels + 1] = {};  // smoother variant per level (index into the table)
   // exact coarse solve on level `coarse` by global fast diagonalisation
   int coarse = 1;
   int gni = 0;                          // interior nodes per direction on that level
@@ -189,15 +190,17 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   const LevelGeom& g = h->geom[l];
   const int nc = 1 << h->dim;
   const T* il = static_cast<const T*>(h->inv_lam);
+  const int v = h->smooth_var[l];
   if (h->smoother == VPS_ADDITIVE) {
     T* r = static_cast<T*>(h->rv[l]);
     VPS_CK(h, fns<T>(h).apply(g, x, b, r, h->stream));
     for (int c = 0; c < nc; ++c)
-      VPS_CK(h, fns<T>(h).smooth_add(g, make_colour(g, c), r, x, il, (T)h->damping, h->stream));
+      VPS_CK(h, fns<T>(h).smooth_add_v[v](g, make_colour(g, c), r, x, il, (T)h->damping,
+                                          h->stream));
   } else {
     for (int i = 0; i < nc; ++i) {
       const int c = forward ? i : nc - 1 - i;
-      VPS_CK(h, fns<T>(h).smooth_mult(g, make_colour(g, c), b, x, il, h->stream));
+      VPS_CK(h, fns<T>(h).smooth_mult_v[v](g, make_colour(g, c), b, x, il, h->stream));
     }
   }
   return VPS_OK;
@@ -416,6 +419,112 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
 
 }  // namespace
 
+namespace {
+
+bool variant_ok(vps_context* h, int v) {
+  if (v < 0 || v >= kSmoothVariants) return false;
+  return h->prec == VPS_FP64 ? (h->smoother == VPS_ADDITIVE ? h->ks->d.smooth_add_v[v] != nullptr
+                                                            : h->ks->d.smooth_mult_v[v] != nullptr)
+                             : (h->smoother == VPS_ADDITIVE ? h->ks->f.smooth_add_v[v] != nullptr
+                                                            : h->ks->f.smooth_mult_v[v] != nullptr);
+}
+
+// Mean time (ms) of `reps` calls of fn on the handle's stream.
+template <typename F>
+int time_ms(vps_context* h, int reps, F fn, float* ms) {
+  cudaEvent_t a, b;
+  VPS_CK(h, cudaEventCreate(&a));
+  VPS_CK(h, cudaEventCreate(&b));
+  int rc = fn();  // warm-up
+  if (!rc) {
+    cudaEventRecord(a, h->stream);
+    for (int i = 0; i < reps && !rc; ++i) rc = fn();
+    cudaEventRecord(b, h->stream);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    *ms /= reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+std::string tune_key(vps_context* h) {
+  char key[96];
+  std::snprintf(key, sizeof(key), "d%d_k%d_%s_%s_L%d_pre%d_post%d", h->dim, h->k,
+                h->prec == VPS_FP64 ? "fp64" : "fp32",
+                h->smoother == VPS_ADDITIVE ? "add" : "mult", h->L, h->n_pre, h->n_post);
+  return key;
+}
+
+// Cache file: one JSON object, one entry per line:
+//   "d3_k4_fp32_mult_L5_pre1_post1": {"coarse": 3, "variants": [1, 1, 2, 0, 1]},
+bool cache_lookup(const char* path, const std::string& key, int* coarse, int* var, int nvar) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  const std::string pat = "\"" + key + "\"";
+  while (std::fgets(line, sizeof(line), f)) {
+    const char* p = std::strstr(line, pat.c_str());
+    if (!p) continue;
+    const char* c = std::strstr(p, "\"coarse\":");
+    const char* v = std::strstr(p, "\"variants\": [");
+    if (!c || !v) continue;
+    *coarse = std::atoi(c + 9);
+    v += 13;
+    int i = 0;
+    while (i < nvar && *v && *v != ']') {
+      while (*v == ' ' || *v == ',') ++v;
+      if (*v == ']' || !*v) break;
+      var[i++] = std::atoi(v);
+      while (*v && *v != ',' && *v != ']') ++v;
+    }
+    found = i == nvar;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, int coarse, const int* var, int nvar) {
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path, "r")) {
+    char line[1024];
+    const std::string pat = "\"" + key + "\"";
+    while (std::fgets(line, sizeof(line), f)) {
+      std::string sline(line);
+      if (sline.find("\": {\"coarse\":") == std::string::npos) continue;
+      if (sline.find(pat) != std::string::npos) continue;
+      while (!sline.empty() && (sline.back() == '\n' || sline.back() == ',')) sline.pop_back();
+      keep.push_back(sline);
+    }
+    std::fclose(f);
+  }
+  std::string entry = "\"" + key + "\": {\"coarse\": " + std::to_string(coarse) + ", \"variants\": [";
+  for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(var[i]);
+  entry += "]}";
+  keep.push_back(entry);
+  if (FILE* f = std::fopen(path, "w")) {
+    std::fputs("{\n", f);
+    for (size_t i = 0; i < keep.size(); ++i)
+      std::fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    std::fputs("}\n", f);
+    std::fclose(f);
+  }
+}
+
+// One CG solve of a smooth right-hand side on the handle's buffers (timing
+// trials of the autotuner).
+int trial_solve(vps_context* h) {
+  const LevelGeom& g = h->geom[h->L];
+  VPS_CK(h, launch_pack<double>(g, h->comp_b, h->cb, h->stream));
+  int it = 0;
+  double rel = 0;
+  return cg_solve(h, 1e-10, 200, &it, &rel);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* vps_status_string(int s) {
@@ -503,6 +612,7 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   }
   int rc;
   for (int l = 1; l <= level; ++l) {
+    h->smooth_var[l] = 1;
     h->geom[l] = make_geom(dim, degree, l);
     const size_t vb = (size_t)h->geom[l].total * h->esz;
     if ((rc = dalloc(h, &h->bv[l], vb)) || (rc = dalloc(h, &h->xv[l], vb)) ||
@@ -646,12 +756,13 @@ int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* 
   if (int rc = set_device(h)) return rc;
   LaunchTally tally(h);
   const LevelGeom& g = h->geom[level];
+  const int v = h->smooth_var[level];
   if (h->prec == VPS_FP64)
-    VPS_CK(h, h->ks->d.smooth_mult(g, make_colour(g, colour), (const double*)b, (double*)x,
-                                   (const double*)h->inv_lam, h->stream));
+    VPS_CK(h, h->ks->d.smooth_mult_v[v](g, make_colour(g, colour), (const double*)b, (double*)x,
+                                        (const double*)h->inv_lam, h->stream));
   else
-    VPS_CK(h, h->ks->f.smooth_mult(g, make_colour(g, colour), (const float*)b, (float*)x,
-                                   (const float*)h->inv_lam, h->stream));
+    VPS_CK(h, h->ks->f.smooth_mult_v[v](g, make_colour(g, colour), (const float*)b, (float*)x,
+                                        (const float*)h->inv_lam, h->stream));
   return VPS_OK;
 }
 
@@ -805,6 +916,115 @@ int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
                             h->stream));
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   *err = std::sqrt(h->host_dots[0]);
+  return VPS_OK;
+}
+
+int vps_set_smooth_variant(vps_handle h, int level, int variant) {
+  if (!h) return VPS_EINVAL;
+  if (!variant_ok(h, variant)) return fail(h, VPS_EINVAL, "smoother variant %d unavailable", variant);
+  if (level != 0)
+    if (int rc = check_level(h, level, 1)) return rc;
+  for (int l = 1; l <= h->L; ++l)
+    if (level == 0 || l == level) h->smooth_var[l] = variant;
+  if (h->prec_graph) {
+    cudaGraphExecDestroy(h->prec_graph);
+    h->prec_graph = nullptr;
+  }
+  return VPS_OK;
+}
+
+int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_per_block) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  const int v = h->smooth_var[level];
+  if (variant) *variant = v;
+  if (patches_per_block)
+    *patches_per_block = h->prec == VPS_FP64 ? h->ks->d.variant_p[v] : h->ks->f.variant_p[v];
+  return VPS_OK;
+}
+
+int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  const std::string key = tune_key(h);
+  int var[kMaxLevels + 1] = {};
+  int coarse = 0;
+  if (from_cache) *from_cache = 0;
+  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, h->L)) {
+    bool ok = coarse >= 1 && coarse <= h->L;
+    for (int l = 1; l <= h->L; ++l) ok = ok && variant_ok(h, var[l]);
+    if (ok) {
+      for (int l = 1; l <= h->L; ++l) h->smooth_var[l] = var[l];
+      if (coarse != h->coarse)
+        if (int rc = setup_coarse(h, coarse)) return rc;
+      if (h->prec_graph) {
+        cudaGraphExecDestroy(h->prec_graph);
+        h->prec_graph = nullptr;
+      }
+      if (from_cache) *from_cache = 1;
+      return VPS_OK;
+    }
+  }
+  // 1) smoother variant per level: fastest smoothing step on the level's buffers
+  for (int l = 2; l <= h->L; ++l) {
+    float best = 1e30f;
+    int bestv = h->smooth_var[l];
+    for (int v = 0; v < kSmoothVariants; ++v) {
+      if (!variant_ok(h, v)) continue;
+      h->smooth_var[l] = v;
+      float ms = 0.f;
+      int rc = h->prec == VPS_FP64
+                   ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
+                                                                    (double*)h->xv[l], true); }, &ms)
+                   : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
+                                                                   (float*)h->xv[l], true); }, &ms);
+      if (rc) return rc;
+      if (ms < best * 0.98f) {  // prefer the earlier (smaller) variant on near ties
+        best = ms;
+        bestv = v;
+      }
+    }
+    h->smooth_var[l] = bestv;
+  }
+  // 2) coarsest level: fastest full CG solve of a smooth right-hand side
+  {
+    const LevelGeom& g = h->geom[h->L];
+    const int ni = g.n1 - 2;
+    std::vector<double> b1d((size_t)h->dim * ni);
+    for (int t = 0; t < h->dim; ++t)
+      for (int j = 0; j < ni; ++j) b1d[(size_t)t * ni + j] = std::sin(M_PI * (j + 1.0) / (ni + 1.0));
+    const size_t need = b1d.size() * sizeof(double);
+    if (need > h->rhs_cap) {
+      if (h->rhs_buf) cudaFree(h->rhs_buf);
+      h->rhs_buf = nullptr;
+      h->rhs_cap = 0;
+      VPS_CK(h, cudaMalloc(&h->rhs_buf, need));
+      h->rhs_cap = need;
+    }
+    VPS_CK(h, cudaMemcpy(h->rhs_buf, b1d.data(), need, cudaMemcpyHostToDevice));
+    VPS_CK(h, launch_rhs_tensor(g, 1, h->rhs_buf, h->comp_b, h->stream));
+    float best = 1e30f;
+    int bestc = h->coarse;
+    for (int c = 1; c <= h->L - 1 || c == 1; ++c) {
+      if (h->k * (1 << c) - 1 > 64) break;  // the global solve grows as ni^(d+1)
+      if (int rc = setup_coarse(h, c)) return rc;
+      float ms = 0.f;
+      int rc = time_ms(h, 2, [&] { return trial_solve(h); }, &ms);
+      if (rc == VPS_ENOCONV || rc == VPS_EBREAKDOWN) ms = 1e30f;  // not a usable candidate
+      else if (rc) return rc;
+      if (ms < best * 0.98f) {
+        best = ms;
+        bestc = c;
+      }
+      if (c >= h->L) break;
+    }
+    if (int rc = setup_coarse(h, bestc)) return rc;
+  }
+  if (cache_path) {
+    for (int l = 1; l <= h->L; ++l) var[l] = h->smooth_var[l];
+    cache_store(cache_path, key, h->coarse, var + 1, h->L);
+  }
   return VPS_OK;
 }
 

@@ -63,14 +63,18 @@ template <typename T>
 __constant__ DevTab<T> c_tab;
 
 // ---------------------------------------------------------------- config
-template <typename T>
+// Patches per block of the middle smoother variant (a power of two).
+constexpr int kPBase = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 8 : K == 3 ? 4 : K <= 5 ? 2 : 1)
+                                : (K <= 3 ? 32 : 16);
+// The autotuner chooses among P = kPBase/2, kPBase, 2 kPBase.
+constexpr int kVarP[kSmoothVariants] = {kPBase / 2 > 0 ? kPBase / 2 : 1, kPBase, 2 * kPBase};
+
+template <typename T, int P_>
 struct SmoothCfg {
-  // patches per block (power of two) and threads per block
-  static constexpr int P = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 8 : K == 3 ? 4 : K <= 5 ? 2 : 1)
-                                    : (K <= 3 ? 32 : 16);
+  static constexpr int P = P_;   // patches per block (power of two)
   static constexpr int lines0 = DIM == 3 ? n * n : n;
   static constexpr int NT0 = ((P * lines0 + 31) / 32) * 32;
-  static constexpr int NT = NT0 > 256 ? 256 : NT0;
+  static constexpr int NT = NT0 > 512 ? 512 : NT0;
   // blocks per SM the register allocation is sized for: about 40 registers
   // per thread for FP32 and 64 for FP64 up to k = 4; the k >= 5 stages hold
   // 2(2k+1) + 2(2k-1) values per thread and get 80 / 128
@@ -79,10 +83,11 @@ struct SmoothCfg {
   static constexpr int MINB = RESIDENT / NT > 8 ? 8 : (RESIDENT / NT < 1 ? 1 : RESIDENT / NT);
   static constexpr int NB = 128 / (int)sizeof(T);  // word-banks per wavefront
   // patch-major stride of the first stage's output, chosen so that the
-  // next stage (patch index fastest) hits P distinct bank groups
+  // next stage (patch index fastest) hits distinct bank groups:
+  // S0 = NB/P (mod NB) for P < NB, S0 = 1 (mod NB) otherwise
   static constexpr int size0 = DIM == 3 ? n * n * m : n * m;
-  static constexpr int S0 = P == 1 ? size0
-                                   : size0 + ((((NB / P) - size0) % NB) + NB) % NB;
+  static constexpr int want0 = P >= NB ? 1 : NB / P;
+  static constexpr int S0 = P == 1 ? size0 : size0 + (((want0 - size0) % NB) + NB) % NB;
   // stage-1 outputs: U and W in 3D, the residual R in 2D
   static constexpr int sizeU = DIM == 3 ? n * m * m : m * m;
   static constexpr int nU = DIM == 3 ? 2 : 1;
@@ -91,6 +96,7 @@ struct SmoothCfg {
   static constexpr size_t elems_mult = (size_t)2 * P * S0 + (size_t)nU * P * sizeU + 2 * P * md;
   static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
   static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md) + sizeof(int) * P;
+  static constexpr bool fits = smem_mult <= 227 * 1024;
 };
 
 // Offset of the first closure node of patch gp of a colour (int: every
@@ -204,11 +210,11 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
 }
 
 // ------------------------------------------------------- multiplicative
-template <typename T>
-__global__ void __launch_bounds__(SmoothCfg<T>::NT, SmoothCfg<T>::MINB)
+template <typename T, int PP>
+__global__ void __launch_bounds__(SmoothCfg<T, PP>::NT, SmoothCfg<T, PP>::MINB)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
                    int px, int pz, ColourGeom cg, T bscale) {
-  using C = SmoothCfg<T>;
+  using C = SmoothCfg<T, PP>;
   constexpr int P = C::P, NT = C::NT, S0 = C::S0, MD = C::md;
   const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,11 +392,11 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
 
 // ------------------------------------------------------------- additive
 // x_I += scale * A_ref^-1 r_I for every patch of one colour.
-template <typename T>
-__global__ void __launch_bounds__(SmoothCfg<T>::NT)
+template <typename T, int PP>
+__global__ void __launch_bounds__(SmoothCfg<T, PP>::NT)
 smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv_lam,
                   int px, int pz, ColourGeom cg, T scale) {
-  using C = SmoothCfg<T>;
+  using C = SmoothCfg<T, PP>;
   constexpr int P = C::P, NT = C::NT, MD = C::md;
   const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1001,29 +1007,29 @@ __global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, i
 }
 
 // ------------------------------------------------------------ launchers
-template <typename T>
+template <typename T, int PP>
 cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                                const T* inv_lam, cudaStream_t s) {
-  using C = SmoothCfg<T>;
+  using C = SmoothCfg<T, PP>;
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_mult_kernel<T><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, (int)g.px,
-                                                                     (int)g.pz, cg, bscale);
+  smooth_mult_kernel<T, PP><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, (int)g.px,
+                                                                         (int)g.pz, cg, bscale);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int PP>
 cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
                               const T* inv_lam, T scale, cudaStream_t s) {
-  using C = SmoothCfg<T>;
+  using C = SmoothCfg<T, PP>;
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T sc = DIM == 3 ? T(scale / g.h) : scale;
   VPS_COUNT_LAUNCH();
-  smooth_add_kernel<T><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, (int)g.px,
-                                                                   (int)g.pz, cg, sc);
+  smooth_add_kernel<T, PP><<<(unsigned)grid, C::NT, C::smem_add, s>>>(r, x, inv_lam, (int)g.px,
+                                                                       (int)g.pz, cg, sc);
   return cudaGetLastError();
 }
 
@@ -1080,14 +1086,54 @@ cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf,
   return cudaGetLastError();
 }
 
+template <typename T, int PP>
+cudaError_t smooth_limits() {
+  using C = SmoothCfg<T, PP>;
+  if constexpr (!C::fits) {
+    return cudaSuccess;
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::smem_mult);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(smooth_add_kernel<T, PP>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_add);
+  }
+}
+
+template <typename T, int PP>
+void register_variant(KernelFns<T>* f, int v) {
+  using C = SmoothCfg<T, PP>;
+  f->variant_p[v] = PP;
+  if constexpr (C::fits) {
+    f->smooth_mult_v[v] = smooth_mult_launch<T, PP>;
+    f->smooth_add_v[v] = smooth_add_launch<T, PP>;
+  } else {
+    f->smooth_mult_v[v] = nullptr;
+    f->smooth_add_v[v] = nullptr;
+  }
+}
+
+template <typename T>
+void register_fns(KernelFns<T>* f) {
+  register_variant<T, kVarP[0]>(f, 0);
+  register_variant<T, kVarP[1]>(f, 1);
+  register_variant<T, kVarP[2]>(f, 2);
+  f->smooth_mult = f->smooth_mult_v[1];
+  f->smooth_add = f->smooth_add_v[1];
+  f->apply = apply_launch<T>;
+  f->prolong_add = prolong_launch<T>;
+  f->restrict_ = restrict_launch<T>;
+}
+
 template <typename T>
 cudaError_t set_smem_limits() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(smooth_mult_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SmoothCfg<T>::smem_mult);
+  e = smooth_limits<T, kVarP[0]>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(smooth_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SmoothCfg<T>::smem_add);
+  e = smooth_limits<T, kVarP[1]>();
+  if (e != cudaSuccess) return e;
+  e = smooth_limits<T, kVarP[2]>();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ApplyCfg::smem<T>());
@@ -1140,16 +1186,8 @@ cudaError_t upload(const HostTables& h) {
 void VPS_CAT(register_kernels_d, VPS_DIM, VPS_K)(KernelSet* ks) {
   ks->present = true;
   ks->upload = upload;
-  ks->f.smooth_mult = smooth_mult_launch<float>;
-  ks->f.smooth_add = smooth_add_launch<float>;
-  ks->f.apply = apply_launch<float>;
-  ks->f.prolong_add = prolong_launch<float>;
-  ks->f.restrict_ = restrict_launch<float>;
-  ks->d.smooth_mult = smooth_mult_launch<double>;
-  ks->d.smooth_add = smooth_add_launch<double>;
-  ks->d.apply = apply_launch<double>;
-  ks->d.prolong_add = prolong_launch<double>;
-  ks->d.restrict_ = restrict_launch<double>;
+  register_fns<float>(&ks->f);
+  register_fns<double>(&ks->d);
 }
 
 }  // namespace vps

@@ -88,14 +88,22 @@ ColourGeom make_colour(const LevelGeom& g, int colour);
 int64_t& launch_counter();
 #define VPS_COUNT_LAUNCH() (++::vps::launch_counter())
 
+// Smoother kernel variants (patches per block) the autotuner chooses from.
+constexpr int kSmoothVariants = 3;
+
 template <typename T>
 struct KernelFns {
+  using SmoothMultFn = cudaError_t (*)(const LevelGeom&, const ColourGeom&, const T* b, T* x,
+                                       const T* inv_lam, cudaStream_t);
+  using SmoothAddFn = cudaError_t (*)(const LevelGeom&, const ColourGeom&, const T* r, T* x,
+                                      const T* inv_lam, T scale, cudaStream_t);
   // one multiplicative colour pass: x += R^T A_j^-1 (R b - Abar Rbar x)
-  cudaError_t (*smooth_mult)(const LevelGeom&, const ColourGeom&, const T* b, T* x,
-                             const T* inv_lam, cudaStream_t) = nullptr;
+  SmoothMultFn smooth_mult = nullptr;            // the default variant
+  SmoothMultFn smooth_mult_v[kSmoothVariants] = {};
   // one additive colour pass from a precomputed residual: x += scale R^T A_ref^-1 R r
-  cudaError_t (*smooth_add)(const LevelGeom&, const ColourGeom&, const T* r, T* x,
-                            const T* inv_lam, T scale, cudaStream_t) = nullptr;
+  SmoothAddFn smooth_add = nullptr;
+  SmoothAddFn smooth_add_v[kSmoothVariants] = {};
+  int variant_p[kSmoothVariants] = {};           // patches per block of each variant
   // y = A x  (b == nullptr)  or  y = b - A x  (residual)
   cudaError_t (*apply)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
   // x_fine += P x_coarse

@@ -221,3 +221,47 @@ def test_invalid_arguments_raise():
         P.vps_smooth_colour(3, 4, x, P.empty_level(3))
     with pytest.raises(vps.VpsError):
         P.vps_apply(4, x, P.empty_level(3))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("d,k,l", [(2, 2, 4), (2, 6, 3), (3, 1, 3), (3, 3, 3), (3, 6, 2)])
+def test_every_smoother_variant_matches_oracle(d, k, l, prec):
+    """Patches per block is a launch choice only: every variant gives the oracle's step."""
+    lv, A, ps = oracle_level(d, k, l)
+    x0 = as_prec(normal_vector(lv.N, 31), prec)
+    b = as_prec(normal_vector(lv.N, 32), prec)
+    ref = smoothers.multiplicative(A, ps, x0, b)
+    P = _poisson(d, k, l, prec)
+    seen = set()
+    for v in range(3):
+        try:
+            P.vps_set_smooth_variant(0, v)
+        except vps.VpsError:
+            continue  # does not fit in shared memory for this degree
+        seen.add(P.vps_get_smooth_variant(l)[1])
+        xg = to_dev(P, x0, l)
+        P.vps_smooth(l, to_dev(P, b, l), xg, 1)
+        assert rel_err(to_host(P, xg, l), ref) <= TOL[prec], v
+    assert len(seen) >= 1
+
+
+def test_autotune_caches_and_keeps_parity(tmp_path):
+    import torch
+    cache = str(tmp_path / "tune.json")
+    d, k, L = 3, 2, 4
+    P = _poisson(d, k, L, 1)
+    assert P.vps_autotune(cache) is False
+    chosen = ([P.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)], P.vps_get_coarse_level())
+    Q = _poisson(d, k, L, 1)
+    assert Q.vps_autotune(cache) is True
+    assert ([Q.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)], Q.vps_get_coarse_level()) == chosen
+    import json
+    assert len(json.load(open(cache))) == 1
+    H = multigrid.Hierarchy(d, k, L, coarse_level=Q.vps_get_coarse_level())
+    b = uniform_vector(H.levels[L].N, 33)
+    bt = torch.as_tensor(b, device="cuda")
+    xt = torch.zeros_like(bt)
+    it, rel = Q.vps_solve(bt, xt, 1e-10, 100)
+    xo, ito, _ = multigrid.pcg(H.A[L], b, H.precondition, rtol=1e-10)
+    assert rel <= 1e-10 and abs(it - ito) <= 1
+    assert rel_err(xt.cpu().numpy(), xo) <= 1e-8
