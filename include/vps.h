@@ -244,6 +244,47 @@ int vps_set_graphs(vps_handle h, int enable);
 int vps_smooth_additive_static(int dim, int degree, int level, int precision, double damping,
                                const void* b, void* x, void* cuda_stream);
 
+/*
+ * Serving: continuous batching of Poisson solve requests (no counterpart in
+ * the paper).  A server owns an engine thread on the device current at
+ * creation.  Requests wait in a queue and are admitted as solver slots
+ * (at most max_active at a time) and device memory (memory_budget bytes)
+ * become free; a slot is a handle on a stream of its own whose level
+ * hierarchy stays resident for later requests of the same (dim, degree,
+ * level); idle slots are evicted least recently used first.  Every admitted
+ * request runs vps_solve's CG one iteration at a time, so requests overlap
+ * on the GPU.  precision: VPS_FP32 (FP32 V-cycle, FP64 CG) or VPS_FP64.
+ * A request's result depends only on its own data: it is the same alone
+ * and in a mix.
+ */
+typedef struct vps_server_ctx* vps_server;
+
+#define VPS_REQ_QUEUED  0
+#define VPS_REQ_RUNNING 1
+#define VPS_REQ_DONE    2
+#define VPS_REQ_FAILED  3
+
+int vps_server_create(size_t memory_budget, int max_active, int precision, double rtol,
+                      int max_it, vps_server* out);
+/* Queue a solve of -Laplace u = f, f = sum_m coef[m] prod_t sin(pi freq[m*dim+t] x_t)
+ * (load vector as vps_assemble_rhs_sines).  x_out: HOST buffer of (k 2^level - 1)^dim
+ * doubles (compact layout) that receives the solution; it must stay valid
+ * until the request is done.  coef/freq are copied.  *id receives the id. */
+int vps_server_submit(vps_server s, int dim, int degree, int level, int n_modes,
+                      const double* coef, const int* freq, double* x_out, int64_t* id);
+/* State (VPS_REQ_*), solver status, CG iterations, relative residual, time
+ * queued and time from submission to result (seconds; -1 if not yet). */
+int vps_server_query(vps_server s, int64_t id, int* state, int* status, int* iters,
+                     double* rel_res, double* queue_s, double* latency_s);
+/* Wait (host side, at most timeout_s) for request id, or for all requests
+ * submitted so far when id == 0.  VPS_ETIMEOUT if the time ran out. */
+int vps_server_wait(vps_server s, int64_t id, double timeout_s);
+int vps_server_stats(vps_server s, int64_t* submitted, int64_t* done, int* active, int* queued);
+const char* vps_server_last_error(vps_server s);
+/* Stops the engine thread (requests still running are abandoned) and frees
+ * every slot. */
+int vps_server_destroy(vps_server s);
+
 /* vps_last_error -- message of the last failure on h (h = NULL: the last
  * failure of vps_create or vps_smooth_additive_static on this thread).
  * Valid until the next call. */

@@ -28,6 +28,7 @@ VPS_FP32 = 1
 VPS_MULTIPLICATIVE = 0
 VPS_ADDITIVE = 1
 VPS_MAX_DEGREE = 7
+VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
 
 # C signatures: name -> (restype, argtypes)
 _i, _d, _p, _i64p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
@@ -56,6 +57,15 @@ SIGNATURES = {
     "vps_get_smooth_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
+    "vps_server_create": (_i, [ctypes.c_size_t, _i, _i, _d, _i, ctypes.POINTER(_p)]),
+    "vps_server_submit": (_i, [_p, _i, _i, _i, _i, _p, _p, _p, _i64p]),
+    "vps_server_query": (_i, [_p, ctypes.c_int64, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                              ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_d),
+                              ctypes.POINTER(_d)]),
+    "vps_server_wait": (_i, [_p, ctypes.c_int64, _d]),
+    "vps_server_stats": (_i, [_p, _i64p, _i64p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "vps_server_last_error": (ctypes.c_char_p, [_p]),
+    "vps_server_destroy": (_i, [_p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -284,3 +294,73 @@ class Poisson:
         out = self.torch.empty(self.n_interior(level), dtype=lev.dtype, device="cuda")
         self.vps_unpack(level, lev, out)
         return out
+
+
+class Server:
+    """Continuous-batching solve server (vps_server_* of the C ABI).
+
+    ``submit`` returns a request id and the numpy array that receives the
+    solution (compact layout, float64); results arrive asynchronously.
+    """
+
+    def __init__(self, memory_budget, max_active=8, precision=VPS_FP32, rtol=1e-10, max_it=100):
+        s = ctypes.c_void_p()
+        rc = lib().vps_server_create(int(memory_budget), int(max_active), int(precision),
+                                     float(rtol), int(max_it), ctypes.byref(s))
+        if rc != VPS_OK:
+            raise VpsError(rc, lib().vps_last_error(None).decode())
+        self.s = s
+        self._bufs = {}
+
+    def submit(self, dim, degree, level, coef, freq):
+        import numpy as np
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        freq = np.ascontiguousarray(freq, dtype=np.int32)
+        n = (degree * 2 ** level - 1) ** dim
+        x = np.zeros(n, dtype=np.float64)
+        rid = ctypes.c_int64()
+        rc = lib().vps_server_submit(self.s, dim, degree, level, len(coef),
+                                     coef.ctypes.data_as(ctypes.c_void_p),
+                                     freq.ctypes.data_as(ctypes.c_void_p),
+                                     x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid))
+        if rc != VPS_OK:
+            raise VpsError(rc, "vps_server_submit")
+        self._bufs[rid.value] = (x, coef, freq)
+        return rid.value, x
+
+    def query(self, rid):
+        st, status, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rel, qs, lat = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        rc = lib().vps_server_query(self.s, int(rid), ctypes.byref(st), ctypes.byref(status),
+                                    ctypes.byref(it), ctypes.byref(rel), ctypes.byref(qs),
+                                    ctypes.byref(lat))
+        if rc != VPS_OK:
+            raise VpsError(rc, "vps_server_query")
+        return dict(state=st.value, status=status.value, iters=it.value, rel_res=rel.value,
+                    queue_s=qs.value, latency_s=lat.value)
+
+    def wait(self, rid=0, timeout_s=600.0):
+        rc = lib().vps_server_wait(self.s, int(rid), float(timeout_s))
+        if rc != VPS_OK:
+            raise VpsError(rc, "vps_server_wait")
+
+    def stats(self):
+        sub, done = ctypes.c_int64(), ctypes.c_int64()
+        act, q = ctypes.c_int(), ctypes.c_int()
+        lib().vps_server_stats(self.s, ctypes.byref(sub), ctypes.byref(done), ctypes.byref(act),
+                               ctypes.byref(q))
+        return dict(submitted=sub.value, done=done.value, active=act.value, queued=q.value)
+
+    def last_error(self):
+        return lib().vps_server_last_error(self.s).decode()
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().vps_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

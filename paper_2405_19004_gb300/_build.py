@@ -38,7 +38,7 @@ def _units():
         for k in range(1, 8):
             units.append((os.path.join(CSRC, "kernels_dk.cu"), os.path.join(OBJ, f"kernels_d{d}_k{k}.o"),
                           [f"-DVPS_DIM={d}", f"-DVPS_K={k}"], headers))
-    for name in ("ops.cu", "noalloc.cu", "setup.cpp", "api.cpp"):
+    for name in ("ops.cu", "noalloc.cu", "setup.cpp", "api.cpp", "server.cpp"):
         src = os.path.join(CSRC, name)
         units.append((src, os.path.join(OBJ, os.path.splitext(name)[0] + ".o"), [], headers))
     return units

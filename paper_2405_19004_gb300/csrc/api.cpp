@@ -107,9 +107,16 @@ struct vps_context {
   std::vector<void*> allocs;
   // captured preconditioner graph (input r = cr, output czn)
   cudaGraphExec_t prec_graph = nullptr;
+  bool own_stream = false;              // stream created (and destroyed) by the library
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
   int smooth_var[kMaxLevels + 1] = {};  // smoother variant per level (index into the table)
+  // asynchronous CG (used by the serving loop)
+  int as_phase = 0;                     // 0 idle, 1 iteration in flight, 2 result copy in flight
+  int as_it = 0, as_maxit = 0, as_status = 0;
+  double as_nb = 0.0, as_rtol = 0.0, as_rel = 0.0;
+  double* host_x = nullptr;             // pinned staging of the compact result
+  cudaEvent_t as_ev = nullptr;
   // exact coarse solve on level `coarse` by global fast diagonalisation
   int coarse = 1;
   int gni = 0;                          // interior nodes per direction on that level
@@ -149,8 +156,8 @@ int dalloc(vps_context* h, void** p, size_t bytes) {
   }
   h->allocs.push_back(*p);
   h->bytes += bytes;
-  e = cudaMemset(*p, 0, bytes);
-  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   return VPS_OK;
 }
 
@@ -269,13 +276,21 @@ int setup_coarse(vps_context* h, int lc) {
       (rc = dalloc(h, &h->gt1, nd * h->esz)) || (rc = dalloc(h, &h->gt2, nd * h->esz)))
     return rc;
   cudaError_t e;
+  // pageable source: the copies are staged before the calls return
   if (h->prec == VPS_FP64) {
-    e = cudaMemcpy(h->gS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->ginv, inv.data(), nd * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(h->gS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ginv, inv.data(), nd * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream);
   } else {
     std::vector<float> Sf(S.begin(), S.end()), invf(inv.begin(), inv.end());
-    e = cudaMemcpy(h->gS, Sf.data(), Sf.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->ginv, invf.data(), nd * sizeof(float), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(h->gS, Sf.data(), Sf.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ginv, invf.data(), nd * sizeof(float), cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   if (e != cudaSuccess) return fail(h, VPS_ECUDA, "coarse tables: %s", cudaGetErrorString(e));
   h->coarse = lc;
@@ -418,6 +433,189 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
 }
 
 }  // namespace
+
+namespace {
+
+// Load vector of f = sum_m coef_m prod_t sin(pi freq_mt x_t) into the compact
+// device vector b: 1D integrals with (k+2)-point Gauss rules on the host,
+// tensor product on the device (asynchronous on the handle's stream).
+int upload_rhs_sines(vps_context* h, int n_modes, const double* coef, const int* freq, double* b) {
+  const LevelGeom& g = h->geom[h->L];
+  const int k = h->k, ni = g.n1 - 2, q = k + 2;
+  double xq[16], wq[16], val[kMaxK + 1];
+  gauss_rule(q, xq, wq);
+  std::vector<double> b1d((size_t)n_modes * h->dim * ni, 0.0);
+  std::vector<double> full(g.n1);
+  for (int md = 0; md < n_modes; ++md)
+    for (int t = 0; t < h->dim; ++t) {
+      const double f = freq[md * h->dim + t];
+      std::fill(full.begin(), full.end(), 0.0);
+      for (int c = 0; c < g.ncell; ++c)
+        for (int qq = 0; qq < q; ++qq) {
+          const double x = (c + xq[qq]) * g.h;
+          const double fv = std::sin(M_PI * f * x) * wq[qq] * g.h;
+          lagrange_eval(k, h->tab.z, xq[qq], val);
+          for (int i = 0; i <= k; ++i) full[k * c + i] += fv * val[i];
+        }
+      const double s = t == 0 ? coef[md] : 1.0;
+      for (int j = 0; j < ni; ++j) b1d[((size_t)md * h->dim + t) * ni + j] = s * full[j + 1];
+    }
+  const size_t need = b1d.size() * sizeof(double);
+  if (need > h->rhs_cap) {
+    if (h->rhs_buf) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->rhs_buf);
+    }
+    h->rhs_buf = nullptr;
+    h->rhs_cap = 0;
+    cudaError_t e = cudaMalloc(&h->rhs_buf, need);
+    if (e != cudaSuccess) return fail(h, VPS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    h->rhs_cap = need;
+  }
+  // pageable source: staged before the call returns
+  VPS_CK(h, cudaMemcpyAsync(h->rhs_buf, b1d.data(), need, cudaMemcpyHostToDevice, h->stream));
+  VPS_CK(h, launch_rhs_tensor(g, n_modes, h->rhs_buf, b, h->stream));
+  return VPS_OK;
+}
+
+// One CG iteration's device work after z_new = B r is known (or, for the
+// first iteration, after p = z): A p, alpha, x and r updates, r.r, and the
+// asynchronous copy of the scalars to the host.
+int cg_async_iteration(vps_context* h, bool first) {
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t n = g.total;
+  if (first) {
+    VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream));
+    VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                              h->stream));
+    VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+  } else {
+    VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
+    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream));
+  }
+  VPS_CK(h, h->ks->d.apply(g, h->cp, nullptr, h->cAp, h->stream));
+  VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
+  VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
+  VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaEventRecord(h->as_ev, h->stream));
+  return VPS_OK;
+}
+
+int cg_async_finish(vps_context* h, int status) {
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t ni = g.n1 - 2;
+  const size_t nbytes = (size_t)(h->dim == 3 ? ni * ni * ni : ni * ni) * sizeof(double);
+  h->as_status = status;
+  VPS_CK(h, launch_unpack<double>(g, h->cx, h->comp_x, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_x, h->comp_x, nbytes, cudaMemcpyDeviceToHost, h->stream));
+  VPS_CK(h, cudaEventRecord(h->as_ev, h->stream));
+  h->as_phase = 2;
+  return VPS_OK;
+}
+
+}  // namespace
+
+namespace vps {
+
+int create_own_stream(int dim, int degree, int level, int precision, vps_handle* out) {
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_thread_error(cudaGetErrorString(e));
+    return VPS_ECUDA;
+  }
+  int rc = vps_create(dim, degree, level, precision, VPS_MULTIPLICATIVE, 1.0, 1, 1, s, out);
+  if (rc) {
+    cudaStreamDestroy(s);
+    return rc;
+  }
+  (*out)->own_stream = true;
+  return VPS_OK;
+}
+
+size_t estimate_device_bytes(int dim, int degree, int level, int precision) {
+  const size_t esz = precision == VPS_FP64 ? 8 : 4;
+  size_t total = 0;
+  for (int l = 1; l <= level; ++l) total += 3 * (size_t)make_geom(dim, degree, l).total * esz;
+  const LevelGeom g = make_geom(dim, degree, level);
+  const size_t ni = g.n1 - 2;
+  total += 7 * (size_t)g.total * 8 + 2 * (dim == 3 ? ni * ni * ni : ni * ni) * 8;
+  return total + (size_t)(4 << 20);  // tables, coarse-level data, scalars
+}
+
+// Starts a CG solve of the sine-mode right-hand side on h without waiting.
+int cg_async_begin(vps_handle h, int n_modes, const double* coef, const int* freq, double rtol,
+                   int max_it) {
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t n = g.total;
+  if (!h->as_ev) VPS_CK(h, cudaEventCreateWithFlags(&h->as_ev, cudaEventDisableTiming));
+  if (!h->host_x) {
+    const int64_t ni = g.n1 - 2;
+    VPS_CK(h, cudaMallocHost(&h->host_x, (size_t)(h->dim == 3 ? ni * ni * ni : ni * ni) *
+                                              sizeof(double)));
+  }
+  h->as_rtol = rtol;
+  h->as_maxit = max_it;
+  h->as_it = 1;
+  h->as_rel = 1.0;
+  h->as_status = VPS_OK;
+  if (int rc = upload_rhs_sines(h, n_modes, coef, freq, h->comp_b)) return rc;
+  VPS_CK(h, launch_pack<double>(g, h->comp_b, h->cb, h->stream));
+  VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
+  VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+  if (int rc = precondition(h)) return rc;
+  if (int rc = cg_async_iteration(h, true)) return rc;
+  h->as_phase = 1;
+  return VPS_OK;
+}
+
+// Advances an asynchronous solve if its pending GPU work has finished.
+// *done = 1 when the solution is in host_x (then *status, *iters, *rel).
+int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
+                  const double** x_host) {
+  *done = 0;
+  if (h->as_phase == 0) return fail(h, VPS_EINVAL, "no solve in flight");
+  const cudaError_t q = cudaEventQuery(h->as_ev);
+  if (q == cudaErrorNotReady) return VPS_OK;
+  if (q != cudaSuccess) return fail(h, VPS_ECUDA, "solve: %s", cudaGetErrorString(q));
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  if (h->as_phase == 2) {
+    h->as_phase = 0;
+    *done = 1;
+    *status = h->as_status;
+    *iters = h->as_it;
+    *rel = h->as_rel;
+    *x_host = h->host_x;
+    return VPS_OK;
+  }
+  if (h->as_it == 1) h->as_nb = std::sqrt(h->host_dots[0]);
+  if (!(h->as_nb > 0.0)) {  // b = 0: x = 0
+    h->as_rel = 0.0;
+    return cg_async_finish(h, std::isfinite(h->as_nb) ? VPS_OK : VPS_EBREAKDOWN);
+  }
+  if (h->host_sc->flag) return cg_async_finish(h, VPS_EBREAKDOWN);
+  h->as_rel = std::sqrt(h->host_sc->rr) / h->as_nb;
+  if (!std::isfinite(h->as_rel)) return cg_async_finish(h, VPS_EBREAKDOWN);
+  if (h->as_rel <= h->as_rtol) return cg_async_finish(h, VPS_OK);
+  if (h->as_it >= h->as_maxit) return cg_async_finish(h, VPS_ENOCONV);
+  if (int rc = precondition(h)) return rc;
+  if (int rc = cg_async_iteration(h, false)) return rc;
+  ++h->as_it;
+  return VPS_OK;
+}
+
+const char* handle_error(vps_handle h) { return h ? h->err.c_str() : ""; }
+
+}  // namespace vps
 
 namespace {
 
@@ -631,10 +829,13 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     }
     if ((rc = dalloc(h, &h->inv_lam, md * h->esz))) return bail(rc);
     if (precision == VPS_FP64) {
-      e = cudaMemcpy(h->inv_lam, il.data(), md * sizeof(double), cudaMemcpyHostToDevice);
+      e = cudaMemcpyAsync(h->inv_lam, il.data(), md * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream);
     } else {
       std::vector<float> f(il.begin(), il.end());
-      e = cudaMemcpy(h->inv_lam, f.data(), md * sizeof(float), cudaMemcpyHostToDevice);
+      e = cudaMemcpyAsync(h->inv_lam, f.data(), md * sizeof(float), cudaMemcpyHostToDevice,
+                          h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     }
     if (e != cudaSuccess) {
       h->err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
@@ -666,7 +867,7 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   e = cudaMallocHost(&p, 8 * sizeof(double));
   if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
   h->host_dots = (double*)p;
-  e = cudaDeviceSynchronize();
+  e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->err = std::string("create: ") + cudaGetErrorString(e);
     return bail(VPS_ECUDA);
@@ -684,6 +885,10 @@ int vps_destroy(vps_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->host_sc) cudaFreeHost(h->host_sc);
   if (h->host_dots) cudaFreeHost(h->host_dots);
+  if (h->host_x) cudaFreeHost(h->host_x);
+  if (h->as_ev) cudaEventDestroy(h->as_ev);
+  if (h->rhs_buf) cudaFree(h->rhs_buf);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return VPS_OK;
 }
@@ -854,38 +1059,7 @@ int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef, const 
     return fail(h, VPS_EINVAL, "bad sine-mode arguments");
   if (int rc = set_device(h)) return rc;
   LaunchTally tally(h);
-  const LevelGeom& g = h->geom[h->L];
-  const int k = h->k, ni = g.n1 - 2, q = k + 2;
-  double xq[16], wq[16], val[kMaxK + 1];
-  gauss_rule(q, xq, wq);
-  // b1d[(mode*dim + t)*ni + j] = int sin(pi f x) phi_{j+1}(x) dx (times coef for t = 0)
-  std::vector<double> b1d((size_t)n_modes * h->dim * ni, 0.0);
-  std::vector<double> full(g.n1);
-  for (int md = 0; md < n_modes; ++md)
-    for (int t = 0; t < h->dim; ++t) {
-      const double f = freq[md * h->dim + t];
-      std::fill(full.begin(), full.end(), 0.0);
-      for (int c = 0; c < g.ncell; ++c)
-        for (int qq = 0; qq < q; ++qq) {
-          const double x = (c + xq[qq]) * g.h;
-          const double fv = std::sin(M_PI * f * x) * wq[qq] * g.h;
-          lagrange_eval(k, h->tab.z, xq[qq], val);
-          for (int i = 0; i <= k; ++i) full[k * c + i] += fv * val[i];
-        }
-      const double s = t == 0 ? coef[md] : 1.0;
-      for (int j = 0; j < ni; ++j) b1d[((size_t)md * h->dim + t) * ni + j] = s * full[j + 1];
-    }
-  const size_t need = b1d.size() * sizeof(double);
-  if (need > h->rhs_cap) {
-    if (h->rhs_buf) cudaFree(h->rhs_buf);
-    h->rhs_buf = nullptr;
-    h->rhs_cap = 0;
-    cudaError_t e = cudaMalloc(&h->rhs_buf, need);
-    if (e != cudaSuccess) return fail(h, VPS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
-    h->rhs_cap = need;
-  }
-  VPS_CK(h, cudaMemcpyAsync(h->rhs_buf, b1d.data(), need, cudaMemcpyHostToDevice, h->stream));
-  VPS_CK(h, launch_rhs_tensor(g, n_modes, h->rhs_buf, b, h->stream));
+  if (int rc = upload_rhs_sines(h, n_modes, coef, freq, b)) return rc;
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   return VPS_OK;
 }

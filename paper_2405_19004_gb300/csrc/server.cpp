@@ -1,0 +1,332 @@
+// Continuous-batching server for Poisson solve requests.
+//
+// Requests (dimension, degree, level, sine-mode right-hand side) wait in a
+// queue.  An engine thread admits them as solver slots and device memory
+// (a fixed budget) become free: a slot is a vps handle on a stream of its
+// own whose level hierarchy stays resident and is reused by later requests
+// of the same shape; idle slots are evicted, least recently used first,
+// when memory is needed.  Every admitted request runs the preconditioned CG
+// of the library one iteration at a time: the engine polls each slot's CUDA
+// event and, when an iteration's scalars have arrived, issues the next one.
+// Requests therefore overlap on the GPU, and one that arrives while others
+// run starts as soon as a slot and memory are free.  A request's numbers
+// depend only on its own slot: its result is the same alone and in a mix.
+//
+// The engine never blocks on the GPU (it polls events); waits on the host
+// side take a timeout.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "vps.h"
+#include "vps_internal.h"
+
+namespace {
+
+double now_s() {
+  using clock = std::chrono::steady_clock;
+  static const clock::time_point t0 = clock::now();
+  return std::chrono::duration<double>(clock::now() - t0).count();
+}
+
+struct Request {
+  int64_t id = 0;
+  int d = 0, k = 0, L = 0;
+  std::vector<double> coef;
+  std::vector<int> freq;
+  double* x_out = nullptr;
+  int64_t n = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  int state = VPS_REQ_QUEUED;
+  int status = VPS_OK;
+  int iters = 0;
+  double rel = 0;
+};
+
+struct Slot {
+  vps_context* h = nullptr;
+  int d = 0, k = 0, L = 0;
+  size_t bytes = 0;
+  int64_t req = 0;  // 0: idle
+  double last_used = 0;
+};
+
+}  // namespace
+
+struct vps_server_ctx {
+  size_t budget = 0;
+  int max_active = 1;
+  int precision = VPS_FP32;
+  double rtol = 1e-10;
+  int max_it = 100;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread engine;
+  std::atomic<bool> stop{false};
+  std::map<int64_t, Request> reqs;
+  std::deque<int64_t> queue;
+  std::vector<Slot> slots;  // engine thread only
+  size_t used = 0;          // engine thread only
+  int64_t next_id = 1;
+  int64_t n_done = 0;
+  int active = 0;
+  std::string err;
+
+  void run();
+  bool admit_one();
+  void finish(Slot& s, int state, int status, int iters, double rel, const double* x);
+};
+
+void vps_server_ctx::finish(Slot& s, int state, int status, int iters, double rel,
+                            const double* x) {
+  std::lock_guard<std::mutex> lock(mu);
+  Request& r = reqs[s.req];
+  if (x && r.x_out) std::memcpy(r.x_out, x, (size_t)r.n * sizeof(double));
+  r.state = state;
+  r.status = status;
+  r.iters = iters;
+  r.rel = rel;
+  r.t_done = now_s();
+  s.req = 0;
+  s.last_used = r.t_done;
+  --active;
+  ++n_done;
+  cv.notify_all();
+}
+
+// Admits the first queued request that fits; returns true if one started.
+bool vps_server_ctx::admit_one() {
+  int64_t id = 0;
+  Request snapshot;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (queue.empty() || active >= max_active) return false;
+    // first queued request with an idle slot of its shape, else the head
+    size_t pick = 0;
+    bool found = false;
+    for (size_t qi = 0; qi < queue.size() && qi < 64 && !found; ++qi) {
+      const Request& r = reqs[queue[qi]];
+      for (const Slot& s : slots)
+        if (!s.req && s.d == r.d && s.k == r.k && s.L == r.L) {
+          pick = qi;
+          found = true;
+          break;
+        }
+    }
+    id = queue[pick];
+    snapshot = reqs[id];
+  }
+  Slot* slot = nullptr;
+  for (Slot& s : slots)
+    if (!s.req && s.d == snapshot.d && s.k == snapshot.k && s.L == snapshot.L) {
+      slot = &s;
+      break;
+    }
+  if (!slot) {
+    const size_t need =
+        vps::estimate_device_bytes(snapshot.d, snapshot.k, snapshot.L, precision);
+    if (need > budget) {  // can never fit
+      std::lock_guard<std::mutex> lock(mu);
+      queue.erase(std::find(queue.begin(), queue.end(), id));
+      Request& r = reqs[id];
+      r.state = VPS_REQ_FAILED;
+      r.status = VPS_ENOMEM;
+      r.t_done = now_s();
+      ++n_done;
+      cv.notify_all();
+      return true;
+    }
+    // evict idle slots, least recently used first, until the request fits
+    while (used + need > budget) {
+      auto victim = slots.end();
+      for (auto it = slots.begin(); it != slots.end(); ++it)
+        if (!it->req && (victim == slots.end() || it->last_used < victim->last_used)) victim = it;
+      if (victim == slots.end()) return false;  // wait for a running request to finish
+      vps_destroy(victim->h);
+      used -= victim->bytes;
+      slots.erase(victim);
+    }
+    Slot s;
+    s.d = snapshot.d;
+    s.k = snapshot.k;
+    s.L = snapshot.L;
+    int rc = vps::create_own_stream(s.d, s.k, s.L, precision, &s.h);
+    if (rc) {
+      std::lock_guard<std::mutex> lock(mu);
+      queue.erase(std::find(queue.begin(), queue.end(), id));
+      Request& r = reqs[id];
+      r.state = VPS_REQ_FAILED;
+      r.status = rc;
+      r.t_done = now_s();
+      ++n_done;
+      err = vps_last_error(nullptr);
+      cv.notify_all();
+      return true;
+    }
+    vps_sizes(s.h, nullptr, nullptr, &s.bytes);
+    used += s.bytes;
+    slots.push_back(s);
+    slot = &slots.back();
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    queue.erase(std::find(queue.begin(), queue.end(), id));
+    Request& r = reqs[id];
+    r.state = VPS_REQ_RUNNING;
+    r.t_start = now_s();
+    ++active;
+  }
+  slot->req = id;
+  const int rc = vps::cg_async_begin(slot->h, (int)snapshot.coef.size(), snapshot.coef.data(),
+                                     snapshot.freq.data(), rtol, max_it);
+  if (rc) {
+    err = vps::handle_error(slot->h);
+    finish(*slot, VPS_REQ_FAILED, rc, 0, 0.0, nullptr);
+  }
+  return true;
+}
+
+void vps_server_ctx::run() {
+  cudaSetDevice(device);
+  while (!stop.load()) {
+    bool progressed = false;
+    for (Slot& s : slots) {
+      if (!s.req) continue;
+      int done = 0, status = 0, iters = 0;
+      double rel = 0;
+      const double* x = nullptr;
+      const int rc = vps::cg_async_poll(s.h, &done, &status, &iters, &rel, &x);
+      if (rc) {
+        err = vps::handle_error(s.h);
+        finish(s, VPS_REQ_FAILED, rc, iters, rel, nullptr);
+        progressed = true;
+      } else if (done) {
+        finish(s, status == VPS_OK ? VPS_REQ_DONE : VPS_REQ_FAILED, status, iters, rel, x);
+        progressed = true;
+      }
+    }
+    while (admit_one()) progressed = true;
+    if (!progressed) {
+      std::unique_lock<std::mutex> lock(mu);
+      if (queue.empty() && active == 0)
+        cv.wait_for(lock, std::chrono::milliseconds(2));
+      else
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+}
+
+extern "C" {
+
+int vps_server_create(size_t memory_budget, int max_active, int precision, double rtol,
+                      int max_it, vps_server* out) {
+  if (!out) return VPS_EINVAL;
+  *out = nullptr;
+  if (memory_budget == 0 || max_active < 1 || max_active > 1024 ||
+      (precision != VPS_FP32 && precision != VPS_FP64) || !(rtol > 0.0) || max_it < 1) {
+    vps::set_thread_error("vps_server_create: invalid argument");
+    return VPS_EINVAL;
+  }
+  auto* s = new vps_server_ctx();
+  s->budget = memory_budget;
+  s->max_active = max_active;
+  s->precision = precision;
+  s->rtol = rtol;
+  s->max_it = max_it;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    vps::set_thread_error("vps_server_create: no CUDA device");
+    return VPS_ECUDA;
+  }
+  s->engine = std::thread([s] { s->run(); });
+  *out = s;
+  return VPS_OK;
+}
+
+int vps_server_submit(vps_server s, int dim, int degree, int level, int n_modes,
+                      const double* coef, const int* freq, double* x_out, int64_t* id) {
+  if (!s || !id || n_modes < 1 || n_modes > 4096 || !coef || !freq || (dim != 2 && dim != 3) ||
+      degree < 1 || degree > VPS_MAX_DEGREE || level < 1 || level > 24)
+    return VPS_EINVAL;
+  Request r;
+  r.d = dim;
+  r.k = degree;
+  r.L = level;
+  r.coef.assign(coef, coef + n_modes);
+  r.freq.assign(freq, freq + n_modes * dim);
+  r.x_out = x_out;
+  const int64_t ni = (int64_t)degree * (1 << level) - 1;
+  r.n = dim == 3 ? ni * ni * ni : ni * ni;
+  std::lock_guard<std::mutex> lock(s->mu);
+  r.id = s->next_id++;
+  r.t_submit = now_s();
+  *id = r.id;
+  s->reqs[r.id] = std::move(r);
+  s->queue.push_back(*id);
+  s->cv.notify_all();
+  return VPS_OK;
+}
+
+int vps_server_query(vps_server s, int64_t id, int* state, int* status, int* iters,
+                     double* rel_res, double* queue_s, double* latency_s) {
+  if (!s) return VPS_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return VPS_EINVAL;
+  const Request& r = it->second;
+  if (state) *state = r.state;
+  if (status) *status = r.status;
+  if (iters) *iters = r.iters;
+  if (rel_res) *rel_res = r.rel;
+  const bool started = r.state != VPS_REQ_QUEUED;
+  const bool ended = r.state == VPS_REQ_DONE || r.state == VPS_REQ_FAILED;
+  if (queue_s) *queue_s = started ? r.t_start - r.t_submit : -1.0;
+  if (latency_s) *latency_s = ended ? r.t_done - r.t_submit : -1.0;
+  return VPS_OK;
+}
+
+int vps_server_wait(vps_server s, int64_t id, double timeout_s) {
+  if (!s) return VPS_EINVAL;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto ready = [&] {
+    if (id == 0) return s->n_done == s->next_id - 1;
+    auto it = s->reqs.find(id);
+    return it == s->reqs.end() || it->second.state == VPS_REQ_DONE ||
+           it->second.state == VPS_REQ_FAILED;
+  };
+  if (!s->cv.wait_for(lock, std::chrono::duration<double>(timeout_s), ready)) return VPS_ETIMEOUT;
+  return VPS_OK;
+}
+
+int vps_server_stats(vps_server s, int64_t* submitted, int64_t* done, int* active, int* queued) {
+  if (!s) return VPS_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (submitted) *submitted = s->next_id - 1;
+  if (done) *done = s->n_done;
+  if (active) *active = s->active;
+  if (queued) *queued = (int)s->queue.size();
+  return VPS_OK;
+}
+
+const char* vps_server_last_error(vps_server s) { return s ? s->err.c_str() : ""; }
+
+int vps_server_destroy(vps_server s) {
+  if (!s) return VPS_OK;
+  s->stop.store(true);
+  s->cv.notify_all();
+  if (s->engine.joinable()) s->engine.join();
+  for (Slot& sl : s->slots) vps_destroy(sl.h);
+  delete s;
+  return VPS_OK;
+}
+
+}  // extern "C"

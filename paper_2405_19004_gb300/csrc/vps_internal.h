@@ -11,6 +11,8 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+struct vps_context;
+
 namespace vps {
 
 constexpr int kMaxK = 7;
@@ -181,5 +183,15 @@ cudaError_t launch_rhs_tensor(const LevelGeom& g, int n_modes, const double* b1d
 // per-cell squared L2 error contributions of u_h - prod sin(pi x) -> partial sums
 cudaError_t launch_l2_error_sine(const LevelGeom& g, const double* xlev, const double* tab,
                                  int q, double* partial, double* out, cudaStream_t s);
+
+// Serving support (api.cpp): a handle on a stream of its own, a device-memory
+// estimate for admission, and a CG solve advanced without blocking.
+int create_own_stream(int dim, int degree, int level, int precision, vps_context** out);
+size_t estimate_device_bytes(int dim, int degree, int level, int precision);
+int cg_async_begin(vps_context* h, int n_modes, const double* coef, const int* freq, double rtol,
+                   int max_it);
+int cg_async_poll(vps_context* h, int* done, int* status, int* iters, double* rel,
+                  const double** x_host);
+const char* handle_error(vps_context* h);
 
 }  // namespace vps
