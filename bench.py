@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64 / additive side measurements")
+    p.add_argument("--serving-requests", type=int, default=512,
+                   help="requests of the serving measurement (0: skip it)")
     p.add_argument("--tune-cache", default=None,
                    help="autotuner cache file (reused when it holds this workload)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
@@ -133,6 +135,35 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- serving
+def run_serving(vps, n_requests, precision, max_active, budget):
+    """Replays a seeded Poisson-arrival stream of solve requests in real time."""
+    from synthetic import request_stream
+    reqs = request_stream(n_requests, 200.0, seed=5)
+    srv = vps.Server(budget, max_active=max_active, precision=precision, rtol=RTOL, max_it=200)
+    ids, dofs = [], []
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = t0 + r["t_arrival"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        rid, x = srv.submit(r["d"], r["k"], r["level"], r["coef"], r["freq"])
+        ids.append(rid)
+        dofs.append(len(x))
+    srv.wait(0, 3600)
+    t_end = time.perf_counter()
+    info = [srv.query(i) for i in ids]
+    srv.close()
+    lat = sorted(q["latency_s"] for q in info)
+    ok = sum(q["state"] == vps.VPS_REQ_DONE for q in info)
+    pct = lambda p: lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+    span = t_end - t0
+    return {"requests": len(ids), "completed": ok, "p50_latency_s": pct(50), "p99_latency_s": pct(99),
+            "mean_latency_s": sum(lat) / len(lat), "span_s": span,
+            "throughput_req_per_s": len(ids) / span, "throughput_dof_per_s": sum(dofs) / span,
+            "max_active": max_active}
 
 
 # ---------------------------------------------------------------- clocks
@@ -354,6 +385,15 @@ def main():
                 add[f"omega_{om:g}"] = {"status": str(e).split(":")[0]}
             Pa.close()
         extras["additive_fp32_mg"] = add
+
+    if not args.no_extras and rank == 0 and args.serving_requests > 0:
+        budget = 48 << 30
+        extras["serving"] = {
+            "workload": f"{args.serving_requests} requests, Poisson arrivals 200/s, d in {{2,3}}, "
+                        "k in 2..6, levels with 1e4..2e7 DoFs, 4 sine modes, seed 5, CG to 1e-10",
+            "fp32_mg_batched": run_serving(vps, args.serving_requests, vps.VPS_FP32, 16, budget),
+            "fp64_one_at_a_time": run_serving(vps, args.serving_requests, vps.VPS_FP64, 1, budget),
+        }
 
     if rank != 0:
         if dist is not None:
