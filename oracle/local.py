@@ -10,7 +10,8 @@ cells of the support).  This gives
                         (Eq. 2.5/2.6, equivalently the localised form of
                         Section 2.2 that only reads the patch closure);
 * ``apply_rows``     -- (A x)_i for chosen nodes i;
-* ``prolongate_rows``-- (I^up x_c)_i for chosen fine nodes i.
+* ``prolongate_rows``-- (I^up x_c)_i for chosen fine nodes i;
+* ``restrict_rows``  -- ((I^up)^T r_f)_j for chosen coarse nodes j.
 
 Inputs are full-grid vectors of a level (n1^d values, boundary entries 0).
 The tests pin each function against the globally assembled oracle at small
@@ -130,4 +131,47 @@ def prolongate_rows(fine, xc_full, nodes):
             val *= V[Lc[:, t]]
             gi += (k * c + Lc[:, t]) * coarse.n1 ** t
         out[r] = val @ xc_full[gi]
+    return out
+
+
+def restrict_rows(fine, rf_full, coarse_nodes):
+    """((I^up)^T r_f)_j at coarse full-grid nodes j: sum over the fine support
+    points i inside the support of coarse basis function j of phi_j(x_i) r_i."""
+    d, k = fine.d, fine.k
+    coarse = fe.Level(d, k, fine.l - 1)
+    H = coarse.h
+    xf1 = fine.node_coords_1d()
+    out = np.zeros(len(coarse_nodes))
+    for r, j in enumerate(coarse_nodes):
+        # per direction: fine nodes in the coarse cells touching node j, and phi_j there
+        idx, wts = [], []
+        for t in range(d):
+            cells = []
+            if j[t] % k == 0:
+                if j[t] // k - 1 >= 0:
+                    cells.append(j[t] // k - 1)
+                if j[t] // k < coarse.ncell:
+                    cells.append(j[t] // k)
+            else:
+                cells.append(j[t] // k)
+            g = sorted(set(f for c in cells for f in range(2 * k * c, 2 * k * (c + 1) + 1)))
+            w = []
+            for f in g:
+                x = xf1[f]
+                c = min(int(np.floor(x / H)), coarse.ncell - 1)
+                if c not in cells:  # a shared endpoint evaluated in the other cell
+                    c = cells[-1] if x >= cells[-1] * H else cells[0]
+                loc = j[t] - k * c
+                w.append(fe.lagrange_values(coarse.z, [(x - c * H) / H])[loc, 0] if 0 <= loc <= k else 0.0)
+            idx.append(np.array(g))
+            wts.append(np.array(w))
+        acc = 0.0
+        grids = np.meshgrid(*[np.arange(len(i)) for i in idx], indexing="ij")
+        for combo in zip(*[gg.ravel() for gg in grids]):
+            w = np.prod([wts[t][combo[t]] for t in range(d)])
+            if w == 0.0:
+                continue
+            f = sum(idx[t][combo[t]] * fine.n1 ** t for t in range(d))
+            acc += w * rf_full[f]
+        out[r] = acc
     return out

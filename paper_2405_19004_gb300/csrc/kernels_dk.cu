@@ -94,10 +94,23 @@ struct SmoothCfg {
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
   // tM, tA | U, W (3D) or R (2D) | b interior | x interior   (elements)
   static constexpr size_t elems_mult = (size_t)2 * P * S0 + (size_t)nU * P * sizeU + 2 * P * md;
-  static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
-  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md) + sizeof(int) * P;
+  // ... | eigenvalue table (md) | patch origins
+  static constexpr size_t smem_mult = sizeof(T) * (elems_mult + md) + sizeof(int) * P;
+  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md + md) + sizeof(int) * P;
   static constexpr bool fits = smem_mult <= 227 * 1024;
 };
+
+// Calls f(t) for every line t = threadIdx.x + r * NT < TOTAL, with the
+// rounds r unrolled at compile time (no loop control per line).
+template <int TOTAL, int NT, class F>
+__device__ __forceinline__ void for_lines(F&& f) {
+  constexpr int R = (TOTAL + NT - 1) / NT;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = (int)threadIdx.x + r * NT;
+    if (TOTAL % NT == 0 || t < TOTAL) f(t);
+  }
+}
 
 // Offset of the first closure node of patch gp of a colour (int: every
 // level vector holds fewer than 2^31 elements).
@@ -145,8 +158,7 @@ template <typename T, int P, int NT, int MODE>
 __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict__ out,
                                          const T* __restrict__ inv_lam) {
   constexpr int NL = DIM == 3 ? m * m : m;
-  const DevTab<T>& tb = c_tab<T>;
-  for (int t = threadIdx.x; t < P * NL; t += NT) {
+  for_lines<P * NL, NT>([&](const int t) {
     const int p = t % P, L = t / P;
     T v[m];
 #pragma unroll
@@ -155,11 +167,11 @@ __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict
     for (int o = 0; o < m; ++o) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(MODE == 2 ? tb.S[o * m + c] : tb.S[c * m + o], v[c], acc);
-      if (MODE == 1) acc *= __ldg(inv_lam + L * m + o);
+      for (int c = 0; c < m; ++c) acc = fma(MODE == 2 ? c_tab<T>.S[o * m + c] : c_tab<T>.S[c * m + o], v[c], acc);
+      if (MODE == 1) acc *= inv_lam[L * m + o];
       out[(L * m + o) * P + p] = acc;
     }
-  }
+  });
 }
 
 // Back-transformation S (x) S (x) S of the scaled coefficients in X0 and the
@@ -170,7 +182,6 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
                                                        const T* xs, const int* s_org, int px,
                                                        int pz, T scale) {
   constexpr int NL = DIM == 3 ? m * m : m;
-  const DevTab<T>& tb = c_tab<T>;
   const T* last_in;
   if constexpr (DIM == 3) {
     fd_stage<T, P, NT, 2>(X0, X1, nullptr);
@@ -183,10 +194,10 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
     __syncthreads();
     last_in = X1;
   }
-  for (int t = threadIdx.x; t < P * NL; t += NT) {
+  for_lines<P * NL, NT>([&](const int t) {
     const int p = t % P, L = t / P;
     const int org = s_org[p];
-    if (org < 0) continue;
+    if (org < 0) return;
     T v[m];
 #pragma unroll
     for (int c = 0; c < m; ++c) v[c] = last_in[(c * NL + L) * P + p];
@@ -202,11 +213,11 @@ __device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restri
     for (int o = 0; o < m; ++o) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(tb.S[o * m + c], v[c], acc);
+      for (int c = 0; c < m; ++c) acc = fma(c_tab<T>.S[o * m + c], v[c], acc);
       const T base = xs ? xs[(L * m + o) * P + p] : dst[o];
       dst[o] = fma(scale, acc, base);
     }
-  }
+  });
 }
 
 // ------------------------------------------------------- multiplicative
@@ -216,15 +227,16 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
                    int px, int pz, ColourGeom cg, T bscale) {
   using C = SmoothCfg<T, PP>;
   constexpr int P = C::P, NT = C::NT, S0 = C::S0, MD = C::md;
-  const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tM = reinterpret_cast<T*>(smem_raw);
   T* tA = tM + P * S0;
   T* U = tA + P * S0;                       // 3D: U, W; 2D: R
   T* bI = U + C::nU * P * C::sizeU;         // interior of b, interleaved [z][y][x][p]
   T* xI = bI + P * MD;                      // interior of x, interleaved
-  int* s_org = reinterpret_cast<int*>(xI + P * MD);
+  T* il = xI + P * MD;                      // 1/(sum of eigenvalues)
+  int* s_org = reinterpret_cast<int*>(il + MD);
   load_origins<P>(s_org, cg, px, pz);
+  for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   load_interior<T, P, NT>(b, s_org, bI, px, pz, bscale);
 
@@ -233,7 +245,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     // Stage 0: lines along z read straight from global memory into
     // registers; tM = M x, tA = A x along z (interior output rows only).
     // The interior values of x are kept for the final update.
-    for (int t = threadIdx.x; t < P * n * n; t += NT) {
+    for_lines<P * n * n, NT>([&](const int t) {
       const int p = t / (n * n), L = t % (n * n);
       const int yy = L / n, xx = L % n;
       const int org = s_org[p];
@@ -257,18 +269,18 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
         T am = T(0), aa = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          am = fma(tb.Mp[o * n + c], v[c], am);
-          aa = fma(tb.Ap[o * n + c], v[c], aa);
+          am = fma(c_tab<T>.Mp[o * n + c], v[c], am);
+          aa = fma(c_tab<T>.Ap[o * n + c], v[c], aa);
         }
         dM[o] = am;
         dA[o] = aa;
       }
-    }
+    });
     __syncthreads();
     // Stage 1: along y.  U = M (M x), W = A (M x) + M (A x)  (the inner sum
     // M x along z is shared by two terms, Section 3.1.1).
     constexpr int NL1 = n * m;
-    for (int t = threadIdx.x; t < P * NL1; t += NT) {
+    for_lines<P * NL1, NT>([&](const int t) {
       const int p = t % P, L = t / P;
       const T* sM = tM + p * S0 + L;
       const T* sA = tA + p * S0 + L;
@@ -283,19 +295,19 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
         T u = T(0), w = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          u = fma(tb.Mp[o * n + c], vm[c], u);
-          w = fma(tb.Ap[o * n + c], vm[c], w);
-          w = fma(tb.Mp[o * n + c], va[c], w);
+          u = fma(c_tab<T>.Mp[o * n + c], vm[c], u);
+          w = fma(c_tab<T>.Ap[o * n + c], vm[c], w);
+          w = fma(c_tab<T>.Mp[o * n + c], va[c], w);
         }
         U[(L * m + o) * P + p] = u;
         W[(L * m + o) * P + p] = w;
       }
-    }
+    });
     __syncthreads();
     // Stage 2: along x.  r = bscale * b - (A U + M W) on the interior.
     constexpr int NL2 = m * m;
     T* R = tM;
-    for (int t = threadIdx.x; t < P * NL2; t += NT) {
+    for_lines<P * NL2, NT>([&](const int t) {
       const int p = t % P, L = t / P;
       T vu[n], vw[n];
 #pragma unroll
@@ -305,27 +317,27 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = bI[(L * m + o) * P + p];
+        T acc = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          acc = fma(-tb.Ap[o * n + c], vu[c], acc);
-          acc = fma(-tb.Mp[o * n + c], vw[c], acc);
+          acc = fma(c_tab<T>.Ap[o * n + c], vu[c], acc);
+          acc = fma(c_tab<T>.Mp[o * n + c], vw[c], acc);
         }
-        R[(L * m + o) * P + p] = acc;
+        R[(L * m + o) * P + p] = bI[(L * m + o) * P + p] - acc;
       }
-    }
+    });
     __syncthreads();
     // Fast diagonalisation: S^T along z, y, x (scaled), then S back.
     fd_stage<T, P, NT, 0>(tM, tA, nullptr);
     __syncthreads();
     fd_stage<T, P, NT, 0>(tA, tM, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(tM, tA, inv_lam);
+    fd_stage<T, P, NT, 1>(tM, tA, il);
     __syncthreads();
     fd_backward_and_update<T, P, NT>(tA, tM, x, xI, s_org, px, pz, T(1));
   } else {
     // 2D.  Stage 0: lines along y from global; tM = M x, tA = A x along y.
-    for (int t = threadIdx.x; t < P * n; t += NT) {
+    for_lines<P * n, NT>([&](const int t) {
       const int p = t / n, L = t % n;
       const int org = s_org[p];
       T v[n];
@@ -348,17 +360,17 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
         T am = T(0), aa = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          am = fma(tb.Mp[o * n + c], v[c], am);
-          aa = fma(tb.Ap[o * n + c], v[c], aa);
+          am = fma(c_tab<T>.Mp[o * n + c], v[c], am);
+          aa = fma(c_tab<T>.Ap[o * n + c], v[c], aa);
         }
         dM[o] = am;
         dA[o] = aa;
       }
-    }
+    });
     __syncthreads();
     // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior.
     T* R = U;
-    for (int t = threadIdx.x; t < P * m; t += NT) {
+    for_lines<P * m, NT>([&](const int t) {
       const int p = t % P, L = t / P;
       const T* sM = tM + p * S0 + L;
       const T* sA = tA + p * S0 + L;
@@ -370,21 +382,21 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = bI[(L * m + o) * P + p];
+        T acc = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          acc = fma(-tb.Ap[o * n + c], vm[c], acc);
-          acc = fma(-tb.Mp[o * n + c], va[c], acc);
+          acc = fma(c_tab<T>.Ap[o * n + c], vm[c], acc);
+          acc = fma(c_tab<T>.Mp[o * n + c], va[c], acc);
         }
-        R[(L * m + o) * P + p] = acc;
+        R[(L * m + o) * P + p] = bI[(L * m + o) * P + p] - acc;
       }
-    }
+    });
     __syncthreads();
     T* X0 = R;
     T* X1 = tM;  // tM/tA are free now; P*S0 >= P*m*m
     fd_stage<T, P, NT, 0>(X0, X1, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
+    fd_stage<T, P, NT, 1>(X1, X0, il);
     __syncthreads();
     fd_backward_and_update<T, P, NT>(X0, X1, x, xI, s_org, px, pz, T(1));
   }
@@ -398,16 +410,17 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
                   int px, int pz, ColourGeom cg, T scale) {
   using C = SmoothCfg<T, PP>;
   constexpr int P = C::P, NT = C::NT, MD = C::md;
-  const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X0 = reinterpret_cast<T*>(smem_raw);
   T* X1 = X0 + P * MD;
-  int* s_org = reinterpret_cast<int*>(X1 + P * MD);
+  T* il = X1 + P * MD;
+  int* s_org = reinterpret_cast<int*>(il + MD);
   load_origins<P>(s_org, cg, px, pz);
+  for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   constexpr int NL = DIM == 3 ? m * m : m;
   // first S^T contraction reads the interior residual lines from global
-  for (int t = threadIdx.x; t < P * NL; t += NT) {
+  for_lines<P * NL, NT>([&](const int t) {
     const int p = t % P, L = t / P;
     const int org = s_org[p];
     T v[m];
@@ -430,19 +443,19 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
     for (int o = 0; o < m; ++o) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(tb.S[c * m + o], v[c], acc);
+      for (int c = 0; c < m; ++c) acc = fma(c_tab<T>.S[c * m + o], v[c], acc);
       X1[(L * m + o) * P + p] = acc;
     }
-  }
+  });
   __syncthreads();
   if constexpr (DIM == 3) {
     fd_stage<T, P, NT, 0>(X1, X0, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(X0, X1, inv_lam);
+    fd_stage<T, P, NT, 1>(X0, X1, il);
     __syncthreads();
     fd_backward_and_update<T, P, NT>(X1, X0, x, nullptr, s_org, px, pz, scale);
   } else {
-    fd_stage<T, P, NT, 1>(X1, X0, inv_lam);
+    fd_stage<T, P, NT, 1>(X1, X0, il);
     __syncthreads();
     fd_backward_and_update<T, P, NT>(X0, X1, x, nullptr, s_org, px, pz, scale);
   }
@@ -482,7 +495,6 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
              int64_t px, int64_t pz, T scale) {
   using C = ApplyCfg;
   constexpr int TN = C::TN, BN = C::BN, RB = C::RB, CT = C::CT, NT = C::NT;
-  const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tm = reinterpret_cast<T*>(smem_raw);
   T* tk = tm + C::a_sz;
@@ -506,8 +518,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int q = 0; q < K; ++q) {
         T am = T(0), ak = T(0);
         VPS_BAND_LOOP(q, j) {
-          am = fma(tb.Mb[q * n + j], v[q + j], am);
-          ak = fma(tb.Kb[q * n + j], v[q + j], ak);
+          am = fma(c_tab<T>.Mb[q * n + j], v[q + j], am);
+          ak = fma(c_tab<T>.Kb[q * n + j], v[q + j], ak);
         }
         tm[((cz * K + q) * BN + yy) * RB + xx] = am;
         tk[((cz * K + q) * BN + yy) * RB + xx] = ak;
@@ -527,9 +539,9 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int q = 0; q < K; ++q) {
         T a = T(0), bb = T(0);
         VPS_BAND_LOOP(q, j) {
-          a = fma(tb.Mb[q * n + j], vm[q + j], a);
-          bb = fma(tb.Kb[q * n + j], vm[q + j], bb);
-          bb = fma(tb.Mb[q * n + j], vk[q + j], bb);
+          a = fma(c_tab<T>.Mb[q * n + j], vm[q + j], a);
+          bb = fma(c_tab<T>.Kb[q * n + j], vm[q + j], bb);
+          bb = fma(c_tab<T>.Mb[q * n + j], vk[q + j], bb);
         }
         mm[(Z * TN + cy * K + q) * RB + xx] = a;
         ww[(Z * TN + cy * K + q) * RB + xx] = bb;
@@ -555,8 +567,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
         if (gx >= n1) continue;
         T acc = T(0);
         VPS_BAND_LOOP(q, j) {
-          acc = fma(tb.Kb[q * n + j], vm[q + j], acc);
-          acc = fma(tb.Mb[q * n + j], vw[q + j], acc);
+          acc = fma(c_tab<T>.Kb[q * n + j], vm[q + j], acc);
+          acc = fma(c_tab<T>.Mb[q * n + j], vw[q + j], acc);
         }
         T out = T(0);
         if (inner_yz && gx >= 1 && gx <= n1 - 2)
@@ -579,8 +591,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int q = 0; q < K; ++q) {
         T am = T(0), ak = T(0);
         VPS_BAND_LOOP(q, j) {
-          am = fma(tb.Mb[q * n + j], v[q + j], am);
-          ak = fma(tb.Kb[q * n + j], v[q + j], ak);
+          am = fma(c_tab<T>.Mb[q * n + j], v[q + j], am);
+          ak = fma(c_tab<T>.Kb[q * n + j], v[q + j], ak);
         }
         tm[(cy * K + q) * RB + xx] = am;
         tk[(cy * K + q) * RB + xx] = ak;
@@ -605,8 +617,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
         if (gx >= n1) continue;
         T acc = T(0);
         VPS_BAND_LOOP(q, j) {
-          acc = fma(tb.Kb[q * n + j], vm[q + j], acc);
-          acc = fma(tb.Mb[q * n + j], vk[q + j], acc);
+          acc = fma(c_tab<T>.Kb[q * n + j], vm[q + j], acc);
+          acc = fma(c_tab<T>.Mb[q * n + j], vk[q + j], acc);
         }
         T out = T(0);
         if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2)
@@ -650,7 +662,6 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
               int px, int pz, T scale) {
   using C = Apply3Cfg;
   constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
-  const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* zbuf = reinterpret_cast<T*>(smem_raw);  // [2][2][BX][RB]: (m, k) x double buffer
   T* MM = zbuf + 4 * BX * RB;                // [TX][RB]
@@ -675,8 +686,8 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
           VPS_BAND_LOOP(q, j) {
             const int gz = z - K + j;
             const T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
-            am = fma(tb.Mb[q * n + j], v, am);
-            ak = fma(tb.Kb[q * n + j], v, ak);
+            am = fma(c_tab<T>.Mb[q * n + j], v, am);
+            ak = fma(c_tab<T>.Kb[q * n + j], v, ak);
           }
         }
         mZ[yy * RB + xx] = am;
@@ -696,9 +707,9 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
         for (int qy = 0; qy < K; ++qy) {
           T a = T(0), bb = T(0);
           VPS_BAND_LOOP(qy, j) {
-            a = fma(tb.Mb[qy * n + j], vm[qy + j], a);
-            bb = fma(tb.Kb[qy * n + j], vm[qy + j], bb);
-            bb = fma(tb.Mb[qy * n + j], vk[qy + j], bb);
+            a = fma(c_tab<T>.Mb[qy * n + j], vm[qy + j], a);
+            bb = fma(c_tab<T>.Kb[qy * n + j], vm[qy + j], bb);
+            bb = fma(c_tab<T>.Mb[qy * n + j], vk[qy + j], bb);
           }
           MM[(cy * K + qy) * RB + xx] = a;
           WW[(cy * K + qy) * RB + xx] = bb;
@@ -725,8 +736,8 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
           if (gx >= n1) continue;
           T acc = T(0);
           VPS_BAND_LOOP(qx, j) {
-            acc = fma(tb.Kb[qx * n + j], vm[qx + j], acc);
-            acc = fma(tb.Mb[qx * n + j], vw[qx + j], acc);
+            acc = fma(c_tab<T>.Kb[qx * n + j], vm[qx + j], acc);
+            acc = fma(c_tab<T>.Mb[qx * n + j], vw[qx + j], acc);
           }
           T out = T(0);
           if (inner_yz && gx >= 1 && gx <= n1 - 2)
@@ -771,7 +782,6 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
                    int64_t pzc, int n1f, int64_t pxf, int64_t pzf) {
   using C = TransferCfg;
   constexpr int CB = C::CB, CBp = C::CBp, FB = C::FB, CC = C::CC, NT = C::NT;
-  const DevTab<T>& tb = c_tab<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t1 = reinterpret_cast<T*>(smem_raw);
   const int cx0 = blockIdx.x * CC, cy0 = blockIdx.y * CC;
@@ -793,7 +803,7 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
       for (int s = 0; s < 2 * K; ++s) {
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
         t1[((2 * K * cz + s) * CB + yy) * CBp + xx] = acc;
       }
     }
@@ -808,7 +818,7 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
       for (int s = 0; s < 2 * K; ++s) {
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
         t2[(Z * FB + 2 * K * cy + s) * CBp + xx] = acc;
       }
     }
@@ -828,7 +838,7 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
         if (gx < 1 || gx > n1f - 2) continue;
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
         dst[gx] += acc;
       }
     }
@@ -847,7 +857,7 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
       for (int s = 0; s < 2 * K; ++s) {
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
         t1[(2 * K * cy + s) * CBp + xx] = acc;
       }
     }
@@ -866,7 +876,7 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
         if (gx < 1 || gx > n1f - 2) continue;
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(tb.P1[s * nl + i], v[i], acc);
+        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
         dst[gx] += acc;
       }
     }
@@ -881,15 +891,14 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
 // v holds the 4K+1 fine values of cells C-1 and C.
 template <typename T>
 __device__ __forceinline__ void restrict_1d(const T (&v)[4 * K + 1], T (&out)[K]) {
-  const DevTab<T>& tb = c_tab<T>;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     T acc = T(0);
 #pragma unroll
-    for (int s = 0; s <= 2 * K; ++s) acc = fma(tb.P1[s * nl + i], v[2 * K + s], acc);
+    for (int s = 0; s <= 2 * K; ++s) acc = fma(c_tab<T>.P1[s * nl + i], v[2 * K + s], acc);
     if (i == 0) {
 #pragma unroll
-      for (int s = 0; s < 2 * K; ++s) acc = fma(tb.P1[s * nl + K], v[s], acc);
+      for (int s = 0; s < 2 * K; ++s) acc = fma(c_tab<T>.P1[s * nl + K], v[s], acc);
     }
     out[i] = acc;
   }

@@ -56,3 +56,16 @@ def test_prolongate_rows_equals_global_prolongation(d, k, l):
     pick = rng.choice(fine.N, size=30, replace=False)
     got = local.prolongate_rows(fine, _full(coarse, xc), Q[pick] + 1)
     np.testing.assert_allclose(got, y[pick], atol=1e-13)
+
+
+@pytest.mark.parametrize("d,k,l", [(2, 3, 3), (3, 2, 3), (2, 1, 4)])
+def test_restrict_rows_equals_global_restriction(d, k, l):
+    fine, coarse = fe.Level(d, k, l), fe.Level(d, k, l - 1)
+    P = assembly.prolongation(fine)
+    rng = np.random.default_rng(10)
+    rf = rng.normal(size=fine.N)
+    y = P.T @ rf
+    Q = fe.multi_indices(coarse.ni, d)
+    pick = rng.choice(coarse.N, size=min(30, coarse.N), replace=False)
+    got = local.restrict_rows(fine, _full(fine, rf), Q[pick] + 1)
+    np.testing.assert_allclose(got, y[pick], atol=1e-13)
