@@ -198,6 +198,8 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   const int nc = 1 << h->dim;
   const T* il = static_cast<const T*>(h->inv_lam);
   const int v = h->smooth_var[l];
+  if (!fns<T>(h).smooth_mult_v[v] || !fns<T>(h).smooth_add_v[v])
+    return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
   if (h->smoother == VPS_ADDITIVE) {
     T* r = static_cast<T*>(h->rv[l]);
     VPS_CK(h, fns<T>(h).apply(g, x, b, r, h->stream));
@@ -809,8 +811,10 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     }
   }
   int rc;
+  const bool mid_ok = precision == VPS_FP64 ? h->ks->d.smooth_mult_v[1] != nullptr
+                                             : h->ks->f.smooth_mult_v[1] != nullptr;
   for (int l = 1; l <= level; ++l) {
-    h->smooth_var[l] = 1;
+    h->smooth_var[l] = mid_ok ? 1 : 0;
     h->geom[l] = make_geom(dim, degree, l);
     const size_t vb = (size_t)h->geom[l].total * h->esz;
     if ((rc = dalloc(h, &h->bv[l], vb)) || (rc = dalloc(h, &h->xv[l], vb)) ||
@@ -962,6 +966,7 @@ int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* 
   LaunchTally tally(h);
   const LevelGeom& g = h->geom[level];
   const int v = h->smooth_var[level];
+  if (!variant_ok(h, v)) return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
   if (h->prec == VPS_FP64)
     VPS_CK(h, h->ks->d.smooth_mult_v[v](g, make_colour(g, colour), (const double*)b, (double*)x,
                                         (const double*)h->inv_lam, h->stream));

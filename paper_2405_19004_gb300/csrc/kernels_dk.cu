@@ -63,41 +63,43 @@ template <typename T>
 __constant__ DevTab<T> c_tab;
 
 // ---------------------------------------------------------------- config
-// Patches per block of the middle smoother variant (a power of two).
-constexpr int kPBase = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 8 : K == 3 ? 4 : K <= 5 ? 2 : 1)
-                                : (K <= 3 ? 32 : 16);
-// The autotuner chooses among P = kPBase/2, kPBase, 2 kPBase.
-constexpr int kVarP[kSmoothVariants] = {kPBase / 2 > 0 ? kPBase / 2 : 1, kPBase, 2 * kPBase};
+// ------------------------------------------------------------- smoother
+// A block holds P = G * Q patches.  In every contraction stage thread t
+// handles line L = t / G of the Q patches g*Q .. g*Q+Q-1 (g = t % G): each
+// coefficient (constant memory) and each address is shared by Q FMAs, and
+// the Q values of a tensor entry are adjacent in shared memory (patch index
+// fastest), so they move as one vector access.  With G and Q powers of two
+// and the odd extents 2k+-1, every warp access is free of bank conflicts.
+// The autotuner chooses Q among kVarQ; G is fixed per (dim, degree) so that
+// a block has enough lines to fill its warps.
+constexpr int kLinesMax = DIM == 3 ? n * n : n;
+constexpr int kG = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 4 : K == 3 ? 2 : 1)
+                            : (K <= 2 ? 32 : (K <= 4 ? 16 : 8));
+constexpr int kVarQ[kSmoothVariants] = {1, 2, 4};
 
-template <typename T, int P_>
+template <class T, int Q>
+struct alignas(sizeof(T) * Q) Pack {
+  T v[Q];
+};
+
+template <typename T, int Q_>
 struct SmoothCfg {
-  static constexpr int P = P_;   // patches per block (power of two)
-  static constexpr int lines0 = DIM == 3 ? n * n : n;
-  static constexpr int NT0 = ((P * lines0 + 31) / 32) * 32;
-  static constexpr int NT = NT0 > 512 ? 512 : NT0;
-  // blocks per SM the register allocation is sized for: about 40 registers
-  // per thread for FP32 and 64 for FP64 up to k = 4; the k >= 5 stages hold
-  // 2(2k+1) + 2(2k-1) values per thread and get 80 / 128
-  static constexpr int RESIDENT = K >= 5 ? (sizeof(T) == 4 ? 768 : 512)
-                                         : (sizeof(T) == 4 ? 1536 : 1024);
-  static constexpr int MINB = RESIDENT / NT > 8 ? 8 : (RESIDENT / NT < 1 ? 1 : RESIDENT / NT);
-  static constexpr int NB = 128 / (int)sizeof(T);  // word-banks per wavefront
-  // patch-major stride of the first stage's output, chosen so that the
-  // next stage (patch index fastest) hits distinct bank groups:
-  // S0 = NB/P (mod NB) for P < NB, S0 = 1 (mod NB) otherwise
-  static constexpr int size0 = DIM == 3 ? n * n * m : n * m;
-  static constexpr int want0 = P >= NB ? 1 : NB / P;
-  static constexpr int S0 = P == 1 ? size0 : size0 + (((want0 - size0) % NB) + NB) % NB;
-  // stage-1 outputs: U and W in 3D, the residual R in 2D
-  static constexpr int sizeU = DIM == 3 ? n * m * m : m * m;
-  static constexpr int nU = DIM == 3 ? 2 : 1;
+  static constexpr int G = kG, Q = Q_, P = G * Q;
+  static constexpr int NT0 = ((G * kLinesMax + 31) / 32) * 32;
+  static constexpr int NT = NT0 > 1024 ? 1024 : NT0;
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
-  // tM, tA | U, W (3D) or R (2D) | b interior | x interior   (elements)
-  static constexpr size_t elems_mult = (size_t)2 * P * S0 + (size_t)nU * P * sizeU + 2 * P * md;
-  // ... | eigenvalue table (md) | patch origins
-  static constexpr size_t smem_mult = sizeof(T) * (elems_mult + md) + sizeof(int) * P;
-  static constexpr size_t smem_add = sizeof(T) * (size_t)(2 * P * md + md) + sizeof(int) * P;
-  static constexpr bool fits = smem_mult <= 227 * 1024;
+  // interleaved buffers [..][p] (elements):
+  //   3D: A0, A1 = n n m P (stage-0 outputs, later FD ping-pong),
+  //       B0, B1 = n m m P (stage-1 outputs), bI, xI = md P, il = md
+  //   2D: A0, A1 = n m P, B0 = m m P (residual), bI, xI = md P, il = md
+  static constexpr int sizeA = DIM == 3 ? n * n * m : n * m;
+  static constexpr int sizeB = DIM == 3 ? n * m * m : m * m;
+  static constexpr int nB = DIM == 3 ? 2 : 1;
+  static constexpr size_t elems_mult =
+      (size_t)P * (2 * sizeA + nB * sizeB + 2 * md) + md;
+  static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
+  static constexpr size_t smem_add = sizeof(T) * ((size_t)P * 2 * md + md) + sizeof(int) * P;
+  static constexpr bool fits = smem_mult <= 227 * 1024 && G * kLinesMax <= 1024;
 };
 
 // Calls f(t) for every line t = threadIdx.x + r * NT < TOTAL, with the
@@ -134,282 +136,403 @@ __device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, i
   }
 }
 
-// Interior values (m^d per patch) of a level vector into the interleaved
-// layout [z][y][x][p], multiplied by `scale`.  Rows are read contiguously.
-template <typename T, int P, int NT>
-__device__ __forceinline__ void load_interior(const T* __restrict__ src, const int* s_org, T* dst,
-                                              int px, int pz, T scale) {
-  constexpr int MD = DIM == 3 ? m * m * m : m * m;
-  for (int e = threadIdx.x; e < P * MD; e += NT) {
-    const int o = e % m, rest = e / m;             // x fastest
-    const int yy = rest % m;
-    const int zz = DIM == 3 ? (rest / m) % m : 0;
-    const int p = DIM == 3 ? rest / (m * m) : rest / m;
-    const int org = s_org[p];
-    T v = T(0);
-    if (org >= 0) v = scale * src[org + (DIM == 3 ? (zz + 1) * pz : 0) + (yy + 1) * px + 1 + o];
-    dst[((DIM == 3 ? (zz * m + yy) * m : yy * m) + o) * P + p] = v;
-  }
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Asynchronous element copy global -> shared (cp.async, sizes 4 or 8 bytes).
+template <typename T>
+__device__ __forceinline__ void async_copy(T* dst, const T* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "n"((int)sizeof(T)));
+}
+__device__ __forceinline__ void async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
 // One fast-diagonalisation contraction over interleaved tensors.
-// MODE 0: out = S^T in, MODE 1: out = (S^T in) * inv_lam, MODE 2: out = S in.
-template <typename T, int P, int NT, int MODE>
+// MODE 0: out = S^T in, MODE 1: out = (S^T in) * il, MODE 2: out = S in.
+template <typename T, int G, int Q, int NT, int MODE>
 __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict__ out,
-                                         const T* __restrict__ inv_lam) {
+                                         const T* __restrict__ il) {
   constexpr int NL = DIM == 3 ? m * m : m;
-  for_lines<P * NL, NT>([&](const int t) {
-    const int p = t % P, L = t / P;
-    T v[m];
+  constexpr int P = G * Q;
+  using PK = Pack<T, Q>;
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    const PK* src = reinterpret_cast<const PK*>(in + L * P + g * Q);
+    T v[m][Q];
 #pragma unroll
-    for (int c = 0; c < m; ++c) v[c] = in[(c * NL + L) * P + p];
+    for (int c = 0; c < m; ++c) {
+      const PK pk = src[c * NL * G];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) v[c][j] = pk.v[j];
+    }
+    PK* dst = reinterpret_cast<PK*>(out + L * m * P + g * Q);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      T acc = T(0);
+      T acc[Q];
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(MODE == 2 ? c_tab<T>.S[o * m + c] : c_tab<T>.S[c * m + o], v[c], acc);
-      if (MODE == 1) acc *= inv_lam[L * m + o];
-      out[(L * m + o) * P + p] = acc;
+      for (int j = 0; j < Q; ++j) acc[j] = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const T w = MODE == 2 ? c_tab<T>.S[o * m + c] : c_tab<T>.S[c * m + o];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) acc[j] = fma(w, v[c][j], acc[j]);
+      }
+      PK r;
+      const T sc = MODE == 1 ? il[L * m + o] : T(1);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) r.v[j] = MODE == 1 ? acc[j] * sc : acc[j];
+      dst[o * G] = r;
     }
   });
 }
 
-// Back-transformation S (x) S (x) S of the scaled coefficients in X0 and the
-// final update of the interior: x_I = base_I + scale * u, where base_I is
-// the interior of x staged in shared memory (xs != nullptr) or read from x.
-template <typename T, int P, int NT>
-__device__ __forceinline__ void fd_backward_and_update(T* X0, T* X1, T* __restrict__ x,
-                                                       const T* xs, const int* s_org, int px,
-                                                       int pz, T scale) {
+// S along the last direction and the update of the interior:
+// x_I = base + scale * u, base from the staged xI (xs) or from x itself.
+template <typename T, int G, int Q, int NT>
+__device__ __forceinline__ void fd_final(const T* __restrict__ in, T* __restrict__ x,
+                                         const T* xs, const int* s_org, int px, int pz, T scale) {
   constexpr int NL = DIM == 3 ? m * m : m;
-  const T* last_in;
-  if constexpr (DIM == 3) {
-    fd_stage<T, P, NT, 2>(X0, X1, nullptr);
-    __syncthreads();
-    fd_stage<T, P, NT, 2>(X1, X0, nullptr);
-    __syncthreads();
-    last_in = X0;
-  } else {
-    fd_stage<T, P, NT, 2>(X0, X1, nullptr);
-    __syncthreads();
-    last_in = X1;
-  }
-  for_lines<P * NL, NT>([&](const int t) {
-    const int p = t % P, L = t / P;
-    const int org = s_org[p];
-    if (org < 0) return;
-    T v[m];
+  constexpr int P = G * Q;
+  using PK = Pack<T, Q>;
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    const PK* src = reinterpret_cast<const PK*>(in + L * P + g * Q);
+    T v[m][Q];
 #pragma unroll
-    for (int c = 0; c < m; ++c) v[c] = last_in[(c * NL + L) * P + p];
-    int row;
+    for (int c = 0; c < m; ++c) {
+      const PK pk = src[c * NL * G];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) v[c][j] = pk.v[j];
+    }
+    int rowoff;
     if constexpr (DIM == 3) {
       const int zz = L / m, yy = L % m;
-      row = org + (zz + 1) * pz + (yy + 1) * px + 1;
+      rowoff = (zz + 1) * pz + (yy + 1) * px + 1;
     } else {
-      row = org + (L + 1) * px + 1;
+      rowoff = (L + 1) * px + 1;
     }
-    T* dst = x + row;
+    T u[m][Q];
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(c_tab<T>.S[o * m + c], v[c], acc);
-      const T base = xs ? xs[(L * m + o) * P + p] : dst[o];
-      dst[o] = fma(scale, acc, base);
+      for (int j = 0; j < Q; ++j) u[o][j] = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const T w = c_tab<T>.S[o * m + c];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) u[o][j] = fma(w, v[c][j], u[o][j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int org = s_org[g * Q + j];
+      if (org < 0) continue;
+      T* dst = x + org + rowoff;
+#pragma unroll
+      for (int o = 0; o < m; ++o) {
+        const T base = xs ? xs[(L * m + o) * P + g * Q + j] : dst[o];
+        dst[o] = fma(scale, u[o][j], base);
+      }
+    }
+  });
+}
+
+// Prefetch of the interior of b (scaled later) into the interleaved layout
+// [z][y][x][p] by the threads that consume it in the residual stage.
+template <typename T, int G, int Q, int NT>
+__device__ __forceinline__ void prefetch_b(const T* __restrict__ b, T* bI, const int* s_org,
+                                           int px, int pz) {
+  constexpr int NL = DIM == 3 ? m * m : m;
+  constexpr int P = G * Q;
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    int rowoff;
+    if constexpr (DIM == 3) {
+      rowoff = (L / m + 1) * pz + (L % m + 1) * px + 1;
+    } else {
+      rowoff = (L + 1) * px + 1;
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int org = s_org[g * Q + j];
+      T* d = bI + L * m * P + g * Q + j;
+      if (org >= 0) {
+        const T* srow = b + org + rowoff;
+#pragma unroll
+        for (int o = 0; o < m; ++o) async_copy(d + o * P, srow + o);
+      } else {
+#pragma unroll
+        for (int o = 0; o < m; ++o) d[o * P] = T(0);
+      }
     }
   });
 }
 
 // ------------------------------------------------------- multiplicative
-template <typename T, int PP>
-__global__ void __launch_bounds__(SmoothCfg<T, PP>::NT, SmoothCfg<T, PP>::MINB)
+template <typename T, int QQ>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ>::NT)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
                    int px, int pz, ColourGeom cg, T bscale) {
-  using C = SmoothCfg<T, PP>;
-  constexpr int P = C::P, NT = C::NT, S0 = C::S0, MD = C::md;
+  using C = SmoothCfg<T, QQ>;
+  constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
+  using PK = Pack<T, Q>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tM = reinterpret_cast<T*>(smem_raw);
-  T* tA = tM + P * S0;
-  T* U = tA + P * S0;                       // 3D: U, W; 2D: R
-  T* bI = U + C::nU * P * C::sizeU;         // interior of b, interleaved [z][y][x][p]
-  T* xI = bI + P * MD;                      // interior of x, interleaved
-  T* il = xI + P * MD;                      // 1/(sum of eigenvalues)
+  T* A0 = reinterpret_cast<T*>(smem_raw);
+  T* A1 = A0 + P * C::sizeA;
+  T* B0 = A1 + P * C::sizeA;
+  T* bI = B0 + C::nB * P * C::sizeB;
+  T* xI = bI + P * MD;
+  T* il = xI + P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
   load_origins<P>(s_org, cg, px, pz);
   for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
-  load_interior<T, P, NT>(b, s_org, bI, px, pz, bscale);
+  prefetch_b<T, G, Q, NT>(b, bI, s_org, px, pz);
 
   if constexpr (DIM == 3) {
-    T* W = U + P * C::sizeU;
-    // Stage 0: lines along z read straight from global memory into
-    // registers; tM = M x, tA = A x along z (interior output rows only).
-    // The interior values of x are kept for the final update.
-    for_lines<P * n * n, NT>([&](const int t) {
-      const int p = t / (n * n), L = t % (n * n);
+    T* B1 = B0 + P * C::sizeB;
+    // Stage 0: z-lines of the closure from global memory; M x and A x along
+    // z (interior rows) into [y][x][oz]; the interior of x is kept in xI.
+    for_lines<G * n * n, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
       const int yy = L / n, xx = L % n;
-      const int org = s_org[p];
-      T v[n];
-      if (org >= 0) {
-        const T* src = x + org + yy * px + xx;
+      T v[n][Q];
 #pragma unroll
-        for (int c = 0; c < n; ++c) v[c] = src[c * pz];
-      } else {
+      for (int j = 0; j < Q; ++j) {
+        const int org = s_org[g * Q + j];
+        const T* src = x + (org >= 0 ? org : 0) + yy * px + xx;
 #pragma unroll
-        for (int c = 0; c < n; ++c) v[c] = T(0);
+        for (int c = 0; c < n; ++c) v[c][j] = org >= 0 ? src[c * pz] : T(0);
       }
       if (yy >= 1 && yy <= m && xx >= 1 && xx <= m) {
+        PK* d = reinterpret_cast<PK*>(xI + ((yy - 1) * m + xx - 1) * P + g * Q);
 #pragma unroll
-        for (int c = 1; c <= m; ++c) xI[(((c - 1) * m + yy - 1) * m + xx - 1) * P + p] = v[c];
+        for (int c = 1; c <= m; ++c) {
+          PK pk;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) pk.v[j] = v[c][j];
+          d[(c - 1) * m * m * G] = pk;
+        }
       }
-      T* dM = tM + p * S0 + L * m;
-      T* dA = tA + p * S0 + L * m;
+      PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+      PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T am = T(0), aa = T(0);
+        PK am, aa;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) am.v[j] = aa.v[j] = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          am = fma(c_tab<T>.Mp[o * n + c], v[c], am);
-          aa = fma(c_tab<T>.Ap[o * n + c], v[c], aa);
+          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            am.v[j] = fma(wm, v[c][j], am.v[j]);
+            aa.v[j] = fma(wa, v[c][j], aa.v[j]);
+          }
         }
-        dM[o] = am;
-        dA[o] = aa;
+        dM[o * G] = am;
+        dA[o * G] = aa;
       }
     });
     __syncthreads();
     // Stage 1: along y.  U = M (M x), W = A (M x) + M (A x)  (the inner sum
     // M x along z is shared by two terms, Section 3.1.1).
     constexpr int NL1 = n * m;
-    for_lines<P * NL1, NT>([&](const int t) {
-      const int p = t % P, L = t / P;
-      const T* sM = tM + p * S0 + L;
-      const T* sA = tA + p * S0 + L;
-      T vm[n], va[n];
+    for_lines<G * NL1, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
+      const PK* sM = reinterpret_cast<const PK*>(A0 + L * P + g * Q);
+      const PK* sA = reinterpret_cast<const PK*>(A1 + L * P + g * Q);
+      T vm[n][Q], va[n][Q];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
-        vm[c] = sM[c * NL1];
-        va[c] = sA[c * NL1];
+        const PK a = sM[c * NL1 * G], bb = sA[c * NL1 * G];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          vm[c][j] = a.v[j];
+          va[c][j] = bb.v[j];
+        }
       }
+      PK* dU = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
+      PK* dW = reinterpret_cast<PK*>(B1 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T u = T(0), w = T(0);
+        PK u, w;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) u.v[j] = w.v[j] = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          u = fma(c_tab<T>.Mp[o * n + c], vm[c], u);
-          w = fma(c_tab<T>.Ap[o * n + c], vm[c], w);
-          w = fma(c_tab<T>.Mp[o * n + c], va[c], w);
+          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            u.v[j] = fma(wm, vm[c][j], u.v[j]);
+            w.v[j] = fma(wa, vm[c][j], w.v[j]);
+            w.v[j] = fma(wm, va[c][j], w.v[j]);
+          }
         }
-        U[(L * m + o) * P + p] = u;
-        W[(L * m + o) * P + p] = w;
+        dU[o * G] = u;
+        dW[o * G] = w;
       }
     });
+    async_wait_all();
     __syncthreads();
-    // Stage 2: along x.  r = bscale * b - (A U + M W) on the interior.
+    // Stage 2: along x.  r = bscale * b - (A U + M W) on the interior, into A0.
     constexpr int NL2 = m * m;
-    T* R = tM;
-    for_lines<P * NL2, NT>([&](const int t) {
-      const int p = t % P, L = t / P;
-      T vu[n], vw[n];
+    for_lines<G * NL2, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
+      const PK* sU = reinterpret_cast<const PK*>(B0 + L * P + g * Q);
+      const PK* sW = reinterpret_cast<const PK*>(B1 + L * P + g * Q);
+      T vu[n][Q], vw[n][Q];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
-        vu[c] = U[(c * NL2 + L) * P + p];
-        vw[c] = W[(c * NL2 + L) * P + p];
+        const PK a = sU[c * NL2 * G], bb = sW[c * NL2 * G];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          vu[c][j] = a.v[j];
+          vw[c][j] = bb.v[j];
+        }
       }
+      const PK* sb = reinterpret_cast<const PK*>(bI + L * m * P + g * Q);
+      PK* dR = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = T(0);
+        T acc[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) acc[j] = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          acc = fma(c_tab<T>.Ap[o * n + c], vu[c], acc);
-          acc = fma(c_tab<T>.Mp[o * n + c], vw[c], acc);
+          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            acc[j] = fma(wa, vu[c][j], acc[j]);
+            acc[j] = fma(wm, vw[c][j], acc[j]);
+          }
         }
-        R[(L * m + o) * P + p] = bI[(L * m + o) * P + p] - acc;
+        const PK bv = sb[o * G];
+        PK r;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+        dR[o * G] = r;
       }
     });
     __syncthreads();
     // Fast diagonalisation: S^T along z, y, x (scaled), then S back.
-    fd_stage<T, P, NT, 0>(tM, tA, nullptr);
+    fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 0>(tA, tM, nullptr);
+    fd_stage<T, G, Q, NT, 0>(A1, A0, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(tM, tA, il);
+    fd_stage<T, G, Q, NT, 1>(A0, A1, il);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(tA, tM, x, xI, s_org, px, pz, T(1));
+    fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
+    __syncthreads();
+    fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);
+    __syncthreads();
+    fd_final<T, G, Q, NT>(A1, x, xI, s_org, px, pz, T(1));
   } else {
-    // 2D.  Stage 0: lines along y from global; tM = M x, tA = A x along y.
-    for_lines<P * n, NT>([&](const int t) {
-      const int p = t / n, L = t % n;
-      const int org = s_org[p];
-      T v[n];
-      if (org >= 0) {
-        const T* src = x + org + L;
+    // 2D.  Stage 0: lines along y from global; M x and A x along y into [x][oy].
+    for_lines<G * n, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
+      T v[n][Q];
 #pragma unroll
-        for (int c = 0; c < n; ++c) v[c] = src[c * px];
-      } else {
+      for (int j = 0; j < Q; ++j) {
+        const int org = s_org[g * Q + j];
+        const T* src = x + (org >= 0 ? org : 0) + L;
 #pragma unroll
-        for (int c = 0; c < n; ++c) v[c] = T(0);
+        for (int c = 0; c < n; ++c) v[c][j] = org >= 0 ? src[c * px] : T(0);
       }
       if (L >= 1 && L <= m) {
+        PK* d = reinterpret_cast<PK*>(xI + (L - 1) * P + g * Q);
 #pragma unroll
-        for (int c = 1; c <= m; ++c) xI[((c - 1) * m + L - 1) * P + p] = v[c];
+        for (int c = 1; c <= m; ++c) {
+          PK pk;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) pk.v[j] = v[c][j];
+          d[(c - 1) * m * G] = pk;
+        }
       }
-      T* dM = tM + p * S0 + L * m;
-      T* dA = tA + p * S0 + L * m;
+      PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+      PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T am = T(0), aa = T(0);
+        PK am, aa;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) am.v[j] = aa.v[j] = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          am = fma(c_tab<T>.Mp[o * n + c], v[c], am);
-          aa = fma(c_tab<T>.Ap[o * n + c], v[c], aa);
+          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            am.v[j] = fma(wm, v[c][j], am.v[j]);
+            aa.v[j] = fma(wa, v[c][j], aa.v[j]);
+          }
         }
-        dM[o] = am;
-        dA[o] = aa;
+        dM[o * G] = am;
+        dA[o * G] = aa;
       }
     });
+    async_wait_all();
     __syncthreads();
-    // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior.
-    T* R = U;
-    for_lines<P * m, NT>([&](const int t) {
-      const int p = t % P, L = t / P;
-      const T* sM = tM + p * S0 + L;
-      const T* sA = tA + p * S0 + L;
-      T vm[n], va[n];
+    // Stage 1: along x.  r = b - (A (M x) + M (A x)) on the interior, into B0.
+    for_lines<G * m, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
+      const PK* sM = reinterpret_cast<const PK*>(A0 + L * P + g * Q);
+      const PK* sA = reinterpret_cast<const PK*>(A1 + L * P + g * Q);
+      T vm[n][Q], va[n][Q];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
-        vm[c] = sM[c * m];
-        va[c] = sA[c * m];
+        const PK a = sM[c * m * G], bb = sA[c * m * G];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          vm[c][j] = a.v[j];
+          va[c][j] = bb.v[j];
+        }
       }
+      const PK* sb = reinterpret_cast<const PK*>(bI + L * m * P + g * Q);
+      PK* dR = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        T acc = T(0);
+        T acc[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) acc[j] = T(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          acc = fma(c_tab<T>.Ap[o * n + c], vm[c], acc);
-          acc = fma(c_tab<T>.Mp[o * n + c], va[c], acc);
+          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            acc[j] = fma(wa, vm[c][j], acc[j]);
+            acc[j] = fma(wm, va[c][j], acc[j]);
+          }
         }
-        R[(L * m + o) * P + p] = bI[(L * m + o) * P + p] - acc;
+        const PK bv = sb[o * G];
+        PK r;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+        dR[o * G] = r;
       }
     });
     __syncthreads();
-    T* X0 = R;
-    T* X1 = tM;  // tM/tA are free now; P*S0 >= P*m*m
-    fd_stage<T, P, NT, 0>(X0, X1, nullptr);
+    fd_stage<T, G, Q, NT, 0>(B0, A0, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(X1, X0, il);
+    fd_stage<T, G, Q, NT, 1>(A0, A1, il);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X0, X1, x, xI, s_org, px, pz, T(1));
+    fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
+    __syncthreads();
+    fd_final<T, G, Q, NT>(A0, x, xI, s_org, px, pz, T(1));
   }
 }
 
 // ------------------------------------------------------------- additive
 // x_I += scale * A_ref^-1 r_I for every patch of one colour.
-template <typename T, int PP>
-__global__ void __launch_bounds__(SmoothCfg<T, PP>::NT)
+template <typename T, int QQ>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ>::NT)
 smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv_lam,
                   int px, int pz, ColourGeom cg, T scale) {
-  using C = SmoothCfg<T, PP>;
-  constexpr int P = C::P, NT = C::NT, MD = C::md;
+  using C = SmoothCfg<T, QQ>;
+  constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
+  using PK = Pack<T, Q>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X0 = reinterpret_cast<T*>(smem_raw);
   T* X1 = X0 + P * MD;
@@ -420,44 +543,56 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
   __syncthreads();
   constexpr int NL = DIM == 3 ? m * m : m;
   // first S^T contraction reads the interior residual lines from global
-  for_lines<P * NL, NT>([&](const int t) {
-    const int p = t % P, L = t / P;
-    const int org = s_org[p];
-    T v[m];
-    if (org >= 0) {
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    T v[m][Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int org = s_org[g * Q + j];
+      const T* src;
+      int stride;
       if constexpr (DIM == 3) {
-        const int yy = L / m, xx = L % m;
-        const T* src = r + org + pz + (yy + 1) * px + 1 + xx;
-#pragma unroll
-        for (int c = 0; c < m; ++c) v[c] = src[c * pz];
+        src = r + (org >= 0 ? org : 0) + pz + (L / m + 1) * px + 1 + L % m;
+        stride = pz;
       } else {
-        const T* src = r + org + px + 1 + L;
-#pragma unroll
-        for (int c = 0; c < m; ++c) v[c] = src[c * px];
+        src = r + (org >= 0 ? org : 0) + px + 1 + L;
+        stride = px;
       }
-    } else {
 #pragma unroll
-      for (int c = 0; c < m; ++c) v[c] = T(0);
+      for (int c = 0; c < m; ++c) v[c][j] = org >= 0 ? src[c * stride] : T(0);
     }
+    PK* dst = reinterpret_cast<PK*>(X1 + L * m * P + g * Q);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      T acc = T(0);
+      PK acc;
 #pragma unroll
-      for (int c = 0; c < m; ++c) acc = fma(c_tab<T>.S[c * m + o], v[c], acc);
-      X1[(L * m + o) * P + p] = acc;
+      for (int j = 0; j < Q; ++j) acc.v[j] = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const T w = c_tab<T>.S[c * m + o];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) acc.v[j] = fma(w, v[c][j], acc.v[j]);
+      }
+      dst[o * G] = acc;
     }
   });
   __syncthreads();
   if constexpr (DIM == 3) {
-    fd_stage<T, P, NT, 0>(X1, X0, nullptr);
+    fd_stage<T, G, Q, NT, 0>(X1, X0, nullptr);
     __syncthreads();
-    fd_stage<T, P, NT, 1>(X0, X1, il);
+    fd_stage<T, G, Q, NT, 1>(X0, X1, il);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X1, X0, x, nullptr, s_org, px, pz, scale);
+    fd_stage<T, G, Q, NT, 2>(X1, X0, nullptr);
+    __syncthreads();
+    fd_stage<T, G, Q, NT, 2>(X0, X1, nullptr);
+    __syncthreads();
+    fd_final<T, G, Q, NT>(X1, x, nullptr, s_org, px, pz, scale);
   } else {
-    fd_stage<T, P, NT, 1>(X1, X0, il);
+    fd_stage<T, G, Q, NT, 1>(X1, X0, il);
     __syncthreads();
-    fd_backward_and_update<T, P, NT>(X0, X1, x, nullptr, s_org, px, pz, scale);
+    fd_stage<T, G, Q, NT, 2>(X0, X1, nullptr);
+    __syncthreads();
+    fd_final<T, G, Q, NT>(X1, x, nullptr, s_org, px, pz, scale);
   }
 }
 
@@ -1019,7 +1154,7 @@ __global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, i
 template <typename T, int PP>
 cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                                const T* inv_lam, cudaStream_t s) {
-  using C = SmoothCfg<T, PP>;
+  using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
@@ -1032,7 +1167,7 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
 template <typename T, int PP>
 cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
                               const T* inv_lam, T scale, cudaStream_t s) {
-  using C = SmoothCfg<T, PP>;
+  using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T sc = DIM == 3 ? T(scale / g.h) : scale;
@@ -1113,7 +1248,7 @@ cudaError_t smooth_limits() {
 template <typename T, int PP>
 void register_variant(KernelFns<T>* f, int v) {
   using C = SmoothCfg<T, PP>;
-  f->variant_p[v] = PP;
+  f->variant_p[v] = C::P;
   if constexpr (C::fits) {
     f->smooth_mult_v[v] = smooth_mult_launch<T, PP>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
@@ -1125,11 +1260,12 @@ void register_variant(KernelFns<T>* f, int v) {
 
 template <typename T>
 void register_fns(KernelFns<T>* f) {
-  register_variant<T, kVarP[0]>(f, 0);
-  register_variant<T, kVarP[1]>(f, 1);
-  register_variant<T, kVarP[2]>(f, 2);
-  f->smooth_mult = f->smooth_mult_v[1];
-  f->smooth_add = f->smooth_add_v[1];
+  register_variant<T, kVarQ[0]>(f, 0);
+  register_variant<T, kVarQ[1]>(f, 1);
+  register_variant<T, kVarQ[2]>(f, 2);
+  // default: the middle variant, or the smallest one where it does not fit
+  f->smooth_mult = f->smooth_mult_v[1] ? f->smooth_mult_v[1] : f->smooth_mult_v[0];
+  f->smooth_add = f->smooth_add_v[1] ? f->smooth_add_v[1] : f->smooth_add_v[0];
   f->apply = apply_launch<T>;
   f->prolong_add = prolong_launch<T>;
   f->restrict_ = restrict_launch<T>;
@@ -1138,11 +1274,11 @@ void register_fns(KernelFns<T>* f) {
 template <typename T>
 cudaError_t set_smem_limits() {
   cudaError_t e;
-  e = smooth_limits<T, kVarP[0]>();
+  e = smooth_limits<T, kVarQ[0]>();
   if (e != cudaSuccess) return e;
-  e = smooth_limits<T, kVarP[1]>();
+  e = smooth_limits<T, kVarQ[1]>();
   if (e != cudaSuccess) return e;
-  e = smooth_limits<T, kVarP[2]>();
+  e = smooth_limits<T, kVarQ[2]>();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ApplyCfg::smem<T>());
