@@ -212,6 +212,36 @@ int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_p
  * kernels the graph holds).  Instrumentation for benchmarks. */
 int vps_kernel_launches(vps_handle h, int64_t* count);
 
+/*
+ * vps_set_outer_operator -- the operator the outer CG (Section 4.1, with
+ * the FP64 outer iteration of Section 4.2) applies to its search direction:
+ *   VPS_OUTER_FP64 (0): FP64 arithmetic (default for VPS_FP64 handles);
+ *   VPS_OUTER_DOUBLE_FLOAT (1): the same sum-factorised operator evaluated
+ *     in double-float arithmetic -- each value a pair of floats, products
+ *     with FMA-exact rounding errors, sums by TwoSum -- about 48 significant
+ *     bits at a fraction of the FP64 cost on this GPU (default for VPS_FP32
+ *     handles).  Its rounding can let the recursive CG residual drift from
+ *     the true one, so convergence is confirmed on r = b - A x evaluated in
+ *     FP64, and CG restarts from that residual if it is still above rtol;
+ *     *rel_res of vps_solve is then that FP64 residual.
+ * The first switch to mode 1 allocates two float vectors of the finest
+ * level.  Errors: VPS_EINVAL (unknown mode), VPS_ENOMEM.
+ */
+#define VPS_OUTER_FP64 0
+#define VPS_OUTER_DOUBLE_FLOAT 1
+int vps_set_outer_operator(vps_handle h, int mode);
+int vps_get_outer_operator(vps_handle h, int* mode);
+
+/*
+ * vps_apply_outer -- y = A x on the finest level with the handle's outer
+ * operator (vps_set_outer_operator): the product the CG forms with its
+ * search direction.  x, y: distinct DOUBLE device vectors in the finest
+ * level's layout, whatever the handle's precision; boundary entries of y
+ * are written 0, padding entries are not written.  Uses the handle's split buffers in mode 1.
+ * Asynchronous on the handle's stream.  Errors: VPS_EINVAL.
+ */
+int vps_apply_outer(vps_handle h, const double* x, double* y);
+
 /* vps_set_graphs -- 1: capture the V-cycle in a CUDA graph on first use and
  * replay it (default on non-default streams); 0: launch kernels directly. */
 int vps_set_graphs(vps_handle h, int enable);

@@ -28,6 +28,8 @@ VPS_FP32 = 1
 VPS_MULTIPLICATIVE = 0
 VPS_ADDITIVE = 1
 VPS_MAX_DEGREE = 7
+VPS_OUTER_FP64 = 0
+VPS_OUTER_DOUBLE_FLOAT = 1
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
 
 # C signatures: name -> (restype, argtypes)
@@ -50,6 +52,9 @@ SIGNATURES = {
     "vps_assemble_rhs_sines": (_i, [_p, _i, _p, _p, _p]),
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
     "vps_set_graphs": (_i, [_p, _i]),
+    "vps_set_outer_operator": (_i, [_p, _i]),
+    "vps_get_outer_operator": (_i, [_p, ctypes.POINTER(_i)]),
+    "vps_apply_outer": (_i, [_p, _p, _p]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
     "vps_set_coarse_level": (_i, [_p, _i]),
     "vps_autotune": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i)]),
@@ -281,6 +286,18 @@ class Poisson:
 
     def vps_set_graphs(self, enable):
         _check(lib().vps_set_graphs(self.h, int(bool(enable))), self.h)
+
+    def vps_set_outer_operator(self, mode):
+        _check(lib().vps_set_outer_operator(self.h, int(mode)), self.h)
+
+    def vps_apply_outer(self, x, y):
+        assert x.dtype == self.torch.float64 and y.dtype == self.torch.float64
+        self._call(lib().vps_apply_outer, _ptr(x), _ptr(y))
+
+    def vps_get_outer_operator(self):
+        c = ctypes.c_int()
+        _check(lib().vps_get_outer_operator(self.h, ctypes.byref(c)), self.h)
+        return c.value
 
     # --- conveniences on compact vectors
     def to_level(self, compact, level=None):

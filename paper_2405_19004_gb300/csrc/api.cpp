@@ -93,6 +93,10 @@ struct vps_context {
   // CG state, FP64, finest level layout
   double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cz = nullptr,
          *czn = nullptr, *cAp = nullptr;
+  // outer operator of the CG: native FP64, or double-float (p split into
+  // two float vectors cph + cpl) with a final FP64 check of the residual
+  int outer = VPS_OUTER_FP64;
+  float *cph = nullptr, *cpl = nullptr;
   double* partial = nullptr;            // 2 * kDotBlocks
   double* dots = nullptr;               // scratch scalars for norms
   CgScalars* sc = nullptr;
@@ -114,6 +118,7 @@ struct vps_context {
   // asynchronous CG (used by the serving loop)
   int as_phase = 0;                     // 0 idle, 1 iteration in flight, 2 result copy in flight
   int as_it = 0, as_maxit = 0, as_status = 0;
+  bool as_verify = false;               // true residual in flight (double-float outer operator)
   double as_nb = 0.0, as_rtol = 0.0, as_rel = 0.0;
   double* host_x = nullptr;             // pinned staging of the compact result
   cudaEvent_t as_ev = nullptr;
@@ -382,6 +387,41 @@ int precondition(vps_context* h) {
   return VPS_OK;
 }
 
+bool outer_df(const vps_context* h) { return h->outer == VPS_OUTER_DOUBLE_FLOAT; }
+
+// p = z (the preconditioned residual in czn), z kept for the Polak-Ribiere
+// beta, rz = r . z.
+int cg_start_direction(vps_context* h) {
+  const int64_t n = h->geom[h->L].total;
+  VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream, outer_df(h) ? h->cph : nullptr,
+                             h->cpl));
+  VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+  return VPS_OK;
+}
+
+// Ap = A p with the handle's outer operator.
+int cg_apply_p(vps_context* h) {
+  const LevelGeom& g = h->geom[h->L];
+  if (outer_df(h)) VPS_CK(h, h->ks->apply_df(g, h->cph, h->cpl, h->cAp, h->stream));
+  else VPS_CK(h, h->ks->d.apply(g, h->cp, nullptr, h->cAp, h->stream));
+  return VPS_OK;
+}
+
+// r = b - A x with the FP64 operator, r . r into sc->rr (asynchronous).
+int cg_true_residual(vps_context* h) {
+  const LevelGeom& g = h->geom[h->L];
+  VPS_CK(h, h->ks->d.apply(g, h->cx, h->cb, h->cr, h->stream));
+  VPS_CK(h, launch_dot1(h->cr, h->cr, g.total, h->partial, &h->sc->rr, h->stream));
+  return VPS_OK;
+}
+
+// Preconditioned CG (Section 4.1's outer solver) with the flexible
+// (Polak-Ribiere) beta.  With the double-float outer operator the recursive
+// residual can drift from the true one by the operator's rounding (about
+// 2^-48 of the sum of the magnitudes of its terms); convergence is therefore
+// confirmed on r = b - A x evaluated in FP64, and the iteration restarts
+// from that residual when it is not yet below the tolerance.
 int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_res) {
   const LevelGeom& g = h->geom[h->L];
   const int64_t n = g.total;
@@ -402,12 +442,10 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
   VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
   int rc = precondition(h);
   if (rc) return rc;
-  VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream));
-  VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+  if ((rc = cg_start_direction(h))) return rc;
   double rel = 1.0;
   for (int it = 1; it <= max_it; ++it) {
-    VPS_CK(h, h->ks->d.apply(g, h->cp, nullptr, h->cAp, h->stream));
+    if ((rc = cg_apply_p(h))) return rc;
     VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
     VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
     VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
@@ -424,12 +462,31 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
     if (rel_res) *rel_res = rel;
     if (!std::isfinite(rel))
       return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
-    if (rel <= rtol) return VPS_OK;
+    bool restart = false;
+    if (rel <= rtol) {
+      if (!outer_df(h)) return VPS_OK;
+      if ((rc = cg_true_residual(h))) return rc;
+      VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                h->stream));
+      VPS_CK(h, cudaStreamSynchronize(h->stream));
+      rel = std::sqrt(h->host_sc->rr) / nb;
+      if (rel_res) *rel_res = rel;
+      if (!std::isfinite(rel))
+        return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
+      if (rel <= rtol) return VPS_OK;
+      restart = true;
+    }
     if (it == max_it) break;
     rc = precondition(h);
     if (rc) return rc;
-    VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
-    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream));
+    if (restart) {
+      VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+      if ((rc = cg_start_direction(h))) return rc;
+    } else {
+      VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
+      VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream,
+                                   outer_df(h) ? h->cph : nullptr, h->cpl));
+    }
   }
   return fail(h, VPS_ENOCONV, "CG did not reach %g in %d iterations (%g)", rtol, max_it, rel);
 }
@@ -487,15 +544,13 @@ int cg_async_iteration(vps_context* h, bool first) {
   const LevelGeom& g = h->geom[h->L];
   const int64_t n = g.total;
   if (first) {
-    VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream));
-    VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice,
-                              h->stream));
-    VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+    if (int rc = cg_start_direction(h)) return rc;
   } else {
     VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
-    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream));
+    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream,
+                                 outer_df(h) ? h->cph : nullptr, h->cpl));
   }
-  VPS_CK(h, h->ks->d.apply(g, h->cp, nullptr, h->cAp, h->stream));
+  if (int rc = cg_apply_p(h)) return rc;
   VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
   VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
   VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
@@ -546,6 +601,7 @@ size_t estimate_device_bytes(int dim, int degree, int level, int precision) {
   const LevelGeom g = make_geom(dim, degree, level);
   const size_t ni = g.n1 - 2;
   total += 7 * (size_t)g.total * 8 + 2 * (dim == 3 ? ni * ni * ni : ni * ni) * 8;
+  if (precision == VPS_FP32) total += 2 * (size_t)g.total * 4;  // double-float split of p
   return total + (size_t)(4 << 20);  // tables, coarse-level data, scalars
 }
 
@@ -567,6 +623,7 @@ int cg_async_begin(vps_handle h, int n_modes, const double* coef, const int* fre
   h->as_it = 1;
   h->as_rel = 1.0;
   h->as_status = VPS_OK;
+  h->as_verify = false;
   if (int rc = upload_rhs_sines(h, n_modes, coef, freq, h->comp_b)) return rc;
   VPS_CK(h, launch_pack<double>(g, h->comp_b, h->cb, h->stream));
   VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
@@ -607,10 +664,26 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
   if (h->host_sc->flag) return cg_async_finish(h, VPS_EBREAKDOWN);
   h->as_rel = std::sqrt(h->host_sc->rr) / h->as_nb;
   if (!std::isfinite(h->as_rel)) return cg_async_finish(h, VPS_EBREAKDOWN);
-  if (h->as_rel <= h->as_rtol) return cg_async_finish(h, VPS_OK);
+  const bool verified = h->as_verify;
+  h->as_verify = false;
+  if (h->as_rel <= h->as_rtol) {
+    if (!outer_df(h) || verified) return cg_async_finish(h, VPS_OK);
+    // confirm on the FP64 residual r = b - A x (see cg_solve)
+    if (int rc = cg_true_residual(h)) return rc;
+    VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                              h->stream));
+    VPS_CK(h, cudaEventRecord(h->as_ev, h->stream));
+    h->as_verify = true;
+    return VPS_OK;
+  }
   if (h->as_it >= h->as_maxit) return cg_async_finish(h, VPS_ENOCONV);
   if (int rc = precondition(h)) return rc;
-  if (int rc = cg_async_iteration(h, false)) return rc;
+  if (verified) {  // the true residual is still above the tolerance: restart from it
+    VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+    if (int rc = cg_async_iteration(h, true)) return rc;
+  } else if (int rc = cg_async_iteration(h, false)) {
+    return rc;
+  }
   ++h->as_it;
   return VPS_OK;
 }
@@ -858,6 +931,9 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   if ((rc = dalloc(h, &p, db))) return bail(rc); h->cz = (double*)p;
   if ((rc = dalloc(h, &p, db))) return bail(rc); h->czn = (double*)p;
   if ((rc = dalloc(h, &p, db))) return bail(rc); h->cAp = (double*)p;
+  if (precision == VPS_FP32) {
+    if ((rc = vps_set_outer_operator(h, VPS_OUTER_DOUBLE_FLOAT))) return bail(rc);
+  }
   if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_b = (double*)p;
   if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_x = (double*)p;
   if ((rc = dalloc(h, &p, 2 * kDotBlocks * sizeof(double)))) return bail(rc); h->partial = (double*)p;
@@ -987,6 +1063,21 @@ int vps_apply(vps_handle h, int level, const void* x, void* y) {
     VPS_CK(h, h->ks->d.apply(g, (const double*)x, nullptr, (double*)y, h->stream));
   else
     VPS_CK(h, h->ks->f.apply(g, (const float*)x, nullptr, (float*)y, h->stream));
+  return VPS_OK;
+}
+
+int vps_apply_outer(vps_handle h, const double* x, double* y) {
+  if (!h) return VPS_EINVAL;
+  if (!x || !y || x == y) return fail(h, VPS_EINVAL, "x and y must be distinct non-NULL vectors");
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  const LevelGeom& g = h->geom[h->L];
+  if (!outer_df(h)) {
+    VPS_CK(h, h->ks->d.apply(g, x, nullptr, y, h->stream));
+    return VPS_OK;
+  }
+  VPS_CK(h, launch_split_df(x, h->cph, h->cpl, g.total, h->stream));
+  VPS_CK(h, h->ks->apply_df(g, h->cph, h->cpl, y, h->stream));
   return VPS_OK;
 }
 
@@ -1227,6 +1318,29 @@ int vps_get_coarse_level(vps_handle h, int* level) {
 int vps_kernel_launches(vps_handle h, int64_t* count) {
   if (!h || !count) return VPS_EINVAL;
   *count = h->kernels;
+  return VPS_OK;
+}
+
+int vps_set_outer_operator(vps_handle h, int mode) {
+  if (!h) return VPS_EINVAL;
+  if (mode != VPS_OUTER_FP64 && mode != VPS_OUTER_DOUBLE_FLOAT)
+    return fail(h, VPS_EINVAL, "outer operator mode %d (expected 0 or 1)", mode);
+  if (mode == VPS_OUTER_DOUBLE_FLOAT && !h->cph) {
+    if (int rc = set_device(h)) return rc;
+    const size_t fb = (size_t)h->geom[h->L].total * sizeof(float);
+    void* p;
+    if (int rc = dalloc(h, &p, fb)) return rc;
+    h->cph = (float*)p;
+    if (int rc = dalloc(h, &p, fb)) return rc;
+    h->cpl = (float*)p;
+  }
+  h->outer = mode;
+  return VPS_OK;
+}
+
+int vps_get_outer_operator(vps_handle h, int* mode) {
+  if (!h || !mode) return VPS_EINVAL;
+  *mode = h->outer;
   return VPS_OK;
 }
 

@@ -57,6 +57,10 @@ struct DevTab {
   T Kb[K * n];
   T Mb[K * n];
   T P1[n * nl];
+  // low words of Kb, Mb (FP32 table only): Kb + Kb_lo is the FP64 value to
+  // about 48 bits, for the double-float operator
+  T Kb_lo[K * n];
+  T Mb_lo[K * n];
 };
 
 template <typename T>
@@ -885,6 +889,197 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
   }
 }
 
+// ------------------------------------------------- double-float operator
+// y = A x in FP64-like accuracy with FP32 arithmetic, for the outer CG of the
+// mixed-precision solver: FP64 runs at 1/64 of the FP32 rate on this GPU,
+// while this operator is a short sum of products per output.  A value is a
+// pair (hi, lo) of floats; a product c x of a coefficient (c_hi + c_lo) and
+// a value is formed exactly up to its cross terms with one FMA for the
+// rounding error of c_hi x_hi; sums use Knuth's TwoSum on the high words
+// and accumulate the low words.  Relative accuracy about 2^-48 of the sum of
+// the magnitudes of the terms.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_madd(DF& s, float ch, float cl, const DF& x) {
+  const float p = ch * x.hi;
+  const float pe = fmaf(ch, x.hi, -p);                       // exact error of ch * x.hi
+  const float pl = fmaf(ch, x.lo, fmaf(cl, x.hi, pe));
+  const float t = s.hi + p;                                  // TwoSum(s.hi, p)
+  const float bb = t - s.hi;
+  const float e = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo = s.lo + (e + pl);
+}
+
+__device__ __forceinline__ DF df_norm(const DF& s) {
+  const float h = s.hi + s.lo;
+  return DF{h, s.lo - (h - s.hi)};
+}
+
+__device__ __forceinline__ void df_add(DF& s, const DF& x) {
+  const float t = s.hi + x.hi;
+  const float bb = t - s.hi;
+  const float e = (s.hi - (t - bb)) + (x.hi - bb);
+  s.hi = t;
+  s.lo = s.lo + (e + x.lo);
+}
+
+#define VPS_DF_MADD(acc, TAB, q, j, v) \
+  df_madd(acc, c_tab<float>.TAB[(q) * n + (j)], c_tab<float>.TAB##_lo[(q) * n + (j)], v)
+
+template <int DUMMY>
+__global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
+apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
+                 double* __restrict__ y, int n1, int px, int pz, double scale) {
+  using C = Apply3Cfg;
+  constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* zbuf = reinterpret_cast<DF*>(smem_raw);  // [2][2][BX][RB]
+  DF* MM = zbuf + 4 * BX * RB;
+  DF* WW = MM + TX * RB;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  const int z0 = blockIdx.z * C::ZR;
+  int buf = 0;
+  for (int cz = 0; cz < C::ZC; ++cz) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int z = z0 + cz * K + q;
+      if (z >= n1 - 1) break;
+      DF* mZ = zbuf + (2 * buf) * BX * RB;
+      DF* kZ = mZ + BX * RB;
+      for (int u = threadIdx.x; u < BX * BX; u += NT) {
+        const int xx = u % BX, yy = u / BX;
+        const int gx = x0 - K + xx, gy = y0 - K + yy;
+        DF am{0.f, 0.f}, ak{0.f, 0.f};
+        if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
+          const int col = gy * px + gx;
+          VPS_BAND_LOOP(q, j) {
+            const int gz = z - K + j;
+            DF v{0.f, 0.f};
+            if (gz >= 0 && gz < n1) v = DF{__ldg(xh + col + gz * pz), __ldg(xl + col + gz * pz)};
+            VPS_DF_MADD(am, Mb, q, j, v);
+            VPS_DF_MADD(ak, Kb, q, j, v);
+          }
+        }
+        mZ[yy * RB + xx] = df_norm(am);
+        kZ[yy * RB + xx] = df_norm(ak);
+      }
+      __syncthreads();
+      for (int u = threadIdx.x; u < BX * CX; u += NT) {
+        const int xx = u % BX, cy = u / BX;
+        DF vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = mZ[(cy * K + i) * RB + xx];
+          vk[i] = kZ[(cy * K + i) * RB + xx];
+        }
+#pragma unroll
+        for (int qy = 0; qy < K; ++qy) {
+          DF a{0.f, 0.f}, bb{0.f, 0.f};
+          VPS_BAND_LOOP(qy, j) {
+            VPS_DF_MADD(a, Mb, qy, j, vm[qy + j]);
+            VPS_DF_MADD(bb, Kb, qy, j, vm[qy + j]);
+            VPS_DF_MADD(bb, Mb, qy, j, vk[qy + j]);
+          }
+          MM[(cy * K + qy) * RB + xx] = df_norm(a);
+          WW[(cy * K + qy) * RB + xx] = df_norm(bb);
+        }
+      }
+      __syncthreads();
+      const bool inner_z = z >= 1 && z <= n1 - 2;
+      for (int u = threadIdx.x; u < TX * CX; u += NT) {
+        const int Y = u % TX, cx = u / TX;
+        const int gy = y0 + Y;
+        if (gy >= n1) continue;
+        DF vm[2 * K + 1], vw[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = MM[Y * RB + cx * K + i];
+          vw[i] = WW[Y * RB + cx * K + i];
+        }
+        const bool inner_yz = inner_z && gy >= 1 && gy <= n1 - 2;
+        const int rowi = z * pz + gy * px;
+#pragma unroll
+        for (int qx = 0; qx < K; ++qx) {
+          const int gx = x0 + cx * K + qx;
+          if (gx >= n1) continue;
+          DF acc{0.f, 0.f};
+          VPS_BAND_LOOP(qx, j) {
+            VPS_DF_MADD(acc, Kb, qx, j, vm[qx + j]);
+            VPS_DF_MADD(acc, Mb, qx, j, vw[qx + j]);
+          }
+          double out = 0.0;
+          if (inner_yz && gx >= 1 && gx <= n1 - 2) out = scale * ((double)acc.hi + (double)acc.lo);
+          y[rowi + gx] = out;
+        }
+      }
+      buf ^= 1;
+    }
+  }
+}
+
+// 2D: tiles of TN x TN outputs, y first from global, then x.
+template <int DUMMY>
+__global__ void __launch_bounds__(ApplyCfg::NT)
+apply2_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl, double* __restrict__ y,
+                 int n1, int px) {
+  using C = ApplyCfg;
+  constexpr int TN = C::TN, BN = C::BN, RB = C::RB, CT = C::CT, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* tm = reinterpret_cast<DF*>(smem_raw);
+  DF* tk = tm + C::a_sz;
+  const int x0 = blockIdx.x * TN, y0 = blockIdx.y * TN;
+  for (int u = threadIdx.x; u < BN * CT; u += NT) {
+    const int xx = u % BN, cy = u / BN;
+    const int gx = x0 - K + xx, gy0 = y0 + cy * K - K;
+    DF v[2 * K + 1];
+#pragma unroll
+    for (int i = 0; i <= 2 * K; ++i) {
+      const int gy = gy0 + i;
+      v[i] = (gx >= 0 && gx < n1 && gy >= 0 && gy < n1)
+                 ? DF{__ldg(xh + gy * px + gx), __ldg(xl + gy * px + gx)}
+                 : DF{0.f, 0.f};
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      DF am{0.f, 0.f}, ak{0.f, 0.f};
+      VPS_BAND_LOOP(q, j) {
+        VPS_DF_MADD(am, Mb, q, j, v[q + j]);
+        VPS_DF_MADD(ak, Kb, q, j, v[q + j]);
+      }
+      tm[(cy * K + q) * RB + xx] = df_norm(am);
+      tk[(cy * K + q) * RB + xx] = df_norm(ak);
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < TN * CT; u += NT) {
+    const int Y = u % TN, cx = u / TN;
+    const int gy = y0 + Y;
+    if (gy >= n1) continue;
+    DF vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+    for (int i = 0; i <= 2 * K; ++i) {
+      vm[i] = tm[Y * RB + cx * K + i];
+      vk[i] = tk[Y * RB + cx * K + i];
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int gx = x0 + cx * K + q;
+      if (gx >= n1) continue;
+      DF acc{0.f, 0.f};
+      VPS_BAND_LOOP(q, j) {
+        VPS_DF_MADD(acc, Kb, q, j, vm[q + j]);
+        VPS_DF_MADD(acc, Mb, q, j, vk[q + j]);
+      }
+      double out = 0.0;
+      if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2) out = (double)acc.hi + (double)acc.lo;
+      y[gy * px + gx] = out;
+    }
+  }
+}
+
 // ------------------------------------------------------------ transfers
 // Tiles of CC coarse cells per direction; the first contraction (slowest
 // direction) reads from global memory.
@@ -1202,6 +1397,31 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t apply_df_launch(const LevelGeom& g, const float* xh, const float* xl, double* y,
+                            cudaStream_t s) {
+  const int span = g.n1 - 1;
+  if constexpr (DIM == 3) {
+    using C3 = Apply3Cfg;
+    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
+    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    VPS_COUNT_LAUNCH();
+    apply3_df_kernel<0><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(xh, xl, y, g.n1,
+                                                                          (int)g.px, (int)g.pz,
+                                                                          g.h);
+  } else {
+    using C = ApplyCfg;
+    const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
+    VPS_COUNT_LAUNCH();
+    apply2_df_kernel<0><<<dim3(t, t, 1), C::NT, C::smem<double>(), s>>>(xh, xl, y, g.n1,
+                                                                       (int)g.px);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
+  zero_upper_faces_kernel<double><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t prolong_launch(const LevelGeom& f, const LevelGeom& c, const T* xc, T* xf,
                            cudaStream_t s) {
@@ -1307,6 +1527,19 @@ void fill_tab(const HostTables& h, DevTab<T>* d) {
     d->Mb[i] = (T)h.Mb[i];
   }
   for (int i = 0; i < n * nl; ++i) d->P1[i] = (T)h.P1[i];
+  for (int i = 0; i < K * n; ++i) {
+    d->Kb_lo[i] = (T)(h.Kb[i] - (double)(T)h.Kb[i]);
+    d->Mb_lo[i] = (T)(h.Mb[i] - (double)(T)h.Mb[i]);
+  }
+}
+
+cudaError_t df_limits() {
+  if constexpr (DIM == 3)
+    return cudaFuncSetAttribute(apply3_df_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Apply3Cfg::smem<double>());
+  else
+    return cudaFuncSetAttribute(apply2_df_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ApplyCfg::smem<double>());
 }
 
 cudaError_t upload(const HostTables& h) {
@@ -1321,6 +1554,8 @@ cudaError_t upload(const HostTables& h) {
   if (e != cudaSuccess) return e;
   e = set_smem_limits<float>();
   if (e != cudaSuccess) return e;
+  e = df_limits();
+  if (e != cudaSuccess) return e;
   return set_smem_limits<double>();
 }
 
@@ -1333,6 +1568,7 @@ void VPS_CAT(register_kernels_d, VPS_DIM, VPS_K)(KernelSet* ks) {
   ks->upload = upload;
   register_fns<float>(&ks->f);
   register_fns<double>(&ks->d);
+  ks->apply_df = apply_df_launch;
 }
 
 }  // namespace vps

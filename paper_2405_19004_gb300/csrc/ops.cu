@@ -137,22 +137,45 @@ __global__ void cg_beta_kernel(CgScalars* sc) {
   sc->rz = sc->rzn;
 }
 
+// p (and, when ph is given, its split into two floats: ph = fl(p),
+// pl = fl(p - ph), the input of the double-float operator)
+__device__ __forceinline__ void store_p(double* p, float* ph, float* pl, int64_t i, double v) {
+  p[i] = v;
+  if (ph) {
+    const float hi = (float)v;
+    ph[i] = hi;
+    pl[i] = (float)(v - (double)hi);
+  }
+}
+
 __global__ void cg_update_p_kernel(double* __restrict__ p, double* __restrict__ z,
                                    const double* __restrict__ zn, const CgScalars* __restrict__ sc,
-                                   int64_t n) {
+                                   float* __restrict__ ph, float* __restrict__ pl, int64_t n) {
   const double beta = sc->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double v = zn[i];
-    p[i] = fma(beta, p[i], v);
+    store_p(p, ph, pl, i, fma(beta, p[i], v));
     z[i] = v;
   }
 }
 
-__global__ void cg_init_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n) {
+__global__ void cg_init_p_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                 float* __restrict__ ph, float* __restrict__ pl, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i];
+    store_p(p, ph, pl, i, z[i]);
+}
+
+__global__ void split_df_kernel(const double* __restrict__ a, float* __restrict__ ph,
+                                float* __restrict__ pl, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float hi = (float)v;
+    ph[i] = hi;
+    pl[i] = (float)(v - (double)hi);
+  }
 }
 
 __global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -346,18 +369,25 @@ cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const dou
 }
 
 cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
-                               cudaStream_t s) {
+                               cudaStream_t s, float* ph, float* pl) {
   VPS_COUNT_LAUNCH();
   cg_beta_kernel<<<1, 1, 0, s>>>(sc);
   VPS_COUNT_LAUNCH();
-  cg_update_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, sc, n);
+  cg_update_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, sc, ph, pl, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s) {
+cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s,
+                             float* ph, float* pl) {
   (void)sc;
   VPS_COUNT_LAUNCH();
-  cg_init_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, n);
+  cg_init_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, ph, pl, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df(const double* a, float* ph, float* pl, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  split_df_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, ph, pl, n);
   return cudaGetLastError();
 }
 

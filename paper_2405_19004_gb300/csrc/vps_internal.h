@@ -123,6 +123,9 @@ struct KernelSet {
   cudaError_t (*upload)(const HostTables&) = nullptr;
   KernelFns<float> f;
   KernelFns<double> d;
+  // y = A x with x given as FP32 pairs (hi, lo) and double-float arithmetic
+  cudaError_t (*apply_df)(const LevelGeom&, const float* xh, const float* xl, double* y,
+                          cudaStream_t) = nullptr;
 };
 
 // Registry indexed [dim-2][k-1]; filled by ensure_registered().
@@ -160,10 +163,14 @@ struct CgScalars {
 };
 cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
                                 CgScalars* sc, int64_t n, cudaStream_t s);
+// ph, pl (optional): also write p split into two floats for the double-float operator
 cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
-                               cudaStream_t s);
-cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s);
+                               cudaStream_t s, float* ph = nullptr, float* pl = nullptr);
+cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s,
+                             float* ph = nullptr, float* pl = nullptr);
 cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
+// ph = fl32(a), pl = fl32(a - ph)
+cudaError_t launch_split_df(const double* a, float* ph, float* pl, int64_t n, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s);

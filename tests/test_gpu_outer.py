@@ -1,0 +1,124 @@
+"""The outer CG operator: FP64 and double-float evaluation of A p (Section 4.2).
+
+The double-float operator evaluates the same sum-factorised product with each
+value held as a pair of floats; its results are compared with the oracle's
+assembled matrix at the FP64 bar (1e-12 relative), on random vectors (no
+cancellation) and on a smooth vector (the terms cancel to O(h^2) of their
+size), where the bound is stated against max (|A| |x|), the scale of the
+floating-point error of any evaluation of the sum.  The mixed-precision
+solve must reach the same tolerance on the true FP64 residual whichever
+outer operator it uses.
+"""
+
+import numpy as np
+import pytest
+
+from synthetic import normal_vector, uniform_vector
+
+from gpu_helpers import oracle_level
+
+pytestmark = pytest.mark.gpu
+
+import paper_2405_19004_gb300 as vps  # noqa: E402
+
+CASES = [(2, 1, 4), (2, 3, 3), (2, 7, 2), (3, 1, 3), (3, 2, 3), (3, 4, 2), (3, 5, 2), (3, 7, 1)]
+
+
+def _pack64(P, x, xl):
+    """Pack a compact FP64 vector into the finest level's layout (padding 0)."""
+    import torch
+    d, n1 = P.dim, P.layout(P.level)[0]
+    px = P.layout(P.level)[1]
+    ni = n1 - 2
+    v = torch.as_tensor(x, device="cuda").reshape((ni,) * d)
+    if d == 3:
+        full = xl.view(n1, n1, px)
+        full[1:n1 - 1, 1:n1 - 1, 1:n1 - 1] = v
+    else:
+        full = xl.view(n1, px)
+        full[1:n1 - 1, 1:n1 - 1] = v
+
+
+def _unpack64(P, y):
+    d, (n1, px, _) = P.dim, P.layout(P.level)
+    if d == 3:
+        full = y.view(n1, n1, px)
+        inner = full[1:n1 - 1, 1:n1 - 1, 1:n1 - 1]
+    else:
+        full = y.view(n1, px)
+        inner = full[1:n1 - 1, 1:n1 - 1]
+    return inner.reshape(-1).cpu().numpy(), full
+
+
+@pytest.mark.parametrize("mode", [vps.VPS_OUTER_FP64, vps.VPS_OUTER_DOUBLE_FLOAT], ids=["fp64", "df"])
+@pytest.mark.parametrize("prec", [vps.VPS_FP64, vps.VPS_FP32], ids=["h64", "h32"])
+@pytest.mark.parametrize("d,k,l", CASES)
+def test_outer_operator_matches_oracle(d, k, l, prec, mode):
+    import torch
+    lv, A, _ = oracle_level(d, k, l)
+    P = vps.Poisson(d, k, l, precision=prec)
+    P.vps_set_outer_operator(mode)
+    assert P.vps_get_outer_operator() == mode
+    absA = abs(A)
+    for x in (normal_vector(lv.N, 61), np.sin(np.pi * np.linspace(0.05, 0.95, lv.N)) + 1.0):
+        xl = P.empty_level(l, dtype=torch.float64)
+        _pack64(P, x, xl)
+        y = xl.clone().fill_(123.0)
+        P.vps_apply_outer(xl, y)
+        got, full = _unpack64(P, y)
+        ref = A @ x
+        scale = (absA @ np.abs(x)).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale
+        # boundary nodes come back 0 (padding columns beyond n1 are not written)
+        n1 = P.layout(l)[0]
+        box = full[..., :n1].cpu().numpy()
+        inner = np.zeros(box.shape, dtype=bool)
+        inner[(slice(1, n1 - 1),) * d] = True
+        assert np.all(box[~inner] == 0.0)
+    # random vectors: the relative 2-norm error at the FP64 bar
+    x = normal_vector(lv.N, 62)
+    xl = P.empty_level(l, dtype=torch.float64)
+    _pack64(P, x, xl)
+    y = xl.clone()
+    P.vps_apply_outer(xl, y)
+    got, _ = _unpack64(P, y)
+    ref = A @ x
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_fp32_handle_defaults_to_double_float():
+    assert vps.Poisson(3, 2, 2, precision=vps.VPS_FP32).vps_get_outer_operator() == \
+        vps.VPS_OUTER_DOUBLE_FLOAT
+    assert vps.Poisson(3, 2, 2, precision=vps.VPS_FP64).vps_get_outer_operator() == vps.VPS_OUTER_FP64
+
+
+def test_outer_operator_rejects_unknown_mode():
+    P = vps.Poisson(2, 2, 2, precision=vps.VPS_FP32)
+    with pytest.raises(vps.VpsError) as e:
+        P.vps_set_outer_operator(2)
+    assert e.value.code == vps.VPS_EINVAL
+    assert P.vps_get_outer_operator() == vps.VPS_OUTER_DOUBLE_FLOAT
+
+
+@pytest.mark.parametrize("rtol", [1e-10, 1e-12])
+@pytest.mark.parametrize("d,k,L", [(3, 3, 3), (2, 4, 4), (3, 2, 4)])
+def test_mixed_solve_with_either_outer_operator(d, k, L, rtol):
+    import torch
+    lv, A, _ = oracle_level(d, k, L)
+    b = uniform_vector(lv.N, 63)
+    sols, its = {}, {}
+    for mode in (vps.VPS_OUTER_FP64, vps.VPS_OUTER_DOUBLE_FLOAT):
+        P = vps.Poisson(d, k, L, precision=vps.VPS_FP32)
+        P.vps_set_outer_operator(mode)
+        bt = torch.as_tensor(b, device="cuda")
+        xt = torch.zeros_like(bt)
+        it, rel = P.vps_solve(bt, xt, rtol, 100)
+        x = xt.cpu().numpy()
+        true_rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert rel <= rtol
+        # the reported residual is an FP64 residual: it agrees with the oracle's
+        assert true_rel <= 1.02 * rtol, (mode, true_rel)
+        sols[mode], its[mode] = x, it
+    assert abs(its[0] - its[1]) <= 2
+    dx = np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[0])
+    assert dx <= 100 * rtol
