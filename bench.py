@@ -255,6 +255,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    def nvtx(name):
+        """Push/pop NVTX range (profilers filter the timed region by it); no-op if unavailable."""
+        import contextlib
+        try:
+            return torch.cuda.nvtx.range(name)
+        except Exception:
+            return contextlib.nullcontext()
+
     its = []
     for _ in range(args.warmup):
         it, rel = P.vps_solve(b, x, RTOL, 100)
@@ -268,17 +276,18 @@ def main():
     launches0 = P.vps_kernel_launches()
     barrier()
     times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        stream.wait_stream(torch.cuda.current_stream())
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, rel = P.vps_solve(b, x, RTOL, 100)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        its.append(it)
+    with nvtx("timed_solves"):
+        for _ in range(args.steps):
+            flush.zero_()
+            stream.wait_stream(torch.cuda.current_stream())
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rel = P.vps_solve(b, x, RTOL, 100)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            its.append(it)
     barrier()
     launches = P.vps_kernel_launches() - launches0
     clocks = sampler.stop()
@@ -319,13 +328,14 @@ def main():
            for _ in range(8 * n_rep)]
     for c in range(8):  # warm-up
         vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
-    for r in range(n_rep):
-        for c in range(8):
-            a, z = evs[r * 8 + c]
-            a.record(stream)
-            vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
-            z.record(stream)
-    torch.cuda.synchronize()
+    with nvtx("smoother_colour_passes"):
+        for r in range(n_rep):
+            for c in range(8):
+                a, z = evs[r * 8 + c]
+                a.record(stream)
+                vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+                z.record(stream)
+        torch.cuda.synchronize()
     launch_ms = [a.elapsed_time(z) for a, z in evs]
     t_launch = statistics.mean(launch_ms) / 1e3
     n_patches = (2 ** L - 1) ** 3

@@ -125,7 +125,7 @@ struct vps_context {
   // exact coarse solve on level `coarse` by global fast diagonalisation
   int coarse = 1;
   int gni = 0;                          // interior nodes per direction on that level
-  void* gS = nullptr;                   // S (gni x gni), working precision
+  void* gS = nullptr;                   // S then S^T (gni x gni each), working precision
   void* ginv = nullptr;                 // h^(2-d) / (sum of eigenvalues), gni^d
   void* gt1 = nullptr;                  // two gni^d work tensors
   void* gt2 = nullptr;
@@ -226,7 +226,8 @@ template <typename T>
 int coarse_solve(vps_context* h, const T* b, T* x) {
   const LevelGeom& g = h->geom[h->coarse];
   const int ni = h->gni, d = h->dim, px = (int)g.px, pz = (int)g.pz;
-  const T* S = static_cast<const T*>(h->gS);
+  const T* S = static_cast<const T*>(h->gS);      // W of the S^T passes
+  const T* St = S + (size_t)ni * ni;               // W of the S passes
   const T* inv = static_cast<const T*>(h->ginv);
   T* t1 = static_cast<T*>(h->gt1);
   T* t2 = static_cast<T*>(h->gt2);
@@ -236,14 +237,14 @@ int coarse_solve(vps_context* h, const T* b, T* x) {
     VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
     VPS_CK(h, launch_fd_global_pass<T>(0, t1, t2, S, inv, ni, d, false, false, px, pz, st));
     VPS_CK(h, launch_fd_global_pass<T>(1, t2, t1, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, t2, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, S, inv, ni, d, false, true, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, t2, St, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, st));
   } else {
     VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
     VPS_CK(h, launch_fd_global_pass<T>(1, t1, t2, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, S, inv, ni, d, false, true, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, st));
   }
   return VPS_OK;
 }
@@ -279,7 +280,11 @@ int setup_coarse(vps_context* h, int lc) {
     }
   h->gS = h->ginv = h->gt1 = h->gt2 = nullptr;
   int rc;
-  if ((rc = dalloc(h, &h->gS, (size_t)ni * ni * h->esz)) || (rc = dalloc(h, &h->ginv, nd * h->esz)) ||
+  // gS: S followed by S^T (both row-major)
+  S.reserve(2 * (size_t)ni * ni);
+  for (int i = 0; i < ni; ++i)
+    for (int j = 0; j < ni; ++j) S.push_back(S[(size_t)j * ni + i]);
+  if ((rc = dalloc(h, &h->gS, 2 * (size_t)ni * ni * h->esz)) || (rc = dalloc(h, &h->ginv, nd * h->esz)) ||
       (rc = dalloc(h, &h->gt1, nd * h->esz)) || (rc = dalloc(h, &h->gt2, nd * h->esz)))
     return rc;
   cudaError_t e;

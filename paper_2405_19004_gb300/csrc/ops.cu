@@ -263,32 +263,90 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
   }
 }
 
+// One pass of the global fast diagonalisation: for every line L of the
+// ni^(d-1) lines along the slowest index c,
+//   out[L][o] = sum_c in[c][L] W[c][o]   (MODE 1: times inv[L][o]),
+// i.e. the product In^T W of an (ni x NL) and an (ni x ni) matrix, written
+// with o fastest (the next pass contracts the next direction).  A block
+// computes FD_TL lines x FD_TO outputs; the whole contraction length fits
+// in shared memory (ni <= 255), so the input and weight tiles are loaded in
+// one stage.  Each thread owns a 4 x 4 register tile: per c, one 4-vector
+// of the input tile (lines) and one of the weight tile (outputs), 16 FMAs.
+constexpr int FD_TL = 32, FD_TO = 64, FD_THREADS = (FD_TL / 4) * (FD_TO / 4);
+
+template <typename T>
+__device__ __forceinline__ void ld4s(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+}
+
 template <typename T, int MODE>
-__global__ void fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out,
-                                      const T* __restrict__ S, const T* __restrict__ inv, int ni,
-                                      int dim, int in_lev, int out_lev, int px, int pz) {
+__global__ void __launch_bounds__(FD_THREADS)
+fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ W,
+                      const T* __restrict__ inv, int ni, int dim, int in_lev, int out_lev, int px,
+                      int pz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);  // [ni][FD_TL]
+  T* Bs = As + (size_t)ni * FD_TL;         // [ni][FD_TO]
   const int NL = dim == 3 ? ni * ni : ni;
-  const int total = NL * ni;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int o = e % ni, L = e / ni;
-    // L splits into (slow, fast) = (a, b) of the two remaining indices
-    const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
-    T acc = T(0);
-    for (int c = 0; c < ni; ++c) {
-      T v;
-      if (in_lev)
+  const int L0 = blockIdx.x * FD_TL, o0 = blockIdx.y * FD_TO;
+  for (int u = threadIdx.x; u < ni * FD_TL; u += FD_THREADS) {
+    const int l = u % FD_TL, c = u / FD_TL, L = L0 + l;
+    T v = T(0);
+    if (L < NL) {
+      if (in_lev) {
+        const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
         v = dim == 3 ? in[(c + 1) * pz + (a + 1) * px + bb + 1] : in[(c + 1) * px + bb + 1];
-      else
-        v = in[c * NL + L];
-      const T w = MODE == 2 ? S[o * ni + c] : S[c * ni + o];
-      acc = fma(w, v, acc);
+      } else {
+        v = in[(size_t)c * NL + L];
+      }
     }
-    if (MODE == 1) acc *= inv[L * ni + o];
-    if (out_lev) {
-      if (dim == 3) out[(a + 1) * pz + (bb + 1) * px + o + 1] = acc;
-      else out[(L + 1) * px + o + 1] = acc;
-    } else {
-      out[L * ni + o] = acc;
+    As[u] = v;
+  }
+  for (int u = threadIdx.x; u < ni * FD_TO; u += FD_THREADS) {
+    const int oo = u % FD_TO, c = u / FD_TO, o = o0 + oo;
+    Bs[u] = o < ni ? W[c * ni + o] : T(0);
+  }
+  __syncthreads();
+  const int tl = threadIdx.x % (FD_TL / 4), to = threadIdx.x / (FD_TL / 4);
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+  for (int c = 0; c < ni; ++c) {
+    T av[4], bv[4];
+    ld4s(As + c * FD_TL + 4 * tl, av);
+    ld4s(Bs + c * FD_TO + 4 * to, bv);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int L = L0 + 4 * tl + i;
+    if (L >= NL) continue;
+    const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + 4 * to + j;
+      if (o >= ni) continue;
+      T r = acc[i][j];
+      if (MODE == 1) r *= inv[(size_t)L * ni + o];
+      if (out_lev) {
+        if (dim == 3) out[(a + 1) * pz + (bb + 1) * px + o + 1] = r;
+        else out[(L + 1) * px + o + 1] = r;
+      } else {
+        out[(size_t)L * ni + o] = r;
+      }
     }
   }
 }
@@ -296,21 +354,20 @@ __global__ void fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* S, const T* inv, int ni,
+cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
                                   int dim, bool in_lev, bool out_lev, int px, int pz,
                                   cudaStream_t s) {
-  const int64_t total = (int64_t)ni * ni * (dim == 3 ? ni : 1);
-  const unsigned grid = grid_for(total);
+  const int NL = dim == 3 ? ni * ni : ni;
+  const dim3 grid((unsigned)((NL + FD_TL - 1) / FD_TL), (unsigned)((ni + FD_TO - 1) / FD_TO));
+  const size_t smem = (size_t)ni * (FD_TL + FD_TO) * sizeof(T);
+  auto kern = mode == 0 ? fd_global_pass_kernel<T, 0>
+                        : (mode == 1 ? fd_global_pass_kernel<T, 1> : fd_global_pass_kernel<T, 2>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   VPS_COUNT_LAUNCH();
-  if (mode == 0)
-    fd_global_pass_kernel<T, 0><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
-                                                          px, pz);
-  else if (mode == 1)
-    fd_global_pass_kernel<T, 1><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
-                                                          px, pz);
-  else
-    fd_global_pass_kernel<T, 2><<<grid, kThreads, 0, s>>>(in, out, S, inv, ni, dim, in_lev, out_lev,
-                                                          px, pz);
+  kern<<<grid, FD_THREADS, smem, s>>>(in, out, W, inv, ni, dim, in_lev, out_lev, px, pz);
   return cudaGetLastError();
 }
 

@@ -176,11 +176,12 @@ template <typename T>
 cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s);
 
 // One pass of the global fast diagonalisation of a level (runtime ni):
-// out[L][o] = sum_c W(c, o) in[c][L] with W = S (MODE 0: S^T, MODE 1: S^T
-// then * inv[L*ni+o], MODE 2: S).  in_lev / out_lev: read / write the
-// interior of a level-layout vector instead of a compact tensor.
+// out[L][o] = sum_c W[c*ni + o] in[c][L], MODE 1 then times inv[L*ni+o]
+// (W = S applies S^T to each line; W = S^T stored row-major applies S).
+// in_lev / out_lev: read / write the interior of a level-layout vector
+// instead of a compact tensor.
 template <typename T>
-cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* S, const T* inv, int ni,
+cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
                                   int dim, bool in_lev, bool out_lev, int px, int pz,
                                   cudaStream_t s);
 

@@ -123,7 +123,7 @@ def test_vcycle_matches_oracle(d, k, L, sm, om, prec, coarse):
     assert rel_err(to_host(P, x, L), H.vcycle(L, b)) <= tol
 
 
-@pytest.mark.parametrize("d,k,L", [(2, 3, 4), (3, 2, 3), (2, 7, 2), (3, 5, 2)])
+@pytest.mark.parametrize("d,k,L", [(2, 3, 4), (3, 2, 3), (2, 7, 2), (3, 5, 2), (2, 7, 5), (2, 4, 6)])
 def test_coarse_level_equal_to_finest_makes_the_vcycle_exact(d, k, L):
     """Global fast diagonalisation of a whole level is its exact inverse."""
     import scipy.sparse.linalg as spla
