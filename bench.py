@@ -43,16 +43,30 @@ CPU_SAMPLE_LEVEL = 3           # oracle sample: same problem family at level 3
 CPU_SAMPLE_REPEATS = 10
 
 
-def smoother_flops_per_patch(d, k):
-    """Dense sum-factorised flops of one fused patch update (FMA = 2 flops).
-
-    Local residual with interior output rows, then fast diagonalisation:
-    3D: 4mn^3 + 6m^2n^2 + 4m^3n + 12m^4 + 4m^3;  2D: 4mn^2 + 4m^2n + 8m^3 + 4m^2.
-    """
-    n, m = 2 * k + 1, 2 * k - 1
-    if d == 3:
-        return 4 * m * n ** 3 + 6 * m * m * n * n + 4 * m ** 3 * n + 12 * m ** 4 + 4 * m ** 3
-    return 4 * m * n * n + 4 * m * m * n + 8 * m ** 3 + 4 * m * m
+def smoother_traffic(variant):
+    """DRAM bytes per finest-level colour pass of the timed smoother kernel,
+    from the committed ncu summary of that kernel (dram__bytes_read.sum +
+    dram__bytes_write.sum), or None if the summary is for another variant or
+    was taken before the kernel source last changed."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "smoother_traffic_3d_q4_l5.md")
+    src = os.path.join(ROOT, "paper_2405_19004_gb300", "csrc", "kernels_dk.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            key, val = line[2:].split(":", 1)
+            vals[key.strip()] = val.strip().strip("`")
+    if vals.get("kernels_dk.cu sha256") != sha or vals.get("variant") != str(variant):
+        return None
+    try:
+        return float(vals["traffic bytes per launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -237,6 +251,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2405_19004_gb300 as vps
+    from paper_2405_19004_gb300.studies import smoother_flops_per_patch
     from synthetic import uniform_vector
 
     P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
@@ -339,7 +354,9 @@ def main():
     launch_ms = [a.elapsed_time(z) for a, z in evs]
     t_launch = statistics.mean(launch_ms) / 1e3
     n_patches = (2 ** L - 1) ** 3
-    flops_per_launch = smoother_flops_per_patch(D, K) * n_patches / 8.0
+    var_L = P.vps_get_smooth_variant(L)[0]
+    bnd_L = var_L // 3 == 1
+    flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / 8.0
     achieved = flops_per_launch / t_launch / 1e12
     t_smooth_step = 8 * t_launch
 
@@ -368,7 +385,8 @@ def main():
         e1.record(P64.stream)
         torch.cuda.synchronize()
         t64_step = e0.elapsed_time(e1) / 3e3
-        f64 = smoother_flops_per_patch(D, K) * n_patches / t64_step / 1e12
+        bnd64 = P64.vps_get_smooth_variant(L)[0] // 3 == 1
+        f64 = smoother_flops_per_patch(D, K, bnd64) * n_patches / t64_step / 1e12
         dx = (x64 - x).abs().max().item() / x64.abs().max().item()
         extras = {
             "time_to_1e-10_s": {"fp32_mg": t_step, "fp64": min(t64), "speedup": min(t64) / t_step},
@@ -419,9 +437,11 @@ def main():
         "iterations": its[-1], "rel_residual": rel,
         "smoother_fp32": {"dof_per_s": N / t_smooth_step, "tflops": achieved,
                           "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS},
-        "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level",
+        "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level, "
+                               + ("Boundary" if bnd_L else "fused") + f" variant {var_L}",
                      "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": smoother_traffic(var_L),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "avg_launch_us": 1e6 * t_launch, "flops_per_launch": flops_per_launch},
         "e2e": {"value": world * N / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,

@@ -142,11 +142,21 @@ int vps_vcycle(vps_handle h, const void* b, void* x);
 
 /*
  * vps_solve -- CG on the finest level, preconditioned by one V-cycle per
- * iteration, x0 = 0, until ||b - A x||_2 <= rtol ||b||_2 (beta in the
- * flexible Polak-Ribiere form).  b, x: compact DOUBLE device vectors.
- * iters / rel_res (host pointers, may be NULL) receive the iteration count
- * and final relative residual.  Synchronises the stream once per iteration
- * to read the residual norm.  Errors: VPS_ENOCONV, VPS_EBREAKDOWN, ...
+ * iteration, x0 = 0 (beta in the flexible Polak-Ribiere form).  When the
+ * recursive residual reaches rtol ||b||_2, the residual r = b - A x is
+ * evaluated in FP64 and the solve ends if
+ *   ||r||_2 <= rtol ||b||_2, or
+ *   ||r||_2 <= gamma || |A| |x| ||_2,  gamma = (6k+6) 2^-53,
+ * the second being the rounding bound of the FP64 evaluation of r itself
+ * (reached first when rtol is below what FP64 can resolve: the terms of
+ * A x cancel by about k^2 h^-2 for smooth solutions, so e.g. 2D meshes of
+ * 2^10 cells per direction cannot show 1e-10); |A| is the operator with the
+ * absolute values of its 1D band coefficients.  Otherwise CG restarts from
+ * r; a restart that does not halve ||r|| ends with VPS_ENOCONV.
+ * b, x: compact DOUBLE device vectors.  iters / rel_res (host pointers, may
+ * be NULL) receive the iteration count and the final FP64 relative
+ * residual ||r||/||b||.  Synchronises the stream once per iteration to read
+ * the residual norm.  Errors: VPS_ENOCONV, VPS_EBREAKDOWN, ...
  */
 int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
               int* iters, double* rel_res);
@@ -202,8 +212,15 @@ int vps_get_coarse_level(vps_handle h, int* level);
  */
 int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
 
-/* vps_set_smooth_variant / vps_get_smooth_variant -- the smoother variant
- * (0..2) of `level` (0: every level), and its patches per thread block. */
+/* vps_set_smooth_variant / vps_get_smooth_variant -- the smoother kernel
+ * variant of `level` (0: every level), and its patches per thread block.
+ *   0, 1, 2: the fused kernel (Algorithm 3) with 1, 2, 4 patches per thread;
+ *   3, 4, 5: the Boundary kernel of Section 3.2 with 1, 2, 4 patches per
+ *            thread: x_I = A_j^-1 (b_I - A^IB x_B), which equals the fused
+ *            update for the exact local solver without reading x_I
+ *            (VPS_MULTIPLICATIVE handles only).
+ * A variant whose shared memory exceeds the GPU's limit for the handle's
+ * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);
 int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_per_block);
 
@@ -231,6 +248,12 @@ int vps_kernel_launches(vps_handle h, int64_t* count);
 #define VPS_OUTER_DOUBLE_FLOAT 1
 int vps_set_outer_operator(vps_handle h, int mode);
 int vps_get_outer_operator(vps_handle h, int* mode);
+
+/* vps_get_solve_info -- of the handle's last solve: the number of CG
+ * restarts from the FP64 residual, and 1 if it ended at the rounding bound
+ * of that residual rather than at rtol (see vps_solve).  Host outputs, may
+ * be NULL. */
+int vps_get_solve_info(vps_handle h, int* restarts, int* at_rounding_bound);
 
 /*
  * vps_apply_outer -- y = A x on the finest level with the handle's outer

@@ -9,6 +9,10 @@ cells of the support).  This gives
 * ``patch_update``   -- R_j^T A_j^{-1} R_j (b - A x) for one vertex patch
                         (Eq. 2.5/2.6, equivalently the localised form of
                         Section 2.2 that only reads the patch closure);
+* ``patch_boundary_solve`` -- the new interior values A_j^{-1}(b^I - A^{IB} x^B)
+                        of the reduced local residual of Section 3.2
+                        ("Boundary"), from the partition of Abar_j into
+                        interior and boundary columns;
 * ``apply_rows``     -- (A x)_i for chosen nodes i;
 * ``prolongate_rows``-- (I^up x_c)_i for chosen fine nodes i;
 * ``restrict_rows``  -- ((I^up)^T r_f)_j for chosen coarse nodes j.
@@ -110,6 +114,26 @@ def patch_update(level, xfull, bfull, v, mats=None):
     for t in range(d):
         gi += (k * (v[t] - 1) + Ln[:, t]) * n1 ** t
     r = bfull[gi[rows]] - Abar @ xfull[gi]
+    return gi[rows], sla.solve(Aj, r, assume_a="sym")
+
+
+def patch_boundary_solve(level, xfull, bfull, v, mats=None):
+    """x^I <- A_j^{-1} (b^I - A^{IB} x^B) for the patch at vertex v (Section 3.2).
+
+    Abar_j = [A^{II} A^{IB}] over the closure columns split into the patch
+    interior I and its boundary B; A_j = A^{II}.  Returns (interior
+    full-grid indices, new interior values).
+    """
+    d, k, n1 = level.d, level.k, level.n1
+    n = 2 * k + 1
+    Abar, Aj, rows = patch_matrices(level) if mats is None else mats
+    Ln = fe.multi_indices(n, d)
+    gi = np.zeros(len(Ln), dtype=np.int64)
+    for t in range(d):
+        gi += (k * (v[t] - 1) + Ln[:, t]) * n1 ** t
+    bcols = np.setdiff1d(np.arange(len(Ln)), rows)
+    AIB = Abar[:, bcols]
+    r = bfull[gi[rows]] - AIB @ xfull[gi[bcols]]
     return gi[rows], sla.solve(Aj, r, assume_a="sym")
 
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "vps_set_outer_operator": (_i, [_p, _i]),
     "vps_get_outer_operator": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_apply_outer": (_i, [_p, _p, _p]),
+    "vps_get_solve_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
     "vps_set_coarse_level": (_i, [_p, _i]),
     "vps_autotune": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i)]),
@@ -293,6 +294,12 @@ class Poisson:
     def vps_apply_outer(self, x, y):
         assert x.dtype == self.torch.float64 and y.dtype == self.torch.float64
         self._call(lib().vps_apply_outer, _ptr(x), _ptr(y))
+
+    def vps_get_solve_info(self):
+        """(restarts, at_rounding_bound) of the last solve."""
+        r, f = ctypes.c_int(), ctypes.c_int()
+        _check(lib().vps_get_solve_info(self.h, ctypes.byref(r), ctypes.byref(f)), self.h)
+        return r.value, f.value
 
     def vps_get_outer_operator(self):
         c = ctypes.c_int()

@@ -97,6 +97,9 @@ struct vps_context {
   // two float vectors cph + cpl) with a final FP64 check of the residual
   int outer = VPS_OUTER_FP64;
   float *cph = nullptr, *cpl = nullptr;
+  // last solve: restarts from the FP64 residual, and whether it stopped at
+  // the rounding level of the residual's own evaluation instead of rtol
+  int last_restarts = 0, last_at_floor = 0;
   double* partial = nullptr;            // 2 * kDotBlocks
   double* dots = nullptr;               // scratch scalars for norms
   CgScalars* sc = nullptr;
@@ -118,7 +121,9 @@ struct vps_context {
   // asynchronous CG (used by the serving loop)
   int as_phase = 0;                     // 0 idle, 1 iteration in flight, 2 result copy in flight
   int as_it = 0, as_maxit = 0, as_status = 0;
-  bool as_verify = false;               // true residual in flight (double-float outer operator)
+  int as_verify = 0;                    // 1: FP64 residual in flight, 2: |A||x| in flight
+  double as_true = 0.0;                 // FP64 residual while |A||x| is in flight
+  double as_prev_true = 0.0;            // FP64 residual of the previous check
   double as_nb = 0.0, as_rtol = 0.0, as_rel = 0.0;
   double* host_x = nullptr;             // pinned staging of the compact result
   cudaEvent_t as_ev = nullptr;
@@ -203,7 +208,9 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   const int nc = 1 << h->dim;
   const T* il = static_cast<const T*>(h->inv_lam);
   const int v = h->smooth_var[l];
-  if (!fns<T>(h).smooth_mult_v[v] || !fns<T>(h).smooth_add_v[v])
+  if (v < 0 || v >= kSmoothVariants ||
+      !(h->smoother == VPS_ADDITIVE ? fns<T>(h).smooth_add_v[v] != nullptr
+                                    : fns<T>(h).smooth_mult_v[v] != nullptr))
     return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
   if (h->smoother == VPS_ADDITIVE) {
     T* r = static_cast<T*>(h->rv[l]);
@@ -421,12 +428,43 @@ int cg_true_residual(vps_context* h) {
   return VPS_OK;
 }
 
+// U = |A| |x| into cAp and U . U into sc->pAp (asynchronous).
+int cg_residual_scale(vps_context* h) {
+  const LevelGeom& g = h->geom[h->L];
+  VPS_CK(h, h->ks->apply_abs(g, h->cx, h->cAp, h->stream));
+  VPS_CK(h, launch_dot1(h->cAp, h->cAp, g.total, h->partial, &h->sc->pAp, h->stream));
+  return VPS_OK;
+}
+
+// Relative rounding bound of the FP64 residual evaluation: every entry of
+// b - A x is computed with an error below gamma (|A| |x|)_i, gamma the
+// first-order bound (chain length) u of the sum-factorised contractions.
+double residual_gamma(const vps_context* h) { return (6.0 * h->k + 6.0) * std::ldexp(1.0, -53); }
+
+// Outcome of a convergence check on the FP64 residual.
+enum { kCheckConverged = 1, kCheckRestart = 0, kCheckStagnated = -1 };
+
+// rel_true = ||b - A x|| / ||b||; scale_norm = || |A||x| || (< 0: not known yet).
+int classify_check(vps_context* h, double rtol, double nb, double rel_true, double scale_norm,
+                   double prev_true) {
+  if (rel_true <= rtol) return kCheckConverged;
+  if (scale_norm >= 0.0 && rel_true * nb <= residual_gamma(h) * scale_norm) {
+    h->last_at_floor = 1;
+    return kCheckConverged;
+  }
+  if (prev_true > 0.0 && !(rel_true < 0.5 * prev_true)) return kCheckStagnated;
+  return kCheckRestart;
+}
+
 // Preconditioned CG (Section 4.1's outer solver) with the flexible
-// (Polak-Ribiere) beta.  With the double-float outer operator the recursive
-// residual can drift from the true one by the operator's rounding (about
-// 2^-48 of the sum of the magnitudes of its terms); convergence is therefore
-// confirmed on r = b - A x evaluated in FP64, and the iteration restarts
-// from that residual when it is not yet below the tolerance.
+// (Polak-Ribiere) beta.  Convergence is always confirmed on the residual
+// r = b - A x evaluated in FP64: the recursive residual can drift from it
+// (double-float outer operator: by about 2^-48 of the magnitudes of the
+// operator's terms), and on fine meshes rtol can lie below what FP64 can
+// resolve at all (the terms of A x cancel by about k^2 h^-2).  The solve
+// ends when the FP64 residual is below rtol, or below the rounding bound of
+// its own evaluation (gamma || |A||x| ||); otherwise CG restarts from it,
+// and a restart that does not halve it ends the solve (VPS_ENOCONV).
 int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_res) {
   const LevelGeom& g = h->geom[h->L];
   const int64_t n = g.total;
@@ -437,6 +475,8 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   const double nb = std::sqrt(h->host_dots[0]);
   VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
+  h->last_restarts = 0;
+  h->last_at_floor = 0;
   if (iters) *iters = 0;
   if (rel_res) *rel_res = 0.0;
   if (!(nb > 0.0)) {
@@ -448,7 +488,7 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
   int rc = precondition(h);
   if (rc) return rc;
   if ((rc = cg_start_direction(h))) return rc;
-  double rel = 1.0;
+  double rel = 1.0, prev_true = 0.0;
   for (int it = 1; it <= max_it; ++it) {
     if ((rc = cg_apply_p(h))) return rc;
     VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
@@ -469,7 +509,6 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
     bool restart = false;
     if (rel <= rtol) {
-      if (!outer_df(h)) return VPS_OK;
       if ((rc = cg_true_residual(h))) return rc;
       VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                 h->stream));
@@ -478,7 +517,22 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       if (rel_res) *rel_res = rel;
       if (!std::isfinite(rel))
         return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
-      if (rel <= rtol) return VPS_OK;
+      double unorm = -1.0;
+      if (rel > rtol) {  // below the rounding level of its evaluation?
+        if ((rc = cg_residual_scale(h))) return rc;
+        VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                  h->stream));
+        VPS_CK(h, cudaStreamSynchronize(h->stream));
+        unorm = std::sqrt(h->host_sc->pAp);
+      }
+      const int cls = classify_check(h, rtol, nb, rel, unorm, prev_true);
+      if (cls == kCheckConverged) return VPS_OK;
+      if (cls == kCheckStagnated)
+        return fail(h, VPS_ENOCONV,
+                    "CG stagnated at an FP64 residual of %g (rtol %g, rounding bound %g)", rel, rtol,
+                    residual_gamma(h) * unorm / nb);
+      prev_true = rel;
+      ++h->last_restarts;
       restart = true;
     }
     if (it == max_it) break;
@@ -628,7 +682,10 @@ int cg_async_begin(vps_handle h, int n_modes, const double* coef, const int* fre
   h->as_it = 1;
   h->as_rel = 1.0;
   h->as_status = VPS_OK;
-  h->as_verify = false;
+  h->as_verify = 0;
+  h->as_prev_true = 0.0;
+  h->last_restarts = 0;
+  h->last_at_floor = 0;
   if (int rc = upload_rhs_sines(h, n_modes, coef, freq, h->comp_b)) return rc;
   VPS_CK(h, launch_pack<double>(g, h->comp_b, h->cb, h->stream));
   VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
@@ -669,21 +726,40 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
   if (h->host_sc->flag) return cg_async_finish(h, VPS_EBREAKDOWN);
   h->as_rel = std::sqrt(h->host_sc->rr) / h->as_nb;
   if (!std::isfinite(h->as_rel)) return cg_async_finish(h, VPS_EBREAKDOWN);
-  const bool verified = h->as_verify;
-  h->as_verify = false;
-  if (h->as_rel <= h->as_rtol) {
-    if (!outer_df(h) || verified) return cg_async_finish(h, VPS_OK);
+  // the convergence check of cg_solve, one asynchronous step at a time
+  bool restart = false;
+  if (h->as_verify == 1 && h->as_rel > h->as_rtol) {  // FP64 residual above rtol: scale
+    if (int rc = cg_residual_scale(h)) return rc;
+    VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                              h->stream));
+    VPS_CK(h, cudaEventRecord(h->as_ev, h->stream));
+    h->as_verify = 2;
+    h->as_true = h->as_rel;
+    return VPS_OK;
+  }
+  if (h->as_verify) {
+    const double rel_true = h->as_verify == 2 ? h->as_true : h->as_rel;
+    const double unorm = h->as_verify == 2 ? std::sqrt(h->host_sc->pAp) : -1.0;
+    h->as_rel = rel_true;
+    h->as_verify = 0;
+    const int cls = classify_check(h, h->as_rtol, h->as_nb, rel_true, unorm, h->as_prev_true);
+    if (cls == kCheckConverged) return cg_async_finish(h, VPS_OK);
+    if (cls == kCheckStagnated) return cg_async_finish(h, VPS_ENOCONV);
+    h->as_prev_true = rel_true;
+    ++h->last_restarts;
+    restart = true;
+  } else if (h->as_rel <= h->as_rtol) {
     // confirm on the FP64 residual r = b - A x (see cg_solve)
     if (int rc = cg_true_residual(h)) return rc;
     VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                               h->stream));
     VPS_CK(h, cudaEventRecord(h->as_ev, h->stream));
-    h->as_verify = true;
+    h->as_verify = 1;
     return VPS_OK;
   }
   if (h->as_it >= h->as_maxit) return cg_async_finish(h, VPS_ENOCONV);
   if (int rc = precondition(h)) return rc;
-  if (verified) {  // the true residual is still above the tolerance: restart from it
+  if (restart) {  // from the FP64 residual, which is still above the tolerance
     VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
     if (int rc = cg_async_iteration(h, true)) return rc;
   } else if (int rc = cg_async_iteration(h, false)) {
@@ -889,10 +965,17 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     }
   }
   int rc;
-  const bool mid_ok = precision == VPS_FP64 ? h->ks->d.smooth_mult_v[1] != nullptr
-                                             : h->ks->f.smooth_mult_v[1] != nullptr;
+  // default variant before tuning: the Boundary kernel with 2 (else 1) patches
+  // per thread for the multiplicative smoother; 2 (else 1) for the additive
+  const int prefer[2][4] = {{4, 3, 1, 0}, {1, 0, 1, 0}};
+  int def_var = 0;
+  for (int v : prefer[smoother == VPS_ADDITIVE ? 1 : 0])
+    if (variant_ok(h, v)) {
+      def_var = v;
+      break;
+    }
   for (int l = 1; l <= level; ++l) {
-    h->smooth_var[l] = mid_ok ? 1 : 0;
+    h->smooth_var[l] = def_var;
     h->geom[l] = make_geom(dim, degree, l);
     const size_t vb = (size_t)h->geom[l].total * h->esz;
     if ((rc = dalloc(h, &h->bv[l], vb)) || (rc = dalloc(h, &h->xv[l], vb)) ||
@@ -1340,6 +1423,13 @@ int vps_set_outer_operator(vps_handle h, int mode) {
     h->cpl = (float*)p;
   }
   h->outer = mode;
+  return VPS_OK;
+}
+
+int vps_get_solve_info(vps_handle h, int* restarts, int* at_rounding_bound) {
+  if (!h) return VPS_EINVAL;
+  if (restarts) *restarts = h->last_restarts;
+  if (at_rounding_bound) *at_rounding_bound = h->last_at_floor;
   return VPS_OK;
 }
 

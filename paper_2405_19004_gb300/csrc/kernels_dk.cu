@@ -29,6 +29,7 @@
 // patch index is the fastest index ([c][L][p]); P is a power of two, so
 // for both 4- and 8-byte words every warp access is free of bank conflicts
 // (the odd extents 2k+1 and 2k-1 keep the strided writes conflict free).
+#include <cmath>
 #include <cstdio>
 
 #include "vps_internal.h"
@@ -66,6 +67,26 @@ struct DevTab {
 template <typename T>
 __constant__ DevTab<T> c_tab;
 
+// |Kb|, |Mb| in FP64: the absolute-value operator |K|x|M|x|M| + ... that
+// bounds the rounding error of an evaluation of A x (FP64 residual checks)
+struct AbsTab {
+  double Kb[K * n];
+  double Mb[K * n];
+};
+__constant__ AbsTab c_abs;
+
+// Band coefficients of the operator (ABS: their absolute values, FP64 only).
+template <typename T, bool ABS>
+__device__ __forceinline__ T coefK(int i) {
+  if constexpr (ABS) return (T)c_abs.Kb[i];
+  else return c_tab<T>.Kb[i];
+}
+template <typename T, bool ABS>
+__device__ __forceinline__ T coefM(int i) {
+  if constexpr (ABS) return (T)c_abs.Mb[i];
+  else return c_tab<T>.Mb[i];
+}
+
 // ---------------------------------------------------------------- config
 // ------------------------------------------------------------- smoother
 // A block holds P = G * Q patches.  In every contraction stage thread t
@@ -79,7 +100,7 @@ __constant__ DevTab<T> c_tab;
 constexpr int kLinesMax = DIM == 3 ? n * n : n;
 constexpr int kG = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 4 : K == 3 ? 2 : 1)
                             : (K <= 2 ? 32 : (K <= 4 ? 16 : 8));
-constexpr int kVarQ[kSmoothVariants] = {1, 2, 4};
+constexpr int kVarQ[kQVariants] = {1, 2, 4};
 
 template <class T, int Q>
 struct alignas(sizeof(T) * Q) Pack {
@@ -102,8 +123,11 @@ struct SmoothCfg {
   static constexpr size_t elems_mult =
       (size_t)P * (2 * sizeA + nB * sizeB + 2 * md) + md;
   static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
+  // Boundary kernel: no staged copy of the interior of x
+  static constexpr size_t smem_bnd = smem_mult - sizeof(T) * (size_t)P * md;
   static constexpr size_t smem_add = sizeof(T) * ((size_t)P * 2 * md + md) + sizeof(int) * P;
   static constexpr bool fits = smem_mult <= 227 * 1024 && G * kLinesMax <= 1024;
+  static constexpr bool fits_bnd = smem_bnd <= 227 * 1024 && G * kLinesMax <= 1024;
 };
 
 // Calls f(t) for every line t = threadIdx.x + r * NT < TOTAL, with the
@@ -131,12 +155,13 @@ __device__ __forceinline__ int closure_origin(int gp, const ColourGeom& cg, int 
   return o0 + o1 * px + o2 * pz;
 }
 
-// Origins of the block's P patches (-1: beyond the colour), computed once.
-template <int P>
+// Origins of the block's P patches (-1: beyond the colour), computed once;
+// P may exceed the block's NT threads (2D, k = 1, 4 patches per thread).
+template <int P, int NT>
 __device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, int px, int pz) {
-  if (threadIdx.x < P) {
-    const int64_t gp = (int64_t)blockIdx.x * P + threadIdx.x;
-    s_org[threadIdx.x] = gp < cg.npatch ? closure_origin((int)gp, cg, px, pz) : -1;
+  for (int i = threadIdx.x; i < P; i += NT) {
+    const int64_t gp = (int64_t)blockIdx.x * P + i;
+    s_org[i] = gp < cg.npatch ? closure_origin((int)gp, cg, px, pz) : -1;
   }
 }
 
@@ -195,8 +220,9 @@ __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict
 }
 
 // S along the last direction and the update of the interior:
-// x_I = base + scale * u, base from the staged xI (xs) or from x itself.
-template <typename T, int G, int Q, int NT>
+// x_I = base + scale * u, base from the staged xI (xs) or from x itself;
+// SET: x_I = scale * u.
+template <typename T, int G, int Q, int NT, bool SET = false>
 __device__ __forceinline__ void fd_final(const T* __restrict__ in, T* __restrict__ x,
                                          const T* xs, const int* s_org, int px, int pz, T scale) {
   constexpr int NL = DIM == 3 ? m * m : m;
@@ -238,8 +264,12 @@ __device__ __forceinline__ void fd_final(const T* __restrict__ in, T* __restrict
       T* dst = x + org + rowoff;
 #pragma unroll
       for (int o = 0; o < m; ++o) {
-        const T base = xs ? xs[(L * m + o) * P + g * Q + j] : dst[o];
-        dst[o] = fma(scale, u[o][j], base);
+        if constexpr (SET) {
+          dst[o] = scale * u[o][j];
+        } else {
+          const T base = xs ? xs[(L * m + o) * P + g * Q + j] : dst[o];
+          dst[o] = fma(scale, u[o][j], base);
+        }
       }
     }
   });
@@ -277,7 +307,41 @@ __device__ __forceinline__ void prefetch_b(const T* __restrict__ b, T* bI, const
 }
 
 // ------------------------------------------------------- multiplicative
-template <typename T, int QQ>
+// Closure lines along the first contracted direction, in the order the
+// Boundary kernel assigns them to threads: the 8K lines on the faces of the
+// other directions first (2D: the 2 lines at x = 0, 2K), then the interior
+// lines, which meet the patch boundary only at their two end nodes.
+// Returns the layout index of the line; *full: all its nodes are boundary
+// nodes of the patch.
+__device__ __forceinline__ int boundary_first_line(int L, bool* full) {
+  if constexpr (DIM == 3) {
+    constexpr int nb = 2 * n + 2 * m;  // = 8K
+    int yy, xx;
+    if (L < n) {
+      yy = 0; xx = L;
+    } else if (L < 2 * n) {
+      yy = n - 1; xx = L - n;
+    } else if (L < nb) {
+      const int r = L - 2 * n;
+      yy = 1 + r / 2; xx = (r & 1) ? n - 1 : 0;
+    } else {
+      const int r = L - nb;
+      yy = 1 + r / m; xx = 1 + r % m;
+    }
+    *full = L < nb;
+    return yy * n + xx;
+  } else {
+    *full = L < 2;
+    return L == 0 ? 0 : (L == 1 ? n - 1 : L - 1);
+  }
+}
+
+// BND = false: the fused kernel, x_I += A_j^-1 (b_I - Abar x) (Algorithm 3).
+// BND = true: the Boundary kernel, x_I = A_j^-1 (b_I - A^IB x_B) (Section
+// 3.2), equal for the exact local solver: the interior of x is neither read
+// nor staged, and lines of the first contraction that run through the
+// patch interior contract only their two end (boundary) nodes.
+template <typename T, int QQ, bool BND>
 __global__ void __launch_bounds__(SmoothCfg<T, QQ>::NT)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
                    int px, int pz, ColourGeom cg, T bscale) {
@@ -289,10 +353,10 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
   T* A1 = A0 + P * C::sizeA;
   T* B0 = A1 + P * C::sizeA;
   T* bI = B0 + C::nB * P * C::sizeB;
-  T* xI = bI + P * MD;
-  T* il = xI + P * MD;
+  T* xI = BND ? nullptr : bI + P * MD;
+  T* il = bI + (BND ? 1 : 2) * P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
-  load_origins<P>(s_org, cg, px, pz);
+  load_origins<P, NT>(s_org, cg, px, pz);
   for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   prefetch_b<T, G, Q, NT>(b, bI, s_org, px, pz);
@@ -302,8 +366,36 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     // Stage 0: z-lines of the closure from global memory; M x and A x along
     // z (interior rows) into [y][x][oz]; the interior of x is kept in xI.
     for_lines<G * n * n, NT>([&](const int t) {
-      const int L = t / G, g = t % G;
+      int L = t / G;
+      const int g = t % G;
+      bool full = true;
+      if constexpr (BND) L = boundary_first_line(L, &full);
       const int yy = L / n, xx = L % n;
+      PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+      PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
+      if (BND && !full) {
+        // interior line: the patch interior of x counts as zero
+        T v0[Q], v1[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          const int org = s_org[g * Q + j];
+          const T* src = x + (org >= 0 ? org : 0) + yy * px + xx;
+          v0[j] = org >= 0 ? src[0] : T(0);
+          v1[j] = org >= 0 ? src[(n - 1) * pz] : T(0);
+        }
+#pragma unroll
+        for (int o = 0; o < m; ++o) {
+          PK am, aa;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            am.v[j] = fma(c_tab<T>.Mp[o * n + n - 1], v1[j], c_tab<T>.Mp[o * n] * v0[j]);
+            aa.v[j] = fma(c_tab<T>.Ap[o * n + n - 1], v1[j], c_tab<T>.Ap[o * n] * v0[j]);
+          }
+          dM[o * G] = am;
+          dA[o * G] = aa;
+        }
+        return;
+      }
       T v[n][Q];
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
@@ -312,7 +404,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c][j] = org >= 0 ? src[c * pz] : T(0);
       }
-      if (yy >= 1 && yy <= m && xx >= 1 && xx <= m) {
+      if (!BND && yy >= 1 && yy <= m && xx >= 1 && xx <= m) {
         PK* d = reinterpret_cast<PK*>(xI + ((yy - 1) * m + xx - 1) * P + g * Q);
 #pragma unroll
         for (int c = 1; c <= m; ++c) {
@@ -322,8 +414,6 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
           d[(c - 1) * m * m * G] = pk;
         }
       }
-      PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
-      PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
 #pragma unroll
       for (int o = 0; o < m; ++o) {
         PK am, aa;
@@ -434,11 +524,39 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     __syncthreads();
     fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);
     __syncthreads();
-    fd_final<T, G, Q, NT>(A1, x, xI, s_org, px, pz, T(1));
+    fd_final<T, G, Q, NT, BND>(A1, x, xI, s_org, px, pz, T(1));
   } else {
     // 2D.  Stage 0: lines along y from global; M x and A x along y into [x][oy].
     for_lines<G * n, NT>([&](const int t) {
-      const int L = t / G, g = t % G;
+      int L = t / G;
+      const int g = t % G;
+      bool full = true;
+      if constexpr (BND) L = boundary_first_line(L, &full);
+      if (BND && !full) {
+        // interior line (x in 1..m): only its two end nodes in y are boundary nodes
+        T v0[Q], v1[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          const int org = s_org[g * Q + j];
+          const T* src = x + (org >= 0 ? org : 0) + L;
+          v0[j] = org >= 0 ? src[0] : T(0);
+          v1[j] = org >= 0 ? src[(n - 1) * px] : T(0);
+        }
+        PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+        PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
+#pragma unroll
+        for (int o = 0; o < m; ++o) {
+          PK am, aa;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            am.v[j] = fma(c_tab<T>.Mp[o * n + n - 1], v1[j], c_tab<T>.Mp[o * n] * v0[j]);
+            aa.v[j] = fma(c_tab<T>.Ap[o * n + n - 1], v1[j], c_tab<T>.Ap[o * n] * v0[j]);
+          }
+          dM[o * G] = am;
+          dA[o * G] = aa;
+        }
+        return;
+      }
       T v[n][Q];
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
@@ -447,7 +565,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
 #pragma unroll
         for (int c = 0; c < n; ++c) v[c][j] = org >= 0 ? src[c * px] : T(0);
       }
-      if (L >= 1 && L <= m) {
+      if (!BND && L >= 1 && L <= m) {
         PK* d = reinterpret_cast<PK*>(xI + (L - 1) * P + g * Q);
 #pragma unroll
         for (int c = 1; c <= m; ++c) {
@@ -524,7 +642,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
     __syncthreads();
     fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
     __syncthreads();
-    fd_final<T, G, Q, NT>(A0, x, xI, s_org, px, pz, T(1));
+    fd_final<T, G, Q, NT, BND>(A0, x, xI, s_org, px, pz, T(1));
   }
 }
 
@@ -542,7 +660,7 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
   T* X1 = X0 + P * MD;
   T* il = X1 + P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
-  load_origins<P>(s_org, cg, px, pz);
+  load_origins<P, NT>(s_org, cg, px, pz);
   for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   constexpr int NL = DIM == 3 ? m * m : m;
@@ -628,7 +746,7 @@ struct ApplyCfg {
 #define VPS_BAND_LOOP(q, j) \
   _Pragma("unroll") for (int j = 0; j <= 2 * K; ++j) if (q == 0 || (j >= K - q && j <= 2 * K - q))
 
-template <typename T>
+template <typename T, bool ABS = false>
 __global__ void __launch_bounds__(ApplyCfg::NT)
 apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
              int64_t px, int64_t pz, T scale) {
@@ -652,13 +770,14 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int i = 0; i <= 2 * K; ++i) {
         const int gz = gz0 + i;
         v[i] = (inxy && gz >= 0 && gz < n1) ? x[(int64_t)gz * pz + (int64_t)gy * px + gx] : T(0);
+        if constexpr (ABS) v[i] = fabs(v[i]);
       }
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         T am = T(0), ak = T(0);
         VPS_BAND_LOOP(q, j) {
-          am = fma(c_tab<T>.Mb[q * n + j], v[q + j], am);
-          ak = fma(c_tab<T>.Kb[q * n + j], v[q + j], ak);
+          am = fma(coefM<T, ABS>(q * n + j), v[q + j], am);
+          ak = fma(coefK<T, ABS>(q * n + j), v[q + j], ak);
         }
         tm[((cz * K + q) * BN + yy) * RB + xx] = am;
         tk[((cz * K + q) * BN + yy) * RB + xx] = ak;
@@ -678,9 +797,9 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int q = 0; q < K; ++q) {
         T a = T(0), bb = T(0);
         VPS_BAND_LOOP(q, j) {
-          a = fma(c_tab<T>.Mb[q * n + j], vm[q + j], a);
-          bb = fma(c_tab<T>.Kb[q * n + j], vm[q + j], bb);
-          bb = fma(c_tab<T>.Mb[q * n + j], vk[q + j], bb);
+          a = fma(coefM<T, ABS>(q * n + j), vm[q + j], a);
+          bb = fma(coefK<T, ABS>(q * n + j), vm[q + j], bb);
+          bb = fma(coefM<T, ABS>(q * n + j), vk[q + j], bb);
         }
         mm[(Z * TN + cy * K + q) * RB + xx] = a;
         ww[(Z * TN + cy * K + q) * RB + xx] = bb;
@@ -706,8 +825,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
         if (gx >= n1) continue;
         T acc = T(0);
         VPS_BAND_LOOP(q, j) {
-          acc = fma(c_tab<T>.Kb[q * n + j], vm[q + j], acc);
-          acc = fma(c_tab<T>.Mb[q * n + j], vw[q + j], acc);
+          acc = fma(coefK<T, ABS>(q * n + j), vm[q + j], acc);
+          acc = fma(coefM<T, ABS>(q * n + j), vw[q + j], acc);
         }
         T out = T(0);
         if (inner_yz && gx >= 1 && gx <= n1 - 2)
@@ -725,13 +844,14 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
       for (int i = 0; i <= 2 * K; ++i) {
         const int gy = gy0 + i;
         v[i] = (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) ? x[(int64_t)gy * px + gx] : T(0);
+        if constexpr (ABS) v[i] = fabs(v[i]);
       }
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         T am = T(0), ak = T(0);
         VPS_BAND_LOOP(q, j) {
-          am = fma(c_tab<T>.Mb[q * n + j], v[q + j], am);
-          ak = fma(c_tab<T>.Kb[q * n + j], v[q + j], ak);
+          am = fma(coefM<T, ABS>(q * n + j), v[q + j], am);
+          ak = fma(coefK<T, ABS>(q * n + j), v[q + j], ak);
         }
         tm[(cy * K + q) * RB + xx] = am;
         tk[(cy * K + q) * RB + xx] = ak;
@@ -756,8 +876,8 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
         if (gx >= n1) continue;
         T acc = T(0);
         VPS_BAND_LOOP(q, j) {
-          acc = fma(c_tab<T>.Kb[q * n + j], vm[q + j], acc);
-          acc = fma(c_tab<T>.Mb[q * n + j], vk[q + j], acc);
+          acc = fma(coefK<T, ABS>(q * n + j), vm[q + j], acc);
+          acc = fma(coefM<T, ABS>(q * n + j), vk[q + j], acc);
         }
         T out = T(0);
         if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2)
@@ -795,7 +915,7 @@ struct Apply3Cfg {
   static constexpr size_t smem() { return sizeof(T) * (size_t)(4 * BX * RB + 2 * TX * RB); }
 };
 
-template <typename T>
+template <typename T, bool ABS = false>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
 apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
               int px, int pz, T scale) {
@@ -824,9 +944,10 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
           const T* col = x + gy * px + gx;
           VPS_BAND_LOOP(q, j) {
             const int gz = z - K + j;
-            const T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
-            am = fma(c_tab<T>.Mb[q * n + j], v, am);
-            ak = fma(c_tab<T>.Kb[q * n + j], v, ak);
+            T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
+            if constexpr (ABS) v = fabs(v);
+            am = fma(coefM<T, ABS>(q * n + j), v, am);
+            ak = fma(coefK<T, ABS>(q * n + j), v, ak);
           }
         }
         mZ[yy * RB + xx] = am;
@@ -846,9 +967,9 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
         for (int qy = 0; qy < K; ++qy) {
           T a = T(0), bb = T(0);
           VPS_BAND_LOOP(qy, j) {
-            a = fma(c_tab<T>.Mb[qy * n + j], vm[qy + j], a);
-            bb = fma(c_tab<T>.Kb[qy * n + j], vm[qy + j], bb);
-            bb = fma(c_tab<T>.Mb[qy * n + j], vk[qy + j], bb);
+            a = fma(coefM<T, ABS>(qy * n + j), vm[qy + j], a);
+            bb = fma(coefK<T, ABS>(qy * n + j), vm[qy + j], bb);
+            bb = fma(coefM<T, ABS>(qy * n + j), vk[qy + j], bb);
           }
           MM[(cy * K + qy) * RB + xx] = a;
           WW[(cy * K + qy) * RB + xx] = bb;
@@ -875,8 +996,8 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
           if (gx >= n1) continue;
           T acc = T(0);
           VPS_BAND_LOOP(qx, j) {
-            acc = fma(c_tab<T>.Kb[qx * n + j], vm[qx + j], acc);
-            acc = fma(c_tab<T>.Mb[qx * n + j], vw[qx + j], acc);
+            acc = fma(coefK<T, ABS>(qx * n + j), vm[qx + j], acc);
+            acc = fma(coefM<T, ABS>(qx * n + j), vw[qx + j], acc);
           }
           T out = T(0);
           if (inner_yz && gx >= 1 && gx <= n1 - 2)
@@ -1346,7 +1467,7 @@ __global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, i
 }
 
 // ------------------------------------------------------------ launchers
-template <typename T, int PP>
+template <typename T, int PP, bool BND>
 cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                                const T* inv_lam, cudaStream_t s) {
   using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
@@ -1354,8 +1475,8 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_mult_kernel<T, PP><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(b, x, inv_lam, (int)g.px,
-                                                                         (int)g.pz, cg, bscale);
+  smooth_mult_kernel<T, PP, BND><<<(unsigned)grid, C::NT, BND ? C::smem_bnd : C::smem_mult, s>>>(
+      b, x, inv_lam, (int)g.px, (int)g.pz, cg, bscale);
   return cudaGetLastError();
 }
 
@@ -1394,6 +1515,32 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
   if (e != cudaSuccess) return e;
   VPS_COUNT_LAUNCH();
   zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
+  return cudaGetLastError();
+}
+
+// y = |A| |x| with the band coefficients replaced by their absolute values
+// (an upper bound of sum_j |A_ij| |x_j| for every row): the scale of the
+// rounding error of any FP64 evaluation of A x.
+cudaError_t apply_abs_launch(const LevelGeom& g, const double* x, double* y, cudaStream_t s) {
+  const int span = g.n1 - 1;
+  if constexpr (DIM == 3) {
+    using C3 = Apply3Cfg;
+    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
+    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    VPS_COUNT_LAUNCH();
+    apply3_kernel<double, true><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(
+        x, nullptr, y, g.n1, (int)g.px, (int)g.pz, g.h);
+  } else {
+    using C = ApplyCfg;
+    const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
+    VPS_COUNT_LAUNCH();
+    apply_kernel<double, true><<<dim3(t, t, 1), C::NT, C::smem<double>(), s>>>(
+        x, nullptr, y, g.n1, g.px, g.pz, 1.0);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
+  zero_upper_faces_kernel<double><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
   return cudaGetLastError();
 }
 
@@ -1453,10 +1600,16 @@ cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf,
 template <typename T, int PP>
 cudaError_t smooth_limits() {
   using C = SmoothCfg<T, PP>;
+  if constexpr (C::fits_bnd) {
+    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::smem_bnd);
+    if (e != cudaSuccess) return e;
+  }
   if constexpr (!C::fits) {
     return cudaSuccess;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP>,
+    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_mult);
     if (e != cudaSuccess) return e;
@@ -1469,8 +1622,12 @@ template <typename T, int PP>
 void register_variant(KernelFns<T>* f, int v) {
   using C = SmoothCfg<T, PP>;
   f->variant_p[v] = C::P;
+  f->variant_p[v + kQVariants] = C::P;
+  f->smooth_add_v[v + kQVariants] = nullptr;
+  if constexpr (C::fits_bnd) f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true>;
+  else f->smooth_mult_v[v + kQVariants] = nullptr;
   if constexpr (C::fits) {
-    f->smooth_mult_v[v] = smooth_mult_launch<T, PP>;
+    f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
   } else {
     f->smooth_mult_v[v] = nullptr;
@@ -1548,10 +1705,26 @@ cudaError_t upload(const HostTables& h) {
   DevTab<double> td;
   fill_tab(h, &tf);
   fill_tab(h, &td);
+  AbsTab ta;
+  for (int i = 0; i < K * n; ++i) {
+    ta.Kb[i] = std::fabs(h.Kb[i]);
+    ta.Mb[i] = std::fabs(h.Mb[i]);
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_tab<float>, &tf, sizeof(tf));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_tab<double>, &td, sizeof(td));
   if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_abs, &ta, sizeof(ta));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(apply_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ApplyCfg::smem<double>());
+  if (e != cudaSuccess) return e;
+  if constexpr (DIM == 3) {
+    e = cudaFuncSetAttribute(apply3_kernel<double, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Apply3Cfg::smem<double>());
+    if (e != cudaSuccess) return e;
+  }
   e = set_smem_limits<float>();
   if (e != cudaSuccess) return e;
   e = df_limits();
@@ -1569,6 +1742,7 @@ void VPS_CAT(register_kernels_d, VPS_DIM, VPS_K)(KernelSet* ks) {
   register_fns<float>(&ks->f);
   register_fns<double>(&ks->d);
   ks->apply_df = apply_df_launch;
+  ks->apply_abs = apply_abs_launch;
 }
 
 }  // namespace vps

@@ -90,8 +90,12 @@ ColourGeom make_colour(const LevelGeom& g, int colour);
 int64_t& launch_counter();
 #define VPS_COUNT_LAUNCH() (++::vps::launch_counter())
 
-// Smoother kernel variants (patches per block) the autotuner chooses from.
-constexpr int kSmoothVariants = 3;
+// Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
+// q = 0, 1, 2 for 1, 2, 4 patches per thread; kind 0 the fused kernel,
+// kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2;
+// multiplicative smoother only, so smooth_add_v[3..5] stay null).
+constexpr int kQVariants = 3;
+constexpr int kSmoothVariants = 2 * kQVariants;
 
 template <typename T>
 struct KernelFns {
@@ -126,6 +130,8 @@ struct KernelSet {
   // y = A x with x given as FP32 pairs (hi, lo) and double-float arithmetic
   cudaError_t (*apply_df)(const LevelGeom&, const float* xh, const float* xl, double* y,
                           cudaStream_t) = nullptr;
+  // y = |A| |x| (absolute band coefficients), FP64: rounding scale of A x
+  cudaError_t (*apply_abs)(const LevelGeom&, const double* x, double* y, cudaStream_t) = nullptr;
 };
 
 // Registry indexed [dim-2][k-1]; filled by ensure_registered().

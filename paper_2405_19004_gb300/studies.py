@@ -31,20 +31,35 @@ FP64_PEAK = 1.25e12                      # flop/s, nominal GB300 FP64
 SMEM_BW = 152 * 32 * 4 * 2.07e9          # bytes/s, shared memory (banks x word x clock)
 
 
-def smoother_flops_per_patch(d, k):
-    """Dense sum-factorised flops of one fused patch update (FMA = 2)."""
+def smoother_flops_per_patch(d, k, boundary=False):
+    """Sum-factorised flops of one patch update (FMA = 2).
+
+    Fused kernel: local residual on the interior rows from the whole closure,
+    fast diagonalisation, x_I += u.
+      3D: 4mn^3 + 6m^2n^2 + 4m^3n + 12m^4 + 4m^3;  2D: 4mn^2 + 4m^2n + 8m^3 + 4m^2.
+    Boundary kernel (Section 3.2): the first contraction only needs the 8k
+    face lines (2 in 2D) in full and 2 end nodes of the m^2 (m) interior
+    lines; x_I = u.
+      3D: 4m(8kn + 2m^2) + 6m^2n^2 + 4m^3n + 12m^4 + 3m^3;
+      2D: 4m(2n + 2m) + 4m^2n + 8m^3 + 3m^2.
+    """
     n, m = 2 * k + 1, 2 * k - 1
     if d == 3:
-        return 4 * m * n ** 3 + 6 * m * m * n * n + 4 * m ** 3 * n + 12 * m ** 4 + 4 * m ** 3
-    return 4 * m * n * n + 4 * m * m * n + 8 * m ** 3 + 4 * m * m
+        s0 = 4 * m * (8 * k * n + 2 * m * m) if boundary else 4 * m * n ** 3
+        upd = 3 * m ** 3 if boundary else 4 * m ** 3
+        return s0 + 6 * m * m * n * n + 4 * m ** 3 * n + 12 * m ** 4 + upd
+    s0 = 4 * m * (2 * n + 2 * m) if boundary else 4 * m * n * n
+    upd = 3 * m * m if boundary else 4 * m * m
+    return s0 + 4 * m * m * n + 8 * m ** 3 + upd
 
 
-def smoother_smem_words_per_patch(d, k):
-    """Shared-memory words read + written per patch by the fused kernel."""
+def smoother_smem_words_per_patch(d, k, boundary=False):
+    """Shared-memory words read + written per patch by the fused kernel (the
+    Boundary kernel neither stages nor reads back the interior of x)."""
     n, m = 2 * k + 1, 2 * k - 1
     if d == 3:
-        return 4 * n * n * m + 4 * n * m * m + 16 * m ** 3
-    return 4 * n * m + 4 * m * m + 14 * m * m
+        return 4 * n * n * m + 4 * n * m * m + (14 if boundary else 16) * m ** 3
+    return 4 * n * m + 4 * m * m + (12 if boundary else 14) * m * m
 
 
 def level_for(d, k, target):
@@ -88,16 +103,19 @@ def sweep(args):
                 torch.cuda.synchronize()
                 t = e0.elapsed_time(e1) / 1e3 / args.apps
                 patches = (2 ** L - 1) ** d
-                flops = smoother_flops_per_patch(d, k) * patches
+                var, ppb = P.vps_get_smooth_variant(L)
+                bnd = var // 3 == 1
+                fpp = smoother_flops_per_patch(d, k, bnd)
+                flops = fpp * patches
                 esz = 4 if prec == vps.VPS_FP32 else 8
-                intensity = smoother_flops_per_patch(d, k) / (esz * smoother_smem_words_per_patch(d, k))
+                intensity = fpp / (esz * smoother_smem_words_per_patch(d, k, bnd))
                 roof_smem = SMEM_BW * intensity
                 peak = FP32_PEAK if prec == vps.VPS_FP32 else FP64_PEAK
                 row = {"dim": d, "degree": k, "level": L, "precision": name, "dofs": N,
                        "ms_per_step": 1e3 * t, "dof_per_s": N / t, "gflops": flops / t / 1e9,
                        "frac_fp_peak": flops / t / peak, "frac_smem_roofline": flops / t / roof_smem,
                        "smem_roofline_tflops": roof_smem / 1e12,
-                       "patches_per_block": P.vps_get_smooth_variant(L)[1]}
+                       "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb}
                 rows.append(row)
                 print(json.dumps(row), flush=True)
                 P.close()

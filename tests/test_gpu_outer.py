@@ -122,3 +122,62 @@ def test_mixed_solve_with_either_outer_operator(d, k, L, rtol):
     assert abs(its[0] - its[1]) <= 2
     dx = np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[0])
     assert dx <= 100 * rtol
+
+
+def _gamma(k):
+    return (6 * k + 6) * 2.0 ** -53
+
+
+@pytest.mark.parametrize("prec,mode", [(vps.VPS_FP32, vps.VPS_OUTER_DOUBLE_FLOAT),
+                                       (vps.VPS_FP32, vps.VPS_OUTER_FP64),
+                                       (vps.VPS_FP64, vps.VPS_OUTER_FP64)])
+@pytest.mark.parametrize("d,k,L", [(2, 2, 7), (2, 5, 5)])
+def test_unattainable_rtol_ends_at_the_rounding_bound(d, k, L, prec, mode):
+    """2D meshes with a smooth right-hand side: the terms of A x cancel by
+    about k^2 h^-2, so rtol = 1e-15 cannot be shown in FP64.  The solve ends
+    (VPS_OK) once the FP64 residual is within the rounding bound of its own
+    evaluation, checked here against the oracle's assembled matrix."""
+    import torch
+    from synthetic import sine_modes
+    lv, A, _ = oracle_level(d, k, L)
+    P = vps.Poisson(d, k, L, precision=prec)
+    P.vps_set_outer_operator(mode)
+    coef, freq = sine_modes(d, 64)
+    b = torch.zeros(lv.N, dtype=torch.float64, device="cuda")
+    P.vps_assemble_rhs_sines(coef, freq, b)
+    x = torch.zeros_like(b)
+    it, rel = P.vps_solve(b, x, 1e-15, 200)
+    restarts, at_bound = P.vps_get_solve_info()
+    assert at_bound == 1 and it < 60
+    bh, xh = b.cpu().numpy(), x.cpu().numpy()
+    r = np.linalg.norm(bh - A @ xh)
+    U = np.linalg.norm(abs(A) @ np.abs(xh))
+    assert r <= 4 * _gamma(k) * U
+    assert abs(rel - r / np.linalg.norm(bh)) <= 0.5 * rel + 4 * _gamma(k) * U / np.linalg.norm(bh)
+
+
+def test_attainable_rtol_does_not_use_the_rounding_bound():
+    import torch
+    d, k, L = 3, 4, 3
+    lv, A, _ = oracle_level(d, k, L)
+    P = vps.Poisson(d, k, L, precision=vps.VPS_FP32)
+    b = torch.as_tensor(uniform_vector(lv.N, 65), device="cuda")
+    x = torch.zeros_like(b)
+    it, rel = P.vps_solve(b, x, 1e-10, 100)
+    assert P.vps_get_solve_info() == (0, 0)
+    true_rel = np.linalg.norm(b.cpu().numpy() - A @ x.cpu().numpy()) / np.linalg.norm(b.cpu().numpy())
+    assert true_rel <= 1.02e-10 and abs(true_rel - rel) <= 1e-3 * rel
+
+
+def test_server_requests_with_unattainable_rtol_complete():
+    from synthetic import sine_modes
+    srv = vps.Server(4 << 30, max_active=3, precision=vps.VPS_FP32, rtol=1e-15, max_it=200)
+    ids = []
+    for i, (d, k, L) in enumerate([(2, 2, 7), (2, 5, 5), (3, 2, 3)]):
+        coef, freq = sine_modes(d, 70 + i)
+        ids.append(srv.submit(d, k, L, coef, freq)[0])
+    srv.wait(0, 300)
+    info = [srv.query(r) for r in ids]
+    srv.close()
+    for q in info:
+        assert q["state"] == vps.VPS_REQ_DONE, q

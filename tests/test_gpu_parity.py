@@ -224,25 +224,41 @@ def test_invalid_arguments_raise():
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("d,k,l", [(2, 2, 4), (2, 6, 3), (3, 1, 3), (3, 3, 3), (3, 6, 2)])
+@pytest.mark.parametrize("d,k,l", [(2, 1, 4), (2, 2, 4), (2, 6, 3), (2, 7, 2), (3, 1, 3), (3, 2, 3),
+                                   (3, 3, 3), (3, 4, 2), (3, 5, 2), (3, 6, 2), (3, 7, 2)])
 def test_every_smoother_variant_matches_oracle(d, k, l, prec):
-    """Patches per block is a launch choice only: every variant gives the oracle's step."""
+    """Patches per block and the fused / Boundary kernel (Section 3.2) are launch
+    choices only: every variant gives the oracle's multiplicative step."""
     lv, A, ps = oracle_level(d, k, l)
     x0 = as_prec(normal_vector(lv.N, 31), prec)
     b = as_prec(normal_vector(lv.N, 32), prec)
     ref = smoothers.multiplicative(A, ps, x0, b)
     P = _poisson(d, k, l, prec)
-    seen = set()
-    for v in range(3):
+    kinds = set()
+    for v in range(6):
         try:
             P.vps_set_smooth_variant(0, v)
         except vps.VpsError:
             continue  # does not fit in shared memory for this degree
-        seen.add(P.vps_get_smooth_variant(l)[1])
+        kinds.add(v // 3)
         xg = to_dev(P, x0, l)
         P.vps_smooth(l, to_dev(P, b, l), xg, 1)
         assert rel_err(to_host(P, xg, l), ref) <= TOL[prec], v
-    assert len(seen) >= 1
+        # a colour pass at a time (the forward and the reverse order of a V-cycle)
+        xg = to_dev(P, x0, l)
+        bg = to_dev(P, b, l)
+        for c in range(2 ** d):
+            P.vps_smooth_colour(l, c, bg, xg)
+        assert rel_err(to_host(P, xg, l), ref) <= TOL[prec], v
+    assert kinds == {0, 1}
+
+
+def test_boundary_variants_are_multiplicative_only():
+    P = _poisson(3, 2, 3, 1, 1, 0.175)
+    for v in (3, 4, 5):
+        with pytest.raises(vps.VpsError) as e:
+            P.vps_set_smooth_variant(0, v)
+        assert e.value.code == vps.VPS_EINVAL
 
 
 def test_autotune_caches_and_keeps_parity(tmp_path):

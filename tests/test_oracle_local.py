@@ -69,3 +69,24 @@ def test_restrict_rows_equals_global_restriction(d, k, l):
     pick = rng.choice(coarse.N, size=min(30, coarse.N), replace=False)
     got = local.restrict_rows(fine, _full(fine, rf), Q[pick] + 1)
     np.testing.assert_allclose(got, y[pick], atol=1e-13)
+
+
+@pytest.mark.parametrize("d,k,l", [(2, 3, 3), (3, 2, 2), (2, 1, 3)])
+def test_boundary_solve_equals_fused_update(d, k, l):
+    """Section 3.2: with the exact local solver, x^I + A_j^{-1} R_j (b - Abar x)
+    equals A_j^{-1} (b^I - A^{IB} x^B), and the result does not depend on x^I."""
+    lv = fe.Level(d, k, l)
+    mats = local.patch_matrices(lv)
+    rng = np.random.default_rng(11)
+    xf, bf = _full(lv, rng.normal(size=lv.N)), _full(lv, rng.normal(size=lv.N))
+    for v in smoothers.vertices(lv)[:6]:
+        gi, u = local.patch_update(lv, xf, bf, v, mats)
+        gi2, xi = local.patch_boundary_solve(lv, xf, bf, v, mats)
+        assert np.array_equal(gi, gi2)
+        np.testing.assert_allclose(xi, xf[gi] + u, rtol=1e-11, atol=1e-11 * np.abs(xi).max())
+        x2 = xf.copy()
+        x2[gi] = rng.normal(size=len(gi))  # other interior values: same new interior
+        _, xi2 = local.patch_boundary_solve(lv, x2, bf, v, mats)
+        np.testing.assert_allclose(xi2, xi, rtol=1e-12, atol=1e-12 * np.abs(xi).max())
+        gi3, u3 = local.patch_update(lv, x2, bf, v, mats)
+        np.testing.assert_allclose(x2[gi3] + u3, xi, rtol=1e-11, atol=1e-11 * np.abs(xi).max())
