@@ -107,11 +107,14 @@ struct alignas(sizeof(T) * Q) Pack {
   T v[Q];
 };
 
-template <typename T, int Q_>
+// W_ = 0: enough warps for every line of the first stage in one round
+// (at most 1024 threads); W_ > 0: W_ warps, each stage in several rounds
+// (one-warp blocks wait at their barriers for no other warp).
+template <typename T, int Q_, int W_ = 0>
 struct SmoothCfg {
   static constexpr int G = kG, Q = Q_, P = G * Q;
   static constexpr int NT0 = ((G * kLinesMax + 31) / 32) * 32;
-  static constexpr int NT = NT0 > 1024 ? 1024 : NT0;
+  static constexpr int NT = W_ > 0 ? 32 * W_ : (NT0 > 1024 ? 1024 : NT0);
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
   // interleaved buffers [..][p] (elements):
   //   3D: A0, A1 = n n m P (stage-0 outputs, later FD ping-pong),
@@ -341,11 +344,11 @@ __device__ __forceinline__ int boundary_first_line(int L, bool* full) {
 // 3.2), equal for the exact local solver: the interior of x is neither read
 // nor staged, and lines of the first contraction that run through the
 // patch interior contract only their two end (boundary) nodes.
-template <typename T, int QQ, bool BND>
-__global__ void __launch_bounds__(SmoothCfg<T, QQ>::NT)
+template <typename T, int QQ, bool BND, int W>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
                    int px, int pz, ColourGeom cg, T bscale) {
-  using C = SmoothCfg<T, QQ>;
+  using C = SmoothCfg<T, QQ, W>;
   constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
   using PK = Pack<T, Q>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1467,16 +1470,16 @@ __global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, i
 }
 
 // ------------------------------------------------------------ launchers
-template <typename T, int PP, bool BND>
+template <typename T, int PP, bool BND, int W>
 cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                                const T* inv_lam, cudaStream_t s) {
-  using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
+  using C = SmoothCfg<T, PP, W>;  // PP: patches per thread (Q), W: warps (0: automatic)
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_mult_kernel<T, PP, BND><<<(unsigned)grid, C::NT, BND ? C::smem_bnd : C::smem_mult, s>>>(
-      b, x, inv_lam, (int)g.px, (int)g.pz, cg, bscale);
+  smooth_mult_kernel<T, PP, BND, W><<<(unsigned)grid, C::NT, BND ? C::smem_bnd : C::smem_mult,
+                                      s>>>(b, x, inv_lam, (int)g.px, (int)g.pz, cg, bscale);
   return cudaGetLastError();
 }
 
@@ -1601,15 +1604,18 @@ template <typename T, int PP>
 cudaError_t smooth_limits() {
   using C = SmoothCfg<T, PP>;
   if constexpr (C::fits_bnd) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true>,
+    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_bnd);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
     if (e != cudaSuccess) return e;
   }
   if constexpr (!C::fits) {
     return cudaSuccess;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false>,
+    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_mult);
     if (e != cudaSuccess) return e;
@@ -1623,11 +1629,18 @@ void register_variant(KernelFns<T>* f, int v) {
   using C = SmoothCfg<T, PP>;
   f->variant_p[v] = C::P;
   f->variant_p[v + kQVariants] = C::P;
+  f->variant_p[v + 2 * kQVariants] = C::P;
   f->smooth_add_v[v + kQVariants] = nullptr;
-  if constexpr (C::fits_bnd) f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true>;
-  else f->smooth_mult_v[v + kQVariants] = nullptr;
+  f->smooth_add_v[v + 2 * kQVariants] = nullptr;
+  if constexpr (C::fits_bnd) {
+    f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true, 0>;
+    f->smooth_mult_v[v + 2 * kQVariants] = smooth_mult_launch<T, PP, true, 1>;
+  } else {
+    f->smooth_mult_v[v + kQVariants] = nullptr;
+    f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
+  }
   if constexpr (C::fits) {
-    f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false>;
+    f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false, 0>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
   } else {
     f->smooth_mult_v[v] = nullptr;

@@ -92,10 +92,11 @@ int64_t& launch_counter();
 
 // Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
 // q = 0, 1, 2 for 1, 2, 4 patches per thread; kind 0 the fused kernel,
-// kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2;
-// multiplicative smoother only, so smooth_add_v[3..5] stay null).
+// kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
+// kind 2 the Boundary kernel in one-warp blocks.  Kinds 1 and 2 serve the
+// multiplicative smoother only (smooth_add_v[3..8] stay null).
 constexpr int kQVariants = 3;
-constexpr int kSmoothVariants = 2 * kQVariants;
+constexpr int kSmoothVariants = 3 * kQVariants;
 
 template <typename T>
 struct KernelFns {

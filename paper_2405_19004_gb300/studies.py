@@ -104,7 +104,7 @@ def sweep(args):
                 t = e0.elapsed_time(e1) / 1e3 / args.apps
                 patches = (2 ** L - 1) ** d
                 var, ppb = P.vps_get_smooth_variant(L)
-                bnd = var // 3 == 1
+                bnd = var // 3 >= 1
                 fpp = smoother_flops_per_patch(d, k, bnd)
                 flops = fpp * patches
                 esz = 4 if prec == vps.VPS_FP32 else 8

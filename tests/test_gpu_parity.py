@@ -227,15 +227,16 @@ def test_invalid_arguments_raise():
 @pytest.mark.parametrize("d,k,l", [(2, 1, 4), (2, 2, 4), (2, 6, 3), (2, 7, 2), (3, 1, 3), (3, 2, 3),
                                    (3, 3, 3), (3, 4, 2), (3, 5, 2), (3, 6, 2), (3, 7, 2)])
 def test_every_smoother_variant_matches_oracle(d, k, l, prec):
-    """Patches per block and the fused / Boundary kernel (Section 3.2) are launch
-    choices only: every variant gives the oracle's multiplicative step."""
+    """Patches per block, warps per block and the fused / Boundary kernel
+    (Section 3.2) are launch choices only: every variant gives the oracle's
+    multiplicative step."""
     lv, A, ps = oracle_level(d, k, l)
     x0 = as_prec(normal_vector(lv.N, 31), prec)
     b = as_prec(normal_vector(lv.N, 32), prec)
     ref = smoothers.multiplicative(A, ps, x0, b)
     P = _poisson(d, k, l, prec)
     kinds = set()
-    for v in range(6):
+    for v in range(9):
         try:
             P.vps_set_smooth_variant(0, v)
         except vps.VpsError:
@@ -250,12 +251,12 @@ def test_every_smoother_variant_matches_oracle(d, k, l, prec):
         for c in range(2 ** d):
             P.vps_smooth_colour(l, c, bg, xg)
         assert rel_err(to_host(P, xg, l), ref) <= TOL[prec], v
-    assert kinds == {0, 1}
+    assert kinds == {0, 1, 2}
 
 
 def test_boundary_variants_are_multiplicative_only():
     P = _poisson(3, 2, 3, 1, 1, 0.175)
-    for v in (3, 4, 5):
+    for v in (3, 4, 5, 6, 7, 8):
         with pytest.raises(vps.VpsError) as e:
             P.vps_set_smooth_variant(0, v)
         assert e.value.code == vps.VPS_EINVAL
