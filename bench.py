@@ -396,6 +396,21 @@ def main():
                               "frac_of_fp64_peak": f64 / FP64_PEAK_TFLOPS,
                               "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"},
         }
+        # full multigrid (Algorithm 2) as a standalone solver, f = 1, tol 1e-9: the
+        # setting of the paper's iteration-count tables
+        fmg = {}
+        for name, Pf in (("fp32_vcycle", P), ("fp64", P64)):
+            xf = torch.zeros(N, dtype=torch.float64, device="cuda")
+            Pf.vps_fmg([1.0], [0, 0, 0], xf, 1e-9, 100)
+            tf = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                itf, relf = Pf.vps_fmg([1.0], [0, 0, 0], xf, 1e-9, 100)
+                tf.append(time.perf_counter() - t0)
+            fmg[name] = {"v_cycles": itf, "rel_residual": relf, "time_s": min(tf),
+                         "coarse_level": Pf.vps_get_coarse_level()}
+        extras["fmg_f1_tol1e-9"] = fmg
         P64.close()
         # additive smoother: damping 0.7 taken literally, and 0.7 of the stability limit
         add = {}

@@ -170,13 +170,37 @@ int vps_solve_host(vps_handle h, const double* b_host, double* x_host, double rt
 
 /*
  * vps_assemble_rhs_sines -- load vector b_i = int f phi_i (Eq. 2.4) on the
- * finest level for f(x) = sum_m coef[m] prod_t sin(pi freq[m*dim+t] x_t),
+ * finest level for f(x) = sum_m coef[m] prod_t sin(pi freq[m*dim+t] x_t)
+ * (a frequency 0 stands for the constant 1 in that direction; negative
+ * frequencies are rejected),
  * with (k+2)-point Gauss quadrature per cell and direction.  coef, freq:
  * HOST arrays of n_modes (n_modes*dim) entries; b: compact DOUBLE device
  * vector.
  */
 int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef,
                            const int* freq, double* b);
+
+/*
+ * vps_fmg -- full multigrid (Algorithm 2) as a standalone solver on the
+ * handle's hierarchy, for f(x) = sum_m coef[m] prod_t g(freq[m*dim+t], x_t)
+ * with g(0, s) = 1 and g(f, s) = sin(pi f s): the load vector of f is
+ * assembled on every level (as vps_assemble_rhs_sines); the coarsest level
+ * (vps_set_coarse_level) is solved exactly; every finer level starts from
+ * the prolongated coarser solution and takes one V-cycle; then V-cycles on
+ * the finest level repeat until ||b - A x||_2 <= tol ||b||_2 (norms and
+ * residuals in FP64; the V-cycle in the handle's precision, applied as the
+ * correction x += V(0, b - A x), equal to V(x, b) since Algorithm 1 is
+ * affine in x).  The V-cycle is the one Algorithm 1 prints: the same colour
+ * order before and after the coarse correction.  If the residual stops
+ * falling at the rounding bound of its own FP64 evaluation (see vps_solve),
+ * the solve ends there with VPS_OK.
+ *   x: compact DOUBLE device output; iters (host, may be NULL): V-cycles of
+ *   the final loop (the count the paper's Tables 1 and 2 report); rel_res:
+ *   the final ||b - A x|| / ||b||.  Synchronous.
+ *   Errors: VPS_EINVAL, VPS_ENOCONV (not within max_it V-cycles), ...
+ */
+int vps_fmg(vps_handle h, int n_modes, const double* coef, const int* freq, double tol,
+            int max_it, double* x, int* iters, double* rel_res);
 
 /*
  * vps_l2_error_sine -- ||u_h - u||_{L2} for u = prod_t sin(pi x_t) and the

@@ -51,6 +51,7 @@ SIGNATURES = {
     "vps_solve_host": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "vps_assemble_rhs_sines": (_i, [_p, _i, _p, _p, _p]),
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
+    "vps_fmg": (_i, [_p, _i, _p, _p, _d, _i, _p, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "vps_set_graphs": (_i, [_p, _i]),
     "vps_set_outer_operator": (_i, [_p, _i]),
     "vps_get_outer_operator": (_i, [_p, ctypes.POINTER(_i)]),
@@ -249,6 +250,18 @@ class Poisson:
         freq = np.ascontiguousarray(freq, dtype=np.int32)
         self._call(lib().vps_assemble_rhs_sines, len(coef), coef.ctypes.data_as(ctypes.c_void_p),
                    freq.ctypes.data_as(ctypes.c_void_p), _ptr(b))
+
+    def vps_fmg(self, coef, freq, x, tol=1e-9, max_it=100):
+        """Full multigrid (Algorithm 2) for f = sum coef prod sin(pi freq x_t)
+        (freq 0: constant 1); x: compact float64 device output.  -> (V-cycles, rel)."""
+        import numpy as np
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        freq = np.ascontiguousarray(freq, dtype=np.int32)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._call(lib().vps_fmg, len(coef), coef.ctypes.data_as(ctypes.c_void_p),
+                   freq.ctypes.data_as(ctypes.c_void_p), float(tol), int(max_it), _ptr(x),
+                   ctypes.byref(it), ctypes.byref(rel))
+        return it.value, rel.value
 
     def vps_l2_error_sine(self, x):
         err = ctypes.c_double()

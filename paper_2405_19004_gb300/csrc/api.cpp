@@ -97,6 +97,11 @@ struct vps_context {
   // two float vectors cph + cpl) with a final FP64 check of the residual
   int outer = VPS_OUTER_FP64;
   float *cph = nullptr, *cpl = nullptr;
+  // full multigrid: FP64 right-hand side, iterate and residual of the levels
+  // below the finest (the finest uses cb, cx, cr)
+  double* fmg_b[kMaxLevels + 1] = {};
+  double* fmg_x[kMaxLevels + 1] = {};
+  double* fmg_r[kMaxLevels + 1] = {};
   // last solve: restarts from the FP64 residual, and whether it stopped at
   // the rounding level of the residual's own evaluation instead of rtol
   int last_restarts = 0, last_at_floor = 0;
@@ -321,20 +326,24 @@ int setup_coarse(vps_context* h, int lc) {
   return VPS_OK;
 }
 
-// x_L = Vcycle_L(A_L, 0, b_L) (Algorithm 1) in working precision T.
+// x_top = Vcycle_top(A_top, 0, b_top) (Algorithm 1) in working precision T,
+// top = 0: the finest level.  symmetric: post-smoothing visits the colours
+// in reverse order (an SPD preconditioner for CG); otherwise in the same
+// order as pre-smoothing (S_l on both sides, as Algorithm 1 prints it).
 template <typename T>
-int vcycle_core(vps_context* h, const T* bL, T* xL) {
+int vcycle_core(vps_context* h, const T* bL, T* xL, int top = 0, bool symmetric = true) {
   const KernelFns<T>& F = fns<T>(h);
+  if (top == 0) top = h->L;
   const T* b[kMaxLevels + 1];
   T* x[kMaxLevels + 1];
   for (int l = 1; l <= h->L; ++l) {
     b[l] = static_cast<const T*>(h->bv[l]);
     x[l] = static_cast<T*>(h->xv[l]);
   }
-  b[h->L] = bL;
-  x[h->L] = xL;
+  b[top] = bL;
+  x[top] = xL;
   const int lc = h->coarse;
-  for (int l = h->L; l > lc; --l) {
+  for (int l = top; l > lc; --l) {
     const LevelGeom& g = h->geom[l];
     VPS_CK(h, cudaMemsetAsync(x[l], 0, g.total * sizeof(T), h->stream));
     for (int s = 0; s < h->n_pre; ++s) {
@@ -350,10 +359,10 @@ int vcycle_core(vps_context* h, const T* bL, T* xL) {
     int rc = coarse_solve<T>(h, b[lc], x[lc]);
     if (rc) return rc;
   }
-  for (int l = lc + 1; l <= h->L; ++l) {
+  for (int l = lc + 1; l <= top; ++l) {
     VPS_CK(h, F.prolong_add(h->geom[l], h->geom[l - 1], x[l - 1], x[l], h->stream));
     for (int s = 0; s < h->n_post; ++s) {
-      int rc = smooth_step<T>(h, l, b[l], x[l], false);
+      int rc = smooth_step<T>(h, l, b[l], x[l], !symmetric);
       if (rc) return rc;
     }
   }
@@ -550,15 +559,142 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
   return fail(h, VPS_ENOCONV, "CG did not reach %g in %d iterations (%g)", rtol, max_it, rel);
 }
 
+int upload_rhs_sines(vps_context* h, int level, int n_modes, const double* coef, const int* freq,
+                     double* b);
+
+// x += V_l(r) for FP64 level vectors: the V-cycle with initial guess x
+// (Algorithm 1 is affine in x: V(x, b) = x + V(0, b - A x)), as printed
+// (the same colour order before and after the coarse correction), in the
+// handle's working precision.  r is clobbered.
+int fmg_correct(vps_context* h, int l, double* r, double* x) {
+  const LevelGeom& g = h->geom[l];
+  if (h->prec == VPS_FP64) {
+    double* c = static_cast<double*>(h->xv[l]);
+    if (int rc = vcycle_core<double>(h, r, c, l, false)) return rc;
+    VPS_CK(h, launch_axpy_inplace<double>(x, c, 1.0, g.total, h->stream));
+  } else {
+    float* bf = static_cast<float*>(h->bv[l]);
+    float* c = static_cast<float*>(h->xv[l]);
+    VPS_CK(h, launch_cast_d2f(r, bf, g.total, h->stream));
+    if (int rc = vcycle_core<float>(h, bf, c, l, false)) return rc;
+    VPS_CK(h, launch_cast_f2d(c, r, g.total, h->stream));
+    VPS_CK(h, launch_axpy_inplace<double>(x, r, 1.0, g.total, h->stream));
+  }
+  return VPS_OK;
+}
+
+// Full multigrid (Algorithm 2): exact solve on the coarsest level, then on
+// every finer level prolongation of the coarser solution and one V-cycle,
+// then V-cycles on the finest level until ||b - A x|| <= tol ||b|| (norms
+// and residuals in FP64).  Right-hand sides: the load vector of f on every
+// level.  *iters: the V-cycles of the final loop.
+int fmg_solve(vps_context* h, int n_modes, const double* coef, const int* freq, double tol,
+              int max_it, int* iters, double* rel_res) {
+  const int L = h->L, lc = h->coarse;
+  h->last_restarts = 0;
+  h->last_at_floor = 0;
+  for (int l = lc; l < L; ++l)
+    if (!h->fmg_b[l]) {
+      const size_t bytes = (size_t)h->geom[l].total * sizeof(double);
+      void* p;
+      if (int rc = dalloc(h, &p, bytes)) return rc;
+      h->fmg_b[l] = (double*)p;
+      if (int rc = dalloc(h, &p, bytes)) return rc;
+      h->fmg_x[l] = (double*)p;
+      if (int rc = dalloc(h, &p, bytes)) return rc;
+      h->fmg_r[l] = (double*)p;
+    }
+  double *fb[kMaxLevels + 1], *fx[kMaxLevels + 1], *fr[kMaxLevels + 1];
+  for (int l = lc; l < L; ++l) {
+    fb[l] = h->fmg_b[l];
+    fx[l] = h->fmg_x[l];
+    fr[l] = h->fmg_r[l];
+  }
+  fb[L] = h->cb;
+  fx[L] = h->cx;
+  fr[L] = h->cr;
+  for (int l = lc; l <= L; ++l) {
+    if (int rc = upload_rhs_sines(h, l, n_modes, coef, freq, h->comp_b)) return rc;
+    VPS_CK(h, launch_pack<double>(h->geom[l], h->comp_b, fb[l], h->stream));
+  }
+  const LevelGeom& gL = h->geom[L];
+  VPS_CK(h, launch_dot1(h->cb, h->cb, gL.total, h->partial, h->dots, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  const double nb = std::sqrt(h->host_dots[0]);
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  if (!(nb > 0.0)) {
+    VPS_CK(h, cudaMemsetAsync(h->cx, 0, gL.total * sizeof(double), h->stream));
+    if (!std::isfinite(nb)) return fail(h, VPS_EBREAKDOWN, "right-hand side is not finite");
+    return VPS_OK;
+  }
+  // coarse grid solver
+  const LevelGeom& gc = h->geom[lc];
+  if (h->prec == VPS_FP64) {
+    if (int rc = coarse_solve<double>(h, fb[lc], fx[lc])) return rc;
+  } else {
+    VPS_CK(h, launch_cast_d2f(fb[lc], static_cast<float*>(h->bv[lc]), gc.total, h->stream));
+    if (int rc = coarse_solve<float>(h, static_cast<const float*>(h->bv[lc]),
+                                     static_cast<float*>(h->xv[lc])))
+      return rc;
+    VPS_CK(h, launch_cast_f2d(static_cast<const float*>(h->xv[lc]), fx[lc], gc.total, h->stream));
+  }
+  // nested iteration: prolongate, one V-cycle per level
+  for (int l = lc + 1; l <= L; ++l) {
+    const LevelGeom& g = h->geom[l];
+    VPS_CK(h, cudaMemsetAsync(fx[l], 0, g.total * sizeof(double), h->stream));
+    VPS_CK(h, h->ks->d.prolong_add(g, h->geom[l - 1], fx[l - 1], fx[l], h->stream));
+    VPS_CK(h, h->ks->d.apply(g, fx[l], fb[l], fr[l], h->stream));
+    if (int rc = fmg_correct(h, l, fr[l], fx[l])) return rc;
+  }
+  // V-cycles on the finest level until the residual norm has dropped by tol
+  VPS_CK(h, h->ks->d.apply(gL, h->cx, h->cb, h->cr, h->stream));
+  double delta = nb, prev = nb;
+  int it = 0;
+  while (delta > tol * nb && it < max_it) {
+    if (int rc = fmg_correct(h, L, h->cr, h->cx)) return rc;
+    VPS_CK(h, h->ks->d.apply(gL, h->cx, h->cb, h->cr, h->stream));
+    VPS_CK(h, launch_dot1(h->cr, h->cr, gL.total, h->partial, h->dots, h->stream));
+    VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    VPS_CK(h, cudaStreamSynchronize(h->stream));
+    delta = std::sqrt(h->host_dots[0]);
+    ++it;
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = delta / nb;
+    if (!std::isfinite(delta)) return fail(h, VPS_EBREAKDOWN, "FMG residual not finite");
+    if (delta > tol * nb && !(delta < 0.5 * prev)) {
+      // stagnation: is the residual at the rounding level of its evaluation?
+      if (int rc = cg_residual_scale(h)) return rc;
+      VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                h->stream));
+      VPS_CK(h, cudaStreamSynchronize(h->stream));
+      if (delta <= residual_gamma(h) * std::sqrt(h->host_sc->pAp)) {
+        h->last_at_floor = 1;
+        return VPS_OK;
+      }
+    }
+    prev = delta;
+  }
+  if (delta > tol * nb)
+    return fail(h, VPS_ENOCONV, "FMG did not reach %g in %d V-cycles (%g)", tol, max_it,
+                delta / nb);
+  return VPS_OK;
+}
+
 }  // namespace
 
 namespace {
 
-// Load vector of f = sum_m coef_m prod_t sin(pi freq_mt x_t) into the compact
-// device vector b: 1D integrals with (k+2)-point Gauss rules on the host,
-// tensor product on the device (asynchronous on the handle's stream).
-int upload_rhs_sines(vps_context* h, int n_modes, const double* coef, const int* freq, double* b) {
-  const LevelGeom& g = h->geom[h->L];
+// Load vector of f = sum_m coef_m prod_t g_mt(x_t), g = sin(pi freq x) (the
+// constant 1 for freq 0), on `level` into the compact device vector b: 1D
+// integrals with (k+2)-point Gauss rules on the host, tensor product on the
+// device (asynchronous on the handle's stream).
+int upload_rhs_sines(vps_context* h, int level, int n_modes, const double* coef, const int* freq,
+                     double* b) {
+  const LevelGeom& g = h->geom[level];
   const int k = h->k, ni = g.n1 - 2, q = k + 2;
   double xq[16], wq[16], val[kMaxK + 1];
   gauss_rule(q, xq, wq);
@@ -571,7 +707,7 @@ int upload_rhs_sines(vps_context* h, int n_modes, const double* coef, const int*
       for (int c = 0; c < g.ncell; ++c)
         for (int qq = 0; qq < q; ++qq) {
           const double x = (c + xq[qq]) * g.h;
-          const double fv = std::sin(M_PI * f * x) * wq[qq] * g.h;
+          const double fv = (f == 0 ? 1.0 : std::sin(M_PI * f * x)) * wq[qq] * g.h;
           lagrange_eval(k, h->tab.z, xq[qq], val);
           for (int i = 0; i <= k; ++i) full[k * c + i] += fv * val[i];
         }
@@ -686,7 +822,7 @@ int cg_async_begin(vps_handle h, int n_modes, const double* coef, const int* fre
   h->as_prev_true = 0.0;
   h->last_restarts = 0;
   h->last_at_floor = 0;
-  if (int rc = upload_rhs_sines(h, n_modes, coef, freq, h->comp_b)) return rc;
+  if (int rc = upload_rhs_sines(h, h->L, n_modes, coef, freq, h->comp_b)) return rc;
   VPS_CK(h, launch_pack<double>(g, h->comp_b, h->cb, h->stream));
   VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
   VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
@@ -1243,9 +1379,29 @@ int vps_assemble_rhs_sines(vps_handle h, int n_modes, const double* coef, const 
     return fail(h, VPS_EINVAL, "bad sine-mode arguments");
   if (int rc = set_device(h)) return rc;
   LaunchTally tally(h);
-  if (int rc = upload_rhs_sines(h, n_modes, coef, freq, b)) return rc;
+  for (int i = 0; i < n_modes * h->dim; ++i)
+    if (freq[i] < 0) return fail(h, VPS_EINVAL, "negative frequency");
+  if (int rc = upload_rhs_sines(h, h->L, n_modes, coef, freq, b)) return rc;
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   return VPS_OK;
+}
+
+int vps_fmg(vps_handle h, int n_modes, const double* coef, const int* freq, double tol,
+            int max_it, double* x, int* iters, double* rel_res) {
+  if (!h) return VPS_EINVAL;
+  if (n_modes < 1 || n_modes > 4096 || !coef || !freq || !x)
+    return fail(h, VPS_EINVAL, "bad arguments");
+  if (!(tol > 0.0) || max_it < 1) return fail(h, VPS_EINVAL, "tol must be > 0 and max_it >= 1");
+  for (int i = 0; i < n_modes * h->dim; ++i)
+    if (freq[i] < 0) return fail(h, VPS_EINVAL, "negative frequency");
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  int rc = fmg_solve(h, n_modes, coef, freq, tol, max_it, iters, rel_res);
+  const LevelGeom& g = h->geom[h->L];
+  cudaError_t e = launch_unpack<double>(g, h->cx, x, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess && rc == VPS_OK) return fail(h, VPS_ECUDA, "fmg: %s", cudaGetErrorString(e));
+  return rc;
 }
 
 int vps_l2_error_sine(vps_handle h, const double* x, double* err) {
