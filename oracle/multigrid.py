@@ -15,6 +15,10 @@
 * PCG: conjugate gradients on level L preconditioned by one V-cycle, x0 = 0,
   stopping at ||b - A x|| <= rtol ||b||; beta in the flexible
   (Polak-Ribiere) form r_{i+1}^T (z_{i+1} - z_i) / r_i^T z_i.
+* FGMRES: GMRES (the paper's outer solver, Section 4) with right
+  preconditioning by one V-cycle, in the flexible form that stores the
+  preconditioned vectors (the V-cycle may be inexact, e.g. in FP32); Arnoldi
+  by modified Gram-Schmidt, Givens rotations, restarts.
 * L2 error: ||u_h - u||_{L2} with (k+2)^d Gauss points per cell.
 """
 
@@ -125,6 +129,65 @@ def fmg_iterations(d, k, L, f, tol=1e-9, max_it=100):
         delta = np.linalg.norm(b[L] - H.A[L] @ x)
         it += 1
     return it
+
+
+def fgmres(A, b, precond, rtol=1e-9, restart=30, max_it=300):
+    """Flexible GMRES, x0 = 0; returns (x, iterations, rel_res, history).
+
+    Each cycle builds an orthonormal basis v_1 = r / ||r||, ..., with
+    z_j = precond(v_j) and A z_j orthogonalised against v_1..v_j (modified
+    Gram-Schmidt); x = x0 + Z y with y minimising ||beta e_1 - H y|| (Givens
+    rotations).  The loop stops when the least-squares residual |g_{j+1}|
+    is <= rtol ||b|| or after max_it products A z; a cycle ends after
+    `restart` of them and the next one starts from r = b - A x.  history:
+    the least-squares residual after every product.
+    """
+    n = len(b)
+    x = np.zeros(n)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0, 0.0, []
+    it, hist = 0, []
+    r = b.copy()
+    beta = np.linalg.norm(r)
+    while True:
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j = 0
+        while j < restart and it < max_it:
+            z = precond(V[j])
+            Z.append(z)
+            w = A @ z
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):  # previous rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            it += 1
+            hist.append(abs(g[j]) / nb)
+            if abs(g[j]) <= rtol * nb:
+                break
+        y = sla.solve_triangular(H[:j, :j], g[:j])
+        x = x + np.array(Z).T @ y
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta <= rtol * nb or it >= max_it:
+            return x, it, beta / nb, hist
 
 
 def l2_error(level, x, u):

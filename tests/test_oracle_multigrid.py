@@ -131,3 +131,67 @@ def test_l2_error_of_exact_interpolant_of_constant_zero():
     assert multigrid.l2_error(lv, np.zeros(lv.N), lambda X: np.zeros(len(X))) == 0.0
     # ||1||_{L2} over the unit square, with u_h = 0: exactly 1
     assert abs(multigrid.l2_error(lv, np.zeros(lv.N), lambda X: np.ones(len(X))) - 1.0) < 1e-14
+
+
+def _krylov_min_residual(A, b, B, k):
+    """min ||b - A Z y|| over span{B r0, B A B r0, ...} (k vectors), brute force."""
+    Z = []
+    v = b.copy()
+    for _ in range(k):
+        z = B @ v
+        Z.append(z)
+        v = A @ z
+    Z = np.array(Z).T
+    Q, _ = np.linalg.qr(A @ Z)
+    return np.linalg.norm(b - Q @ (Q.T @ b))
+
+
+@pytest.mark.parametrize("pre", ["none", "jacobi", "vcycle"])
+def test_fgmres_is_the_minimal_residual_method(pre):
+    """With a fixed linear preconditioner B, FGMRES after k steps attains the
+    minimal residual over b + A span{B r0, (B A) B r0, ...}: the Krylov space of
+    A B, mapped by B (brute-force least squares on a small problem)."""
+    H = multigrid.Hierarchy(2, 2, 3, symmetric=False)
+    A = H.A[3].toarray()
+    n = A.shape[0]
+    b = np.random.default_rng(21).normal(size=n)
+    if pre == "none":
+        B = np.eye(n)
+    elif pre == "jacobi":
+        B = np.diag(1.0 / np.diag(A))
+    else:  # the V-cycle as a matrix (it is linear in its right-hand side)
+        B = np.column_stack([H.vcycle(3, e) for e in np.eye(n)])
+    _, it, rel, hist = multigrid.fgmres(A, b, lambda v: B @ v, rtol=1e-14, restart=200, max_it=8)
+    nb = np.linalg.norm(b)
+    checked = 0
+    for k in range(1, len(hist) + 1):
+        ref = _krylov_min_residual(A, b, B, k) / nb
+        if ref < 1e-10:  # both at round-off (the monomial basis is ill-conditioned)
+            break
+        assert abs(hist[k - 1] - ref) <= 1e-8 * ref, (k, hist[k - 1], ref)
+        checked += 1
+    assert checked >= 3
+
+
+def test_fgmres_finite_termination_and_restart():
+    """Without restarts GMRES solves an n x n system in at most n steps; with
+    restarts the least-squares estimate agrees with the true residual."""
+    rng = np.random.default_rng(22)
+    n = 12
+    M = rng.normal(size=(n, n)) + n * np.eye(n)
+    b = rng.normal(size=n)
+    x, it, rel, _ = multigrid.fgmres(M, b, lambda v: v, rtol=1e-13, restart=n, max_it=n)
+    assert it <= n and np.linalg.norm(b - M @ x) <= 1e-11 * np.linalg.norm(b)
+    x, it, rel, hist = multigrid.fgmres(M, b, lambda v: v, rtol=1e-10, restart=3, max_it=200)
+    assert rel <= 1e-10 and np.isclose(rel, np.linalg.norm(b - M @ x) / np.linalg.norm(b))
+    assert np.all(np.diff(hist[:3]) <= 1e-15)  # monotone within a cycle
+
+
+def test_fgmres_with_vcycle_solves_the_poisson_problem():
+    H = multigrid.Hierarchy(3, 2, 3, symmetric=False)
+    b = np.random.default_rng(23).uniform(-1, 1, H.levels[3].N)
+    x, it, rel, _ = multigrid.fgmres(H.A[3], b, H.precondition, rtol=1e-9)
+    assert rel <= 1e-9 and it <= 12
+    import scipy.sparse.linalg as spla
+    xd = spla.spsolve(H.A[3].tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
