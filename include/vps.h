@@ -162,6 +162,24 @@ int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
               int* iters, double* rel_res);
 
 /*
+ * vps_gmres -- the paper's outer solver (Section 4): flexible GMRES on the
+ * finest level, right-preconditioned by one V-cycle of Algorithm 1 as
+ * printed (the same colour order before and after the coarse correction,
+ * i.e. not symmetric), x0 = 0, restarted every `restart` (1..512) products
+ * A z.  FP64 Krylov vectors; the V-cycle in the handle's precision and A
+ * by the outer operator (vps_set_outer_operator).  Each cycle ends when
+ * the least-squares residual reaches rtol ||b||; the residual is then
+ * evaluated in FP64 and checked as in vps_solve (rtol, or the rounding
+ * bound of its own evaluation), else the next cycle starts from it.
+ *   b, x: compact DOUBLE device vectors; iters / rel_res (host, may be
+ *   NULL): products A z and the final FP64 relative residual.  Allocates
+ *   2 restart + 1 vectors of the finest level on first use.  Synchronises
+ *   once per iteration.  Errors: VPS_EINVAL, VPS_ENOCONV, VPS_EBREAKDOWN.
+ */
+int vps_gmres(vps_handle h, const double* b, double* x, double rtol, int restart, int max_it,
+              int* iters, double* rel_res);
+
+/*
  * vps_solve_host -- as vps_solve, but b and x are HOST pointers (compact,
  * double).  Copies b to the device, solves, copies x back; synchronous.
  */

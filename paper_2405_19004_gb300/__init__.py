@@ -49,6 +49,7 @@ SIGNATURES = {
     "vps_vcycle": (_i, [_p, _p, _p]),
     "vps_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "vps_solve_host": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "vps_gmres": (_i, [_p, _p, _p, _d, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "vps_assemble_rhs_sines": (_i, [_p, _i, _p, _p, _p]),
     "vps_l2_error_sine": (_i, [_p, _p, ctypes.POINTER(_d)]),
     "vps_fmg": (_i, [_p, _i, _p, _p, _d, _i, _p, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
@@ -235,6 +236,12 @@ class Poisson:
         it, rel = ctypes.c_int(), ctypes.c_double()
         self._call(lib().vps_solve, _ptr(b), _ptr(x), float(rtol), int(max_it), ctypes.byref(it),
                    ctypes.byref(rel))
+        return it.value, rel.value
+
+    def vps_gmres(self, b, x, rtol=1e-9, restart=30, max_it=300):
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._call(lib().vps_gmres, _ptr(b), _ptr(x), float(rtol), int(restart), int(max_it),
+                   ctypes.byref(it), ctypes.byref(rel))
         return it.value, rel.value
 
     def vps_solve_host(self, b_host, x_host, rtol=1e-10, max_it=100):

@@ -97,6 +97,12 @@ struct vps_context {
   // two float vectors cph + cpl) with a final FP64 check of the residual
   int outer = VPS_OUTER_FP64;
   float *cph = nullptr, *cpl = nullptr;
+  // GMRES: Krylov basis V (m + 1 vectors) and preconditioned vectors Z (m),
+  // leading dimension gm_ld; Hessenberg column buffers on device and host
+  int gm_m = 0;
+  int64_t gm_ld = 0;
+  double *gmV = nullptr, *gmZ = nullptr, *gm_partial = nullptr, *gm_dev = nullptr;
+  double* gm_host = nullptr;            // pinned
   // full multigrid: FP64 right-hand side, iterate and residual of the levels
   // below the finest (the finest uses cb, cx, cr)
   double* fmg_b[kMaxLevels + 1] = {};
@@ -119,6 +125,8 @@ struct vps_context {
   std::vector<void*> allocs;
   // captured preconditioner graph (input r = cr, output czn)
   cudaGraphExec_t prec_graph = nullptr;
+  cudaGraphExec_t prec_graph_ns = nullptr;  // the non-symmetric cycle (GMRES)
+  int64_t graph_kernels_ns = 0;
   bool own_stream = false;              // stream created (and destroyed) by the library
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
@@ -183,6 +191,14 @@ int set_device(vps_context* h) {
     if (e != cudaSuccess) return fail(h, VPS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
   }
   return VPS_OK;
+}
+
+// Drops the captured V-cycle graphs (after a change of level data, variant
+// or coarse level); they are captured again on next use.
+void drop_graphs(vps_context* h) {
+  if (h->prec_graph) cudaGraphExecDestroy(h->prec_graph);
+  if (h->prec_graph_ns) cudaGraphExecDestroy(h->prec_graph_ns);
+  h->prec_graph = h->prec_graph_ns = nullptr;
 }
 
 // Adds the kernels launched during an entry point to the handle's tally.
@@ -319,10 +335,7 @@ int setup_coarse(vps_context* h, int lc) {
   if (e != cudaSuccess) return fail(h, VPS_ECUDA, "coarse tables: %s", cudaGetErrorString(e));
   h->coarse = lc;
   h->gni = ni;
-  if (h->prec_graph) {
-    cudaGraphExecDestroy(h->prec_graph);
-    h->prec_graph = nullptr;
-  }
+  drop_graphs(h);
   return VPS_OK;
 }
 
@@ -369,26 +382,29 @@ int vcycle_core(vps_context* h, const T* bL, T* xL, int top = 0, bool symmetric 
   return VPS_OK;
 }
 
-// z = B r for the CG: FP64 V-cycle, or cast -> FP32 V-cycle -> cast.
-int precondition_direct(vps_context* h) {
+// czn = B cr: FP64 V-cycle, or cast -> FP32 V-cycle -> cast; symmetric
+// cycle for CG, the non-symmetric one of Algorithm 1 for GMRES.
+int precondition_direct(vps_context* h, bool symmetric) {
   const LevelGeom& g = h->geom[h->L];
-  if (h->prec == VPS_FP64) return vcycle_core<double>(h, h->cr, h->czn);
+  if (h->prec == VPS_FP64) return vcycle_core<double>(h, h->cr, h->czn, 0, symmetric);
   VPS_CK(h, launch_cast_d2f(h->cr, static_cast<float*>(h->bv[h->L]), g.total, h->stream));
   int rc = vcycle_core<float>(h, static_cast<const float*>(h->bv[h->L]),
-                              static_cast<float*>(h->xv[h->L]));
+                              static_cast<float*>(h->xv[h->L]), 0, symmetric);
   if (rc) return rc;
   VPS_CK(h, launch_cast_f2d(static_cast<const float*>(h->xv[h->L]), h->czn, g.total, h->stream));
   return VPS_OK;
 }
 
-int precondition(vps_context* h) {
-  if (!h->use_graphs) return precondition_direct(h);
-  if (!h->prec_graph) {
+int precondition(vps_context* h, bool symmetric = true) {
+  if (!h->use_graphs) return precondition_direct(h, symmetric);
+  cudaGraphExec_t& exec = symmetric ? h->prec_graph : h->prec_graph_ns;
+  int64_t& nk = symmetric ? h->graph_kernels : h->graph_kernels_ns;
+  if (!exec) {
     cudaGraph_t graph = nullptr;
     VPS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     const int64_t before = launch_counter();
-    int rc = precondition_direct(h);
-    h->graph_kernels = launch_counter() - before;
+    int rc = precondition_direct(h, symmetric);
+    nk = launch_counter() - before;
     launch_counter() = before;  // captured, not launched
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (rc) {
@@ -396,15 +412,15 @@ int precondition(vps_context* h) {
       return rc;
     }
     if (e != cudaSuccess) return fail(h, VPS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->prec_graph, graph, 0);
+    e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      h->prec_graph = nullptr;
+      exec = nullptr;
       return fail(h, VPS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
   }
-  VPS_CK(h, cudaGraphLaunch(h->prec_graph, h->stream));
-  launch_counter() += h->graph_kernels;
+  VPS_CK(h, cudaGraphLaunch(exec, h->stream));
+  launch_counter() += nk;
   return VPS_OK;
 }
 
@@ -557,6 +573,168 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
     }
   }
   return fail(h, VPS_ENOCONV, "CG did not reach %g in %d iterations (%g)", rtol, max_it, rel);
+}
+
+// GMRES buffers for restart length m (allocated on first use, kept).
+int gmres_alloc(vps_context* h, int m) {
+  if (h->gm_m == m) return VPS_OK;
+  for (double* p : {h->gmV, h->gmZ, h->gm_partial, h->gm_dev})
+    if (p) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(p);
+      for (auto& q : h->allocs)
+        if (q == p) q = nullptr;
+    }
+  h->gmV = h->gmZ = h->gm_partial = h->gm_dev = nullptr;
+  if (h->gm_host) cudaFreeHost(h->gm_host);
+  h->gm_host = nullptr;
+  h->gm_m = 0;
+  const int64_t ld = (h->geom[h->L].total + 31) / 32 * 32;
+  void* p;
+  if (int rc = dalloc(h, &p, (size_t)(m + 1) * ld * sizeof(double))) return rc;
+  h->gmV = (double*)p;
+  if (int rc = dalloc(h, &p, (size_t)m * ld * sizeof(double))) return rc;
+  h->gmZ = (double*)p;
+  if (int rc = dalloc(h, &p, (size_t)(m + 1) * kDotBlocks * sizeof(double))) return rc;
+  h->gm_partial = (double*)p;
+  if (int rc = dalloc(h, &p, (size_t)(3 * m + 8) * sizeof(double))) return rc;
+  h->gm_dev = (double*)p;
+  VPS_CK(h, cudaMallocHost(&p, (size_t)(3 * m + 8) * sizeof(double)));
+  h->gm_host = (double*)p;
+  h->gm_ld = ld;
+  h->gm_m = m;
+  return VPS_OK;
+}
+
+// Flexible GMRES on the finest level (the outer solver of Section 4),
+// right-preconditioned by the V-cycle of Algorithm 1 (non-symmetric),
+// x0 = 0, restarted every m products A z.  Arnoldi by classical
+// Gram-Schmidt applied twice (two block reductions per step, deterministic);
+// Givens rotations on the host.  A cycle ends when the least-squares
+// residual reaches rtol ||b||, then the residual is evaluated in FP64 and
+// checked as in cg_solve (rtol, or the rounding bound of its evaluation);
+// otherwise the next cycle starts from it.  *iters: products A z.
+int gmres_solve(vps_context* h, int m, double rtol, int max_it, int* iters, double* rel_res) {
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t n = g.total;
+  if (int rc = gmres_alloc(h, m)) return rc;
+  const int64_t ld = h->gm_ld;
+  double* V = h->gmV;
+  double* Z = h->gmZ;
+  double* hd = h->gm_dev;   // [0, m]: first projection, [m+1, 2m+1]: second, [2m+2]: ||w||^2
+  double* hh = h->gm_host;
+  h->last_restarts = 0;
+  h->last_at_floor = 0;
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  VPS_CK(h, launch_dot1(h->cb, h->cb, n, h->partial, h->dots, h->stream));
+  VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  const double nb = std::sqrt(h->host_dots[0]);
+  VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
+  if (!(nb > 0.0)) {
+    if (!std::isfinite(nb)) return fail(h, VPS_EBREAKDOWN, "right-hand side is not finite");
+    return VPS_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  VPS_CK(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  double beta = nb, prev_true = 0.0;
+  int it = 0;
+  while (true) {
+    VPS_CK(h, launch_scale(V, h->cr, 1.0 / beta, n, h->stream));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    double est = beta / nb;
+    while (j < m && it < max_it) {
+      double* vj = V + (size_t)j * ld;
+      double* zj = Z + (size_t)j * ld;
+      double* w = V + (size_t)(j + 1) * ld;
+      // z_j = B v_j (input cr, output czn), w = A z_j
+      VPS_CK(h, cudaMemcpyAsync(h->cr, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      if (int rc = precondition(h, false)) return rc;
+      VPS_CK(h, cudaMemcpyAsync(zj, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      if (outer_df(h)) {
+        VPS_CK(h, launch_split_df(zj, h->cph, h->cpl, n, h->stream));
+        VPS_CK(h, h->ks->apply_df(g, h->cph, h->cpl, w, h->stream));
+      } else {
+        VPS_CK(h, h->ks->d.apply(g, zj, nullptr, w, h->stream));
+      }
+      // w -= V h twice (classical Gram-Schmidt with one reorthogonalisation)
+      VPS_CK(h, launch_multi_dot(V, ld, j + 1, w, n, h->gm_partial, hd, h->stream));
+      VPS_CK(h, launch_multi_axpy(w, V, ld, j + 1, hd, -1.0, n, h->stream));
+      VPS_CK(h, launch_multi_dot(V, ld, j + 1, w, n, h->gm_partial, hd + m + 1, h->stream));
+      VPS_CK(h, launch_multi_axpy(w, V, ld, j + 1, hd + m + 1, -1.0, n, h->stream));
+      VPS_CK(h, launch_dot1(w, w, n, h->partial, hd + 2 * m + 2, h->stream));
+      VPS_CK(h, cudaMemcpyAsync(hh, hd, (size_t)(2 * m + 3) * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+      VPS_CK(h, cudaStreamSynchronize(h->stream));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = hh[i] + hh[m + 1 + i];
+      const double hn = std::sqrt(hh[2 * m + 2]);
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn))
+        return fail(h, VPS_EBREAKDOWN, "GMRES: non-finite Arnoldi vector at step %d", it + 1);
+      if (hn > 0.0) VPS_CK(h, launch_scale(w, w, 1.0 / hn, n, h->stream));
+      for (int i = 0; i < j; ++i) {  // previous rotations on the new column
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      if (!(den > 0.0)) return fail(h, VPS_EBREAKDOWN, "GMRES: breakdown at step %d", it + 1);
+      cs[j] = Hij(j, j) / den;
+      sn[j] = Hij(j + 1, j) / den;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++j;
+      ++it;
+      est = std::fabs(gv[j]) / nb;
+      if (iters) *iters = it;
+      if (rel_res) *rel_res = est;
+      if (est <= rtol || hn == 0.0) break;
+    }
+    // x += Z y,  H[:j,:j] y = g[:j]
+    for (int i = j - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int q = i + 1; q < j; ++q) t -= Hij(i, q) * y[q];
+      y[i] = t / Hij(i, i);
+    }
+    for (int i = 0; i < j; ++i) hh[i] = y[i];
+    VPS_CK(h, cudaMemcpyAsync(hd, hh, (size_t)j * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+    VPS_CK(h, launch_multi_axpy(h->cx, Z, ld, j, hd, 1.0, n, h->stream));
+    // FP64 residual
+    if (int rc = cg_true_residual(h)) return rc;
+    VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                              h->stream));
+    VPS_CK(h, cudaStreamSynchronize(h->stream));
+    const double rel_true = std::sqrt(h->host_sc->rr) / nb;
+    if (rel_res) *rel_res = rel_true;
+    if (!std::isfinite(rel_true)) return fail(h, VPS_EBREAKDOWN, "GMRES residual not finite");
+    if (rel_true <= rtol) return VPS_OK;
+    if (est <= rtol) {  // the least-squares residual had converged: drift or rounding
+      if (int rc = cg_residual_scale(h)) return rc;
+      VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                h->stream));
+      VPS_CK(h, cudaStreamSynchronize(h->stream));
+      const double unorm = std::sqrt(h->host_sc->pAp);
+      const int cls = classify_check(h, rtol, nb, rel_true, unorm, prev_true);
+      if (cls == kCheckConverged) return VPS_OK;
+      if (cls == kCheckStagnated)
+        return fail(h, VPS_ENOCONV, "GMRES stagnated at an FP64 residual of %g (rtol %g)",
+                    rel_true, rtol);
+      prev_true = rel_true;
+      ++h->last_restarts;
+    }
+    if (it >= max_it)
+      return fail(h, VPS_ENOCONV, "GMRES did not reach %g in %d iterations (%g)", rtol, max_it,
+                  rel_true);
+    beta = rel_true * nb;
+  }
 }
 
 int upload_rhs_sines(vps_context* h, int level, int n_modes, const double* coef, const int* freq,
@@ -1185,8 +1363,9 @@ int vps_destroy(vps_handle h) {
   if (h->device >= 0) cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  if (h->prec_graph) cudaGraphExecDestroy(h->prec_graph);
+  drop_graphs(h);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->gm_host) cudaFreeHost(h->gm_host);
   if (h->host_sc) cudaFreeHost(h->host_sc);
   if (h->host_dots) cudaFreeHost(h->host_dots);
   if (h->host_x) cudaFreeHost(h->host_x);
@@ -1358,6 +1537,24 @@ int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
   return VPS_OK;
 }
 
+int vps_gmres(vps_handle h, const double* b, double* x, double rtol, int restart, int max_it,
+              int* iters, double* rel_res) {
+  if (!h) return VPS_EINVAL;
+  if (!b || !x) return fail(h, VPS_EINVAL, "NULL vector");
+  if (!(rtol > 0.0) || max_it < 1) return fail(h, VPS_EINVAL, "need rtol > 0 and max_it >= 1");
+  if (restart < 1 || restart > 512) return fail(h, VPS_EINVAL, "restart must be in 1..512");
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  const LevelGeom& g = h->geom[h->L];
+  VPS_CK(h, launch_pack<double>(g, b, h->cb, h->stream));
+  int rc = gmres_solve(h, restart, rtol, max_it, iters, rel_res);
+  cudaError_t e = launch_unpack<double>(g, h->cx, x, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(h, VPS_ECUDA, "unpack: %s", cudaGetErrorString(e));
+  return VPS_OK;
+}
+
 int vps_solve_host(vps_handle h, const double* b_host, double* x_host, double rtol, int max_it,
                    int* iters, double* rel_res) {
   if (!h) return VPS_EINVAL;
@@ -1440,10 +1637,7 @@ int vps_set_smooth_variant(vps_handle h, int level, int variant) {
     if (int rc = check_level(h, level, 1)) return rc;
   for (int l = 1; l <= h->L; ++l)
     if (level == 0 || l == level) h->smooth_var[l] = variant;
-  if (h->prec_graph) {
-    cudaGraphExecDestroy(h->prec_graph);
-    h->prec_graph = nullptr;
-  }
+  drop_graphs(h);
   return VPS_OK;
 }
 
@@ -1472,10 +1666,7 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
       for (int l = 1; l <= h->L; ++l) h->smooth_var[l] = var[l];
       if (coarse != h->coarse)
         if (int rc = setup_coarse(h, coarse)) return rc;
-      if (h->prec_graph) {
-        cudaGraphExecDestroy(h->prec_graph);
-        h->prec_graph = nullptr;
-      }
+      drop_graphs(h);
       if (from_cache) *from_cache = 1;
       return VPS_OK;
     }

@@ -105,6 +105,50 @@ dot_final_kernel(const double* __restrict__ partial, double* __restrict__ out, i
   }
 }
 
+// Block-Krylov helpers (GMRES).  V: nv vectors of length n, vector i at
+// V + i * ld.  partial[i * kDotBlocks + block] = V_i . w over the block's
+// fixed subset (the same fixed order as dot_partial_kernel).
+__global__ void __launch_bounds__(kThreads)
+multi_dot_partial_kernel(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                         int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const double* v = V + blockIdx.y * ld;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)kDotBlocks * kThreads)
+    acc[0] = fma(v[i], w[i], acc[0]);
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.y * kDotBlocks + blockIdx.x] = acc[0];
+}
+
+// out[i] = sum of partial[i * kDotBlocks ..] in a fixed order (one block per i).
+__global__ void __launch_bounds__(kThreads)
+multi_dot_final_kernel(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) acc[0] += partial[blockIdx.x * kDotBlocks + i];
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc[0];
+}
+
+// w += sign * sum_i c[i] V_i  (c on the device).
+__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V, int64_t ld,
+                                  int nv, const double* __restrict__ c, double sign, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < nv; ++i) acc = fma(sign * __ldg(c + i), V[i * ld + e], acc);
+    w[e] = acc;
+  }
+}
+
+__global__ void scale_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                             int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = a * x[e];
+}
+
 __global__ void cg_alpha_kernel(CgScalars* sc) {
   const double pAp = sc->pAp;
   if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(sc->rz)) {
@@ -408,6 +452,28 @@ cudaError_t launch_dot2(const double* a, const double* b, const double* c, const
   dot_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
   VPS_COUNT_LAUNCH();
   dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, c ? 2 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n,
+                             double* partial, double* out, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  multi_dot_partial_kernel<<<dim3(kDotBlocks, nv), kThreads, 0, s>>>(V, ld, w, n, partial);
+  VPS_COUNT_LAUNCH();
+  multi_dot_final_kernel<<<nv, kThreads, 0, s>>>(partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy(double* w, const double* V, int64_t ld, int nv, const double* c,
+                              double sign, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  multi_axpy_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(w, V, ld, nv, c, sign, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  scale_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(y, x, a, n);
   return cudaGetLastError();
 }
 

@@ -176,6 +176,13 @@ cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars
 cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s,
                              float* ph = nullptr, float* pl = nullptr);
 cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
+// GMRES block operations: out[i] = V_i . w (i < nv; partial: nv * kDotBlocks
+// doubles), w += sign * sum_i c[i] V_i (c on the device), y = a x.
+cudaError_t launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n,
+                             double* partial, double* out, cudaStream_t s);
+cudaError_t launch_multi_axpy(double* w, const double* V, int64_t ld, int nv, const double* c,
+                              double sign, int64_t n, cudaStream_t s);
+cudaError_t launch_scale(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 // ph = fl32(a), pl = fl32(a - ph)
 cudaError_t launch_split_df(const double* a, float* ph, float* pl, int64_t n, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float* a, double* b, int64_t n, cudaStream_t s);
