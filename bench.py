@@ -82,6 +82,9 @@ def parse():
                    help="requests of the serving measurement (0: skip it)")
     p.add_argument("--tune-cache", default=None,
                    help="autotuner cache file (reused when it holds this workload)")
+    p.add_argument("--smoother-variant", type=int, default=None,
+                   help="pin the finest level's smoother variant after tuning (profiling runs; "
+                        "default: the autotuner's choice)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--repeats", type=int, default=CPU_SAMPLE_REPEATS, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -256,8 +259,12 @@ def main():
 
     P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
     P.vps_autotune(args.tune_cache)  # timed trials on this GPU, before the timed region
+    if args.smoother_variant is not None:
+        P.vps_set_smooth_variant(L, args.smoother_variant)
     tuned = {"coarse_level": P.vps_get_coarse_level(),
-             "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)]}
+             "smoother_variants": [P.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
+             "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)],
+             "finest_variant_pinned": args.smoother_variant is not None}
     N = P.n_interior()
     b = torch.as_tensor(uniform_vector(N, 1 + rank), device="cuda")
     x = torch.zeros_like(b)
