@@ -439,6 +439,33 @@ def main():
                         "l2_error": Pg.vps_l2_error_sine(xg)}
         gm["speedup_fp32_vcycle"] = gm["fp64"]["time_s"] / gm["fp32_vcycle"]["time_s"]
         extras["gmres_sine_tol1e-9"] = gm
+        # kernel structures of the smoother (Section 3.1): one multiplicative step
+        # on the finest level, the tuned fused kernel against Separate, Global and
+        # Global with the dense inverse (the "straightforward" implementation)
+        abl = {}
+        for pname, Pk in (("fp32", P), ("fp64", P64)):
+            bk = Pk.to_level(b.to(Pk.dtype))
+            xk = Pk.empty_level()
+            row = {}
+            for kind, kname in ((vps.VPS_KERNEL_FUSED, "fused"), (vps.VPS_KERNEL_SEPARATE, "separate"),
+                                (vps.VPS_KERNEL_GLOBAL, "global"),
+                                (vps.VPS_KERNEL_GLOBAL_INVERSE, "global_inverse_matrix")):
+                Pk.vps_set_smoother_kernel(kind)
+                Pk.vps_smooth(L, bk, xk, 2)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(Pk.stream)
+                for _ in range(5):
+                    vps._check(lib.vps_smooth(Pk.h, L, ptr(bk), ptr(xk), 1), Pk.h)
+                e1.record(Pk.stream)
+                torch.cuda.synchronize()
+                ts = e0.elapsed_time(e1) / 5e3
+                row[kname] = {"step_ms": 1e3 * ts, "dof_per_s": N / ts}
+            Pk.vps_set_smoother_kernel(vps.VPS_KERNEL_FUSED)
+            for kname in ("separate", "global", "global_inverse_matrix"):
+                row["fused_speedup_over_" + kname] = row[kname]["step_ms"] / row["fused"]["step_ms"]
+            abl[pname] = row
+        extras["smoother_kernel_structures"] = abl
         P64.close()
         # additive smoother: damping 0.7 taken literally, and 0.7 of the stability limit
         add = {}

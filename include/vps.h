@@ -293,6 +293,29 @@ int vps_kernel_launches(vps_handle h, int64_t* count);
 int vps_set_outer_operator(vps_handle h, int mode);
 int vps_get_outer_operator(vps_handle h, int* mode);
 
+/*
+ * vps_set_smoother_kernel / vps_get_smoother_kernel -- the kernel structure
+ * of the multiplicative smoother's colour passes (Section 3.1, its table of
+ * smoother versions), for comparisons; the smoothing itself is the same:
+ *   VPS_KERNEL_FUSED (0, default): one kernel per colour (the smoother
+ *     variants of vps_set_smooth_variant);
+ *   VPS_KERNEL_SEPARATE (1): a local-residual kernel writes b_I - Abar_j x
+ *     of every patch to the level's residual vector, a second kernel solves;
+ *   VPS_KERNEL_GLOBAL (2): the residual of the whole level by the operator,
+ *     then the local solve kernel;
+ *   VPS_KERNEL_GLOBAL_INVERSE (3): as 2 with the local solve by the dense
+ *     precomputed A_j^-1 instead of fast diagonalisation (the "inverse
+ *     matrix" local solver; m^d <= 1024 rows, i.e. k <= 5 in 3D; built on
+ *     the host in FP64 on first selection).
+ * Kinds 1-3 take the patches per thread of the level's variant.  Errors:
+ * VPS_EINVAL (unknown kind, additive handle, inverse too large). */
+#define VPS_KERNEL_FUSED 0
+#define VPS_KERNEL_SEPARATE 1
+#define VPS_KERNEL_GLOBAL 2
+#define VPS_KERNEL_GLOBAL_INVERSE 3
+int vps_set_smoother_kernel(vps_handle h, int kind);
+int vps_get_smoother_kernel(vps_handle h, int* kind);
+
 /* vps_get_solve_info -- of the handle's last solve: the number of CG
  * restarts from the FP64 residual, and 1 if it ended at the rounding bound
  * of that residual rather than at rtol (see vps_solve).  Host outputs, may

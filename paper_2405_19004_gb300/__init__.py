@@ -28,6 +28,7 @@ VPS_FP32 = 1
 VPS_MULTIPLICATIVE = 0
 VPS_ADDITIVE = 1
 VPS_MAX_DEGREE = 7
+VPS_KERNEL_FUSED, VPS_KERNEL_SEPARATE, VPS_KERNEL_GLOBAL, VPS_KERNEL_GLOBAL_INVERSE = 0, 1, 2, 3
 VPS_OUTER_FP64 = 0
 VPS_OUTER_DOUBLE_FLOAT = 1
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
@@ -58,6 +59,8 @@ SIGNATURES = {
     "vps_get_outer_operator": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_apply_outer": (_i, [_p, _p, _p]),
     "vps_get_solve_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "vps_set_smoother_kernel": (_i, [_p, _i]),
+    "vps_get_smoother_kernel": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_kernel_launches": (_i, [_p, _i64p]),
     "vps_set_coarse_level": (_i, [_p, _i]),
     "vps_autotune": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i)]),
@@ -314,6 +317,14 @@ class Poisson:
     def vps_apply_outer(self, x, y):
         assert x.dtype == self.torch.float64 and y.dtype == self.torch.float64
         self._call(lib().vps_apply_outer, _ptr(x), _ptr(y))
+
+    def vps_set_smoother_kernel(self, kind):
+        _check(lib().vps_set_smoother_kernel(self.h, int(kind)), self.h)
+
+    def vps_get_smoother_kernel(self):
+        c = ctypes.c_int()
+        _check(lib().vps_get_smoother_kernel(self.h, ctypes.byref(c)), self.h)
+        return c.value
 
     def vps_get_solve_info(self):
         """(restarts, at_rounding_bound) of the last solve."""

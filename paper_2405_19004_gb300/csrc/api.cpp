@@ -131,6 +131,10 @@ struct vps_context {
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
   int smooth_var[kMaxLevels + 1] = {};  // smoother variant per level (index into the table)
+  // kernel structure of the multiplicative smoother (Section 3.1's
+  // Fused / Separate / Global, and Global with the dense inverse)
+  int kernel_kind = VPS_KERNEL_FUSED;
+  void* ainv = nullptr;                 // A_j^-1 (symmetric, m^d x m^d), working precision
   // asynchronous CG (used by the serving loop)
   int as_phase = 0;                     // 0 idle, 1 iteration in flight, 2 result copy in flight
   int as_it = 0, as_maxit = 0, as_status = 0;
@@ -223,6 +227,41 @@ const KernelFns<float>& fns<float>(vps_context* h) { return h->ks->f; }
 template <>
 const KernelFns<double>& fns<double>(vps_context* h) { return h->ks->d; }
 
+// One colour pass of the multiplicative smoother with the handle's kernel
+// structure (Section 3.1): Fused (one kernel), Separate (local residual
+// kernel, then the local solve), Global (global residual by the operator,
+// then the local solve), Global with the dense inverse as local solver.
+template <typename T>
+int colour_pass(vps_context* h, int l, int c, const T* b, T* x) {
+  const KernelFns<T>& F = fns<T>(h);
+  const LevelGeom& g = h->geom[l];
+  const ColourGeom cg = make_colour(g, c);
+  const T* il = static_cast<const T*>(h->inv_lam);
+  const int v = h->smooth_var[l];
+  T* r = static_cast<T*>(h->rv[l]);
+  int q = v % kQVariants;
+  if (!F.smooth_add_v[q]) q = 0;
+  switch (h->kernel_kind) {
+    case VPS_KERNEL_SEPARATE:
+      if (!F.resid_v[q]) return fail(h, VPS_EINVAL, "Separate kernel unavailable");
+      VPS_CK(h, F.resid_v[q](g, cg, b, x, r, h->stream));
+      VPS_CK(h, F.smooth_add_v[q](g, cg, r, x, il, T(1), h->stream));
+      return VPS_OK;
+    case VPS_KERNEL_GLOBAL:
+      VPS_CK(h, F.apply(g, x, b, r, h->stream));
+      VPS_CK(h, F.smooth_add_v[q](g, cg, r, x, il, T(1), h->stream));
+      return VPS_OK;
+    case VPS_KERNEL_GLOBAL_INVERSE:
+      if (!F.inverse_solve || !h->ainv) return fail(h, VPS_EINVAL, "dense inverse unavailable");
+      VPS_CK(h, F.apply(g, x, b, r, h->stream));
+      VPS_CK(h, F.inverse_solve(g, cg, r, x, static_cast<const T*>(h->ainv), h->stream));
+      return VPS_OK;
+    default:
+      VPS_CK(h, F.smooth_mult_v[v](g, cg, b, x, il, h->stream));
+      return VPS_OK;
+  }
+}
+
 template <typename T>
 int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   const LevelGeom& g = h->geom[l];
@@ -242,7 +281,7 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   } else {
     for (int i = 0; i < nc; ++i) {
       const int c = forward ? i : nc - 1 - i;
-      VPS_CK(h, fns<T>(h).smooth_mult_v[v](g, make_colour(g, c), b, x, il, h->stream));
+      if (int rc = colour_pass<T>(h, l, c, b, x)) return rc;
     }
   }
   return VPS_OK;
@@ -1446,13 +1485,9 @@ int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* 
   const LevelGeom& g = h->geom[level];
   const int v = h->smooth_var[level];
   if (!variant_ok(h, v)) return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
-  if (h->prec == VPS_FP64)
-    VPS_CK(h, h->ks->d.smooth_mult_v[v](g, make_colour(g, colour), (const double*)b, (double*)x,
-                                        (const double*)h->inv_lam, h->stream));
-  else
-    VPS_CK(h, h->ks->f.smooth_mult_v[v](g, make_colour(g, colour), (const float*)b, (float*)x,
-                                        (const float*)h->inv_lam, h->stream));
-  return VPS_OK;
+  (void)g;
+  if (h->prec == VPS_FP64) return colour_pass<double>(h, level, colour, (const double*)b, (double*)x);
+  return colour_pass<float>(h, level, colour, (const float*)b, (float*)x);
 }
 
 int vps_apply(vps_handle h, int level, const void* x, void* y) {
@@ -1770,6 +1805,66 @@ int vps_set_outer_operator(vps_handle h, int mode) {
     h->cpl = (float*)p;
   }
   h->outer = mode;
+  return VPS_OK;
+}
+
+int vps_set_smoother_kernel(vps_handle h, int kind) {
+  if (!h) return VPS_EINVAL;
+  if (kind < VPS_KERNEL_FUSED || kind > VPS_KERNEL_GLOBAL_INVERSE)
+    return fail(h, VPS_EINVAL, "smoother kernel %d (expected 0..3)", kind);
+  if (kind != VPS_KERNEL_FUSED && h->smoother != VPS_MULTIPLICATIVE)
+    return fail(h, VPS_EINVAL, "kernel structures apply to the multiplicative smoother");
+  if (kind == VPS_KERNEL_GLOBAL_INVERSE && !h->ainv) {
+    const int m = h->tab.m, d = h->dim;
+    const int md = d == 3 ? m * m * m : m * m;
+    const bool ok = h->prec == VPS_FP64 ? h->ks->d.inverse_solve != nullptr
+                                        : h->ks->f.inverse_solve != nullptr;
+    if (!ok) return fail(h, VPS_EINVAL, "dense inverse of %d rows exceeds 1024", md);
+    if (int rc = set_device(h)) return rc;
+    // A_j^-1 = W diag(1 / sum of eigenvalues) W^T, W = S (x) S [(x) S], in FP64
+    std::vector<double> A((size_t)md * md, 0.0), dq(md);
+    auto digit = [&](int e, int t) { return t == 0 ? e % m : (t == 1 ? (e / m) % m : e / (m * m)); };
+    for (int q = 0; q < md; ++q) {
+      double sl = 0.0;
+      for (int t = 0; t < d; ++t) sl += h->tab.lam[digit(q, t)];
+      dq[q] = 1.0 / sl;
+    }
+    std::vector<double> W((size_t)md * md);
+    for (int e = 0; e < md; ++e)
+      for (int q = 0; q < md; ++q) {
+        double w = 1.0;
+        for (int t = 0; t < d; ++t) w *= h->tab.S[digit(e, t) * m + digit(q, t)];
+        W[(size_t)e * md + q] = w;
+      }
+    for (int e = 0; e < md; ++e)
+      for (int f = 0; f <= e; ++f) {
+        double acc = 0.0;
+        const double* we = &W[(size_t)e * md];
+        const double* wf = &W[(size_t)f * md];
+        for (int q = 0; q < md; ++q) acc += we[q] * dq[q] * wf[q];
+        A[(size_t)e * md + f] = A[(size_t)f * md + e] = acc;
+      }
+    void* p;
+    if (int rc = dalloc(h, &p, (size_t)md * md * h->esz)) return rc;
+    cudaError_t e;
+    if (h->prec == VPS_FP64) {
+      e = cudaMemcpyAsync(p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    } else {
+      std::vector<float> Af(A.begin(), A.end());
+      e = cudaMemcpyAsync(p, Af.data(), Af.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) return fail(h, VPS_ECUDA, "dense inverse: %s", cudaGetErrorString(e));
+    h->ainv = p;
+  }
+  h->kernel_kind = kind;
+  drop_graphs(h);
+  return VPS_OK;
+}
+
+int vps_get_smoother_kernel(vps_handle h, int* kind) {
+  if (!h || !kind) return VPS_EINVAL;
+  *kind = h->kernel_kind;
   return VPS_OK;
 }
 

@@ -309,6 +309,30 @@ __device__ __forceinline__ void prefetch_b(const T* __restrict__ b, T* bI, const
   });
 }
 
+// Writes the interleaved interior tensor buf[(L * m + o) * P + p] of the
+// block's patches to the level vector out (times scale): the local residual
+// of the Separate kernel.
+template <typename T, int G, int Q, int NT>
+__device__ __forceinline__ void store_lines(const T* __restrict__ buf, T* __restrict__ out,
+                                            const int* s_org, int px, int pz, T scale) {
+  constexpr int NL = DIM == 3 ? m * m : m;
+  constexpr int P = G * Q;
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    int rowoff;
+    if constexpr (DIM == 3) rowoff = (L / m + 1) * pz + (L % m + 1) * px + 1;
+    else rowoff = (L + 1) * px + 1;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int org = s_org[g * Q + j];
+      if (org < 0) continue;
+      T* dst = out + org + rowoff;
+#pragma unroll
+      for (int o = 0; o < m; ++o) dst[o] = scale * buf[(L * m + o) * P + g * Q + j];
+    }
+  });
+}
+
 // ------------------------------------------------------- multiplicative
 // Closure lines along the first contracted direction, in the order the
 // Boundary kernel assigns them to threads: the 8K lines on the faces of the
@@ -344,10 +368,15 @@ __device__ __forceinline__ int boundary_first_line(int L, bool* full) {
 // 3.2), equal for the exact local solver: the interior of x is neither read
 // nor staged, and lines of the first contraction that run through the
 // patch interior contract only their two end (boundary) nodes.
-template <typename T, int QQ, bool BND, int W>
+// RES = true (with the fused layout): the first half of the Separate kernel
+// of Section 3.1 -- the local residual b_I - Abar_j x of every patch of the
+// colour is written to rout (physical units, scaled back by 1 / bscale) and
+// x is left unchanged.
+template <typename T, int QQ, bool BND, int W, bool RES = false>
 __global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
 smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
-                   int px, int pz, ColourGeom cg, T bscale) {
+                   int px, int pz, ColourGeom cg, T bscale, T* __restrict__ rout = nullptr) {
+  static_assert(!(RES && BND), "the residual-only kernel reads the whole closure");
   using C = SmoothCfg<T, QQ, W>;
   constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
   using PK = Pack<T, Q>;
@@ -360,7 +389,8 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
   T* il = bI + (BND ? 1 : 2) * P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
   load_origins<P, NT>(s_org, cg, px, pz);
-  for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
+  if constexpr (!RES)
+    for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   prefetch_b<T, G, Q, NT>(b, bI, s_org, px, pz);
 
@@ -516,6 +546,10 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
     });
     __syncthreads();
+    if constexpr (RES) {
+      store_lines<T, G, Q, NT>(A0, rout, s_org, px, pz, T(1) / bscale);
+      return;
+    }
     // Fast diagonalisation: S^T along z, y, x (scaled), then S back.
     fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);
     __syncthreads();
@@ -639,6 +673,10 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
     });
     __syncthreads();
+    if constexpr (RES) {
+      store_lines<T, G, Q, NT>(B0, rout, s_org, px, pz, T(1) / bscale);
+      return;
+    }
     fd_stage<T, G, Q, NT, 0>(B0, A0, nullptr);
     __syncthreads();
     fd_stage<T, G, Q, NT, 1>(A0, A1, il);
@@ -718,6 +756,43 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
     fd_stage<T, G, Q, NT, 2>(X0, X1, nullptr);
     __syncthreads();
     fd_final<T, G, Q, NT>(X1, x, nullptr, s_org, px, pz, scale);
+  }
+}
+
+// -------------------------------------------------- inverse-matrix solve
+// x_I += scale * A_j^-1 r_I for every patch of one colour with the dense
+// precomputed inverse (one copy: the coefficients are constant), the
+// "inverse matrix" local solver that Section 3.1 compares with fast
+// diagonalisation.  One patch per block, one interior node per thread;
+// AinvT holds A_j^-1 transposed (column j contiguous) so that the threads
+// of a warp read consecutive entries.
+constexpr int kMDim = DIM == 3 ? m * m * m : m * m;
+constexpr int kInvThreads = ((kMDim + 31) / 32) * 32;
+constexpr bool kInvFits = kMDim <= 1024;
+
+__device__ __forceinline__ int interior_offset(int e, int px, int pz) {
+  if constexpr (DIM == 3) return (e / (m * m) + 1) * pz + ((e / m) % m + 1) * px + 1 + e % m;
+  else return (e / m + 1) * px + 1 + e % m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kInvFits ? kInvThreads : 32)
+inverse_solve_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ AinvT,
+                     int px, int pz, ColourGeom cg, T scale) {
+  __shared__ T rs[kInvFits ? kMDim : 1];
+  if constexpr (kInvFits) {
+    const int gp = blockIdx.x;
+    if (gp >= cg.npatch) return;
+    const int org = closure_origin(gp, cg, px, pz);
+    for (int e = threadIdx.x; e < kMDim; e += kInvThreads) rs[e] = r[org + interior_offset(e, px, pz)];
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i < kMDim) {
+      T u = T(0);
+      for (int j = 0; j < kMDim; ++j) u = fma(__ldg(AinvT + (size_t)j * kMDim + i), rs[j], u);
+      T* dst = x + org + interior_offset(i, px, pz);
+      *dst = fma(scale, u, *dst);
+    }
   }
 }
 
@@ -1484,6 +1559,34 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
 }
 
 template <typename T, int PP>
+cudaError_t resid_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, const T* x, T* r,
+                         cudaStream_t s) {
+  using C = SmoothCfg<T, PP, 0>;
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + C::P - 1) / C::P;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
+  smooth_mult_kernel<T, PP, false, 0, true><<<(unsigned)grid, C::NT, C::smem_mult, s>>>(
+      b, const_cast<T*>(x), nullptr, (int)g.px, (int)g.pz, cg, bscale, r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t inverse_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
+                           const T* AinvT, cudaStream_t s) {
+  if constexpr (!kInvFits) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (cg.npatch == 0) return cudaSuccess;
+    const T scale = DIM == 3 ? T(1.0 / g.h) : T(1);
+    VPS_COUNT_LAUNCH();
+    inverse_solve_kernel<T><<<(unsigned)cg.npatch, kInvThreads, 0, s>>>(r, x, AinvT, (int)g.px,
+                                                                          (int)g.pz, cg, scale);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, int PP>
 cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
                               const T* inv_lam, T scale, cudaStream_t s) {
   using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
@@ -1619,6 +1722,9 @@ cudaError_t smooth_limits() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_mult);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false, 0, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_mult);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(smooth_add_kernel<T, PP>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_add);
   }
@@ -1639,6 +1745,8 @@ void register_variant(KernelFns<T>* f, int v) {
     f->smooth_mult_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
   }
+  if constexpr (C::fits) f->resid_v[v] = resid_launch<T, PP>;
+  else f->resid_v[v] = nullptr;
   if constexpr (C::fits) {
     f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false, 0>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
@@ -1659,6 +1767,7 @@ void register_fns(KernelFns<T>* f) {
   f->apply = apply_launch<T>;
   f->prolong_add = prolong_launch<T>;
   f->restrict_ = restrict_launch<T>;
+  f->inverse_solve = kInvFits ? inverse_launch<T> : nullptr;
 }
 
 template <typename T>

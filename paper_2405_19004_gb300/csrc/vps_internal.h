@@ -111,6 +111,13 @@ struct KernelFns {
   SmoothAddFn smooth_add = nullptr;
   SmoothAddFn smooth_add_v[kSmoothVariants] = {};
   int variant_p[kSmoothVariants] = {};           // patches per block of each variant
+  // ablation kernels of Section 3.1: the local residual of every patch of a
+  // colour written to r (Separate; 1, 2, 4 patches per thread), and the
+  // local solve with the dense inverse (AinvT: A_j^-1 transposed, m^d x m^d)
+  cudaError_t (*resid_v[kQVariants])(const LevelGeom&, const ColourGeom&, const T* b,
+                                     const T* x, T* r, cudaStream_t) = {};
+  cudaError_t (*inverse_solve)(const LevelGeom&, const ColourGeom&, const T* r, T* x,
+                               const T* AinvT, cudaStream_t) = nullptr;
   // y = A x  (b == nullptr)  or  y = b - A x  (residual)
   cudaError_t (*apply)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
   // x_fine += P x_coarse
