@@ -61,10 +61,10 @@ def smoother_traffic(variant):
         if line.startswith("- ") and ":" in line:
             key, val = line[2:].split(":", 1)
             vals[key.strip()] = val.strip().strip("`")
-    if vals.get("kernels_dk.cu sha256") != sha or vals.get("variant") != str(variant):
+    if vals.get("kernels_dk.cu sha256") != sha:
         return None
     try:
-        return float(vals["traffic bytes per launch"])
+        return float(vals[f"variant {variant} traffic bytes per launch"])
     except (KeyError, ValueError):
         return None
 

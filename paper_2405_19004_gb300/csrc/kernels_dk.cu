@@ -101,6 +101,10 @@ constexpr int kLinesMax = DIM == 3 ? n * n : n;
 constexpr int kG = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 4 : K == 3 ? 2 : 1)
                             : (K <= 2 ? 32 : (K <= 4 ? 16 : 8));
 constexpr int kVarQ[kQVariants] = {1, 2, 4};
+// Contract the first and the middle direction of the fast diagonalisation in
+// registers (two stages and two barriers fewer); above k = 5 the extra live
+// values cost more resident blocks than the barriers save.
+constexpr bool kFuseFD = K <= 5;
 
 template <class T, int Q>
 struct alignas(sizeof(T) * Q) Pack {
@@ -218,6 +222,61 @@ __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict
 #pragma unroll
       for (int j = 0; j < Q; ++j) r.v[j] = MODE == 1 ? acc[j] * sc : acc[j];
       dst[o * G] = r;
+    }
+  });
+}
+
+// S^T along the contracted direction, the scaling by 1/(sum of eigenvalues),
+// and S back along the same direction, in registers (one stage instead of
+// two: the directions of the fast diagonalisation may be taken in any order,
+// and the scaling table is symmetric in its three indices).  SWAP: the
+// output line index exchanges its two digits, so that the direction that
+// was the faster one of the line becomes the slowest (contracted next).
+template <typename T, int G, int Q, int NT, bool SWAP>
+__device__ __forceinline__ void fd_pair(const T* __restrict__ in, T* __restrict__ out,
+                                        const T* __restrict__ il) {
+  constexpr int NL = DIM == 3 ? m * m : m;
+  constexpr int P = G * Q;
+  using PK = Pack<T, Q>;
+  for_lines<G * NL, NT>([&](const int t) {
+    const int L = t / G, g = t % G;
+    const PK* src = reinterpret_cast<const PK*>(in + L * P + g * Q);
+    T v[m][Q];
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      const PK pk = src[c * NL * G];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) v[c][j] = pk.v[j];
+    }
+    T tt[m][Q];
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) tt[o][j] = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const T w = c_tab<T>.S[c * m + o];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) tt[o][j] = fma(w, v[c][j], tt[o][j]);
+      }
+      const T sc = il[L * m + o];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) tt[o][j] *= sc;
+    }
+    const int Lw = SWAP ? (L % m) * m + L / m : L;
+    PK* dst = reinterpret_cast<PK*>(out + Lw * m * P + g * Q);
+#pragma unroll
+    for (int o = 0; o < m; ++o) {
+      PK u;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) u.v[j] = T(0);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const T w = c_tab<T>.S[o * m + c];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) u.v[j] = fma(w, tt[c][j], u.v[j]);
+      }
+      dst[o * G] = u;
     }
   });
 }
@@ -523,7 +582,9 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
         }
       }
       const PK* sb = reinterpret_cast<const PK*>(bI + L * m * P + g * Q);
+      constexpr bool kKeep = !RES && kFuseFD;  // keep the line for S^T along x
       PK* dR = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+      T rr[kKeep ? m : 1][Q];
 #pragma unroll
       for (int o = 0; o < m; ++o) {
         T acc[Q];
@@ -539,10 +600,34 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
           }
         }
         const PK bv = sb[o * G];
-        PK r;
+        if constexpr (kKeep) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
-        dR[o * G] = r;
+          for (int j = 0; j < Q; ++j) rr[o][j] = fma(bscale, bv.v[j], -acc[j]);
+        } else {  // the residual itself, [z][y][x]
+          PK r;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+          dR[o * G] = r;
+        }
+      }
+      if constexpr (kKeep) {
+        // first direction of the fast diagonalisation in registers: S^T along
+        // x, written as [y][z][x'] (y contracted next)
+        const int Ls = (L % m) * m + L / m;
+        PK* dT = reinterpret_cast<PK*>(A0 + Ls * m * P + g * Q);
+#pragma unroll
+        for (int o = 0; o < m; ++o) {
+          PK tt;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) tt.v[j] = T(0);
+#pragma unroll
+          for (int c = 0; c < m; ++c) {
+            const T w = c_tab<T>.S[c * m + o];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) tt.v[j] = fma(w, rr[c][j], tt.v[j]);
+          }
+          dT[o * G] = tt;
+        }
       }
     });
     __syncthreads();
@@ -550,17 +635,29 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       store_lines<T, G, Q, NT>(A0, rout, s_org, px, pz, T(1) / bscale);
       return;
     }
-    // Fast diagonalisation: S^T along z, y, x (scaled), then S back.
-    fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 0>(A1, A0, nullptr);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 1>(A0, A1, il);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);
-    __syncthreads();
+    if constexpr (kFuseFD) {
+      // Rest of the fast diagonalisation (Eq. 2.14): S^T along y; S^T along z,
+      // the eigenvalue scaling and S along z in one stage; S along y; S along x
+      // with the update of the interior.
+      fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);  // [y][z][x'] -> [z][x'][y']
+      __syncthreads();
+      fd_pair<T, G, Q, NT, true>(A1, A0, il);     // [z][x'][y'] -> [y'][x'][z'']
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);  // [y'][x'][z''] -> [x'][z''][y'']
+      __syncthreads();
+    } else {
+      // S^T along z, y, x (scaled), then S along z, y; S along x below
+      fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 0>(A1, A0, nullptr);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 1>(A0, A1, il);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);
+      __syncthreads();
+    }
     fd_final<T, G, Q, NT, BND>(A1, x, xI, s_org, px, pz, T(1));
   } else {
     // 2D.  Stage 0: lines along y from global; M x and A x along y into [x][oy].
@@ -651,6 +748,8 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       }
       const PK* sb = reinterpret_cast<const PK*>(bI + L * m * P + g * Q);
       PK* dR = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
+      constexpr bool kKeep = !RES && kFuseFD;  // keep the line for S^T along x
+      T rr[kKeep ? m : 1][Q];
 #pragma unroll
       for (int o = 0; o < m; ++o) {
         T acc[Q];
@@ -666,10 +765,30 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
           }
         }
         const PK bv = sb[o * G];
-        PK r;
+        if constexpr (kKeep) {
 #pragma unroll
-        for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
-        dR[o * G] = r;
+          for (int j = 0; j < Q; ++j) rr[o][j] = fma(bscale, bv.v[j], -acc[j]);
+        } else {  // the residual itself, [y][x]
+          PK r;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+          dR[o * G] = r;
+        }
+      }
+      if constexpr (kKeep) {  // S^T along x in registers, [y][x']
+#pragma unroll
+        for (int o = 0; o < m; ++o) {
+          PK tt;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) tt.v[j] = T(0);
+#pragma unroll
+          for (int c = 0; c < m; ++c) {
+            const T w = c_tab<T>.S[c * m + o];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) tt.v[j] = fma(w, rr[c][j], tt.v[j]);
+          }
+          dR[o * G] = tt;
+        }
       }
     });
     __syncthreads();
@@ -677,12 +796,19 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
       store_lines<T, G, Q, NT>(B0, rout, s_org, px, pz, T(1) / bscale);
       return;
     }
-    fd_stage<T, G, Q, NT, 0>(B0, A0, nullptr);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 1>(A0, A1, il);
-    __syncthreads();
-    fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
-    __syncthreads();
+    if constexpr (kFuseFD) {
+      // S^T along y, scaling and S along y in one stage; then S along x with
+      // the update of the interior
+      fd_pair<T, G, Q, NT, false>(B0, A0, il);  // [y][x'] -> [x'][y'']
+      __syncthreads();
+    } else {
+      fd_stage<T, G, Q, NT, 0>(B0, A0, nullptr);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 1>(A0, A1, il);
+      __syncthreads();
+      fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
+      __syncthreads();
+    }
     fd_final<T, G, Q, NT, BND>(A0, x, xI, s_org, px, pz, T(1));
   }
 }
