@@ -1100,6 +1100,12 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
 // costs two barriers.  Halo recomputation: ((T+2K)/T)^2 in the z stage and
 // (T+2K)/T in the y stage, against ((T+2K)/T)^2 and (T+2K)/T with T = K*CT
 // small for cubic tiles.
+// Cells per block in z of the 3D operator (planes per block: kApplyZC * K);
+// the same for every precision (fewer planes per block, i.e. more blocks,
+// measured slower for FP32 at k = 4).
+template <typename T>
+constexpr int kApplyZC = K >= 4 ? 2 : (K == 1 ? 8 : 4);
+
 struct Apply3Cfg {
   // cells per tile in x and y: a power of two, so that tiles of TX nodes
   // cover the nodes 0 .. n1-2 = k 2^l - 1 exactly (no ragged tiles)
@@ -1107,8 +1113,7 @@ struct Apply3Cfg {
   static constexpr int TX = K * CX;
   static constexpr int BX = TX + 2 * K;
   static constexpr int RB = BX | 1;
-  static constexpr int ZC = K >= 4 ? 2 : (K == 1 ? 8 : 4);  // cells per block in z
-  static constexpr int ZR = ZC * K;                          // planes per block
+
   // threads: one y-stage unit each (BX * CX units), so that stage is one
   // round; the z and x stages then take about K+2 and one round
   static constexpr int UB = BX * CX;
@@ -1130,9 +1135,9 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
   T* MM = zbuf + 4 * BX * RB;                // [TX][RB]
   T* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
-  const int z0 = blockIdx.z * C::ZR;         // a multiple of K
+  const int z0 = blockIdx.z * (kApplyZC<T> * K);  // a multiple of K
   int buf = 0;
-  for (int cz = 0; cz < C::ZC; ++cz) {
+  for (int cz = 0; cz < kApplyZC<T>; ++cz) {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int z = z0 + cz * K + q;
@@ -1243,14 +1248,6 @@ __device__ __forceinline__ DF df_norm(const DF& s) {
   return DF{h, s.lo - (h - s.hi)};
 }
 
-__device__ __forceinline__ void df_add(DF& s, const DF& x) {
-  const float t = s.hi + x.hi;
-  const float bb = t - s.hi;
-  const float e = (s.hi - (t - bb)) + (x.hi - bb);
-  s.hi = t;
-  s.lo = s.lo + (e + x.lo);
-}
-
 #define VPS_DF_MADD(acc, TAB, q, j, v) \
   df_madd(acc, c_tab<float>.TAB[(q) * n + (j)], c_tab<float>.TAB##_lo[(q) * n + (j)], v)
 
@@ -1265,9 +1262,9 @@ apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
   DF* MM = zbuf + 4 * BX * RB;
   DF* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
-  const int z0 = blockIdx.z * C::ZR;
+  const int z0 = blockIdx.z * (kApplyZC<double> * K);
   int buf = 0;
-  for (int cz = 0; cz < C::ZC; ++cz) {
+  for (int cz = 0; cz < kApplyZC<double>; ++cz) {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int z = z0 + cz * K + q;
@@ -1439,6 +1436,8 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
   constexpr int CB = C::CB, CBp = C::CBp, FB = C::FB, CC = C::CC, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t1 = reinterpret_cast<T*>(smem_raw);
+  __shared__ T sP1[2 * K * nl];
+  for (int e = threadIdx.x; e < 2 * K * nl; e += NT) sP1[e] = c_tab<T>.P1[e];
   const int cx0 = blockIdx.x * CC, cy0 = blockIdx.y * CC;
   if constexpr (DIM == 3) {
     const int cz0 = blockIdx.z * CC;
@@ -1478,24 +1477,20 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
       }
     }
     __syncthreads();
-    // along x: units (fine y fastest, fine z, coarse cell x); accumulate
-    for (int u = threadIdx.x; u < FB * FB * CC; u += NT) {
-      const int Y = u % FB, Z = (u / FB) % FB, cx = u / (FB * FB);
-      const int gy = 2 * K * cy0 + Y, gz = 2 * K * cz0 + Z;
-      if (gy < 1 || gy > n1f - 2 || gz < 1 || gz > n1f - 2) continue;
-      T v[K + 1];
+    // along x: one fine node per thread, x fastest, so that the update of the
+    // fine vector is coalesced; the 1D weights come from shared memory (the
+    // lanes of a warp need different rows of P1)
+    for (int u = threadIdx.x; u < FB * FB * FB; u += NT) {
+      const int X = u % FB, Y = (u / FB) % FB, Z = u / (FB * FB);
+      const int gx = 2 * K * cx0 + X, gy = 2 * K * cy0 + Y, gz = 2 * K * cz0 + Z;
+      if (gx < 1 || gx > n1f - 2 || gy < 1 || gy > n1f - 2 || gz < 1 || gz > n1f - 2) continue;
+      const int cx = X / (2 * K), sx = X % (2 * K);
+      const T* src = t2 + (Z * FB + Y) * CBp + K * cx;
+      const T* w = sP1 + sx * nl;
+      T acc = T(0);
 #pragma unroll
-      for (int i = 0; i <= K; ++i) v[i] = t2[(Z * FB + Y) * CBp + K * cx + i];
-      T* dst = xf + (int64_t)gz * pzf + (int64_t)gy * pxf;
-#pragma unroll
-      for (int s = 0; s < 2 * K; ++s) {
-        const int gx = 2 * K * (cx0 + cx) + s;
-        if (gx < 1 || gx > n1f - 2) continue;
-        T acc = T(0);
-#pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
-        dst[gx] += acc;
-      }
+      for (int i = 0; i <= K; ++i) acc = fma(w[i], src[i], acc);
+      xf[(int64_t)gz * pzf + (int64_t)gy * pxf + gx] += acc;
     }
   } else {
     // along y from global: units (coarse x) x coarse cell y
@@ -1517,23 +1512,17 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
       }
     }
     __syncthreads();
-    for (int u = threadIdx.x; u < FB * CC; u += NT) {
-      const int Y = u % FB, cx = u / FB;
-      const int gy = 2 * K * cy0 + Y;
-      if (gy < 1 || gy > n1f - 2) continue;
-      T v[K + 1];
+    for (int u = threadIdx.x; u < FB * FB; u += NT) {  // one fine node per thread, x fastest
+      const int X = u % FB, Y = u / FB;
+      const int gx = 2 * K * cx0 + X, gy = 2 * K * cy0 + Y;
+      if (gx < 1 || gx > n1f - 2 || gy < 1 || gy > n1f - 2) continue;
+      const int cx = X / (2 * K), sx = X % (2 * K);
+      const T* src = t1 + Y * CBp + K * cx;
+      const T* w = sP1 + sx * nl;
+      T acc = T(0);
 #pragma unroll
-      for (int i = 0; i <= K; ++i) v[i] = t1[Y * CBp + K * cx + i];
-      T* dst = xf + (int64_t)gy * pxf;
-#pragma unroll
-      for (int s = 0; s < 2 * K; ++s) {
-        const int gx = 2 * K * (cx0 + cx) + s;
-        if (gx < 1 || gx > n1f - 2) continue;
-        T acc = T(0);
-#pragma unroll
-        for (int i = 0; i <= K; ++i) acc = fma(c_tab<T>.P1[s * nl + i], v[i], acc);
-        dst[gx] += acc;
-      }
+      for (int i = 0; i <= K; ++i) acc = fma(w[i], src[i], acc);
+      xf[(int64_t)gy * pxf + gx] += acc;
     }
   }
   (void)pzc;
@@ -1733,7 +1722,7 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
   if constexpr (DIM == 3) {
     using C3 = Apply3Cfg;
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
     VPS_COUNT_LAUNCH();
     apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
                                                                    (int)g.pz, T(g.h));
@@ -1758,7 +1747,7 @@ cudaError_t apply_abs_launch(const LevelGeom& g, const double* x, double* y, cud
   if constexpr (DIM == 3) {
     using C3 = Apply3Cfg;
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    const unsigned tz = (unsigned)((span + (kApplyZC<double> * K) - 1) / (kApplyZC<double> * K));
     VPS_COUNT_LAUNCH();
     apply3_kernel<double, true><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(
         x, nullptr, y, g.n1, (int)g.px, (int)g.pz, g.h);
@@ -1782,7 +1771,7 @@ cudaError_t apply_df_launch(const LevelGeom& g, const float* xh, const float* xl
   if constexpr (DIM == 3) {
     using C3 = Apply3Cfg;
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + C3::ZR - 1) / C3::ZR);
+    const unsigned tz = (unsigned)((span + (kApplyZC<double> * K) - 1) / (kApplyZC<double> * K));
     VPS_COUNT_LAUNCH();
     apply3_df_kernel<0><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(xh, xl, y, g.n1,
                                                                           (int)g.px, (int)g.pz,
