@@ -112,6 +112,7 @@ struct vps_context {
   // the rounding level of the residual's own evaluation instead of rtol
   int last_restarts = 0, last_at_floor = 0;
   double* partial = nullptr;            // 2 * kDotBlocks
+  double* partial2 = nullptr;           // 2 * kDotBlocks (a second set for fused CG steps)
   double* dots = nullptr;               // scratch scalars for norms
   CgScalars* sc = nullptr;
   CgScalars* host_sc = nullptr;         // pinned
@@ -123,9 +124,14 @@ struct vps_context {
   double* l2_tab = nullptr;             // basis table for the L2 error
   size_t bytes = 0;
   std::vector<void*> allocs;
-  // captured preconditioner graph (input r = cr, output czn)
+  // captured V-cycle graphs (input r = cr; output czn, or xv[L] for the
+  // symmetric FP32 cycle of the CG)
   cudaGraphExec_t prec_graph = nullptr;
   cudaGraphExec_t prec_graph_ns = nullptr;  // the non-symmetric cycle (GMRES)
+  // CG iterations on the device: a while-node whose body is one iteration
+  cudaGraphExec_t cg_loop_graph = nullptr;
+  int64_t cg_loop_kernels = 0;          // kernels per loop iteration
+  bool cg_loop_off = false;             // the loop graph could not be built here
   int64_t graph_kernels_ns = 0;
   bool own_stream = false;              // stream created (and destroyed) by the library
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
@@ -202,7 +208,8 @@ int set_device(vps_context* h) {
 void drop_graphs(vps_context* h) {
   if (h->prec_graph) cudaGraphExecDestroy(h->prec_graph);
   if (h->prec_graph_ns) cudaGraphExecDestroy(h->prec_graph_ns);
-  h->prec_graph = h->prec_graph_ns = nullptr;
+  if (h->cg_loop_graph) cudaGraphExecDestroy(h->cg_loop_graph);
+  h->prec_graph = h->prec_graph_ns = h->cg_loop_graph = nullptr;
 }
 
 // Adds the kernels launched during an entry point to the handle's tally.
@@ -421,8 +428,10 @@ int vcycle_core(vps_context* h, const T* bL, T* xL, int top = 0, bool symmetric 
   return VPS_OK;
 }
 
-// czn = B cr: FP64 V-cycle, or cast -> FP32 V-cycle -> cast; symmetric
-// cycle for CG, the non-symmetric one of Algorithm 1 for GMRES.
+// z_new = B cr: FP64 V-cycle into czn, or cast -> FP32 V-cycle; the
+// symmetric cycle (CG) leaves its FP32 output in xv[L], which the CG
+// kernels read directly; the non-symmetric one of Algorithm 1 (GMRES)
+// converts it into czn.
 int precondition_direct(vps_context* h, bool symmetric) {
   const LevelGeom& g = h->geom[h->L];
   if (h->prec == VPS_FP64) return vcycle_core<double>(h, h->cr, h->czn, 0, symmetric);
@@ -430,7 +439,8 @@ int precondition_direct(vps_context* h, bool symmetric) {
   int rc = vcycle_core<float>(h, static_cast<const float*>(h->bv[h->L]),
                               static_cast<float*>(h->xv[h->L]), 0, symmetric);
   if (rc) return rc;
-  VPS_CK(h, launch_cast_f2d(static_cast<const float*>(h->xv[h->L]), h->czn, g.total, h->stream));
+  if (!symmetric)
+    VPS_CK(h, launch_cast_f2d(static_cast<const float*>(h->xv[h->L]), h->czn, g.total, h->stream));
   return VPS_OK;
 }
 
@@ -465,14 +475,38 @@ int precondition(vps_context* h, bool symmetric = true) {
 
 bool outer_df(const vps_context* h) { return h->outer == VPS_OUTER_DOUBLE_FLOAT; }
 
-// p = z (the preconditioned residual in czn), z kept for the Polak-Ribiere
-// beta, rz = r . z.
+// p = z_old = z_new (the preconditioned residual: xv[L] in FP32, czn in
+// FP64), rzn = r . z_new for the first alpha.
 int cg_start_direction(vps_context* h) {
   const int64_t n = h->geom[h->L].total;
-  VPS_CK(h, launch_cg_init_p(h->cp, h->czn, h->sc, n, h->stream, outer_df(h) ? h->cph : nullptr,
-                             h->cpl));
-  VPS_CK(h, cudaMemcpyAsync(h->cz, h->czn, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  VPS_CK(h, launch_dot1(h->cr, h->czn, n, h->partial, &h->sc->rz, h->stream));
+  float* ph = outer_df(h) ? h->cph : nullptr;
+  if (h->prec == VPS_FP32)
+    VPS_CK(h, launch_cg_start<float>(h->cp, h->cz, static_cast<const float*>(h->xv[h->L]), h->cr,
+                                     n, h->partial, h->sc, h->stream, ph, h->cpl));
+  else
+    VPS_CK(h, launch_cg_start<double>(h->cp, h->cz, h->czn, h->cr, n, h->partial, h->sc,
+                                      h->stream, ph, h->cpl));
+  return VPS_OK;
+}
+
+// beta, p = z_new + beta p, z_old = z_new (after precondition(h)).
+int cg_next_direction(vps_context* h) {
+  const int64_t n = h->geom[h->L].total;
+  float* ph = outer_df(h) ? h->cph : nullptr;
+  if (h->prec == VPS_FP32)
+    VPS_CK(h, launch_cg_next_p<float>(h->cp, h->cz, static_cast<const float*>(h->xv[h->L]), h->cr,
+                                      n, h->partial, h->sc, h->stream, ph, h->cpl));
+  else
+    VPS_CK(h, launch_cg_next_p<double>(h->cp, h->cz, h->czn, h->cr, n, h->partial, h->sc,
+                                       h->stream, ph, h->cpl));
+  return VPS_OK;
+}
+
+// alpha, x and r updates, r . r (after A p).
+int cg_step(vps_context* h) {
+  const int64_t n = h->geom[h->L].total;
+  VPS_CK(h, launch_cg_step_xr(h->cx, h->cr, h->cp, h->cAp, n, h->partial, h->partial2, h->sc,
+                              h->stream));
   return VPS_OK;
 }
 
@@ -520,6 +554,61 @@ int classify_check(vps_context* h, double rtol, double nb, double rel_true, doub
   return kCheckRestart;
 }
 
+// The device-side CG loop: a graph whose conditional while-node repeats one
+// iteration (V-cycle, direction, A p, x/r update, r.r and the stopping
+// test) without returning to the host; the host takes over to confirm
+// convergence on the FP64 residual.  Built on first use; if this driver
+// cannot build it, the host loop is used.
+int ensure_cg_loop(vps_context* h) {
+  if (h->cg_loop_graph || h->cg_loop_off) return VPS_OK;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->cg_loop_off = true;
+    return VPS_OK;
+  }
+  const int64_t before = launch_counter();
+  int rc = precondition_direct(h, true);
+  if (!rc) rc = cg_next_direction(h);
+  if (!rc) rc = cg_apply_p(h);
+  if (!rc) rc = cg_step(h);
+  if (!rc) {
+    cudaError_t ek = launch_cg_loop_check(cond, h->sc, h->stream);
+    if (ek != cudaSuccess) rc = fail(h, VPS_ECUDA, "loop check: %s", cudaGetErrorString(ek));
+  }
+  h->cg_loop_kernels = launch_counter() - before;
+  launch_counter() = before;  // captured, not launched
+  e = cudaStreamEndCapture(h->stream, &body);
+  if (rc == VPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->cg_loop_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    h->cg_loop_graph = nullptr;
+    cudaGetLastError();
+    h->cg_loop_off = true;
+  }
+  return VPS_OK;
+}
+
 // Preconditioned CG (Section 4.1's outer solver) with the flexible
 // (Polak-Ribiere) beta.  Convergence is always confirmed on the residual
 // r = b - A x evaluated in FP64: the recursive residual can drift from it
@@ -553,14 +642,18 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
   if (rc) return rc;
   if ((rc = cg_start_direction(h))) return rc;
   double rel = 1.0, prev_true = 0.0;
-  for (int it = 1; it <= max_it; ++it) {
-    if ((rc = cg_apply_p(h))) return rc;
-    VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
-    VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
-    VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
-    VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
-                              h->stream));
-    VPS_CK(h, cudaStreamSynchronize(h->stream));
+  int it = 0;
+  bool fresh = false;  // host_sc already holds the scalars of iteration it
+  while (true) {
+    if (!fresh) {
+      if ((rc = cg_apply_p(h))) return rc;
+      if ((rc = cg_step(h))) return rc;
+      ++it;
+      VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                h->stream));
+      VPS_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    fresh = false;
     if (h->host_sc->flag) {
       if (iters) *iters = it;
       return fail(h, VPS_EBREAKDOWN, "CG breakdown at iteration %d (p^T A p = %g)", it,
@@ -599,16 +692,28 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       ++h->last_restarts;
       restart = true;
     }
-    if (it == max_it) break;
+    if (it >= max_it) break;
+    if (!restart && h->use_graphs) {
+      if ((rc = ensure_cg_loop(h))) return rc;
+      if (h->cg_loop_graph) {  // the next iterations on the device
+        VPS_CK(h, launch_cg_loop_init(h->sc, it, max_it, nb, rtol, h->stream));
+        VPS_CK(h, cudaGraphLaunch(h->cg_loop_graph, h->stream));
+        VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                  h->stream));
+        VPS_CK(h, cudaStreamSynchronize(h->stream));
+        launch_counter() += (int64_t)(h->host_sc->it - it) * h->cg_loop_kernels;
+        it = h->host_sc->it;
+        fresh = true;
+        continue;
+      }
+    }
     rc = precondition(h);
     if (rc) return rc;
     if (restart) {
       VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
       if ((rc = cg_start_direction(h))) return rc;
-    } else {
-      VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
-      VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream,
-                                   outer_df(h) ? h->cph : nullptr, h->cpl));
+    } else if ((rc = cg_next_direction(h))) {
+      return rc;
     }
   }
   return fail(h, VPS_ENOCONV, "CG did not reach %g in %d iterations (%g)", rtol, max_it, rel);
@@ -955,17 +1060,14 @@ int upload_rhs_sines(vps_context* h, int level, int n_modes, const double* coef,
 int cg_async_iteration(vps_context* h, bool first) {
   const LevelGeom& g = h->geom[h->L];
   const int64_t n = g.total;
+  (void)n;
   if (first) {
     if (int rc = cg_start_direction(h)) return rc;
-  } else {
-    VPS_CK(h, launch_dot2(h->cr, h->czn, h->cr, h->cz, n, h->partial, &h->sc->rzn, h->stream));
-    VPS_CK(h, launch_cg_update_p(h->cp, h->cz, h->czn, h->sc, n, h->stream,
-                                 outer_df(h) ? h->cph : nullptr, h->cpl));
+  } else if (int rc = cg_next_direction(h)) {
+    return rc;
   }
   if (int rc = cg_apply_p(h)) return rc;
-  VPS_CK(h, launch_dot1(h->cp, h->cAp, n, h->partial, &h->sc->pAp, h->stream));
-  VPS_CK(h, launch_cg_update_xr(h->cx, h->cr, h->cp, h->cAp, h->sc, n, h->stream));
-  VPS_CK(h, launch_dot1(h->cr, h->cr, n, h->partial, &h->sc->rr, h->stream));
+  if (int rc = cg_step(h)) return rc;
   VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                             h->stream));
   VPS_CK(h, cudaMemcpyAsync(h->host_dots, h->dots, sizeof(double), cudaMemcpyDeviceToHost,
@@ -1378,6 +1480,7 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_b = (double*)p;
   if ((rc = dalloc(h, &p, cbytes))) return bail(rc); h->comp_x = (double*)p;
   if ((rc = dalloc(h, &p, 2 * kDotBlocks * sizeof(double)))) return bail(rc); h->partial = (double*)p;
+  if ((rc = dalloc(h, &p, 2 * kDotBlocks * sizeof(double)))) return bail(rc); h->partial2 = (double*)p;
   if ((rc = dalloc(h, &p, 8 * sizeof(double)))) return bail(rc); h->dots = (double*)p;
   if ((rc = dalloc(h, &p, sizeof(CgScalars)))) return bail(rc); h->sc = (CgScalars*)p;
   if ((rc = dalloc(h, &p, 256 * sizeof(double)))) return bail(rc); h->l2_tab = (double*)p;

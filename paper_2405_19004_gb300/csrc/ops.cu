@@ -72,15 +72,16 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
 }
 
 // partial[j * kDotBlocks + block] = sum over this block's fixed subset.
+template <typename TB>
 __global__ void __launch_bounds__(kThreads)
-dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b,
+dot_partial_kernel(const double* __restrict__ a, const TB* __restrict__ b,
                    const double* __restrict__ c, const double* __restrict__ e, int64_t n,
                    double* __restrict__ partial) {
   __shared__ double sh[2 * kThreads];
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)kDotBlocks * kThreads) {
-    v[0] = fma(a[i], b[i], v[0]);
+    v[0] = fma(a[i], (double)b[i], v[0]);
     if (c) v[1] = fma(c[i], e[i], v[1]);
   }
   block_sum<2>(v, sh);
@@ -149,38 +150,6 @@ __global__ void scale_kernel(double* __restrict__ y, const double* __restrict__ 
     y[e] = a * x[e];
 }
 
-__global__ void cg_alpha_kernel(CgScalars* sc) {
-  const double pAp = sc->pAp;
-  if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(sc->rz)) {
-    sc->flag = 1;
-    sc->alpha = 0.0;
-  } else {
-    sc->alpha = sc->rz / pAp;
-  }
-}
-
-__global__ void cg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
-                                    const double* __restrict__ p, const double* __restrict__ Ap,
-                                    const CgScalars* __restrict__ sc, int64_t n) {
-  const double alpha = sc->alpha;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    r[i] = fma(-alpha, Ap[i], r[i]);
-  }
-}
-
-__global__ void cg_beta_kernel(CgScalars* sc) {
-  const double rz = sc->rz;
-  if (!(rz != 0.0) || !isfinite(sc->rzn) || !isfinite(sc->rzo)) {
-    sc->flag = 1;
-    sc->beta = 0.0;
-  } else {
-    sc->beta = (sc->rzn - sc->rzo) / rz;
-  }
-  sc->rz = sc->rzn;
-}
-
 // p (and, when ph is given, its split into two floats: ph = fl(p),
 // pl = fl(p - ph), the input of the double-float operator)
 __device__ __forceinline__ void store_p(double* p, float* ph, float* pl, int64_t i, double v) {
@@ -192,23 +161,17 @@ __device__ __forceinline__ void store_p(double* p, float* ph, float* pl, int64_t
   }
 }
 
-__global__ void cg_update_p_kernel(double* __restrict__ p, double* __restrict__ z,
-                                   const double* __restrict__ zn, const CgScalars* __restrict__ sc,
-                                   float* __restrict__ ph, float* __restrict__ pl, int64_t n) {
-  const double beta = sc->beta;
+// p = z_old = z_new (the first direction, or after a restart)
+template <typename TZ>
+__global__ void cg_init_p_kernel(double* __restrict__ p, double* __restrict__ z,
+                                 const TZ* __restrict__ zn, float* __restrict__ ph,
+                                 float* __restrict__ pl, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = zn[i];
-    store_p(p, ph, pl, i, fma(beta, p[i], v));
-    z[i] = v;
+    const double zi = (double)zn[i];
+    store_p(p, ph, pl, i, zi);
+    z[i] = zi;
   }
-}
-
-__global__ void cg_init_p_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                 float* __restrict__ ph, float* __restrict__ pl, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    store_p(p, ph, pl, i, z[i]);
 }
 
 __global__ void split_df_kernel(const double* __restrict__ a, float* __restrict__ ph,
@@ -220,6 +183,95 @@ __global__ void split_df_kernel(const double* __restrict__ a, float* __restrict_
     ph[i] = hi;
     pl[i] = (float)(v - (double)hi);
   }
+}
+
+// The sum of the kDotBlocks partials of a dot product, in the fixed order
+// of dot_final_kernel (every block of a grid computes the same value).
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ partial,
+                                                double (&v)[NV], double* sh) {
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads)
+    for (int j = 0; j < NV; ++j) v[j] += partial[j * kDotBlocks + i];
+  block_sum<NV>(v, sh);
+  __syncthreads();  // sh is reused by the caller
+}
+
+// CG, after z_new = B r: beta = (r.z_new - r.z_old) / rz from the partials
+// of the two products, p = z_new + beta p (and its double-float split),
+// z_old = z_new; rzn (r.z_new) is kept for alpha.  z_new in FP32 (the
+// FP32 V-cycle's output, converted exactly) or FP64.
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads)
+cg_update_p_fused_kernel(double* __restrict__ p, double* __restrict__ z,
+                         const TZ* __restrict__ zn, const double* __restrict__ partial,
+                         CgScalars* __restrict__ sc, float* __restrict__ ph,
+                         float* __restrict__ pl, int64_t n) {
+  __shared__ double sh[2 * kThreads];
+  double v[2];
+  reduce_partials<2>(partial, v, sh);
+  const double rzn = v[0], rzo = v[1], rz = sc->rz;
+  const bool bad = !(rz != 0.0) || !isfinite(rzn) || !isfinite(rzo);
+  const double beta = bad ? 0.0 : (rzn - rzo) / rz;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rzn = rzn;
+    sc->rzo = rzo;
+    sc->beta = beta;
+    if (bad) sc->flag = 1;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)zn[i];
+    store_p(p, ph, pl, i, fma(beta, p[i], zi));
+    z[i] = zi;
+  }
+}
+
+// CG, after A p: alpha = rzn / p.Ap from the partials of p.Ap, x += alpha p,
+// r -= alpha A p, and the partials of r.r (same partition and order as
+// dot_partial_kernel: the grid is kDotBlocks blocks).  rz <- rzn for beta.
+__global__ void __launch_bounds__(kThreads)
+cg_update_xr_fused_kernel(double* __restrict__ x, double* __restrict__ r,
+                          const double* __restrict__ p, const double* __restrict__ Ap,
+                          const double* __restrict__ partial_pAp, CgScalars* __restrict__ sc,
+                          double* __restrict__ partial_rr, int64_t n) {
+  __shared__ double sh[kThreads];
+  double v[1];
+  reduce_partials<1>(partial_pAp, v, sh);
+  const double pAp = v[0], rz = sc->rzn;
+  const bool bad = !(pAp > 0.0) || !isfinite(pAp) || !isfinite(rz);
+  const double alpha = bad ? 0.0 : rz / pAp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->pAp = pAp;
+    sc->alpha = alpha;
+    sc->rz = rz;
+    if (bad) sc->flag = 1;
+  }
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)kDotBlocks * kThreads) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+  }
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) partial_rr[blockIdx.x] = acc[0];
+}
+
+__global__ void cg_loop_check_kernel(cudaGraphConditionalHandle cond, CgScalars* sc) {
+  const int it = sc->it + 1;
+  sc->it = it;
+  const double rr = sc->rr, lim = sc->rtol * sc->nb;
+  const bool more = !sc->flag && isfinite(rr) && rr > lim * lim && it < sc->max_it;
+  cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+__global__ void cg_loop_init_kernel(CgScalars* sc, int it, int max_it, double nb, double rtol) {
+  sc->it = it;
+  sc->max_it = max_it;
+  sc->nb = nb;
+  sc->rtol = rtol;
 }
 
 __global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -449,7 +501,7 @@ cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s) {
 cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
                         int64_t n, double* partial, double* out, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  dot_partial_kernel<<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
+  dot_partial_kernel<double><<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
   VPS_COUNT_LAUNCH();
   dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, c ? 2 : 1);
   return cudaGetLastError();
@@ -482,35 +534,69 @@ cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* par
   return launch_dot2(a, b, nullptr, nullptr, n, partial, out, s);
 }
 
-cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
-                                CgScalars* sc, int64_t n, cudaStream_t s) {
+template <typename TZ>
+cudaError_t launch_cg_start(double* p, double* z, const TZ* zn, const double* r, int64_t n,
+                            double* partial, CgScalars* sc, cudaStream_t s, float* ph,
+                            float* pl) {
   VPS_COUNT_LAUNCH();
-  cg_alpha_kernel<<<1, 1, 0, s>>>(sc);
+  cg_init_p_kernel<TZ><<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, ph, pl, n);
   VPS_COUNT_LAUNCH();
-  cg_update_xr_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(x, r, p, Ap, sc, n);
+  dot_partial_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(r, zn, nullptr, nullptr, n, partial);
+  VPS_COUNT_LAUNCH();
+  dot_final_kernel<<<1, kThreads, 0, s>>>(partial, &sc->rzn, 1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
-                               cudaStream_t s, float* ph, float* pl) {
+template <typename TZ>
+cudaError_t launch_cg_next_p(double* p, double* z, const TZ* zn, const double* r, int64_t n,
+                             double* partial, CgScalars* sc, cudaStream_t s, float* ph,
+                             float* pl) {
   VPS_COUNT_LAUNCH();
-  cg_beta_kernel<<<1, 1, 0, s>>>(sc);
+  dot_partial_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(r, zn, r, z, n, partial);
   VPS_COUNT_LAUNCH();
-  cg_update_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, sc, ph, pl, n);
+  cg_update_p_fused_kernel<TZ><<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, partial, sc, ph, pl,
+                                                                    n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s,
-                             float* ph, float* pl) {
-  (void)sc;
+cudaError_t launch_cg_step_xr(double* x, double* r, const double* p, const double* Ap, int64_t n,
+                              double* partial, double* partial2, CgScalars* sc, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  cg_init_p_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(p, z, ph, pl, n);
+  dot_partial_kernel<double><<<kDotBlocks, kThreads, 0, s>>>(p, Ap, nullptr, nullptr, n, partial);
+  VPS_COUNT_LAUNCH();
+  cg_update_xr_fused_kernel<<<kDotBlocks, kThreads, 0, s>>>(x, r, p, Ap, partial, sc, partial2, n);
+  VPS_COUNT_LAUNCH();
+  dot_final_kernel<<<1, kThreads, 0, s>>>(partial2, &sc->rr, 1);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_cg_start<float>(double*, double*, const float*, const double*, int64_t,
+                                            double*, CgScalars*, cudaStream_t, float*, float*);
+template cudaError_t launch_cg_start<double>(double*, double*, const double*, const double*,
+                                             int64_t, double*, CgScalars*, cudaStream_t, float*,
+                                             float*);
+template cudaError_t launch_cg_next_p<float>(double*, double*, const float*, const double*, int64_t,
+                                             double*, CgScalars*, cudaStream_t, float*, float*);
+template cudaError_t launch_cg_next_p<double>(double*, double*, const double*, const double*,
+                                              int64_t, double*, CgScalars*, cudaStream_t, float*,
+                                              float*);
 
 cudaError_t launch_split_df(const double* a, float* ph, float* pl, int64_t n, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
   split_df_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, ph, pl, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_loop_check(cudaGraphConditionalHandle cond, CgScalars* sc, cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  cg_loop_check_kernel<<<1, 1, 0, s>>>(cond, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_loop_init(CgScalars* sc, int it, int max_it, double nb, double rtol,
+                                cudaStream_t s) {
+  VPS_COUNT_LAUNCH();
+  cg_loop_init_kernel<<<1, 1, 0, s>>>(sc, it, max_it, nb, rtol);
   return cudaGetLastError();
 }
 

@@ -174,14 +174,33 @@ struct CgScalars {
   double rzo;     // r_{i+1} . z_i
   double beta;
   int flag;       // 1: breakdown detected on the device
+  // device-side iteration loop (a CUDA graph with a conditional node):
+  int it;         // iterations done
+  int max_it;
+  double nb;      // ||b||
+  double rtol;
 };
-cudaError_t launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap,
-                                CgScalars* sc, int64_t n, cudaStream_t s);
-// ph, pl (optional): also write p split into two floats for the double-float operator
-cudaError_t launch_cg_update_p(double* p, double* z, const double* zn, CgScalars* sc, int64_t n,
-                               cudaStream_t s, float* ph = nullptr, float* pl = nullptr);
-cudaError_t launch_cg_init_p(double* p, const double* z, CgScalars* sc, int64_t n, cudaStream_t s,
-                             float* ph = nullptr, float* pl = nullptr);
+// Ends the body of the device-side CG loop: ++it, and clears the loop's
+// condition once r.r has reached (rtol ||b||)^2, it == max_it, or the
+// breakdown flag is set.
+cudaError_t launch_cg_loop_check(cudaGraphConditionalHandle cond, CgScalars* sc, cudaStream_t s);
+cudaError_t launch_cg_loop_init(CgScalars* sc, int it, int max_it, double nb, double rtol,
+                                cudaStream_t s);
+// CG steps (deterministic reductions; partial, partial2: 2 * kDotBlocks doubles each):
+//  start : p = z_old = z_new (+ split into ph, pl when given), rzn = r . z_new
+//  next_p: beta = (r.z_new - r.z_old) / rz, p = z_new + beta p, z_old = z_new
+//  step_xr: alpha = rzn / p.Ap, x += alpha p, r -= alpha Ap, rr = r . r, rz = rzn
+// z_new in FP32 (the FP32 V-cycle's output) or FP64.
+template <typename TZ>
+cudaError_t launch_cg_start(double* p, double* z, const TZ* zn, const double* r, int64_t n,
+                            double* partial, CgScalars* sc, cudaStream_t s, float* ph = nullptr,
+                            float* pl = nullptr);
+template <typename TZ>
+cudaError_t launch_cg_next_p(double* p, double* z, const TZ* zn, const double* r, int64_t n,
+                             double* partial, CgScalars* sc, cudaStream_t s, float* ph = nullptr,
+                             float* pl = nullptr);
+cudaError_t launch_cg_step_xr(double* x, double* r, const double* p, const double* Ap, int64_t n,
+                              double* partial, double* partial2, CgScalars* sc, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
 // GMRES block operations: out[i] = V_i . w (i < nv; partial: nv * kDotBlocks
 // doubles), w += sign * sum_i c[i] V_i (c on the device), y = a x.
