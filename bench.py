@@ -85,6 +85,9 @@ def parse():
     p.add_argument("--smoother-variant", type=int, default=None,
                    help="pin the finest level's smoother variant after tuning (profiling runs; "
                         "default: the autotuner's choice)")
+    p.add_argument("--no-graphs", action="store_true",
+                   help="launch every kernel directly (no CUDA graphs, host-driven CG iterations): "
+                        "the same kernels, for profilers that do not follow graph conditional nodes")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--repeats", type=int, default=CPU_SAMPLE_REPEATS, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -261,10 +264,13 @@ def main():
     P.vps_autotune(args.tune_cache)  # timed trials on this GPU, before the timed region
     if args.smoother_variant is not None:
         P.vps_set_smooth_variant(L, args.smoother_variant)
+    if args.no_graphs:
+        P.vps_set_graphs(False)
     tuned = {"coarse_level": P.vps_get_coarse_level(),
              "smoother_variants": [P.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
              "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)],
-             "finest_variant_pinned": args.smoother_variant is not None}
+             "finest_variant_pinned": args.smoother_variant is not None,
+             "cuda_graphs": not args.no_graphs}
     N = P.n_interior()
     b = torch.as_tensor(uniform_vector(N, 1 + rank), device="cuda")
     x = torch.zeros_like(b)

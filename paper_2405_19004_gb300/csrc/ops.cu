@@ -554,8 +554,8 @@ cudaError_t launch_cg_next_p(double* p, double* z, const TZ* zn, const double* r
   VPS_COUNT_LAUNCH();
   dot_partial_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(r, zn, r, z, n, partial);
   VPS_COUNT_LAUNCH();
-  cg_update_p_fused_kernel<TZ><<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, partial, sc, ph, pl,
-                                                                    n);
+  // kDotBlocks blocks: every block reduces the partials once
+  cg_update_p_fused_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(p, z, zn, partial, sc, ph, pl, n);
   return cudaGetLastError();
 }
 

@@ -181,3 +181,24 @@ def test_server_requests_with_unattainable_rtol_complete():
     srv.close()
     for q in info:
         assert q["state"] == vps.VPS_REQ_DONE, q
+
+
+@pytest.mark.parametrize("prec", [vps.VPS_FP32, vps.VPS_FP64], ids=["h32", "h64"])
+@pytest.mark.parametrize("rtol", [1e-10, 1e-13])
+def test_device_loop_equals_host_loop(prec, rtol):
+    """With graphs the CG iterations after the first run on the device (a
+    conditional while-node); without, every iteration returns to the host.
+    Same kernels in the same order: bit-identical solutions and counts (also
+    through the restarts an unattainable rtol forces)."""
+    import torch
+    d, k, L = 2, 2, 6
+    out = []
+    for graphs in (True, False):
+        P = vps.Poisson(d, k, L, precision=prec)
+        P.vps_set_graphs(graphs)
+        b = torch.as_tensor(uniform_vector(P.n_interior(), 66), device="cuda")
+        x = torch.zeros_like(b)
+        it, rel = P.vps_solve(b, x, rtol, 200)
+        out.append((it, rel, P.vps_get_solve_info(), x.cpu()))
+    assert out[0][:3] == out[1][:3]
+    assert torch.equal(out[0][3], out[1][3])
