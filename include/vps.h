@@ -144,15 +144,14 @@ int vps_vcycle(vps_handle h, const void* b, void* x);
  * vps_solve -- CG on the finest level, preconditioned by one V-cycle per
  * iteration, x0 = 0 (beta in the flexible Polak-Ribiere form).  When the
  * recursive residual reaches rtol ||b||_2, the residual r = b - A x is
- * evaluated in FP64 and the solve ends if
- *   ||r||_2 <= rtol ||b||_2, or
- *   ||r||_2 <= gamma || |A| |x| ||_2,  gamma = (6k+6) 2^-53,
- * the second being the rounding bound of the FP64 evaluation of r itself
- * (reached first when rtol is below what FP64 can resolve: the terms of
- * A x cancel by about k^2 h^-2 for smooth solutions, so e.g. 2D meshes of
- * 2^10 cells per direction cannot show 1e-10); |A| is the operator with the
- * absolute values of its 1D band coefficients.  Otherwise CG restarts from
- * r; a restart that does not halve ||r|| ends with VPS_ENOCONV.
+ * evaluated in FP64; the solve ends if ||r||_2 <= rtol ||b||_2, else CG
+ * restarts from r.  Once a restart fails to halve ||r||, the solve ends:
+ * with VPS_OK if ||r||_2 <= gamma || |A| |x| ||_2, gamma = (6k+6) 2^-53,
+ * the rounding bound of the FP64 evaluation of r itself (rtol below what
+ * FP64 can resolve: the terms of A x cancel by about k^2 h^-2 for smooth
+ * solutions, so e.g. 2D meshes of 2^10 cells per direction cannot show
+ * 1e-10; |A| is the operator with the absolute values of its 1D band
+ * coefficients), with VPS_ENOCONV otherwise.
  * b, x: compact DOUBLE device vectors.  iters / rel_res (host pointers, may
  * be NULL) receive the iteration count and the final FP64 relative
  * residual ||r||/||b||.  Synchronises the stream once per iteration to read

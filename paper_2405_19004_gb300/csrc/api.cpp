@@ -542,16 +542,25 @@ double residual_gamma(const vps_context* h) { return (6.0 * h->k + 6.0) * std::l
 // Outcome of a convergence check on the FP64 residual.
 enum { kCheckConverged = 1, kCheckRestart = 0, kCheckStagnated = -1 };
 
-// rel_true = ||b - A x|| / ||b||; scale_norm = || |A||x| || (< 0: not known yet).
+// A restart from the FP64 residual that did not halve it: the residual has
+// stopped falling, and the rounding bound decides (needs_scale).
+bool stagnating(double rel_true, double prev_true) {
+  return prev_true > 0.0 && !(rel_true < 0.5 * prev_true);
+}
+
+// rel_true = ||b - A x|| / ||b||; scale_norm = || |A||x| || (needed only when
+// stagnating).  Above rtol the solve first restarts from the FP64 residual;
+// the rounding bound (a worst-case bound, so it is only trusted once the
+// residual has stopped falling) then ends it with VPS_OK or VPS_ENOCONV.
 int classify_check(vps_context* h, double rtol, double nb, double rel_true, double scale_norm,
                    double prev_true) {
   if (rel_true <= rtol) return kCheckConverged;
+  if (!stagnating(rel_true, prev_true)) return kCheckRestart;
   if (scale_norm >= 0.0 && rel_true * nb <= residual_gamma(h) * scale_norm) {
     h->last_at_floor = 1;
     return kCheckConverged;
   }
-  if (prev_true > 0.0 && !(rel_true < 0.5 * prev_true)) return kCheckStagnated;
-  return kCheckRestart;
+  return kCheckStagnated;
 }
 
 // The device-side CG loop: a graph whose conditional while-node repeats one
@@ -675,7 +684,7 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       if (!std::isfinite(rel))
         return fail(h, VPS_EBREAKDOWN, "CG residual not finite at iteration %d", it);
       double unorm = -1.0;
-      if (rel > rtol) {  // below the rounding level of its evaluation?
+      if (rel > rtol && stagnating(rel, prev_true)) {  // at the rounding level of its evaluation?
         if ((rc = cg_residual_scale(h))) return rc;
         VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                   h->stream));
@@ -861,11 +870,14 @@ int gmres_solve(vps_context* h, int m, double rtol, int max_it, int* iters, doub
     if (!std::isfinite(rel_true)) return fail(h, VPS_EBREAKDOWN, "GMRES residual not finite");
     if (rel_true <= rtol) return VPS_OK;
     if (est <= rtol) {  // the least-squares residual had converged: drift or rounding
-      if (int rc = cg_residual_scale(h)) return rc;
-      VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
-                                h->stream));
-      VPS_CK(h, cudaStreamSynchronize(h->stream));
-      const double unorm = std::sqrt(h->host_sc->pAp);
+      double unorm = -1.0;
+      if (stagnating(rel_true, prev_true)) {
+        if (int rc = cg_residual_scale(h)) return rc;
+        VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                  h->stream));
+        VPS_CK(h, cudaStreamSynchronize(h->stream));
+        unorm = std::sqrt(h->host_sc->pAp);
+      }
       const int cls = classify_check(h, rtol, nb, rel_true, unorm, prev_true);
       if (cls == kCheckConverged) return VPS_OK;
       if (cls == kCheckStagnated)
@@ -1183,7 +1195,8 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
   if (!std::isfinite(h->as_rel)) return cg_async_finish(h, VPS_EBREAKDOWN);
   // the convergence check of cg_solve, one asynchronous step at a time
   bool restart = false;
-  if (h->as_verify == 1 && h->as_rel > h->as_rtol) {  // FP64 residual above rtol: scale
+  if (h->as_verify == 1 && h->as_rel > h->as_rtol &&
+      stagnating(h->as_rel, h->as_prev_true)) {  // FP64 residual stopped falling: scale
     if (int rc = cg_residual_scale(h)) return rc;
     VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                               h->stream));
