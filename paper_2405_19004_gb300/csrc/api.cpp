@@ -1598,10 +1598,8 @@ int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* 
   if (colour < 0 || colour >= (1 << h->dim)) return fail(h, VPS_EINVAL, "colour out of range");
   if (int rc = set_device(h)) return rc;
   LaunchTally tally(h);
-  const LevelGeom& g = h->geom[level];
   const int v = h->smooth_var[level];
   if (!variant_ok(h, v)) return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
-  (void)g;
   if (h->prec == VPS_FP64) return colour_pass<double>(h, level, colour, (const double*)b, (double*)x);
   return colour_pass<float>(h, level, colour, (const float*)b, (float*)x);
 }

@@ -1876,8 +1876,7 @@ void register_fns(KernelFns<T>* f) {
   register_variant<T, kVarQ[0]>(f, 0);
   register_variant<T, kVarQ[1]>(f, 1);
   register_variant<T, kVarQ[2]>(f, 2);
-  // default: the middle variant, or the smallest one where it does not fit
-  f->smooth_mult = f->smooth_mult_v[1] ? f->smooth_mult_v[1] : f->smooth_mult_v[0];
+  // default additive variant: the middle one, or the smallest where it does not fit
   f->smooth_add = f->smooth_add_v[1] ? f->smooth_add_v[1] : f->smooth_add_v[0];
   f->apply = apply_launch<T>;
   f->prolong_add = prolong_launch<T>;

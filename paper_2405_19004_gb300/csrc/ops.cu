@@ -51,13 +51,6 @@ __global__ void unpack_kernel(const T* __restrict__ lev, T* __restrict__ comp, i
   }
 }
 
-template <typename T>
-__global__ void zero_kernel(T* __restrict__ p, int64_t n) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    p[e] = T(0);
-}
-
 // Fixed-order block reduction of NV values per thread.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
@@ -491,13 +484,6 @@ cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStre
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s) {
-  VPS_COUNT_LAUNCH();
-  zero_kernel<T><<<grid_for(n, 4), kThreads, 0, s>>>(p, n);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
                         int64_t n, double* partial, double* out, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
@@ -642,8 +628,6 @@ template cudaError_t launch_pack<float>(const LevelGeom&, const float*, float*, 
 template cudaError_t launch_pack<double>(const LevelGeom&, const double*, double*, cudaStream_t);
 template cudaError_t launch_unpack<float>(const LevelGeom&, const float*, float*, cudaStream_t);
 template cudaError_t launch_unpack<double>(const LevelGeom&, const double*, double*, cudaStream_t);
-template cudaError_t launch_zero<float>(float*, int64_t, cudaStream_t);
-template cudaError_t launch_zero<double>(double*, int64_t, cudaStream_t);
 template cudaError_t launch_axpy_inplace<float>(float*, const float*, float, int64_t, cudaStream_t);
 template cudaError_t launch_axpy_inplace<double>(double*, const double*, double, int64_t,
                                                  cudaStream_t);

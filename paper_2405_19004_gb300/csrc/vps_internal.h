@@ -105,10 +105,9 @@ struct KernelFns {
   using SmoothAddFn = cudaError_t (*)(const LevelGeom&, const ColourGeom&, const T* r, T* x,
                                       const T* inv_lam, T scale, cudaStream_t);
   // one multiplicative colour pass: x += R^T A_j^-1 (R b - Abar Rbar x)
-  SmoothMultFn smooth_mult = nullptr;            // the default variant
   SmoothMultFn smooth_mult_v[kSmoothVariants] = {};
   // one additive colour pass from a precomputed residual: x += scale R^T A_ref^-1 R r
-  SmoothAddFn smooth_add = nullptr;
+  SmoothAddFn smooth_add = nullptr;              // default variant (allocation-free entry point)
   SmoothAddFn smooth_add_v[kSmoothVariants] = {};
   int variant_p[kSmoothVariants] = {};           // patches per block of each variant
   // ablation kernels of Section 3.1: the local residual of every patch of a
@@ -152,8 +151,6 @@ template <typename T>
 cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s);
 template <typename T>
 cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStream_t s);
-template <typename T>
-cudaError_t launch_zero(T* p, int64_t n, cudaStream_t s);
 
 // Deterministic dot products over a whole level buffer: partial sums per
 // block into `partial` (kDotBlocks doubles per product), then one block
