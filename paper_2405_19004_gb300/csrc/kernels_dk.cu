@@ -1100,11 +1100,13 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
 // costs two barriers.  Halo recomputation: ((T+2K)/T)^2 in the z stage and
 // (T+2K)/T in the y stage, against ((T+2K)/T)^2 and (T+2K)/T with T = K*CT
 // small for cubic tiles.
-// Cells per block in z of the 3D operator (planes per block: kApplyZC * K);
-// the same for every precision (fewer planes per block, i.e. more blocks,
-// measured slower for FP32 at k = 4).
+// Cells per block in z of the 3D operator (planes per block: kApplyZC * K).
+// For k >= 4 the FP64 and double-float operators (8-byte type) take one
+// cell of planes per block: twice the blocks spread more evenly over the
+// 152 SMs (4 % faster at 2^5 and 2^6 cells); the FP32 operator was measured
+// slower that way and keeps two.
 template <typename T>
-constexpr int kApplyZC = K >= 4 ? 2 : (K == 1 ? 8 : 4);
+constexpr int kApplyZC = K >= 4 ? (sizeof(T) == 8 ? 1 : 2) : (K == 1 ? 8 : 4);
 
 struct Apply3Cfg {
   // cells per tile in x and y: a power of two, so that tiles of TX nodes
