@@ -261,7 +261,8 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
  *            update for the exact local solver without reading x_I
  *            (VPS_MULTIPLICATIVE handles only);
  *   6, 7, 8: the Boundary kernel in blocks of one warp (1, 2, 4 patches
- *            per thread), each stage in several rounds of 32 lines.
+ *            per thread), each stage in several rounds of 32 lines
+ *            (degrees 1..3 only).
  * A variant whose shared memory exceeds the GPU's limit for the handle's
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);

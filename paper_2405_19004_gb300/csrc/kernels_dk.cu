@@ -105,6 +105,10 @@ constexpr int kVarQ[kQVariants] = {1, 2, 4};
 // registers (two stages and two barriers fewer); above k = 5 the extra live
 // values cost more resident blocks than the barriers save.
 constexpr bool kFuseFD = K <= 5;
+// Blocks of one warp (variants 6-8) only for k <= 3: measured faster at
+// k = 1 and never faster from k = 4 on, where their many unrolled rounds of
+// 32 lines dominated the compile time.
+constexpr bool kOneWarpVariants = K <= 3;
 
 template <class T, int Q>
 struct alignas(sizeof(T) * Q) Pack {
@@ -1828,9 +1832,11 @@ cudaError_t smooth_limits() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_bnd);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
-    if (e != cudaSuccess) return e;
+    if constexpr (kOneWarpVariants) {
+      e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+      if (e != cudaSuccess) return e;
+    }
   }
   if constexpr (!C::fits) {
     return cudaSuccess;
@@ -1857,7 +1863,10 @@ void register_variant(KernelFns<T>* f, int v) {
   f->smooth_add_v[v + 2 * kQVariants] = nullptr;
   if constexpr (C::fits_bnd) {
     f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true, 0>;
-    f->smooth_mult_v[v + 2 * kQVariants] = smooth_mult_launch<T, PP, true, 1>;
+    if constexpr (kOneWarpVariants)
+      f->smooth_mult_v[v + 2 * kQVariants] = smooth_mult_launch<T, PP, true, 1>;
+    else
+      f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
   } else {
     f->smooth_mult_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
