@@ -106,17 +106,21 @@ int vps_unpack(vps_handle h, int level, const void* level_vec, void* compact);
 /*
  * vps_smooth -- n_steps smoothing steps S_l(x, b) on `level` (level layout,
  * working precision), in place on x.  Multiplicative: one step visits the
- * 2^d colours in increasing order; every colour is one fused kernel that
- * gathers each patch's closure, forms the local residual
- * r_j = R_j b - Abar_j Rbar_j x (Section 2.2) and adds A_j^{-1} r_j by fast
- * diagonalisation (Eq. 2.13/2.14).  Additive: x += damping *
+ * 2^d colours in increasing order; with the default kernel structure every
+ * colour is one kernel that gathers each patch's closure, forms the local
+ * residual r_j = R_j b - Abar_j Rbar_j x (Section 2.2) and adds
+ * A_j^{-1} r_j by fast diagonalisation (Eq. 2.13/2.14) -- the fused kernel,
+ * or (default variant) the Boundary kernel of Section 3.2, the same update
+ * without reading the interior of x (vps_set_smooth_variant,
+ * vps_set_smoother_kernel).  Additive: x += damping *
  * sum_j R_j^T A_j^{-1} R_j (b - A x).  Requires level >= 2 (level 1 holds a
  * single patch: use vps_vcycle).  b and x must not alias.
  */
 int vps_smooth(vps_handle h, int level, const void* b, void* x, int n_steps);
 
 /* vps_smooth_colour -- one multiplicative colour pass (0 <= colour < 2^d) on
- * `level` (>= 1), in place on x.  Used to test single launches. */
+ * `level` (>= 1), in place on x, with the handle's variant and kernel
+ * structure.  Used to test and time single launches. */
 int vps_smooth_colour(vps_handle h, int level, int colour, const void* b, void* x);
 
 /* vps_apply -- y = A_level x (Eq. 2.3, matrix-free), working precision,
