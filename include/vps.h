@@ -417,6 +417,30 @@ const char* vps_last_error(vps_handle h);
 /* vps_status_string -- name of a status code. */
 const char* vps_status_string(int status);
 
+/*
+ * vps_check_fp_conversions -- diagnostic of the library's own conversions
+ * between float and double, which the vector kernels of the mixed-precision
+ * CG use instead of the hardware conversions (those are FP64 instructions,
+ * which issue at about 1/64 of the FP32 rate on this GPU).  For each of the
+ * n 64-bit patterns in the DEVICE array `patterns` (caller-owned, read only;
+ * may be NULL when n is 0):
+ *   mismatches[0] counts patterns whose low 32 bits, as a float, convert to
+ *     a double that differs from the cast (float -> double, exact);
+ *   mismatches[1] counts patterns that, as a double, round to a float that
+ *     differs from the cast (round to nearest, ties to even; NaNs compare
+ *     equal);
+ *   mismatches[2] counts patterns whose double-float split hi + lo breaks
+ *     its contract: hi = the value truncated to 24 bits, lo = the next bits
+ *     truncated, both of the value's sign, remainder below 2^-47 of the
+ *     value, for binary64 exponents in [-73, 127]; zeros give signed zeros;
+ *     outside that range hi = fl(v), lo = fl(v - hi).
+ * Runs on cuda_stream and synchronises it; allocates 24 bytes from the
+ * stream-ordered pool.  Errors: VPS_EINVAL, VPS_ECUDA (message via
+ * vps_last_error(NULL)).
+ */
+int vps_check_fp_conversions(const void* patterns, int64_t n, int64_t* mismatches,
+                             void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

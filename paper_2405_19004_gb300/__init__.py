@@ -79,6 +79,7 @@ SIGNATURES = {
     "vps_server_destroy": (_i, [_p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
+    "vps_check_fp_conversions": (_i, [_p, ctypes.c_int64, _i64p, _p]),
 }
 
 _lib = None
@@ -133,6 +134,17 @@ def vps_smooth_additive_static(dim, degree, level, precision, damping, b, x, str
     rc = lib().vps_smooth_additive_static(dim, degree, level, precision, float(damping), _ptr(b),
                                           _ptr(x), ctypes.c_void_p(stream.cuda_stream))
     return _check(rc, None)
+
+
+def vps_check_fp_conversions(patterns, stream):
+    """Mismatch counts (f2d, d2f_rn, split) of the library's float/double
+    conversions against the hardware ones on a CUDA int64 tensor of bit
+    patterns (see vps.h)."""
+    out = (ctypes.c_int64 * 3)()
+    rc = lib().vps_check_fp_conversions(_ptr(patterns), patterns.numel(), out,
+                                        ctypes.c_void_p(stream.cuda_stream))
+    _check(rc, None)
+    return list(out)
 
 
 class Poisson:

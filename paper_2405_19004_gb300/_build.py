@@ -32,7 +32,8 @@ def _nvcc():
 
 
 def _units():
-    headers = [os.path.join(CSRC, "vps_internal.h"), os.path.join(INCLUDE, "vps.h")]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(INCLUDE, "vps.h"))
     units = []
     for d in (2, 3):
         for k in range(1, 8):

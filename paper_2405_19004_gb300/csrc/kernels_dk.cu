@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "fp_bits.cuh"
 #include "vps_internal.h"
 
 #ifndef VPS_DIM
@@ -85,6 +86,15 @@ template <typename T, bool ABS>
 __device__ __forceinline__ T coefM(int i) {
   if constexpr (ABS) return (T)c_abs.Mb[i];
   else return c_tab<T>.Mb[i];
+}
+
+// Programmatic dependent launch (launch_pdl): let the next kernel of the
+// stream be scheduled as this one's blocks start, and wait until every
+// earlier kernel has completed and its writes are visible.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------- config
@@ -451,9 +461,12 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
   T* xI = BND ? nullptr : bI + P * MD;
   T* il = bI + (BND ? 1 : 2) * P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
+  // the origins and the eigenvalue table (written at setup) do not depend
+  // on the previous kernel: read them before waiting for it to complete
   load_origins<P, NT>(s_org, cg, px, pz);
   if constexpr (!RES)
     for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
+  grid_dependency_wait();
   __syncthreads();
   prefetch_b<T, G, Q, NT>(b, bI, s_org, px, pz);
 
@@ -1260,7 +1273,7 @@ __device__ __forceinline__ DF df_norm(const DF& s) {
 template <int DUMMY>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
 apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
-                 double* __restrict__ y, int n1, int px, int pz, double scale) {
+                 double* __restrict__ y, int n1, int px, int pz, float scale) {
   using C = Apply3Cfg;
   constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1338,8 +1351,10 @@ apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
             VPS_DF_MADD(acc, Kb, qx, j, vm[qx + j]);
             VPS_DF_MADD(acc, Mb, qx, j, vw[qx + j]);
           }
+          // scale = h, a power of two: exact on both words; the words are
+          // widened by integer operations and added with one FP64 addition
           double out = 0.0;
-          if (inner_yz && gx >= 1 && gx <= n1 - 2) out = scale * ((double)acc.hi + (double)acc.lo);
+          if (inner_yz && gx >= 1 && gx <= n1 - 2) out = f2d(acc.hi * scale) + f2d(acc.lo * scale);
           y[rowi + gx] = out;
         }
       }
@@ -1402,7 +1417,7 @@ apply2_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl, dou
         VPS_DF_MADD(acc, Mb, q, j, vk[q + j]);
       }
       double out = 0.0;
-      if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2) out = (double)acc.hi + (double)acc.lo;
+      if (gx >= 1 && gx <= n1 - 2 && gy >= 1 && gy <= n1 - 2) out = f2d(acc.hi) + f2d(acc.lo);
       y[gy * px + gx] = out;
     }
   }
@@ -1674,9 +1689,9 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_mult_kernel<T, PP, BND, W><<<(unsigned)grid, C::NT, BND ? C::smem_bnd : C::smem_mult,
-                                      s>>>(b, x, inv_lam, (int)g.px, (int)g.pz, cg, bscale);
-  return cudaGetLastError();
+  return launch_pdl(smooth_mult_kernel<T, PP, BND, W, false>, dim3((unsigned)grid), dim3(C::NT),
+                    BND ? C::smem_bnd : C::smem_mult, s, b, x, inv_lam, (int)g.px, (int)g.pz,
+                    cg, bscale, static_cast<T*>(nullptr));
 }
 
 template <typename T, int PP>
@@ -1779,9 +1794,10 @@ cudaError_t apply_df_launch(const LevelGeom& g, const float* xh, const float* xl
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
     const unsigned tz = (unsigned)((span + (kApplyZC<double> * K) - 1) / (kApplyZC<double> * K));
     VPS_COUNT_LAUNCH();
+    // g.h = 1 / 2^level: exact as a float
     apply3_df_kernel<0><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(xh, xl, y, g.n1,
                                                                           (int)g.px, (int)g.pz,
-                                                                          g.h);
+                                                                          (float)g.h);
   } else {
     using C = ApplyCfg;
     const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);

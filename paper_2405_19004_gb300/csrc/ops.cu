@@ -6,7 +6,10 @@
 // a fixed grid and fixed trees, so a result does not depend on scheduling:
 // the same inputs give bit-identical scalars on every run.
 #include <cmath>
+#include <cstdio>
 
+#include "fp_bits.cuh"
+#include "vps.h"
 #include "vps_internal.h"
 
 namespace vps {
@@ -14,6 +17,18 @@ namespace vps {
 namespace {
 
 constexpr int kThreads = 256;
+
+// Chunked grid-stride loop of the bandwidth-bound vector kernels: thread t
+// of block B takes the chunks that start at i0 = (B + j gridDim) kU kThreads
+// + t (j = 0, 1, ..), elements i0 + u kThreads (u < kU; coalesced for every
+// u).  A kernel loads all kU elements of a chunk before it uses any, so each
+// thread keeps kU loads in flight: with one element per thread and
+// iteration, the resident threads hold too few bytes in flight to cover the
+// DRAM latency and the kernels run at a fraction of the bandwidth.
+constexpr int kU = 4;
+#define VPS_CHUNKS(i0, n)                                                         \
+  for (int64_t i0 = blockIdx.x * (int64_t)(kU * kThreads) + threadIdx.x; i0 < (n); \
+       i0 += (int64_t)gridDim.x * (kU * kThreads))
 
 inline unsigned grid_for(int64_t n, int per_thread = 1) {
   int64_t g = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
@@ -51,36 +66,72 @@ __global__ void unpack_kernel(const T* __restrict__ lev, T* __restrict__ comp, i
   }
 }
 
-// Fixed-order block reduction of NV values per thread.
+// Fixed-order block reduction of NV values per thread; every thread gets
+// the sums.  Butterflies of shuffles within each warp, then over the warp
+// sums in warp 0 (the partners of a butterfly add the same two values, so
+// all lanes hold identical bits).  sh: at least NV * 33 doubles.  The
+// additions are FP64 instructions, the slow pipe of this GPU: a tree over
+// shared memory costs every warp one addition per level, the butterflies
+// five per warp plus three.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
-  for (int j = 0; j < NV; ++j) sh[j * kThreads + threadIdx.x] = v[j];
-  __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int j = 0; j < NV; ++j) sh[j * kThreads + threadIdx.x] += sh[j * kThreads + threadIdx.x + s];
-    __syncthreads();
+  constexpr int kWarps = kThreads / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    if (lane == 0) sh[j * 32 + w] = v[j];
   }
-  for (int j = 0; j < NV; ++j) v[j] = sh[j * kThreads];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < kWarps ? sh[j * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = kWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) sh[NV * 32 + j] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = sh[NV * 32 + j];
 }
 
-// partial[j * kDotBlocks + block] = sum over this block's fixed subset.
-template <typename TB>
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return f2d(v); }
+
+// partial[j * kDotBlocks + block] = sum over this block's fixed subset of
+// the products a.b (j = 0) and, with NP = 2, a.e (j = 1; partial[1..] is
+// 0 for NP = 1).  b and e in FP32 (converted exactly) or FP64.
+template <typename TB, int NP>
 __global__ void __launch_bounds__(kThreads)
 dot_partial_kernel(const double* __restrict__ a, const TB* __restrict__ b,
-                   const double* __restrict__ c, const double* __restrict__ e, int64_t n,
-                   double* __restrict__ partial) {
-  __shared__ double sh[2 * kThreads];
-  double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)kDotBlocks * kThreads) {
-    v[0] = fma(a[i], (double)b[i], v[0]);
-    if (c) v[1] = fma(c[i], e[i], v[1]);
+                   const TB* __restrict__ e, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[2 * 33];
+  double v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) v[j] = 0.0;
+  VPS_CHUNKS(i0, n) {
+    double av[kU], bv[kU], ev[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      const bool in = i < n;
+      av[u] = in ? a[i] : 0.0;
+      bv[u] = in ? to_d(b[i]) : 0.0;
+      if constexpr (NP == 2) ev[u] = in ? to_d(e[i]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      v[0] = fma(av[u], bv[u], v[0]);
+      if constexpr (NP == 2) v[NP - 1] = fma(av[u], ev[u], v[NP - 1]);
+    }
   }
-  block_sum<2>(v, sh);
+  block_sum<NP>(v, sh);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = v[0];
-    partial[kDotBlocks + blockIdx.x] = v[1];
+    partial[kDotBlocks + blockIdx.x] = NP == 2 ? v[NP - 1] : 0.0;
   }
 }
 
@@ -108,9 +159,17 @@ multi_dot_partial_kernel(const double* __restrict__ V, int64_t ld, const double*
   __shared__ double sh[kThreads];
   const double* v = V + blockIdx.y * ld;
   double acc[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)kDotBlocks * kThreads)
-    acc[0] = fma(v[i], w[i], acc[0]);
+  VPS_CHUNKS(i0, n) {
+    double vv[kU], wv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      vv[u] = i < n ? v[i] : 0.0;
+      wv[u] = i < n ? w[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc[0] = fma(vv[u], wv[u], acc[0]);
+  }
   block_sum<1>(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.y * kDotBlocks + blockIdx.x] = acc[0];
 }
@@ -143,38 +202,61 @@ __global__ void scale_kernel(double* __restrict__ y, const double* __restrict__ 
     y[e] = a * x[e];
 }
 
-// p (and, when ph is given, its split into two floats: ph = fl(p),
-// pl = fl(p - ph), the input of the double-float operator)
+// p (and, when ph is given, its split into two floats ph + pl, the input
+// of the double-float operator: split_f2, p - ph - pl below 2^-47 |p|)
 __device__ __forceinline__ void store_p(double* p, float* ph, float* pl, int64_t i, double v) {
   p[i] = v;
   if (ph) {
-    const float hi = (float)v;
+    float hi, lo;
+    split_f2(v, hi, lo);
     ph[i] = hi;
-    pl[i] = (float)(v - (double)hi);
+    pl[i] = lo;
   }
 }
 
-// p = z_old = z_new (the first direction, or after a restart)
+// p = z_new, z_old = z_new (the first direction, or after a restart); z_old
+// is kept in the type of z_new (exact).
 template <typename TZ>
-__global__ void cg_init_p_kernel(double* __restrict__ p, double* __restrict__ z,
+__global__ void cg_init_p_kernel(double* __restrict__ p, TZ* __restrict__ z,
                                  const TZ* __restrict__ zn, float* __restrict__ ph,
                                  float* __restrict__ pl, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = (double)zn[i];
-    store_p(p, ph, pl, i, zi);
-    z[i] = zi;
+  VPS_CHUNKS(i0, n) {
+    TZ zi[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      zi[u] = i < n ? zn[i] : TZ(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < n) {
+        store_p(p, ph, pl, i, to_d(zi[u]));
+        z[i] = zi[u];
+      }
+    }
   }
 }
 
 __global__ void split_df_kernel(const double* __restrict__ a, float* __restrict__ ph,
                                 float* __restrict__ pl, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = a[i];
-    const float hi = (float)v;
-    ph[i] = hi;
-    pl[i] = (float)(v - (double)hi);
+  VPS_CHUNKS(i0, n) {
+    double v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      v[u] = i < n ? a[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < n) {
+        float hi, lo;
+        split_f2(v[u], hi, lo);
+        ph[i] = hi;
+        pl[i] = lo;
+      }
+    }
   }
 }
 
@@ -192,15 +274,15 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ parti
 
 // CG, after z_new = B r: beta = (r.z_new - r.z_old) / rz from the partials
 // of the two products, p = z_new + beta p (and its double-float split),
-// z_old = z_new; rzn (r.z_new) is kept for alpha.  z_new in FP32 (the
-// FP32 V-cycle's output, converted exactly) or FP64.
+// z_old = z_new; rzn (r.z_new) is kept for alpha.  z_new and z_old in FP32
+// (the FP32 V-cycle's output, converted exactly) or FP64.
 template <typename TZ>
 __global__ void __launch_bounds__(kThreads)
-cg_update_p_fused_kernel(double* __restrict__ p, double* __restrict__ z,
+cg_update_p_fused_kernel(double* __restrict__ p, TZ* __restrict__ z,
                          const TZ* __restrict__ zn, const double* __restrict__ partial,
                          CgScalars* __restrict__ sc, float* __restrict__ ph,
                          float* __restrict__ pl, int64_t n) {
-  __shared__ double sh[2 * kThreads];
+  __shared__ double sh[2 * 33];
   double v[2];
   reduce_partials<2>(partial, v, sh);
   const double rzn = v[0], rzo = v[1], rz = sc->rz;
@@ -212,23 +294,35 @@ cg_update_p_fused_kernel(double* __restrict__ p, double* __restrict__ z,
     sc->beta = beta;
     if (bad) sc->flag = 1;
   }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = (double)zn[i];
-    store_p(p, ph, pl, i, fma(beta, p[i], zi));
-    z[i] = zi;
+  VPS_CHUNKS(i0, n) {
+    TZ zi[kU];
+    double pi[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      zi[u] = i < n ? zn[i] : TZ(0);
+      pi[u] = i < n ? p[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < n) {
+        store_p(p, ph, pl, i, fma(beta, pi[u], to_d(zi[u])));
+        z[i] = zi[u];
+      }
+    }
   }
 }
 
 // CG, after A p: alpha = rzn / p.Ap from the partials of p.Ap, x += alpha p,
-// r -= alpha A p, and the partials of r.r (same partition and order as
+// r -= alpha A p, and the partials of r.r (same chunks and order as
 // dot_partial_kernel: the grid is kDotBlocks blocks).  rz <- rzn for beta.
 __global__ void __launch_bounds__(kThreads)
 cg_update_xr_fused_kernel(double* __restrict__ x, double* __restrict__ r,
                           const double* __restrict__ p, const double* __restrict__ Ap,
                           const double* __restrict__ partial_pAp, CgScalars* __restrict__ sc,
                           double* __restrict__ partial_rr, int64_t n) {
-  __shared__ double sh[kThreads];
+  __shared__ double sh[33];
   double v[1];
   reduce_partials<1>(partial_pAp, v, sh);
   const double pAp = v[0], rz = sc->rzn;
@@ -241,12 +335,27 @@ cg_update_xr_fused_kernel(double* __restrict__ x, double* __restrict__ r,
     if (bad) sc->flag = 1;
   }
   double acc[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)kDotBlocks * kThreads) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, Ap[i], r[i]);
-    r[i] = ri;
-    acc[0] = fma(ri, ri, acc[0]);
+  VPS_CHUNKS(i0, n) {
+    double xv[kU], pv[kU], av[kU], rv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      const bool in = i < n;
+      xv[u] = in ? x[i] : 0.0;
+      pv[u] = in ? p[i] : 0.0;
+      av[u] = in ? Ap[i] : 0.0;
+      rv[u] = in ? r[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      const double ri = fma(-alpha, av[u], rv[u]);
+      if (i < n) {
+        x[i] = fma(alpha, pv[u], xv[u]);
+        r[i] = ri;
+      }
+      acc[0] = fma(ri, ri, acc[0]);
+    }
   }
   block_sum<1>(acc, sh);
   if (threadIdx.x == 0) partial_rr[blockIdx.x] = acc[0];
@@ -268,15 +377,65 @@ __global__ void cg_loop_init_kernel(CgScalars* sc, int it, int max_it, double nb
 }
 
 __global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+  VPS_CHUNKS(i0, n) {
+    double v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      v[u] = i < n ? a[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < n) b[i] = d2f_rn(v[u]);
+    }
+  }
 }
 
 __global__ void cast_f2d_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+    b[i] = f2d(a[i]);
+}
+
+// Diagnostic: the conversions of fp_bits.cuh against the hardware ones on
+// bit patterns pat[i] (low 32 bits as a float, all 64 as a double).
+// bad[0]: f2d differs from the cast; bad[1]: d2f_rn differs from the cast
+// (NaNs compare as equal); bad[2]: split_f2 breaks its contract.
+__global__ void check_fp_bits_kernel(const unsigned long long* __restrict__ pat, int64_t n,
+                                     unsigned long long* __restrict__ bad) {
+  unsigned long long nb[3] = {0ull, 0ull, 0ull};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = pat[i];
+    const float f = __uint_as_float((unsigned)b);
+    const double d = __longlong_as_double((long long)b);
+    const double x = f2d(f), xr = (double)f;
+    if (isnan(xr) ? !isnan(x) : __double_as_longlong(x) != __double_as_longlong(xr)) ++nb[0];
+    const float y = d2f_rn(d), yr = (float)d;
+    if (isnan(yr) ? !isnan(y) : __float_as_uint(y) != __float_as_uint(yr)) ++nb[1];
+    float hi, lo;
+    split_f2(d, hi, lo);
+    bool ok = true;
+    const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+    if (d == 0.0) {
+      ok = __float_as_uint(hi) == __float_as_uint(lo) && signbit(hi) == signbit(d) &&
+           hi == 0.0f;
+    } else if (E - 950u < 201u) {
+      const double t = (d - (double)hi) - (double)lo;  // both differences are exact
+      const double ulp = ldexp(1.0, ilogbf(hi) - 23);
+      ok = fabs(t) < ldexp(fabs(d), -47) && signbit(hi) == signbit(d) &&
+           (lo == 0.0f || signbit(lo) == signbit(d)) && fabs((double)hi) <= fabs(d) &&
+           fabs((double)lo) < ulp && fabs(d - (double)hi) < ulp;
+    } else if (!isnan(d)) {
+      const float h2 = (float)d, l2 = (float)(d - (double)h2);
+      ok = __float_as_uint(hi) == __float_as_uint(h2) &&
+           (isnan(l2) ? isnan(lo) : __float_as_uint(lo) == __float_as_uint(l2));
+    }
+    if (!ok) ++nb[2];
+  }
+  for (int j = 0; j < 3; ++j)
+    if (nb[j]) atomicAdd(bad + j, nb[j]);
 }
 
 template <typename T>
@@ -359,9 +518,27 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
 // with o fastest (the next pass contracts the next direction).  A block
 // computes FD_TL lines x FD_TO outputs; the whole contraction length fits
 // in shared memory (ni <= 255), so the input and weight tiles are loaded in
-// one stage.  Each thread owns a 4 x 4 register tile: per c, one 4-vector
-// of the input tile (lines) and one of the weight tile (outputs), 16 FMAs.
-constexpr int FD_TL = 32, FD_TO = 64, FD_THREADS = (FD_TL / 4) * (FD_TO / 4);
+// one stage, by asynchronous copies that are all in flight at once (the
+// tiles come from L2; copied one element per thread and round trip, the
+// load stage took most of a pass).  Each thread owns a 4 x 4 register
+// tile: per c, one 4-vector of the input tile (lines) and one of the
+// weight tile (outputs), 16 FMAs.
+constexpr int FD_TL = 16, FD_TO = 64, FD_THREADS = (FD_TL / 4) * (FD_TO / 4);
+
+// One element global -> shared without staging in registers; with valid
+// false the element is filled with zeros and nothing is read (src is then
+// only a placeholder address inside the source buffer).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(sz)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(sz)
+                 : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ void ld4s(const T* p, T (&v)[4]) {
@@ -376,7 +553,7 @@ __device__ __forceinline__ void ld4s(const T* p, T (&v)[4]) {
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(FD_THREADS)
+__global__ void __launch_bounds__(FD_THREADS, 8)
 fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ W,
                       const T* __restrict__ inv, int ni, int dim, int in_lev, int out_lev, int px,
                       int pz) {
@@ -387,21 +564,22 @@ fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __
   const int L0 = blockIdx.x * FD_TL, o0 = blockIdx.y * FD_TO;
   for (int u = threadIdx.x; u < ni * FD_TL; u += FD_THREADS) {
     const int l = u % FD_TL, c = u / FD_TL, L = L0 + l;
-    T v = T(0);
+    const T* src = in;
     if (L < NL) {
       if (in_lev) {
         const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
-        v = dim == 3 ? in[(c + 1) * pz + (a + 1) * px + bb + 1] : in[(c + 1) * px + bb + 1];
+        src = dim == 3 ? in + ((c + 1) * pz + (a + 1) * px + bb + 1) : in + ((c + 1) * px + bb + 1);
       } else {
-        v = in[(size_t)c * NL + L];
+        src = in + ((size_t)c * NL + L);
       }
     }
-    As[u] = v;
+    cp_async_elem(As + u, src, L < NL);
   }
   for (int u = threadIdx.x; u < ni * FD_TO; u += FD_THREADS) {
     const int oo = u % FD_TO, c = u / FD_TO, o = o0 + oo;
-    Bs[u] = o < ni ? W[c * ni + o] : T(0);
+    cp_async_elem(Bs + u, o < ni ? W + (c * ni + o) : W, o < ni);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   const int tl = threadIdx.x % (FD_TL / 4), to = threadIdx.x / (FD_TL / 4);
   T acc[4][4];
@@ -484,12 +662,12 @@ cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
-                        int64_t n, double* partial, double* out, cudaStream_t s) {
+cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* partial, double* out,
+                        cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  dot_partial_kernel<double><<<kDotBlocks, kThreads, 0, s>>>(a, b, c, e, n, partial);
+  dot_partial_kernel<double, 1><<<kDotBlocks, kThreads, 0, s>>>(a, b, nullptr, n, partial);
   VPS_COUNT_LAUNCH();
-  dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, c ? 2 : 1);
+  dot_final_kernel<<<1, kThreads, 0, s>>>(partial, out, 1);
   return cudaGetLastError();
 }
 
@@ -515,19 +693,16 @@ cudaError_t launch_scale(double* y, const double* x, double a, int64_t n, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* partial, double* out,
-                        cudaStream_t s) {
-  return launch_dot2(a, b, nullptr, nullptr, n, partial, out, s);
-}
 
 template <typename TZ>
 cudaError_t launch_cg_start(double* p, double* z, const TZ* zn, const double* r, int64_t n,
                             double* partial, CgScalars* sc, cudaStream_t s, float* ph,
                             float* pl) {
   VPS_COUNT_LAUNCH();
-  cg_init_p_kernel<TZ><<<grid_for(n, 4), kThreads, 0, s>>>(p, z, zn, ph, pl, n);
+  cg_init_p_kernel<TZ>
+      <<<grid_for(n, kU), kThreads, 0, s>>>(p, reinterpret_cast<TZ*>(z), zn, ph, pl, n);
   VPS_COUNT_LAUNCH();
-  dot_partial_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(r, zn, nullptr, nullptr, n, partial);
+  dot_partial_kernel<TZ, 1><<<kDotBlocks, kThreads, 0, s>>>(r, zn, nullptr, n, partial);
   VPS_COUNT_LAUNCH();
   dot_final_kernel<<<1, kThreads, 0, s>>>(partial, &sc->rzn, 1);
   return cudaGetLastError();
@@ -538,17 +713,18 @@ cudaError_t launch_cg_next_p(double* p, double* z, const TZ* zn, const double* r
                              double* partial, CgScalars* sc, cudaStream_t s, float* ph,
                              float* pl) {
   VPS_COUNT_LAUNCH();
-  dot_partial_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(r, zn, r, z, n, partial);
+  TZ* zo = reinterpret_cast<TZ*>(z);  // z_old in the type of z_new
+  dot_partial_kernel<TZ, 2><<<kDotBlocks, kThreads, 0, s>>>(r, zn, zo, n, partial);
   VPS_COUNT_LAUNCH();
   // kDotBlocks blocks: every block reduces the partials once
-  cg_update_p_fused_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(p, z, zn, partial, sc, ph, pl, n);
+  cg_update_p_fused_kernel<TZ><<<kDotBlocks, kThreads, 0, s>>>(p, zo, zn, partial, sc, ph, pl, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_step_xr(double* x, double* r, const double* p, const double* Ap, int64_t n,
                               double* partial, double* partial2, CgScalars* sc, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  dot_partial_kernel<double><<<kDotBlocks, kThreads, 0, s>>>(p, Ap, nullptr, nullptr, n, partial);
+  dot_partial_kernel<double, 1><<<kDotBlocks, kThreads, 0, s>>>(p, Ap, nullptr, n, partial);
   VPS_COUNT_LAUNCH();
   cg_update_xr_fused_kernel<<<kDotBlocks, kThreads, 0, s>>>(x, r, p, Ap, partial, sc, partial2, n);
   VPS_COUNT_LAUNCH();
@@ -569,7 +745,7 @@ template cudaError_t launch_cg_next_p<double>(double*, double*, const double*, c
 
 cudaError_t launch_split_df(const double* a, float* ph, float* pl, int64_t n, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  split_df_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, ph, pl, n);
+  split_df_kernel<<<grid_for(n, kU), kThreads, 0, s>>>(a, ph, pl, n);
   return cudaGetLastError();
 }
 
@@ -588,7 +764,7 @@ cudaError_t launch_cg_loop_init(CgScalars* sc, int it, int max_it, double nb, do
 
 cudaError_t launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
   VPS_COUNT_LAUNCH();
-  cast_d2f_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(a, b, n);
+  cast_d2f_kernel<<<grid_for(n, kU), kThreads, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 
@@ -633,3 +809,37 @@ template cudaError_t launch_axpy_inplace<double>(double*, const double*, double,
                                                  cudaStream_t);
 
 }  // namespace vps
+
+extern "C" int vps_check_fp_conversions(const void* patterns, int64_t n, int64_t* mismatches,
+                                        void* cuda_stream) {
+  using namespace vps;
+  set_thread_error("");
+  char buf[256];
+  if (!mismatches || n < 0 || (n > 0 && !patterns)) {
+    set_thread_error("mismatches must be non-NULL, n >= 0, patterns non-NULL if n > 0");
+    return VPS_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long* bad = nullptr;
+  unsigned long long host[3] = {0ull, 0ull, 0ull};
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(host), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(host), s);
+  if (e == cudaSuccess && n > 0) {
+    check_fp_bits_kernel<<<grid_for(n, 4), kThreads, 0, s>>>(
+        static_cast<const unsigned long long*>(patterns), n, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, bad, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (bad) {
+    const cudaError_t e2 = cudaFreeAsync(bad, s);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    snprintf(buf, sizeof(buf), "vps_check_fp_conversions: %s", cudaGetErrorString(e));
+    set_thread_error(buf);
+    return VPS_ECUDA;
+  }
+  for (int j = 0; j < 3; ++j) mismatches[j] = (int64_t)host[j];
+  return VPS_OK;
+}

@@ -8,6 +8,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -90,6 +91,28 @@ ColourGeom make_colour(const LevelGeom& g, int colour);
 int64_t& launch_counter();
 #define VPS_COUNT_LAUNCH() (++::vps::launch_counter())
 
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel of the stream drains (its blocks occupy free SM slots and
+// run their prologue), and waits with griddepcontrol.wait (vps_grid_wait)
+// before it reads anything an earlier kernel writes.  Only kernels that
+// execute vps_grid_wait before such reads may be launched this way.  Stream
+// capture records the dependency as a programmatic graph edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
 // q = 0, 1, 2 for 1, 2, 4 patches per thread; kind 0 the fused kernel,
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
@@ -156,8 +179,6 @@ cudaError_t launch_unpack(const LevelGeom& g, const T* lev, T* compact, cudaStre
 // block into `partial` (kDotBlocks doubles per product), then one block
 // reduces them in a fixed order into out[0..nprod).
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
-cudaError_t launch_dot2(const double* a, const double* b, const double* c, const double* e,
-                        int64_t n, double* partial, double* out, cudaStream_t s);
 cudaError_t launch_dot1(const double* a, const double* b, int64_t n, double* partial,
                         double* out, cudaStream_t s);
 
