@@ -1141,7 +1141,19 @@ struct Apply3Cfg {
   static constexpr int MINB = (NT <= 512 && K <= 5) ? 2 : 1;
   template <typename T>
   static constexpr size_t smem() { return sizeof(T) * (size_t)(4 * BX * RB + 2 * TX * RB); }
+  // apply3c_kernel: the z contractions of a cell's K planes, then two
+  // buffers of the y stage's outputs
+  template <typename T>
+  static constexpr size_t smem_c() { return sizeof(T) * (size_t)(2 * K * BX * RB + 4 * TX * RB); }
 };
+
+// The FP32 operator takes apply3c_kernel where its shared memory leaves room
+// for two blocks per SM (k <= 4); the FP64 and |A||x| operators, whose FP64
+// arithmetic bounds them, keep apply3_kernel.
+template <typename T>
+constexpr bool kApply3C = sizeof(T) == 4 && K <= 4;
+// cells of planes per block of apply3c_kernel
+constexpr int kApply3CZ = K == 1 ? 8 : (K <= 3 ? 4 : 2);
 
 template <typename T, bool ABS = false>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
@@ -1235,6 +1247,118 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
       }
       buf ^= 1;
     }
+  }
+}
+
+// 3D operator on the same tiles as apply3_kernel, with the z contraction
+// taken a whole cell at a time.  The K planes z0 .. z0+K-1 of a cell couple
+// only the 2K+1 planes z0-K .. z0+K (the vertex row both neighbouring cells,
+// the interior rows their own cell), so each column of the halo'd tile
+// loads that window once, all loads in flight together, and writes the M
+// and K contractions of all K planes; then y and x per plane as before,
+// with the y stage's outputs double-buffered (one barrier per plane).  The
+// per-plane z stage of apply3_kernel loads 2K+1 values for the vertex plane
+// and K+1 for each other plane, one plane at a time, and was bound by the
+// latency of those loads (long-scoreboard stalls, a third of the issue
+// slots used).
+template <typename T>
+__global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
+apply3c_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
+               int px, int pz, T scale) {
+  using C = Apply3Cfg;
+  constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* zb = reinterpret_cast<T*>(smem_raw);  // [K][M, K rows][BX][RB]
+  T* mw = zb + 2 * K * BX * RB;            // [2 buffers][MM, WW][TX][RB]
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  for (int cz = 0; cz < kApply3CZ; ++cz) {
+    const int z0 = (blockIdx.z * kApply3CZ + cz) * K;
+    if (z0 >= n1 - 1) break;  // uniform in the block; plane n1-1 is zeroed elsewhere
+    for (int u = threadIdx.x; u < BX * BX; u += NT) {
+      const int xx = u % BX, yy = u / BX;
+      const int gx = x0 - K + xx, gy = y0 - K + yy;
+      const bool in = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+      T w[2 * K + 1];
+#pragma unroll
+      for (int t = 0; t <= 2 * K; ++t) {
+        const int gz = z0 - K + t;
+        w[t] = (in && gz >= 0 && gz < n1) ? __ldg(x + (gz * pz + gy * px + gx)) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        T am = T(0), ak = T(0);
+        VPS_BAND_LOOP(q, j) {
+          am = fma(coefM<T, false>(q * n + j), w[q + j], am);
+          ak = fma(coefK<T, false>(q * n + j), w[q + j], ak);
+        }
+        zb[(2 * q * BX + yy) * RB + xx] = am;
+        zb[((2 * q + 1) * BX + yy) * RB + xx] = ak;
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int q = 0; q < K; ++q) {
+      const T* mZ = zb + 2 * q * BX * RB;
+      const T* kZ = mZ + BX * RB;
+      T* MM = mw + (q & 1) * 2 * TX * RB;
+      T* WW = MM + TX * RB;
+      // y contraction: units (x over the halo, cell segment in y)
+      for (int u = threadIdx.x; u < BX * CX; u += NT) {
+        const int xx = u % BX, cy = u / BX;
+        T vm[2 * K + 1], vk[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = mZ[(cy * K + i) * RB + xx];
+          vk[i] = kZ[(cy * K + i) * RB + xx];
+        }
+#pragma unroll
+        for (int qy = 0; qy < K; ++qy) {
+          T a = T(0), bb = T(0);
+          VPS_BAND_LOOP(qy, j) {
+            a = fma(coefM<T, false>(qy * n + j), vm[qy + j], a);
+            bb = fma(coefK<T, false>(qy * n + j), vm[qy + j], bb);
+            bb = fma(coefM<T, false>(qy * n + j), vk[qy + j], bb);
+          }
+          MM[(cy * K + qy) * RB + xx] = a;
+          WW[(cy * K + qy) * RB + xx] = bb;
+        }
+      }
+      __syncthreads();
+      // x contraction and store: units (y fastest, cell segment in x)
+      const int z = z0 + q;
+      const bool inner_z = z >= 1 && z <= n1 - 2;
+      for (int u = threadIdx.x; u < TX * CX; u += NT) {
+        const int Y = u % TX, cx = u / TX;
+        const int gy = y0 + Y;
+        if (gy >= n1) continue;
+        T vm[2 * K + 1], vw[2 * K + 1];
+#pragma unroll
+        for (int i = 0; i <= 2 * K; ++i) {
+          vm[i] = MM[Y * RB + cx * K + i];
+          vw[i] = WW[Y * RB + cx * K + i];
+        }
+        const bool inner_yz = inner_z && gy >= 1 && gy <= n1 - 2;
+        const int rowi = z * pz + gy * px;
+#pragma unroll
+        for (int qx = 0; qx < K; ++qx) {
+          const int gx = x0 + cx * K + qx;
+          if (gx >= n1) continue;
+          T acc = T(0);
+          VPS_BAND_LOOP(qx, j) {
+            acc = fma(coefK<T, false>(qx * n + j), vm[qx + j], acc);
+            acc = fma(coefM<T, false>(qx * n + j), vw[qx + j], acc);
+          }
+          T out = T(0);
+          if (inner_yz && gx >= 1 && gx <= n1 - 2)
+            out = bvec ? bvec[rowi + gx] - scale * acc : scale * acc;
+          y[rowi + gx] = out;
+        }
+      }
+      // no barrier: the next y stage writes the other buffer; the one after
+      // it follows the barrier that ends this x stage's reads
+    }
+    // no barrier: the next cell's z stage writes zb, which the y stages have
+    // finished reading (the barrier after the last of them)
   }
 }
 
@@ -1743,10 +1867,16 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
   if constexpr (DIM == 3) {
     using C3 = Apply3Cfg;
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
     VPS_COUNT_LAUNCH();
-    apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
-                                                                   (int)g.pz, T(g.h));
+    if constexpr (kApply3C<T>) {
+      const unsigned tz = (unsigned)((span + kApply3CZ * K - 1) / (kApply3CZ * K));
+      apply3c_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem_c<T>(), s>>>(x, b, y, g.n1, (int)g.px,
+                                                                        (int)g.pz, T(g.h));
+    } else {
+      const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
+      apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
+                                                                     (int)g.pz, T(g.h));
+    }
   } else {
     using C = ApplyCfg;
     const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
@@ -1927,6 +2057,11 @@ cudaError_t set_smem_limits() {
     e = cudaFuncSetAttribute(apply3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Apply3Cfg::smem<T>());
     if (e != cudaSuccess) return e;
+    if constexpr (kApply3C<T>) {
+      e = cudaFuncSetAttribute(apply3c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Apply3Cfg::smem_c<T>());
+      if (e != cudaSuccess) return e;
+    }
   }
   e = cudaFuncSetAttribute(prolong_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)TransferCfg::smem_prolong<T>());
