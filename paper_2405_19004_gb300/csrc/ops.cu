@@ -520,10 +520,12 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
 // in shared memory (ni <= 255), so the input and weight tiles are loaded in
 // one stage, by asynchronous copies that are all in flight at once (the
 // tiles come from L2; copied one element per thread and round trip, the
-// load stage took most of a pass).  Each thread owns a 4 x 4 register
-// tile: per c, one 4-vector of the input tile (lines) and one of the
-// weight tile (outputs), 16 FMAs.
-constexpr int FD_TL = 16, FD_TO = 64, FD_THREADS = (FD_TL / 4) * (FD_TO / 4);
+// load stage took most of a pass).  Each thread owns a 2 x 2 register
+// tile: per c, one pair of the input tile (lines) and one of the weight
+// tile (outputs), 4 FMAs.  Small register tiles give the small coarse
+// problems enough warps to hide latency (4 x 4 tiles left about three
+// warps per SM on 63^3 unknowns).
+constexpr int FD_TL = 16, FD_TO = 32, FD_R = 2, FD_THREADS = (FD_TL / FD_R) * (FD_TO / FD_R);
 
 // One element global -> shared without staging in registers; with valid
 // false the element is filled with zeros and nothing is read (src is then
@@ -541,14 +543,13 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) 
 }
 
 template <typename T>
-__device__ __forceinline__ void ld4s(const T* p, T (&v)[4]) {
+__device__ __forceinline__ void ld2s(const T* p, T (&v)[2]) {
   if constexpr (sizeof(T) == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
   } else {
-    const double2 q0 = reinterpret_cast<const double2*>(p)[0];
-    const double2 q1 = reinterpret_cast<const double2*>(p)[1];
-    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
   }
 }
 
@@ -581,30 +582,30 @@ fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  const int tl = threadIdx.x % (FD_TL / 4), to = threadIdx.x / (FD_TL / 4);
-  T acc[4][4];
+  const int tl = threadIdx.x % (FD_TL / FD_R), to = threadIdx.x / (FD_TL / FD_R);
+  T acc[FD_R][FD_R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < FD_R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 4
+    for (int j = 0; j < FD_R; ++j) acc[i][j] = T(0);
+#pragma unroll 8
   for (int c = 0; c < ni; ++c) {
-    T av[4], bv[4];
-    ld4s(As + c * FD_TL + 4 * tl, av);
-    ld4s(Bs + c * FD_TO + 4 * to, bv);
+    T av[FD_R], bv[FD_R];
+    ld2s(As + c * FD_TL + FD_R * tl, av);
+    ld2s(Bs + c * FD_TO + FD_R * to, bv);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < FD_R; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < FD_R; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int L = L0 + 4 * tl + i;
+  for (int i = 0; i < FD_R; ++i) {
+    const int L = L0 + FD_R * tl + i;
     if (L >= NL) continue;
     const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int o = o0 + 4 * to + j;
+    for (int j = 0; j < FD_R; ++j) {
+      const int o = o0 + FD_R * to + j;
       if (o >= ni) continue;
       T r = acc[i][j];
       if (MODE == 1) r *= inv[(size_t)L * ni + o];
