@@ -1394,6 +1394,46 @@ __device__ __forceinline__ DF df_norm(const DF& s) {
 #define VPS_DF_MADD(acc, TAB, q, j, v) \
   df_madd(acc, c_tab<float>.TAB[(q) * n + (j)], c_tab<float>.TAB##_lo[(q) * n + (j)], v)
 
+// z contraction of plane z = z0 + Q (Q: the plane's position in its cell,
+// which selects the band) over the halo'd tile, double-float.
+template <int Q>
+__device__ __forceinline__ void df_zstage(const float* __restrict__ xh,
+                                          const float* __restrict__ xl, DF* mZ, DF* kZ, int x0,
+                                          int y0, int z, int n1, int px, int pz) {
+  using C = Apply3Cfg;
+  constexpr int BX = C::BX, RB = C::RB, NT = C::NT;
+  for (int u = threadIdx.x; u < BX * BX; u += NT) {
+    const int xx = u % BX, yy = u / BX;
+    const int gx = x0 - K + xx, gy = y0 - K + yy;
+    DF am{0.f, 0.f}, ak{0.f, 0.f};
+    if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
+      const int col = gy * px + gx;
+      VPS_BAND_LOOP(Q, j) {
+        const int gz = z - K + j;
+        DF v{0.f, 0.f};
+        if (gz >= 0 && gz < n1) v = DF{__ldg(xh + col + gz * pz), __ldg(xl + col + gz * pz)};
+        VPS_DF_MADD(am, Mb, Q, j, v);
+        VPS_DF_MADD(ak, Kb, Q, j, v);
+      }
+    }
+    mZ[yy * RB + xx] = df_norm(am);
+    kZ[yy * RB + xx] = df_norm(ak);
+  }
+}
+
+// df_zstage<q> for a run-time q < K: the plane loop of apply3_df_kernel
+// stays rolled, so its large y and x stages are compiled once (unrolled over
+// the K planes, the kernel's code stalled on instruction fetch).
+template <int Qc>
+__device__ __forceinline__ void df_zstage_at(int q, const float* __restrict__ xh,
+                                             const float* __restrict__ xl, DF* mZ, DF* kZ,
+                                             int x0, int y0, int z, int n1, int px, int pz) {
+  if constexpr (Qc < K) {
+    if (q == Qc) df_zstage<Qc>(xh, xl, mZ, kZ, x0, y0, z, n1, px, pz);
+    else df_zstage_at<Qc + 1>(q, xh, xl, mZ, kZ, x0, y0, z, n1, px, pz);
+  }
+}
+
 template <int DUMMY>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
 apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
@@ -1408,29 +1448,13 @@ apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
   const int z0 = blockIdx.z * (kApplyZC<double> * K);
   int buf = 0;
   for (int cz = 0; cz < kApplyZC<double>; ++cz) {
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < K; ++q) {
       const int z = z0 + cz * K + q;
       if (z >= n1 - 1) break;
       DF* mZ = zbuf + (2 * buf) * BX * RB;
       DF* kZ = mZ + BX * RB;
-      for (int u = threadIdx.x; u < BX * BX; u += NT) {
-        const int xx = u % BX, yy = u / BX;
-        const int gx = x0 - K + xx, gy = y0 - K + yy;
-        DF am{0.f, 0.f}, ak{0.f, 0.f};
-        if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
-          const int col = gy * px + gx;
-          VPS_BAND_LOOP(q, j) {
-            const int gz = z - K + j;
-            DF v{0.f, 0.f};
-            if (gz >= 0 && gz < n1) v = DF{__ldg(xh + col + gz * pz), __ldg(xl + col + gz * pz)};
-            VPS_DF_MADD(am, Mb, q, j, v);
-            VPS_DF_MADD(ak, Kb, q, j, v);
-          }
-        }
-        mZ[yy * RB + xx] = df_norm(am);
-        kZ[yy * RB + xx] = df_norm(ak);
-      }
+      df_zstage_at<0>(q, xh, xl, mZ, kZ, x0, y0, z, n1, px, pz);
       __syncthreads();
       for (int u = threadIdx.x; u < BX * CX; u += NT) {
         const int xx = u % BX, cy = u / BX;
