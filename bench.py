@@ -343,8 +343,12 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
 
-    # dominant kernel: finest-level FP32 smoother colour passes, CUDA events on the
-    # library's stream around each launch (same kernel and data sizes as in the solve)
+    # dominant kernel: finest-level FP32 smoother colour passes (same kernel and data
+    # sizes as in the solve), CUDA events on the library's stream around each run of the
+    # 8 passes of a smoothing step, launched back to back as in the V-cycle (the passes
+    # are programmatic dependent launches: a pass is scheduled while the previous one
+    # drains, which an event between two passes would prevent); the average launch
+    # duration is the run's time / 8
     lib = vps.lib()
     import ctypes
     bs = P.to_level(b.float())
@@ -353,18 +357,18 @@ def main():
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     n_rep = 20
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(8 * n_rep)]
+           for _ in range(n_rep)]
     for c in range(8):  # warm-up
         vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
     with nvtx("smoother_colour_passes"):
         for r in range(n_rep):
+            a, z = evs[r]
+            a.record(stream)
             for c in range(8):
-                a, z = evs[r * 8 + c]
-                a.record(stream)
                 vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
-                z.record(stream)
+            z.record(stream)
         torch.cuda.synchronize()
-    launch_ms = [a.elapsed_time(z) for a, z in evs]
+    launch_ms = [a.elapsed_time(z) / 8.0 for a, z in evs]
     t_launch = statistics.mean(launch_ms) / 1e3
     n_patches = (2 ** L - 1) ** 3
     var_L = P.vps_get_smooth_variant(L)[0]
