@@ -101,31 +101,77 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return f2d(v); }
 
+// s += a b for a double a = ah + al (split_f2) and a float b in double-float
+// arithmetic, FP32 instructions only: ah b exactly as p + e (one FMA for e),
+// al b rounded, the high words summed by TwoSum and every error into s.lo.
+// Relative error about 2^-46 of the sum of |a b| over a thread's terms.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ void f2_madd(F2& s, float ah, float al, float b) {
+  const float p = ah * b;
+  const float e = fmaf(ah, b, -p);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + fmaf(al, b, e);
+}
+
 // partial[j * kDotBlocks + block] = sum over this block's fixed subset of
 // the products a.b (j = 0) and, with NP = 2, a.e (j = 1; partial[1..] is
-// 0 for NP = 1).  b and e in FP32 (converted exactly) or FP64.
+// 0 for NP = 1).  b and e in FP64, or in FP32: then the per-thread sums are
+// double-float (the FP64 multiply-adds, which issue at 1/64 of the FP32 rate
+// on this GPU, bounded the kernel), widened to FP64 for the block sum.
 template <typename TB, int NP>
 __global__ void __launch_bounds__(kThreads)
 dot_partial_kernel(const double* __restrict__ a, const TB* __restrict__ b,
                    const TB* __restrict__ e, int64_t n, double* __restrict__ partial) {
   __shared__ double sh[2 * 33];
   double v[NP];
+  if constexpr (sizeof(TB) == 4) {
+    F2 f[NP];
 #pragma unroll
-  for (int j = 0; j < NP; ++j) v[j] = 0.0;
-  VPS_CHUNKS(i0, n) {
-    double av[kU], bv[kU], ev[kU];
+    for (int j = 0; j < NP; ++j) f[j] = F2{0.f, 0.f};
+    VPS_CHUNKS(i0, n) {
+      double av[kU];
+      float bv[kU], ev[kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int64_t i = i0 + u * kThreads;
-      const bool in = i < n;
-      av[u] = in ? a[i] : 0.0;
-      bv[u] = in ? to_d(b[i]) : 0.0;
-      if constexpr (NP == 2) ev[u] = in ? to_d(e[i]) : 0.0;
+      for (int u = 0; u < kU; ++u) {
+        const int64_t i = i0 + u * kThreads;
+        const bool in = i < n;
+        av[u] = in ? a[i] : 0.0;
+        bv[u] = in ? b[i] : 0.f;
+        if constexpr (NP == 2) ev[u] = in ? e[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        float ah, al;
+        split_f2(av[u], ah, al);
+        f2_madd(f[0], ah, al, bv[u]);
+        if constexpr (NP == 2) f2_madd(f[NP - 1], ah, al, ev[u]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      v[0] = fma(av[u], bv[u], v[0]);
-      if constexpr (NP == 2) v[NP - 1] = fma(av[u], ev[u], v[NP - 1]);
+    for (int j = 0; j < NP; ++j) v[j] = f2d(f[j].hi) + f2d(f[j].lo);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) v[j] = 0.0;
+    VPS_CHUNKS(i0, n) {
+      double av[kU], bv[kU], ev[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t i = i0 + u * kThreads;
+        const bool in = i < n;
+        av[u] = in ? a[i] : 0.0;
+        bv[u] = in ? to_d(b[i]) : 0.0;
+        if constexpr (NP == 2) ev[u] = in ? to_d(e[i]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        v[0] = fma(av[u], bv[u], v[0]);
+        if constexpr (NP == 2) v[NP - 1] = fma(av[u], ev[u], v[NP - 1]);
+      }
     }
   }
   block_sum<NP>(v, sh);
