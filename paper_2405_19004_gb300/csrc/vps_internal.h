@@ -93,10 +93,13 @@ int64_t& launch_counter();
 
 // Programmatic dependent launch: the kernel may be scheduled while the
 // previous kernel of the stream drains (its blocks occupy free SM slots and
-// run their prologue), and waits with griddepcontrol.wait (vps_grid_wait)
-// before it reads anything an earlier kernel writes.  Only kernels that
-// execute vps_grid_wait before such reads may be launched this way.  Stream
-// capture records the dependency as a programmatic graph edge.
+// run their prologue), and waits with griddepcontrol.wait
+// (grid_dependency_wait in kernels_dk.cu) before it reads anything an
+// earlier kernel writes.  Only kernels that execute that wait before such
+// reads may be launched this way.  The relaxed dependency applies only to a
+// previous kernel that requests it (launch_dependents); after a copy or a
+// memset the launch is ordered as usual.  Stream capture records the
+// dependency as a programmatic graph edge.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args&&... args) {
