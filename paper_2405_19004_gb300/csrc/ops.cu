@@ -18,13 +18,13 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Chunked grid-stride loop of the bandwidth-bound vector kernels: thread t
-// of block B takes the chunks that start at i0 = (B + j gridDim) kU kThreads
-// + t (j = 0, 1, ..), elements i0 + u kThreads (u < kU; coalesced for every
-// u).  A kernel loads all kU elements of a chunk before it uses any, so each
-// thread keeps kU loads in flight: with one element per thread and
-// iteration, the resident threads hold too few bytes in flight to cover the
-// DRAM latency and the kernels run at a fraction of the bandwidth.
+// Chunked grid-stride loop of the vector kernels: thread t of block B takes
+// the chunks that start at i0 = (B + j gridDim) kU kThreads + t (j = 0, 1,
+// ..), elements i0 + u kThreads (u < kU; coalesced for every u).  A kernel
+// loads all kU elements of a chunk before it uses any, so each thread keeps
+// kU loads in flight (the fixed 608-block grid of the reductions holds 1024
+// threads per SM: with one element per thread and iteration, few bytes are
+// in flight for the DRAM latency).
 constexpr int kU = 4;
 #define VPS_CHUNKS(i0, n)                                                         \
   for (int64_t i0 = blockIdx.x * (int64_t)(kU * kThreads) + threadIdx.x; i0 < (n); \
