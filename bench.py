@@ -257,7 +257,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2405_19004_gb300 as vps
-    from paper_2405_19004_gb300.studies import smoother_flops_per_patch
+    from paper_2405_19004_gb300.studies import (SMEM_BW, smoother_flops_per_patch,
+                                                smoother_smem_words_per_patch)
     from synthetic import uniform_vector
 
     P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
@@ -374,6 +375,8 @@ def main():
     var_L = P.vps_get_smooth_variant(L)[0]
     bnd_L = var_L // 3 >= 1
     flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / 8.0
+    smem_roof_tflops = SMEM_BW * smoother_flops_per_patch(D, K, bnd_L) / (
+        4.0 * smoother_smem_words_per_patch(D, K, bnd_L)) / 1e12
     achieved = flops_per_launch / t_launch / 1e12
     t_smooth_step = 8 * t_launch
 
@@ -516,7 +519,12 @@ def main():
                           "autotuned": tuned}),
         "iterations": its[-1], "rel_residual": rel,
         "smoother_fp32": {"dof_per_s": N / t_smooth_step, "tflops": achieved,
-                          "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS},
+                          "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS,
+                          # shared-memory roofline R = B F / (d_r + d_w) (Section 4.3),
+                          # B = 152 SMs x 32 banks x 4 B x 2.07 GHz, the kernel's own
+                          # shared-memory words per patch
+                          "frac_of_smem_roofline": achieved / smem_roof_tflops,
+                          "smem_roofline_tflops": smem_roof_tflops},
         "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level, "
                                + ("Boundary" if bnd_L else "fused") + f" variant {var_L}",
                      "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
