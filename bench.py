@@ -35,38 +35,49 @@ if ROOT not in sys.path:
 METRIC = "smoother DoF/s & % FP32/FP64 peak; time-to-1e-10 residual FP32-MG vs FP64; p50/p99"
 D, K, L = 3, 4, 5
 RTOL = 1e-10
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 peak of GB300 (nominal, dense)
-FP64_PEAK_TFLOPS = 1.25
-CPU_SAMPLE_LEVEL = 3           # oracle sample: same problem family at level 3
-CPU_SAMPLE_REPEATS = 10
+FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (Blackwell)
+CPU_SAMPLE_LEVEL = 4           # oracle sample: the same problem at level 4 (250,047 DoFs)
+CPU_SAMPLE_REPEATS = 3         # best of 3 solves
+REF_STEP_BUDGET_S = 240.0      # reference arm: whole run within about four minutes
+REF_STEP_S_LEVEL4 = 10.0       # one oracle solve at level 4 on one host core (measured)
 
 
 def smoother_traffic(variant):
-    """DRAM bytes per finest-level colour pass of the timed smoother kernel,
-    from the committed ncu summary of that kernel (dram__bytes_read.sum +
-    dram__bytes_write.sum), or None if the summary is for another variant or
-    was taken before the kernel source last changed."""
+    """DRAM bytes per finest-level colour pass of the timed smoother kernel
+    from the committed ncu record (dram__bytes_read.sum + dram__bytes_write.sum
+    of the kernel, summarised in profiles/smoother_traffic_3d_q4_l5.md), or
+    None if the record is for another variant or was taken before the kernel
+    source last changed."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "smoother_traffic_3d_q4_l5.md")
+    path = os.path.join(ROOT, "profiles", "smoother_traffic_3d_q4_l5.json")
     src = os.path.join(ROOT, "paper_2405_19004_gb300", "csrc", "kernels_dk.cu")
     try:
-        text = open(path).read()
+        rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for line in text.splitlines():
-        if line.startswith("- ") and ":" in line:
-            key, val = line[2:].split(":", 1)
-            vals[key.strip()] = val.strip().strip("`")
-    if vals.get("kernels_dk.cu sha256") != sha:
+    if rec.get("kernels_dk.cu sha256") != sha:
         return None
+    v = rec.get("traffic_bytes_per_launch", {}).get(str(variant))
+    return float(v) if v is not None else None
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
     try:
-        return float(vals[f"variant {variant} traffic bytes per launch"])
-    except (KeyError, ValueError):
-        return None
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def parse():
@@ -90,41 +101,75 @@ def parse():
                         "the same kernels, for profilers that do not follow graph conditional nodes")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--repeats", type=int, default=CPU_SAMPLE_REPEATS, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-level", type=int, default=CPU_SAMPLE_LEVEL, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
 # ---------------------------------------------------------------- oracle
-def cpu_worker(repeats):
-    """Times the oracle PCG solve (FP64, multiplicative V-cycle) on the host."""
-    import numpy as np  # noqa: F401
+def cpu_worker(repeats, level):
+    """Times the oracle PCG solve (FP64, multiplicative V-cycle) on the host:
+    setup (assembly, patch factorisations) once, then `repeats` solves."""
+    import resource
     from oracle import multigrid
     from synthetic import uniform_vector
-    H = multigrid.Hierarchy(D, K, CPU_SAMPLE_LEVEL)
-    N = H.levels[CPU_SAMPLE_LEVEL].N
+    t0 = time.perf_counter()
+    H = multigrid.Hierarchy(D, K, level)
+    setup = time.perf_counter() - t0
+    N = H.levels[level].N
     b = uniform_vector(N, 1)
     times, its = [], []
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    w0 = time.perf_counter()
     for _ in range(repeats):
         t0 = time.perf_counter()
-        _, it, rel = multigrid.pcg(H.A[CPU_SAMPLE_LEVEL], b, H.precondition, RTOL, 100)
+        _, it, rel = multigrid.pcg(H.A[level], b, H.precondition, RTOL, 100)
         times.append(time.perf_counter() - t0)
         its.append(it)
-    print(json.dumps({"n": N, "times": times, "iters": its, "rel": rel}))
+    wall = time.perf_counter() - w0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    print(json.dumps({"n": N, "level": level, "times": times, "iters": its, "rel": rel,
+                      "setup_s": setup, "cpu_s": cpu_s, "wall_s": wall,
+                      "nnz": int(H.A[level].nnz)}))
 
 
-def run_cpu_sample(repeats):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def run_cpu_sample(repeats, level):
+    """Runs cpu_worker in a fresh process with every BLAS allowed all host
+    threads; returns its record plus the thread count and CPU model."""
+    nthreads = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(nthreads), OPENBLAS_NUM_THREADS=str(nthreads),
+               MKL_NUM_THREADS=str(nthreads))
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
-                          "--repeats", str(repeats)], capture_output=True, text=True, env=env,
-                         cwd=ROOT, timeout=1800)
+                          "--repeats", str(repeats), "--cpu-level", str(level)],
+                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=3600)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    rec["threads_available"] = nthreads
+    # threads it actually kept busy: CPU time over wall time of the solves
+    rec["threads_used"] = max(1, int(round(rec["cpu_s"] / max(rec["wall_s"], 1e-9))))
+    rec["cpu_model"] = cpu_model()
+    return rec
 
 
-def sample_desc(n, repeats):
-    return (f"oracle FP64 PCG (multiplicative V-cycle, 1/1 smoothing) of the same 3D Q4 problem at "
-            f"level {CPU_SAMPLE_LEVEL} ({n} DoFs; the workload is level {L}), {repeats} solves, "
-            f"setup excluded, BLAS threads 1")
+def cpu_baseline_entry(rec, value, best=True):
+    t = min(rec["times"]) if best else statistics.mean(rec["times"])
+    return {"value": value, "unit": "DoF/s", "cores": rec["threads_used"], "kind": "oracle",
+            "sample": sample_desc(rec, best),
+            "threads_available": rec["threads_available"], "cpu_model": rec["cpu_model"],
+            "level": rec["level"], "dofs": rec["n"], "seconds_per_solve": t,
+            "setup_s": rec["setup_s"]}
+
+
+def sample_desc(rec, best=True):
+    n, lev, reps = rec["n"], rec["level"], len(rec["times"])
+    how = f"best of {reps} solves" if best else f"mean of {reps} solves"
+    return (f"oracle FP64 PCG (multiplicative V-cycle, 1/1 smoothing, sparse CSR matrices of "
+            f"{rec['nnz']} nonzeros on the finest level) of the same 3D Q4 problem at level {lev} "
+            f"({n} DoFs; the workload is level {L}: its CSR matrix alone would hold 1.5e9 "
+            f"nonzeros), {how}, setup ({rec['setup_s']:.1f} s) excluded, BLAS threads "
+            f"{rec['threads_available']} (the sparse products run on one thread), "
+            f"CPU {rec['cpu_model']}")
 
 
 def config(extra=None):
@@ -141,17 +186,20 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     W, Kst = args.warmup, args.steps
-    res = run_cpu_sample(W + Kst)
+    # each step one oracle solve at level 4, unless W + K of them would not
+    # finish within about four minutes: then at level 3 (29,791 DoFs)
+    level = CPU_SAMPLE_LEVEL if (W + Kst) * REF_STEP_S_LEVEL4 <= REF_STEP_BUDGET_S else 3
+    res = run_cpu_sample(W + Kst, level)
     t = res["times"][W:]
+    res_t = dict(res, times=t)
     n = res["n"]
     value = n / statistics.mean(t)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s",
             "n_gpus": args.gpus, "steps": Kst, "warmup": W,
             "ms_per_step": 1e3 * statistics.mean(t), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config({"sample": f"level {CPU_SAMPLE_LEVEL} ({n} DoFs)"}),
-            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                             "sample": sample_desc(n, Kst)},
+            "config": config({"sample": f"level {level} ({n} DoFs)"}),
+            "cpu_baseline": cpu_baseline_entry(res_t, value, best=False),
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -233,7 +281,7 @@ class ClockSampler:
 def main():
     args = parse()
     if args.cpu_worker:
-        cpu_worker(args.repeats)
+        cpu_worker(args.repeats, args.cpu_level)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -247,7 +295,7 @@ def main():
     # the oracle's host sample runs first, in a fresh process, before any CUDA call
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_sample(CPU_SAMPLE_REPEATS)
+        cpu = run_cpu_sample(CPU_SAMPLE_REPEATS, CPU_SAMPLE_LEVEL)
 
     import torch
     torch.cuda.set_device(local)
@@ -257,9 +305,16 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2405_19004_gb300 as vps
-    from paper_2405_19004_gb300.studies import (SMEM_BW, smoother_flops_per_patch,
-                                                smoother_smem_words_per_patch)
+    from paper_2405_19004_gb300.studies import (device_peaks, fp32_peak, mixed_precision_solve,
+                                                smem_bandwidth, smoother_flops_per_patch,
+                                                smoother_point, smoother_smem_words_per_patch)
     from synthetic import uniform_vector
+
+    # roofline denominators of this device: SM count, maximum SM clock, and the
+    # measured FP32 / FP64 multiply-add throughput (vps_fma_peak)
+    peaks = device_peaks(vps, torch)
+    props = torch.cuda.get_device_properties(local)
+    peaks["sm_count_torch"] = props.multi_processor_count
 
     P = vps.Poisson(D, K, L, precision=vps.VPS_FP32, smoother=vps.VPS_MULTIPLICATIVE)
     P.vps_autotune(args.tune_cache)  # timed trials on this GPU, before the timed region
@@ -375,8 +430,13 @@ def main():
     var_L = P.vps_get_smooth_variant(L)[0]
     bnd_L = var_L // 3 >= 1
     flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / 8.0
-    smem_roof_tflops = SMEM_BW * smoother_flops_per_patch(D, K, bnd_L) / (
-        4.0 * smoother_smem_words_per_patch(D, K, bnd_L)) / 1e12
+    # FP32 peak from the unit counts and the device's maximum SM clock; the
+    # shared-memory roofline of Section 4.3 at the SM clock sampled under load
+    fp32_peak_tflops = fp32_peak(peaks["sm_count"], peaks["sm_max_mhz"]) / 1e12
+    smem_mhz = clocks.get("sm_mhz") or peaks["sm_max_mhz"]
+    smem_words = smoother_smem_words_per_patch(D, K, bnd_L)
+    smem_roof_tflops = smem_bandwidth(peaks["sm_count"], smem_mhz) * smoother_flops_per_patch(
+        D, K, bnd_L) / (4.0 * smem_words) / 1e12
     achieved = flops_per_launch / t_launch / 1e12
     t_smooth_step = 8 * t_launch
 
@@ -408,14 +468,24 @@ def main():
         bnd64 = P64.vps_get_smooth_variant(L)[0] // 3 >= 1
         f64 = smoother_flops_per_patch(D, K, bnd64) * n_patches / t64_step / 1e12
         dx = (x64 - x).abs().max().item() / x64.abs().max().item()
+        f64_peak = peaks["fp64_fma_measured_flops"] / 1e12
         extras = {
             "time_to_1e-10_s": {"fp32_mg": t_step, "fp64": min(t64), "speedup": min(t64) / t_step},
             "iterations": {"fp32_mg": its[-1], "fp64": it64},
             "fp32_vs_fp64_solution_rel_maxdiff": dx,
             "smoother_fp64": {"dof_per_s": N / t64_step, "tflops": f64,
-                              "frac_of_fp64_peak": f64 / FP64_PEAK_TFLOPS,
-                              "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"},
+                              "frac_of_fp64_peak": f64 / f64_peak, "peak_tflops": f64_peak,
+                              "peak_source": "measured FP64 multiply-add throughput (vps_fma_peak)"},
         }
+        # one point of the degree sweep at about 1e8 DoFs (3D Q4 on 2^7 cells,
+        # 1.35e8 DoFs), FP32 and FP64, 20 smoothing steps each
+        extras["smoother_3d_q4_l7"] = [
+            smoother_point(vps, torch, 3, 4, 7, prec, 20, peaks, True, args.tune_cache)
+            for prec in (vps.VPS_FP32, vps.VPS_FP64)]
+        # the mixed-precision setting: 3D Q3 on 2^7 cells, manufactured sine, 2/2
+        # smoothing, FP32 V-cycle in FP64 CG against the FP64 V-cycle, to 1e-10
+        extras["mixed_precision_3d_q3_l7"] = mixed_precision_solve(vps, torch, 7, 3,
+                                                                   args.tune_cache)
         # full multigrid (Algorithm 2) as a standalone solver, f = 1, tol 1e-9: the
         # setting of the paper's iteration-count tables
         fmg = {}
@@ -518,19 +588,26 @@ def main():
         "config": config({"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                           "autotuned": tuned}),
         "iterations": its[-1], "rel_residual": rel,
+        "peaks": peaks,
         "smoother_fp32": {"dof_per_s": N / t_smooth_step, "tflops": achieved,
-                          "frac_of_fp32_peak": achieved / FP32_PEAK_TFLOPS,
+                          "frac_of_fp32_peak": achieved / fp32_peak_tflops,
+                          "frac_of_measured_fma_peak":
+                              achieved / (peaks["fp32_fma_measured_flops"] / 1e12),
                           # shared-memory roofline R = B F / (d_r + d_w) (Section 4.3),
-                          # B = 152 SMs x 32 banks x 4 B x 2.07 GHz, the kernel's own
-                          # shared-memory words per patch
+                          # B = SMs x 32 banks x 4 B x the SM clock sampled under load,
+                          # d_r + d_w = the kernel's modelled shared-memory words per patch
                           "frac_of_smem_roofline": achieved / smem_roof_tflops,
-                          "smem_roofline_tflops": smem_roof_tflops},
+                          "smem_roofline_tflops": smem_roof_tflops,
+                          "smem_roofline_clock_mhz": smem_mhz,
+                          "smem_words_per_patch_model": smem_words},
         "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level, "
                                + ("Boundary" if bnd_L else "fused") + f" variant {var_L}",
-                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                      "traffic": smoother_traffic(var_L),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "peak_source": f"{peaks['sm_count']} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                    f"flop x {peaks['sm_max_mhz']:g} MHz ({peaks['sm_max_mhz_source']})"
+                                    "; measured FMA throughput in peaks.fp32_fma_measured_flops",
                      "avg_launch_us": 1e6 * t_launch, "flops_per_launch": flops_per_launch},
         "e2e": {"value": world * N / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N},
@@ -538,9 +615,7 @@ def main():
         "clocks": clocks,
     }
     if cpu is not None:
-        cpu_v = cpu["n"] / statistics.mean(cpu["times"])
-        line["cpu_baseline"] = {"value": cpu_v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                                "sample": sample_desc(cpu["n"], len(cpu["times"]))}
+        line["cpu_baseline"] = cpu_baseline_entry(cpu, cpu["n"] / min(cpu["times"]))
     line.update(extras)
     print(json.dumps(line))
     if dist is not None:

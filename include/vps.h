@@ -158,8 +158,14 @@ int vps_vcycle(vps_handle h, const void* b, void* x);
  * coefficients), with VPS_ENOCONV otherwise.
  * b, x: compact DOUBLE device vectors.  iters / rel_res (host pointers, may
  * be NULL) receive the iteration count and the final FP64 relative
- * residual ||r||/||b||.  Synchronises the stream once per iteration to read
- * the residual norm.  Errors: VPS_ENOCONV, VPS_EBREAKDOWN, ...
+ * residual ||r||/||b||.  The first iteration is issued from the host; on a
+ * handle with CUDA graphs enabled (a stream was given, see vps_set_graphs)
+ * the later iterations run on the device as one graph whose conditional
+ * while-node repeats the iteration until r.r <= (rtol ||b||)^2, max_it or a
+ * breakdown (no host round trip per iteration); without graphs the host
+ * issues every iteration and synchronises once per iteration to read r.r.
+ * The host synchronises again for each FP64 residual check.  Errors:
+ * VPS_ENOCONV, VPS_EBREAKDOWN, ...
  */
 int vps_solve(vps_handle h, const double* b, double* x, double rtol, int max_it,
               int* iters, double* rel_res);
@@ -353,17 +359,25 @@ int vps_set_graphs(vps_handle h, int enable);
  *   dim, degree, level, precision, damping: as for vps_create; b, x: device
  *   vectors in the level layout of `level` (float for VPS_FP32, double for
  *   VPS_FP64), caller-owned, distinct.  cuda_stream: the stream to run on.
- *   Scratch: the residual and the eigenvalue table live in one static device
- *   array of 32 MiB inside the library; a level whose residual needs more
- *   than 32 MiB - 32 KiB (for example 3D Q4 on more than 2^5 cells per
- *   direction) is rejected with VPS_EINVAL and a message.  The array stays
- *   allocated on every GPU that loaded the library until the process exits.
- *   The first call on a device (with that device current) looks up the
- *   array's device address and uploads the degree's constant tables; make
- *   that first call before any stream capture begins.  Every call shares
- *   the array and overwrites it: calls whose work overlaps on one GPU race,
- *   so issue them in one stream or order them.  Errors: VPS_EINVAL,
- *   VPS_ECUDA; message via vps_last_error(NULL).
+ *   Scratch: the residual lives in a static device array of 32 MiB inside
+ *   the library, and the tables of 1/(sum of eigenvalues) in a second static
+ *   array of 66,048 bytes (one slot per dimension, degree and precision).
+ *   A level whose residual needs more than 32 MiB (for example 3D Q4 on
+ *   more than 2^5 cells per direction) is rejected with VPS_EINVAL and a
+ *   message before any CUDA call; the size is computed in floating point,
+ *   so levels whose element count would overflow an integer are rejected
+ *   too.  Both arrays stay allocated on every GPU that loaded the library
+ *   until the process exits.
+ *   Set-up: the first call on a device (with that device current) looks up
+ *   both arrays' device addresses; the first call of each (dim, degree,
+ *   precision) on a device also uploads that degree's constant tables and
+ *   fills its eigenvalue-table slot with synchronous copies.  Make those
+ *   first calls before any stream capture begins.  Later calls of a shape
+ *   issue kernels only, on cuda_stream.
+ *   Every call shares the residual array and overwrites it (nothing in it
+ *   has to start at zero): calls whose work overlaps on one GPU race, so
+ *   issue them in one stream or order them.  Errors: VPS_EINVAL, VPS_ECUDA;
+ *   message via vps_last_error(NULL).
  */
 int vps_smooth_additive_static(int dim, int degree, int level, int precision, double damping,
                                const void* b, void* x, void* cuda_stream);
@@ -408,6 +422,21 @@ const char* vps_server_last_error(vps_server s);
 /* Stops the engine thread (requests still running are abandoned) and frees
  * every slot. */
 int vps_server_destroy(vps_server s);
+
+/*
+ * vps_fma_peak -- measured multiply-add throughput of the GPU's FP32 or FP64
+ * pipe, the denominator of the smoother's fraction of arithmetic peak (the
+ * paper quotes its kernels as a fraction of the CUDA-core peak, Section 4.3).
+ * Not part of the method.  Runs a kernel of independent multiply-add chains
+ * on every SM (8 blocks of 256 threads per SM) twice after one warm-up
+ * launch on cuda_stream, timed with CUDA events; synchronises the stream.
+ * precision: VPS_FP32 or VPS_FP64.  flops_per_s (host, required) receives
+ * 2 x multiply-adds / seconds of the faster timed launch; seconds and
+ * sm_count (host, may be NULL) its duration and the device's multiprocessor
+ * count.  Allocates nothing.  Errors: VPS_EINVAL, VPS_ECUDA.
+ */
+int vps_fma_peak(int precision, double* flops_per_s, double* seconds, int* sm_count,
+                 void* cuda_stream);
 
 /* vps_last_error -- message of the last failure on h (h = NULL: the last
  * failure of vps_create or vps_smooth_additive_static on this thread).

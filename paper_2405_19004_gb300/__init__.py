@@ -80,6 +80,7 @@ SIGNATURES = {
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
     "vps_check_fp_conversions": (_i, [_p, ctypes.c_int64, _i64p, _p]),
+    "vps_fma_peak": (_i, [_i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i), _p]),
 }
 
 _lib = None
@@ -134,6 +135,18 @@ def vps_smooth_additive_static(dim, degree, level, precision, damping, b, x, str
     rc = lib().vps_smooth_additive_static(dim, degree, level, precision, float(damping), _ptr(b),
                                           _ptr(x), ctypes.c_void_p(stream.cuda_stream))
     return _check(rc, None)
+
+
+def vps_fma_peak(precision, stream):
+    """Measured FP32 / FP64 multiply-add throughput: (flop/s, seconds of the
+    timed launch, multiprocessor count)."""
+    f = ctypes.c_double()
+    t = ctypes.c_double()
+    sm = ctypes.c_int()
+    rc = lib().vps_fma_peak(precision, ctypes.byref(f), ctypes.byref(t), ctypes.byref(sm),
+                            ctypes.c_void_p(stream.cuda_stream))
+    _check(rc, None)
+    return f.value, t.value, sm.value
 
 
 def vps_check_fp_conversions(patterns, stream):

@@ -1121,14 +1121,17 @@ int create_own_stream(int dim, int degree, int level, int precision, vps_handle*
 }
 
 size_t estimate_device_bytes(int dim, int degree, int level, int precision) {
-  const size_t esz = precision == VPS_FP64 ? 8 : 4;
-  size_t total = 0;
-  for (int l = 1; l <= level; ++l) total += 3 * (size_t)make_geom(dim, degree, l).total * esz;
-  const LevelGeom g = make_geom(dim, degree, level);
-  const size_t ni = g.n1 - 2;
-  total += 7 * (size_t)g.total * 8 + 2 * (dim == 3 ? ni * ni * ni : ni * ni) * 8;
-  if (precision == VPS_FP32) total += 2 * (size_t)g.total * 4;  // double-float split of p
-  return total + (size_t)(4 << 20);  // tables, coarse-level data, scalars
+  // in floating point: a level too large to address gives SIZE_MAX (it can
+  // never fit a budget) instead of a wrapped product
+  const double esz = precision == VPS_FP64 ? 8 : 4;
+  double total = 0;
+  for (int l = 1; l <= level; ++l) total += 3 * level_elements(dim, degree, l) * esz;
+  const double elems = level_elements(dim, degree, level);
+  const double ni = (double)degree * std::ldexp(1.0, level) - 1.0;
+  total += 7 * elems * 8 + 2 * (dim == 3 ? ni * ni * ni : ni * ni) * 8;
+  if (precision == VPS_FP32) total += 2 * elems * 4;  // double-float split of p
+  total += (double)(4 << 20);                         // tables, coarse-level data, scalars
+  return total < 1.8e19 ? (size_t)total : SIZE_MAX;
 }
 
 // Starts a CG solve of the sine-mode right-hand side on h without waiting.
@@ -1384,10 +1387,10 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   if (n_pre < 0 || n_post < 0 || n_pre > 64 || n_post > 64)
     return fail(nullptr, VPS_EINVAL, "n_pre/n_post must be 0..64");
   {
-    const LevelGeom g = make_geom(dim, degree, level);
-    if ((double)g.total > 2147483647.0)
-      return fail(nullptr, VPS_EINVAL, "level %d too large: %lld elements per vector", level,
-                  (long long)g.total);
+    const double elems = level_elements(dim, degree, level);
+    if (!(elems <= 2147483647.0))
+      return fail(nullptr, VPS_EINVAL, "level %d too large: %.4g elements per vector", level,
+                  elems);
   }
   register_all();
   vps_context* h = new vps_context();

@@ -890,3 +890,88 @@ extern "C" int vps_check_fp_conversions(const void* patterns, int64_t n, int64_t
   for (int j = 0; j < 3; ++j) mismatches[j] = (int64_t)host[j];
   return VPS_OK;
 }
+
+// ------------------------------------------------------- FMA throughput
+namespace vps {
+namespace {
+
+// Sink of the throughput kernel: written only when the accumulators take a
+// value they never take, so that the compiler keeps every multiply-add.
+__device__ double g_fma_sink;
+
+constexpr int kFmaChains = 8;   // independent accumulators per thread
+constexpr int kFmaUnroll = 16;  // multiply-adds per chain and loop trip
+
+// kFmaChains x kFmaUnroll dependent-free multiply-adds per trip: x = x a + c
+// with |a| < 1, so the values stay bounded.  Every multiply-add is one FMA
+// instruction of the type's pipe.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_throughput_kernel(int trips, T a, T c) {
+  T x[kFmaChains];
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) x[j] = (T)(threadIdx.x + j);
+  for (int i = 0; i < trips; ++i) {
+#pragma unroll
+    for (int u = 0; u < kFmaUnroll; ++u)
+#pragma unroll
+      for (int j = 0; j < kFmaChains; ++j) x[j] = fma(x[j], a, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) s += x[j];
+  if (s == (T)-1.2345e30) g_fma_sink = (double)s;
+}
+
+}  // namespace
+}  // namespace vps
+
+extern "C" int vps_fma_peak(int precision, double* flops_per_s, double* seconds,
+                            int* sm_count, void* cuda_stream) {
+  using namespace vps;
+  set_thread_error("");
+  char buf[256];
+  if (!flops_per_s || (precision != VPS_FP32 && precision != VPS_FP64)) {
+    set_thread_error("vps_fma_peak: flops_per_s must be non-NULL, precision VPS_FP32 or VPS_FP64");
+    return VPS_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // 8 blocks of 256 threads per SM (2048 threads: every warp slot busy);
+  // trips chosen for tens of milliseconds per launch
+  const int blocks = 8 * (sms > 0 ? sms : 1);
+  const int trips = precision == VPS_FP32 ? 16384 : 512;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.0f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // launch 0 warms up
+    if (rep > 0) e = cudaEventRecord(e0, s);
+    if (e != cudaSuccess) break;
+    if (precision == VPS_FP32)
+      fma_throughput_kernel<float><<<blocks, 256, 0, s>>>(trips, 0.9999999f, 1e-7f);
+    else
+      fma_throughput_kernel<double><<<blocks, 256, 0, s>>>(trips, 0.9999999, 1e-7);
+    VPS_COUNT_LAUNCH();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && rep > 0) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess && rep > 0) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess && rep > 0) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (ms == 0.0f || t < ms)) ms = t;  // best of two
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess || !(ms > 0.0f)) {
+    snprintf(buf, sizeof(buf), "vps_fma_peak: %s",
+             e != cudaSuccess ? cudaGetErrorString(e) : "no time measured");
+    set_thread_error(buf);
+    return VPS_ECUDA;
+  }
+  const double flops = 2.0 * blocks * 256.0 * trips * kFmaUnroll * kFmaChains;
+  *flops_per_s = flops / (ms * 1e-3);
+  if (seconds) *seconds = ms * 1e-3;
+  if (sm_count) *sm_count = sms;
+  return VPS_OK;
+}

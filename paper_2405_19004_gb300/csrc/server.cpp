@@ -257,6 +257,9 @@ int vps_server_submit(vps_server s, int dim, int degree, int level, int n_modes,
   if (!s || !id || n_modes < 1 || n_modes > 4096 || !coef || !freq || (dim != 2 && dim != 3) ||
       degree < 1 || degree > VPS_MAX_DEGREE || level < 1 || level > 24)
     return VPS_EINVAL;
+  // the same size limit as vps_create (checked in floating point, before
+  // any product below can overflow)
+  if (!(vps::level_elements(dim, degree, level) <= 2147483647.0)) return VPS_EINVAL;
   Request r;
   r.d = dim;
   r.k = degree;

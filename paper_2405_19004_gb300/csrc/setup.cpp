@@ -336,9 +336,22 @@ bool build_global_fd(int k, int level, std::vector<double>* S, std::vector<doubl
   return true;
 }
 
+double level_elements(int dim, int k, int level) {
+  if (level < 0 || level > 30 || k < 1 || k > kMaxK || (dim != 2 && dim != 3)) return HUGE_VAL;
+  const double n1 = (double)k * std::ldexp(1.0, level) + 1.0;
+  const double px = std::ceil(n1 / 8.0) * 8.0;
+  return dim == 2 ? px * n1 : px * n1 * n1;
+}
+
 LevelGeom make_geom(int dim, int k, int level) {
   LevelGeom g;
   g.dim = dim; g.k = k; g.level = level;
+  // every caller checks level_elements (or the saturated total below)
+  // before it uses a level: no product here may overflow
+  if (!(level_elements(dim, k, level) <= kMaxLevelElements)) {
+    g.total = INT64_MAX;
+    return g;
+  }
   g.ncell = 1 << level;
   g.n1 = k * g.ncell + 1;
   g.px = (g.n1 + 7) / 8 * 8;

@@ -75,6 +75,17 @@ struct LevelGeom {
   double h = 0.0;
 };
 
+// Elements of a level vector (pitched rows, boundary included), computed in
+// floating point: finite and exact for every valid (dim, k, level), HUGE_VAL
+// for invalid arguments, and never wrapped, so comparing it with a limit
+// rejects levels whose size does not fit in 64-bit integers.
+double level_elements(int dim, int k, int level);
+// Largest level vector the library addresses (every index fits in int64 and
+// the products in make_geom cannot overflow).
+constexpr double kMaxLevelElements = 4.0e18;
+
+// Geometry of a level.  A level with more than kMaxLevelElements elements
+// gets total = INT64_MAX and no other field set: callers reject it.
 LevelGeom make_geom(int dim, int k, int level);
 
 // Patches of one colour on one level.

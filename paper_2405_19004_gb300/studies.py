@@ -7,10 +7,12 @@ sweep -- smoother-only degree sweep: Q_k for k = 1..7 in 3D and 2D, the mesh
     level whose DoF count is closest (log scale) to 1e8 (3D) or 2.5e8 (2D),
     seeded N(0,1) vectors, FP32 and FP64, 20 multiplicative smoothing steps
     per point timed with CUDA events after two warm-up steps.  Reported:
-    DoF/s, algorithmic GFLOP/s and their fraction of the FP32 / FP64 peak and
-    of the shared-memory roofline R = B F / (d_r + d_w) of Section 4.3 (Eq.
-    4.3), B = 152 SMs x 32 banks x 4 bytes x 2.07 GHz, with the kernel's own
-    shared-memory words per patch.
+    DoF/s, algorithmic GFLOP/s and their fraction of the FP32 / FP64 peak
+    (measured by vps_fma_peak on the same GPU) and of the shared-memory
+    roofline R = B F / (d_r + d_w) of Section 4.3 (Eq. 4.3), B = SMs x 32
+    banks x 4 bytes x SM clock, with the kernel's own shared-memory words per
+    patch (a model of the kernel's accesses; ncu's shared-memory byte
+    counters are recorded beside it under profiles/).
 mixed -- mixed precision (Section 4.2): 3D Q3 on 2^7 cells per direction,
     manufactured solution u = prod sin(pi x_t), two pre- and two
     post-smoothing steps, autotuned and graph-captured FP32 V-cycle inside
@@ -26,9 +28,38 @@ import json
 import math
 import time
 
-FP32_PEAK = 152 * 128 * 2 * 2.07e9      # flop/s, FP32 pipe at the maximum SM clock
-FP64_PEAK = 1.25e12                      # flop/s, nominal GB300 FP64
-SMEM_BW = 152 * 32 * 4 * 2.07e9          # bytes/s, shared memory (banks x word x clock)
+FP32_LANES_PER_SM = 128                  # FP32 FMA lanes per SM
+
+
+def fp32_peak(sm_count, sm_mhz):
+    """FP32 CUDA-core peak in flop/s from the unit counts and the clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+
+
+def smem_bandwidth(sm_count, sm_mhz):
+    """Shared-memory bandwidth of Section 4.3: SMs x 32 banks x 4 bytes x clock."""
+    return sm_count * 32 * 4 * sm_mhz * 1e6
+
+
+def device_peaks(vps, torch):
+    """SM count, the SM clock the device reports as its maximum (nvidia-smi;
+    2070 MHz if unavailable) and the measured FP32 / FP64 multiply-add
+    throughput (vps_fma_peak) of the current device."""
+    import subprocess
+    stream = torch.cuda.current_stream()
+    f32, _, sms = vps.vps_fma_peak(vps.VPS_FP32, stream)
+    f64, _, _ = vps.vps_fma_peak(vps.VPS_FP64, stream)
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(torch.cuda.current_device())],
+                             capture_output=True, text=True, timeout=20).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except Exception:
+        mhz = None
+    return {"sm_count": sms, "sm_max_mhz": mhz or 2070.0, "sm_max_mhz_source":
+            "nvidia-smi clocks.max.sm" if mhz else "assumed 2070 MHz",
+            "fp32_fma_measured_flops": f32, "fp64_fma_measured_flops": f64}
 
 
 def smoother_flops_per_patch(d, k, boundary=False):
@@ -74,75 +105,89 @@ def level_for(d, k, target):
     return best
 
 
+def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cache=None,
+                   seed=None):
+    """Times `apps` multiplicative smoothing steps of Q_k on level L (after two
+    warm-up steps) and returns the measurement row."""
+    P = vps.Poisson(d, k, L, precision=prec)
+    if tune:
+        P.vps_autotune(tune_cache)
+    N = P.n_interior()
+    gen = torch.Generator(device="cuda").manual_seed(2 + k if seed is None else seed)
+    b = P.empty_level()
+    x = P.empty_level()
+    P.vps_pack(L, torch.randn(N, generator=gen, device="cuda", dtype=P.dtype), b)
+    P.vps_pack(L, torch.randn(N, generator=gen, device="cuda", dtype=P.dtype), x)
+    P.vps_smooth(L, b, x, 2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(P.stream)
+    P.vps_smooth(L, b, x, apps)
+    e1.record(P.stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / apps
+    patches = (2 ** L - 1) ** d
+    var, ppb = P.vps_get_smooth_variant(L)
+    bnd = var // 3 >= 1
+    fpp = smoother_flops_per_patch(d, k, bnd)
+    flops = fpp * patches
+    esz = 4 if prec == vps.VPS_FP32 else 8
+    intensity = fpp / (esz * smoother_smem_words_per_patch(d, k, bnd))
+    roof_smem = smem_bandwidth(peaks["sm_count"], peaks["sm_max_mhz"]) * intensity
+    fp32 = prec == vps.VPS_FP32
+    derived = fp32_peak(peaks["sm_count"], peaks["sm_max_mhz"]) if fp32 else None
+    measured = peaks["fp32_fma_measured_flops" if fp32 else "fp64_fma_measured_flops"]
+    row = {"dim": d, "degree": k, "level": L, "precision": "fp32" if fp32 else "fp64",
+           "dofs": N, "ms_per_step": 1e3 * t, "dof_per_s": N / t, "gflops": flops / t / 1e9,
+           "frac_of_measured_fma_peak": flops / t / measured,
+           "frac_smem_roofline": flops / t / roof_smem, "smem_roofline_tflops": roof_smem / 1e12,
+           "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb}
+    if derived:
+        row["frac_of_fp32_peak"] = flops / t / derived
+    P.close()
+    del b, x
+    torch.cuda.empty_cache()
+    return row
+
+
 def sweep(args):
     import torch
     import paper_2405_19004_gb300 as vps
-    from synthetic import normal_vector
+    peaks = device_peaks(vps, torch)
+    print(json.dumps({"peaks": peaks}), flush=True)
     rows = []
     for d in args.dims:
         target = 1e8 if d == 3 else 2.5e8
         for k in args.degrees:
             L = level_for(d, k, target)
-            for prec, name in ((vps.VPS_FP32, "fp32"), (vps.VPS_FP64, "fp64")):
-                P = vps.Poisson(d, k, L, precision=prec)
-                if args.tune:
-                    P.vps_autotune(args.tune_cache)
-                N = P.n_interior()
-                gen = torch.Generator(device="cuda").manual_seed(2 + k)
-                b = P.empty_level()
-                x = P.empty_level()
-                P.vps_pack(L, torch.randn(N, generator=gen, device="cuda", dtype=P.dtype), b)
-                P.vps_pack(L, torch.randn(N, generator=gen, device="cuda", dtype=P.dtype), x)
-                P.vps_smooth(L, b, x, 2)
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(P.stream)
-                P.vps_smooth(L, b, x, args.apps)
-                e1.record(P.stream)
-                torch.cuda.synchronize()
-                t = e0.elapsed_time(e1) / 1e3 / args.apps
-                patches = (2 ** L - 1) ** d
-                var, ppb = P.vps_get_smooth_variant(L)
-                bnd = var // 3 >= 1
-                fpp = smoother_flops_per_patch(d, k, bnd)
-                flops = fpp * patches
-                esz = 4 if prec == vps.VPS_FP32 else 8
-                intensity = fpp / (esz * smoother_smem_words_per_patch(d, k, bnd))
-                roof_smem = SMEM_BW * intensity
-                peak = FP32_PEAK if prec == vps.VPS_FP32 else FP64_PEAK
-                row = {"dim": d, "degree": k, "level": L, "precision": name, "dofs": N,
-                       "ms_per_step": 1e3 * t, "dof_per_s": N / t, "gflops": flops / t / 1e9,
-                       "frac_fp_peak": flops / t / peak, "frac_smem_roofline": flops / t / roof_smem,
-                       "smem_roofline_tflops": roof_smem / 1e12,
-                       "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb}
+            for prec in (vps.VPS_FP32, vps.VPS_FP64):
+                row = smoother_point(vps, torch, d, k, L, prec, args.apps, peaks, args.tune,
+                                     args.tune_cache)
                 rows.append(row)
                 print(json.dumps(row), flush=True)
-                P.close()
-                del b, x
-                torch.cuda.empty_cache()
     return rows
 
 
-def mixed(args):
-    import torch
-    import paper_2405_19004_gb300 as vps
+def mixed_precision_solve(vps, torch, level=7, repeats=3, tune_cache=None):
+    """The mixed-precision setting of Section 4.2 on 3D Q3 (see the module
+    docstring); returns the record."""
     from synthetic import manufactured_sine
-    d, k, L = 3, 3, args.level
+    d, k, L = 3, 3, level
     coef, freq = manufactured_sine(d)
     out = {"workload": f"3D Q{k}, 2^{L} cells per direction, u = prod sin(pi x_t), 2 pre / 2 post "
                        "smoothing, CG to 1e-10"}
     sols = {}
     for prec, name in ((vps.VPS_FP32, "fp32_mg"), (vps.VPS_FP64, "fp64")):
         P = vps.Poisson(d, k, L, precision=prec, n_pre=2, n_post=2)
-        P.vps_autotune(args.tune_cache)
+        P.vps_autotune(tune_cache)
         N = P.n_interior()
         b = torch.zeros(N, dtype=torch.float64, device="cuda")
         P.vps_assemble_rhs_sines(coef, freq, b)
         x = torch.zeros_like(b)
         P.vps_solve(b, x, 1e-10, 100)  # warm-up (captures the graph)
         ts = []
-        for _ in range(args.repeats):
+        for _ in range(repeats):
             x.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -152,9 +197,18 @@ def mixed(args):
                      "l2_error": P.vps_l2_error_sine(x), "coarse_level": P.vps_get_coarse_level()}
         sols[name] = x.clone()
         P.close()
+        del b, x
+        torch.cuda.empty_cache()
     diff = (sols["fp32_mg"] - sols["fp64"]).abs().max().item() / sols["fp64"].abs().max().item()
     out["solution_rel_maxdiff"] = diff
     out["speedup_fp32_mg_over_fp64"] = out["fp64"]["time_to_1e-10_s"] / out["fp32_mg"]["time_to_1e-10_s"]
+    return out
+
+
+def mixed(args):
+    import torch
+    import paper_2405_19004_gb300 as vps
+    out = mixed_precision_solve(vps, torch, args.level, args.repeats, args.tune_cache)
     print(json.dumps(out), flush=True)
     return out
 

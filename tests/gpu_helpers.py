@@ -23,10 +23,21 @@ def oracle_prolongation(d, k, l):
 
 
 def rel_err(got, ref):
+    """The larger of the relative 2-norm error and the largest element error
+    relative to the largest element of ref: a single bad element cannot hide
+    under the norm of a long vector."""
     ref = np.asarray(ref, dtype=np.float64)
     got = np.asarray(got, dtype=np.float64)
-    den = np.linalg.norm(ref)
-    return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)
+    if ref.size == 0:
+        return 0.0 if got.size == 0 else np.inf
+    den2 = np.linalg.norm(ref)
+    deninf = np.max(np.abs(ref))
+    e = got - ref
+    if not np.all(np.isfinite(e)):
+        return np.inf
+    r2 = np.linalg.norm(e) / (den2 if den2 > 0 else 1.0)
+    rinf = np.max(np.abs(e)) / (deninf if deninf > 0 else 1.0)
+    return max(r2, rinf)
 
 
 def as_prec(v, prec):

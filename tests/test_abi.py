@@ -54,7 +54,7 @@ def test_binding_signatures_cover_the_header(lib):
     ((2, 2, 3, 0, 0, float("nan"), 1, 1), "damping"),
     ((2, 2, 3, 0, 0, 1.0, -1, 1), "n_pre"),
     ((3, 7, 11, 0, 0, 1.0, 1, 1), "too large"),
-])
+] + [((3, k, l, 0, 0, 1.0, 1, 1), "too large") for k in (1, 4, 7) for l in (19, 21, 24)])
 def test_create_rejects_invalid_arguments_without_touching_cuda(lib, args, needle):
     h = ctypes.c_void_p()
     rc = lib.vps_create(*args, None, ctypes.byref(h))
@@ -76,3 +76,21 @@ def test_no_cpu_fallback_in_the_package():
     for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(f).read()
         assert "import oracle" not in src and "from oracle" not in src, f
+
+
+@pytest.mark.parametrize("d,k,l,prec", [(3, 4, 6, 0), (2, 7, 10, 0), (3, 7, 6, 1)]
+                         + [(3, k, l, 0) for k in (1, 4, 7) for l in (19, 20, 21, 22, 23, 24)])
+def test_static_step_rejects_oversized_levels_before_any_cuda_call(lib, d, k, l, prec):
+    """Levels whose residual does not fit the static scratch, including those
+    whose element count overflows 64-bit integers (3D, levels 19..24), are
+    rejected by the size check that runs before any CUDA call.  Only run
+    without a GPU: the placeholder pointers are never dereferenced here, and
+    the GPU suite repeats the check with real device buffers."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("covered with device buffers by the GPU suite")
+    rc = lib.vps_smooth_additive_static(d, k, l, prec, 0.175, ctypes.c_void_p(16),
+                                        ctypes.c_void_p(32), None)
+    assert rc == -1
+    assert b"static scratch" in lib.vps_last_error(None)
+
