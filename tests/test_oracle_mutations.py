@@ -82,3 +82,39 @@ def test_same_order_post_smoothing_breaks_symmetry_pin():
     N = H.levels[3].N
     B = np.stack([H.vcycle(3, np.eye(N)[i]) for i in range(N)], axis=1)
     assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()
+
+
+def test_extra_smoothing_step_breaks_the_operator_pin():
+    """A V-cycle that smooths twice before the coarse correction no longer
+    equals Algorithm 1's product of error propagators."""
+    from test_oracle_multigrid import _patch_sets, _smoothing_propagator, _vcycle_matrix
+    H = multigrid.Hierarchy(2, 2, 3, symmetric=True)
+    H.n_pre = 2
+    B = None
+    for l in range(1, 4):
+        A = H.A[l].toarray()
+        if l == 1:
+            B = np.linalg.inv(A)
+            continue
+        sets = _patch_sets(2, 2, l)
+        S = _smoothing_propagator(A, sets, range(4))
+        Sr = _smoothing_propagator(A, sets, range(3, -1, -1))
+        P = H.P[l].toarray()
+        E = Sr @ (np.eye(len(A)) - P @ B @ P.T @ A) @ S
+        B = (np.eye(len(A)) - E) @ np.linalg.inv(A)
+    assert np.abs(_vcycle_matrix(H) - B).max() > 1e-6 * np.abs(B).max()
+
+
+def test_coarse_right_hand_side_on_too_few_levels_breaks_the_3d_count_pin(monkeypatch):
+    """Full multigrid whose nested iteration gets no right-hand side below the
+    finest level (its start is then zero) needs more V-cycles: the count the
+    two-sided 3D pin compares with Table 2 is sensitive to that mistake."""
+    f = lambda X: np.ones(len(X))
+    good = multigrid.fmg_iterations(3, 2, 3, f)
+    orig = assembly.load_vector
+
+    def zero_below_finest(level, ff):
+        b = orig(level, ff)
+        return b if level.l == 3 else 0.0 * b
+    monkeypatch.setattr(assembly, "load_vector", zero_below_finest)
+    assert multigrid.fmg_iterations(3, 2, 3, f) > good
