@@ -387,13 +387,22 @@ int vps_smooth_additive_static(int dim, int degree, int level, int precision, do
  * the paper).  A server owns an engine thread on the device current at
  * creation.  Requests wait in a queue and are admitted as solver slots
  * (at most max_active at a time) and device memory (memory_budget bytes)
- * become free; a slot is a handle on a stream of its own whose level
- * hierarchy stays resident for later requests of the same (dim, degree,
- * level); idle slots are evicted least recently used first.  Every admitted
- * request runs vps_solve's CG one iteration at a time, so requests overlap
- * on the GPU.  precision: VPS_FP32 (FP32 V-cycle, FP64 CG) or VPS_FP64.
- * A request's result depends only on its own data: it is the same alone
- * and in a mix.
+ * become free; a slot is a handle whose level hierarchy stays resident for
+ * later requests of the same (dim, degree, level); idle slots are evicted
+ * least recently used first.  Admitted requests of one (dim, degree) form a
+ * cohort on one CUDA stream: each runs vps_solve's CG as an asynchronous
+ * state machine, and whenever none of the cohort's work is in flight the
+ * engine runs the V-cycles of all members that wait for one together --
+ * the colour passes, restrictions and prolongations of all their levels as
+ * persistent kernels that take tiles from a device-side queue, one launch
+ * per smoothing colour or transfer step -- and then the rest of each
+ * member's iteration.  Requests join their cohort between these steps;
+ * cohorts run concurrently.  precision: VPS_FP32 (FP32 V-cycle, FP64 CG)
+ * or VPS_FP64.  A request's result depends only on its own data: every
+ * level of it goes through the operations of its own V-cycle in the same
+ * order, so it is the same alone and in a mix.  Besides the budget, each
+ * cohort holds 4 MiB of device memory (and 4 MiB of pinned host memory)
+ * for its queues.
  */
 typedef struct vps_server_ctx* vps_server;
 
@@ -419,6 +428,13 @@ int vps_server_query(vps_server s, int64_t id, int* state, int* status, int* ite
 int vps_server_wait(vps_server s, int64_t id, double timeout_s);
 int vps_server_stats(vps_server s, int64_t* submitted, int64_t* done, int* active, int* queued);
 const char* vps_server_last_error(vps_server s);
+/* vps_server_batch_stats -- batching counters since creation: cohort V-cycle
+ * steps (ticks), batched launches, and the largest number of requests whose
+ * tiles one batched launch processed (max_requests_per_launch) or one tick
+ * served (max_requests_per_tick).  Host pointers, each may be NULL.
+ * Errors: VPS_EINVAL (s NULL). */
+int vps_server_batch_stats(vps_server s, int64_t* ticks, int64_t* batched_launches,
+                           int* max_requests_per_launch, int* max_requests_per_tick);
 /* Stops the engine thread (requests still running are abandoned) and frees
  * every slot. */
 int vps_server_destroy(vps_server s);

@@ -76,6 +76,7 @@ SIGNATURES = {
     "vps_server_wait": (_i, [_p, ctypes.c_int64, _d]),
     "vps_server_stats": (_i, [_p, _i64p, _i64p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_server_last_error": (ctypes.c_char_p, [_p]),
+    "vps_server_batch_stats": (_i, [_p, _i64p, _i64p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_server_destroy": (_i, [_p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
@@ -397,12 +398,15 @@ class Server:
         coef = np.ascontiguousarray(coef, dtype=np.float64)
         freq = np.ascontiguousarray(freq, dtype=np.int32)
         n = (degree * 2 ** level - 1) ** dim
-        x = np.zeros(n, dtype=np.float64)
+        # no host buffer for sizes the library rejects anyway (it checks the
+        # level before anything else)
+        x = np.zeros(n, dtype=np.float64) if n < 2 ** 31 else None
         rid = ctypes.c_int64()
         rc = lib().vps_server_submit(self.s, dim, degree, level, len(coef),
                                      coef.ctypes.data_as(ctypes.c_void_p),
                                      freq.ctypes.data_as(ctypes.c_void_p),
-                                     x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid))
+                                     None if x is None else x.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(rid))
         if rc != VPS_OK:
             raise VpsError(rc, "vps_server_submit")
         self._bufs[rid.value] = (x, coef, freq)
@@ -430,6 +434,16 @@ class Server:
         lib().vps_server_stats(self.s, ctypes.byref(sub), ctypes.byref(done), ctypes.byref(act),
                                ctypes.byref(q))
         return dict(submitted=sub.value, done=done.value, active=act.value, queued=q.value)
+
+    def batch_stats(self):
+        """Cohort V-cycle steps, batched launches, and the largest number of
+        requests in one batched launch / one step."""
+        t, bl = ctypes.c_int64(), ctypes.c_int64()
+        ml, mt = ctypes.c_int(), ctypes.c_int()
+        _check(lib().vps_server_batch_stats(self.s, ctypes.byref(t), ctypes.byref(bl),
+                                            ctypes.byref(ml), ctypes.byref(mt)), None)
+        return dict(ticks=t.value, batched_launches=bl.value, max_requests_per_launch=ml.value,
+                    max_requests_per_tick=mt.value)
 
     def last_error(self):
         return lib().vps_server_last_error(self.s).decode()

@@ -5,7 +5,9 @@
 // file only validates arguments, owns device memory, sequences launches on
 // the handle's stream and, on non-default streams, captures the V-cycle
 // into a CUDA graph that is replayed on every later call.
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -143,6 +145,13 @@ struct vps_context {
   void* ainv = nullptr;                 // A_j^-1 (symmetric, m^d x m^d), working precision
   // asynchronous CG (used by the serving loop)
   int as_phase = 0;                     // 0 idle, 1 iteration in flight, 2 result copy in flight
+  // the V-cycles of the asynchronous CG are run by the caller (cohort_vcycle,
+  // batched with other handles) instead of by the handle itself: the CG then
+  // stops before each V-cycle with as_need = 3 (first iteration), 1 (restart
+  // from the FP64 residual) or 2 (next iteration), and cg_async_resume issues
+  // the rest of the iteration once the caller has run the V-cycle
+  bool as_external = false;
+  int as_need = 0;
   int as_it = 0, as_maxit = 0, as_status = 0;
   int as_verify = 0;                    // 1: FP64 residual in flight, 2: |A||x| in flight
   double as_true = 0.0;                 // FP64 residual while |A||x| is in flight
@@ -1162,11 +1171,34 @@ int cg_async_begin(vps_handle h, int n_modes, const double* coef, const int* fre
   VPS_CK(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double), h->stream));
   VPS_CK(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+  if (h->as_external) {  // the caller runs the first V-cycle, then cg_async_resume
+    h->as_need = 3;
+    h->as_phase = 1;
+    return VPS_OK;
+  }
   if (int rc = precondition(h)) return rc;
   if (int rc = cg_async_iteration(h, true)) return rc;
   h->as_phase = 1;
   return VPS_OK;
 }
+
+// After the caller's V-cycle (z = B r in xv[L] or czn): the rest of the
+// pending iteration of an asynchronous CG with external V-cycles.
+int cg_async_resume(vps_handle h) {
+  if (!h->as_external || h->as_need == 0) return fail(h, VPS_EINVAL, "no V-cycle pending");
+  if (int rc = set_device(h)) return rc;
+  LaunchTally tally(h);
+  const int need = h->as_need;
+  h->as_need = 0;
+  if (need == 1) VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
+  if (int rc = cg_async_iteration(h, need != 2)) return rc;
+  if (need != 3) ++h->as_it;
+  return VPS_OK;
+}
+
+int cg_async_pending_vcycle(vps_handle h) { return h->as_external && h->as_need != 0; }
+
+void set_external_vcycle(vps_handle h, bool on) { h->as_external = on; }
 
 // Advances an asynchronous solve if its pending GPU work has finished.
 // *done = 1 when the solution is in host_x (then *status, *iters, *rel).
@@ -1174,6 +1206,7 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
                   const double** x_host) {
   *done = 0;
   if (h->as_phase == 0) return fail(h, VPS_EINVAL, "no solve in flight");
+  if (h->as_need) return VPS_OK;  // waiting for the caller's V-cycle
   const cudaError_t q = cudaEventQuery(h->as_ev);
   if (q == cudaErrorNotReady) return VPS_OK;
   if (q != cudaSuccess) return fail(h, VPS_ECUDA, "solve: %s", cudaGetErrorString(q));
@@ -1229,6 +1262,10 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
     return VPS_OK;
   }
   if (h->as_it >= h->as_maxit) return cg_async_finish(h, VPS_ENOCONV);
+  if (h->as_external) {  // the caller runs the V-cycle, then cg_async_resume
+    h->as_need = restart ? 1 : 2;
+    return VPS_OK;
+  }
   if (int rc = precondition(h)) return rc;
   if (restart) {  // from the FP64 residual, which is still above the tolerance
     VPS_CK(h, cudaMemsetAsync(h->sc, 0, sizeof(CgScalars), h->stream));
@@ -1238,6 +1275,243 @@ int cg_async_poll(vps_handle h, int* done, int* status, int* iters, double* rel,
   }
   ++h->as_it;
   return VPS_OK;
+}
+
+
+namespace {
+
+// Host side of one cohort V-cycle's queues: packed one after another in a
+// pinned staging buffer, copied to the device in one transfer before the
+// launches that read them.
+struct QueueWriter {
+  unsigned char* host;
+  unsigned char* dev;
+  size_t cap, used = 0;
+  int64_t launches = 0;
+  int max_items = 0;
+  BatchQueue* open(size_t* off) {
+    const size_t sz = sizeof(BatchQueue);
+    if (used + sz > cap) return nullptr;
+    *off = used;
+    BatchQueue* q = reinterpret_cast<BatchQueue*>(host + used);
+    q->head = 0;
+    q->ntiles = 0;
+    q->nitems = 0;
+    q->pad_ = 0;
+    return q;
+  }
+  // closes queue q at offset off: only its header and nitems items are kept
+  void close(BatchQueue* q, size_t off) {
+    const size_t sz = offsetof(BatchQueue, items) + (size_t)q->nitems * sizeof(BatchItem);
+    used = off + (sz + 255) / 256 * 256;
+    max_items = std::max(max_items, q->nitems);
+  }
+  BatchQueue* dev_at(size_t off) const { return reinterpret_cast<BatchQueue*>(dev + off); }
+};
+
+// One recorded batched launch: kind 0 colour pass (variant v), 1
+// restriction (+ zeroed upper faces), 2 prolongation; or a per-member step
+// (kind 3 memset of x, 4 residual, 5 coarse solve, 6 FP32 cast) of member m
+// on level l.
+struct CohortOp {
+  int kind, v, m, l;
+  size_t off;
+  int64_t ntiles;
+  int nitems;
+};
+
+template <typename T>
+int cohort_vcycle_t(vps_context* const* hs, int n, QueueWriter* qw, cudaStream_t st) {
+  vps_context* h0 = hs[0];
+  const KernelFns<T>& F = fns<T>(h0);
+  const int nc = 1 << h0->dim;
+  std::vector<const T*> bL(n);
+  std::vector<T*> xL(n);
+  for (int m = 0; m < n; ++m) {
+    vps_context* h = hs[m];
+    if (h->prec == VPS_FP64) {
+      bL[m] = reinterpret_cast<const T*>(h->cr);
+      xL[m] = reinterpret_cast<T*>(h->czn);
+    } else {
+      bL[m] = static_cast<const T*>(h->bv[h->L]);
+      xL[m] = static_cast<T*>(h->xv[h->L]);
+    }
+  }
+  auto bptr = [&](int m, int l) -> const T* {
+    return l == hs[m]->L ? bL[m] : static_cast<const T*>(hs[m]->bv[l]);
+  };
+  auto xptr = [&](int m, int l) -> T* {
+    return l == hs[m]->L ? xL[m] : static_cast<T*>(hs[m]->xv[l]);
+  };
+  int D = 0;
+  for (int m = 0; m < n; ++m) D = std::max(D, hs[m]->L - hs[m]->coarse);
+  // record the whole cycle first (queues into the staging buffer), then copy
+  // the queues and issue the launches in the recorded order
+  std::vector<CohortOp> ops;
+  auto fail_all = [&](const char* msg) { return fail(h0, VPS_ENOMEM, "%s", msg); };
+  auto colour_ops = [&](const std::vector<int>& act, const std::vector<int>& lev, int c) -> int {
+    // one launch per smoother variant present among the members
+    std::vector<int> vs;
+    for (size_t i = 0; i < act.size(); ++i) {
+      const int v = hs[act[i]]->smooth_var[lev[i]];
+      if (std::find(vs.begin(), vs.end(), v) == vs.end()) vs.push_back(v);
+    }
+    for (int v : vs) {
+      if (v < 0 || v >= kSmoothVariants || !F.smooth_mult_batch_v[v])
+        return fail(h0, VPS_EINVAL, "smoother variant %d has no batched kernel", v);
+      size_t off;
+      BatchQueue* q = qw->open(&off);
+      if (!q) return fail_all("cohort queue buffer full");
+      const int P = F.variant_p[v];
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int m = act[i], l = lev[i];
+        if (hs[m]->smooth_var[l] != v) continue;
+        const LevelGeom& g = hs[m]->geom[l];
+        const ColourGeom cg = make_colour(g, c);
+        if (cg.npatch == 0) continue;
+        if (q->nitems == kMaxBatch) return fail_all("cohort larger than a queue");
+        BatchItem& it = q->items[q->nitems++];
+        it = BatchItem();
+        it.in = bptr(m, l);
+        it.out = xptr(m, l);
+        it.tile0 = q->ntiles;
+        it.n1a = g.n1;
+        it.pxa = g.px;
+        it.pza = g.pz;
+        it.cg = cg;
+        it.bscale = h0->dim == 3 ? 1.0 / g.h : 1.0;
+        q->ntiles += (cg.npatch + P - 1) / P;
+      }
+      qw->close(q, off);
+      ops.push_back({0, v, -1, c, off, q->ntiles, q->nitems});
+    }
+    return VPS_OK;
+  };
+  auto transfer_op = [&](int kind, const std::vector<int>& act, const std::vector<int>& lev) -> int {
+    size_t off;
+    BatchQueue* q = qw->open(&off);
+    if (!q) return fail_all("cohort queue buffer full");
+    for (size_t i = 0; i < act.size(); ++i) {
+      const int m = act[i], l = lev[i];  // l: the fine level
+      const LevelGeom& f = hs[m]->geom[l];
+      const LevelGeom& c = hs[m]->geom[l - 1];
+      if (q->nitems == kMaxBatch) return fail_all("cohort larger than a queue");
+      BatchItem& it = q->items[q->nitems++];
+      it = BatchItem();
+      if (kind == 1) {
+        it.in = hs[m]->rv[l];
+        it.out = const_cast<T*>(bptr(m, l - 1));
+      } else {
+        it.in = xptr(m, l - 1);
+        it.out = xptr(m, l);
+      }
+      it.tile0 = q->ntiles;
+      it.n1a = c.n1;
+      it.pxa = c.px;
+      it.pza = c.pz;
+      it.n1b = f.n1;
+      it.pxb = f.px;
+      it.pzb = f.pz;
+      const int t = (c.ncell + F.transfer_cells - 1) / F.transfer_cells;
+      it.tiles_per_dim = t;
+      q->ntiles += h0->dim == 3 ? (int64_t)t * t * t : (int64_t)t * t;
+    }
+    qw->close(q, off);
+    ops.push_back({kind, 0, -1, 0, off, q->ntiles, q->nitems});
+    return VPS_OK;
+  };
+  // members whose top level is their coarse level: the cycle is the exact solve
+  for (int m = 0; m < n; ++m)
+    if (hs[m]->L == hs[m]->coarse) ops.push_back({5, 0, m, hs[m]->L, 0, 0, 0});
+  for (int s = 0; s < D; ++s) {  // descent
+    std::vector<int> act, lev;
+    for (int m = 0; m < n; ++m)
+      if (hs[m]->L - s > hs[m]->coarse) {
+        act.push_back(m);
+        lev.push_back(hs[m]->L - s);
+      }
+    for (size_t i = 0; i < act.size(); ++i) ops.push_back({3, 0, act[i], lev[i], 0, 0, 0});
+    for (int p = 0; p < h0->n_pre; ++p)
+      for (int c = 0; c < nc; ++c)
+        if (int rc = colour_ops(act, lev, c)) return rc;
+    for (size_t i = 0; i < act.size(); ++i) ops.push_back({4, 0, act[i], lev[i], 0, 0, 0});
+    if (int rc = transfer_op(1, act, lev)) return rc;
+    for (size_t i = 0; i < act.size(); ++i)
+      if (lev[i] - 1 == hs[act[i]]->coarse) ops.push_back({5, 0, act[i], lev[i] - 1, 0, 0, 0});
+  }
+  for (int s = D - 1; s >= 0; --s) {  // ascent
+    std::vector<int> act, lev;
+    for (int m = 0; m < n; ++m)
+      if (hs[m]->L - s > hs[m]->coarse) {
+        act.push_back(m);
+        lev.push_back(hs[m]->L - s);
+      }
+    if (int rc = transfer_op(2, act, lev)) return rc;
+    for (int p = 0; p < h0->n_post; ++p)
+      for (int i = 0; i < nc; ++i)  // reverse colour order: the symmetric cycle of the CG
+        if (int rc = colour_ops(act, lev, nc - 1 - i)) return rc;
+  }
+  // issue
+  VPS_CK(h0, cudaMemcpyAsync(qw->dev, qw->host, qw->used, cudaMemcpyHostToDevice, st));
+  for (int m = 0; m < n; ++m)
+    if (hs[m]->prec == VPS_FP32)
+      VPS_CK(h0, launch_cast_d2f(hs[m]->cr, static_cast<float*>(hs[m]->bv[hs[m]->L]),
+                                 hs[m]->geom[hs[m]->L].total, st));
+  const T* il = static_cast<const T*>(h0->inv_lam);
+  for (const CohortOp& op : ops) {
+    switch (op.kind) {
+      case 0:
+        VPS_CK(h0, F.smooth_mult_batch_v[op.v](qw->dev_at(op.off), op.ntiles, il, st));
+        ++qw->launches;
+        break;
+      case 1:
+        VPS_CK(h0, F.restrict_batch(qw->dev_at(op.off), op.ntiles, st));
+        VPS_CK(h0, F.zero_faces_batch(qw->dev_at(op.off), op.nitems, st));
+        qw->launches += 2;
+        break;
+      case 2:
+        VPS_CK(h0, F.prolong_batch(qw->dev_at(op.off), op.ntiles, st));
+        ++qw->launches;
+        break;
+      case 3:
+        VPS_CK(h0, cudaMemsetAsync(xptr(op.m, op.l), 0, hs[op.m]->geom[op.l].total * sizeof(T), st));
+        break;
+      case 4: {
+        vps_context* h = hs[op.m];
+        VPS_CK(h0, F.apply(h->geom[op.l], xptr(op.m, op.l), bptr(op.m, op.l),
+                           static_cast<T*>(h->rv[op.l]), st));
+        break;
+      }
+      case 5:
+        if (int rc = coarse_solve<T>(hs[op.m], bptr(op.m, op.l), xptr(op.m, op.l))) return rc;
+        break;
+    }
+  }
+  return VPS_OK;
+}
+
+}  // namespace
+
+int cohort_vcycle(vps_context* const* hs, int n, void* q_host, void* q_dev, size_t q_cap,
+                  int64_t* batched_launches, int* max_items) {
+  if (n <= 0) return VPS_OK;
+  vps_context* h0 = hs[0];
+  for (int m = 0; m < n; ++m) {
+    vps_context* h = hs[m];
+    if (h->dim != h0->dim || h->k != h0->k || h->prec != h0->prec || h->stream != h0->stream ||
+        h->n_pre != h0->n_pre || h->n_post != h0->n_post || h->smoother != VPS_MULTIPLICATIVE ||
+        h->kernel_kind != VPS_KERNEL_FUSED || !h->as_external || h->as_need == 0)
+      return fail(h0, VPS_EINVAL, "cohort members must share shape, precision and stream");
+  }
+  if (n > kMaxBatch) return fail(h0, VPS_EINVAL, "at most %d cohort members", kMaxBatch);
+  if (int rc = set_device(h0)) return rc;
+  LaunchTally tally(h0);
+  QueueWriter qw{static_cast<unsigned char*>(q_host), static_cast<unsigned char*>(q_dev), q_cap};
+  const int rc = h0->prec == VPS_FP64 ? cohort_vcycle_t<double>(hs, n, &qw, h0->stream)
+                                      : cohort_vcycle_t<float>(hs, n, &qw, h0->stream);
+  if (batched_launches) *batched_launches += qw.launches;
+  if (max_items) *max_items = std::max(*max_items, qw.max_items);
+  return rc;
 }
 
 const char* handle_error(vps_handle h) { return h ? h->err.c_str() : ""; }

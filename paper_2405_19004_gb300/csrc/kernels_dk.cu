@@ -179,9 +179,10 @@ __device__ __forceinline__ int closure_origin(int gp, const ColourGeom& cg, int 
 // Origins of the block's P patches (-1: beyond the colour), computed once;
 // P may exceed the block's NT threads (2D, k = 1, 4 patches per thread).
 template <int P, int NT>
-__device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, int px, int pz) {
+__device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, int px, int pz,
+                                             int64_t tile) {
   for (int i = threadIdx.x; i < P; i += NT) {
-    const int64_t gp = (int64_t)blockIdx.x * P + i;
+    const int64_t gp = tile * P + i;
     s_org[i] = gp < cg.npatch ? closure_origin((int)gp, cg, px, pz) : -1;
   }
 }
@@ -445,10 +446,15 @@ __device__ __forceinline__ int boundary_first_line(int L, bool* full) {
 // of Section 3.1 -- the local residual b_I - Abar_j x of every patch of the
 // colour is written to rout (physical units, scaled back by 1 / bscale) and
 // x is left unchanged.
+//
+// The body processes tile `tile` of the colour (patches tile*P .. tile*P+P-1);
+// smooth_mult_kernel runs tile blockIdx.x, smooth_mult_batch_kernel the
+// tiles it takes from a queue of several levels' colour passes.
 template <typename T, int QQ, bool BND, int W, bool RES = false>
-__global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
-smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
-                   int px, int pz, ColourGeom cg, T bscale, T* __restrict__ rout = nullptr) {
+__device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __restrict__ x,
+                                                 const T* __restrict__ inv_lam, int px, int pz,
+                                                 const ColourGeom& cg, T bscale,
+                                                 T* __restrict__ rout, int64_t tile) {
   static_assert(!(RES && BND), "the residual-only kernel reads the whole closure");
   using C = SmoothCfg<T, QQ, W>;
   constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
@@ -463,7 +469,7 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
   int* s_org = reinterpret_cast<int*>(il + MD);
   // the origins and the eigenvalue table (written at setup) do not depend
   // on the previous kernel: read them before waiting for it to complete
-  load_origins<P, NT>(s_org, cg, px, pz);
+  load_origins<P, NT>(s_org, cg, px, pz, tile);
   if constexpr (!RES)
     for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   grid_dependency_wait();
@@ -830,6 +836,54 @@ smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restri
   }
 }
 
+template <typename T, int QQ, bool BND, int W, bool RES = false>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
+smooth_mult_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
+                   int px, int pz, ColourGeom cg, T bscale, T* __restrict__ rout = nullptr) {
+  smooth_mult_body<T, QQ, BND, W, RES>(b, x, inv_lam, px, pz, cg, bscale, rout, blockIdx.x);
+}
+
+// Takes the next tile of a batched launch from the queue (one atomic per
+// tile, by thread 0) and finds the queue item it belongs to; returns false
+// once every tile has been taken.  Tiles of one item are processed exactly
+// as the single-level kernel processes its blocks, so a level's result does
+// not depend on the other items of the launch or on which block ran a tile.
+__device__ __forceinline__ bool next_batch_tile(BatchQueue* q, int64_t* tile, int* item) {
+  __shared__ int64_t s_tile;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) {
+    const int64_t t = (int64_t)atomicAdd(&q->head, 1ull);
+    const int ni = q->nitems;
+    int it = 0;
+    while (it + 1 < ni && q->items[it + 1].tile0 <= t) ++it;
+    s_tile = t;
+    s_item = it;
+  }
+  __syncthreads();
+  *tile = s_tile;
+  *item = s_item;
+  const bool more = s_tile < q->ntiles;
+  __syncthreads();  // s_tile / s_item are rewritten by the next call
+  return more;
+}
+
+// Persistent multiplicative colour passes of several levels (one queue item
+// per level: b, x, layout, colour, bscale): each block takes tiles until
+// the queue is empty.
+template <typename T, int QQ, bool BND, int W>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
+smooth_mult_batch_kernel(BatchQueue* __restrict__ q, const T* __restrict__ inv_lam) {
+  int64_t t;
+  int it;
+  while (next_batch_tile(q, &t, &it)) {
+    const BatchItem& I = q->items[it];
+    smooth_mult_body<T, QQ, BND, W, false>(static_cast<const T*>(I.in), static_cast<T*>(I.out),
+                                           inv_lam, (int)I.pxa, (int)I.pza, I.cg, (T)I.bscale,
+                                           nullptr, t - I.tile0);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
 // ------------------------------------------------------------- additive
 // x_I += scale * A_ref^-1 r_I for every patch of one colour.
 template <typename T, int QQ>
@@ -844,7 +898,7 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
   T* X1 = X0 + P * MD;
   T* il = X1 + P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
-  load_origins<P, NT>(s_org, cg, px, pz);
+  load_origins<P, NT>(s_org, cg, px, pz, blockIdx.x);
   for (int e = threadIdx.x; e < MD; e += NT) il[e] = __ldg(inv_lam + e);
   __syncthreads();
   constexpr int NL = DIM == 3 ? m * m : m;
@@ -1597,19 +1651,20 @@ struct TransferCfg {
 // x_fine += P x_coarse.  Fine node 2K*C + s (s < 2K) of coarse cell C is
 // sum_i P1[s][i] x_c[K*C + i] per direction; each block owns the fine nodes
 // of its coarse cells (half-open), so no two blocks write the same node.
+// The body processes the tile (bx, by, bz) of coarse cells; sP1 holds the 1D
+// weights (filled by the caller, followed by a barrier).
 template <typename T>
-__global__ void __launch_bounds__(TransferCfg::NT)
-prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_t pxc,
-                   int64_t pzc, int n1f, int64_t pxf, int64_t pzf) {
+__device__ __forceinline__ void prolong_add_body(const T* __restrict__ xc, T* __restrict__ xf,
+                                                 int n1c, int64_t pxc, int64_t pzc, int n1f,
+                                                 int64_t pxf, int64_t pzf, int bx, int by, int bz,
+                                                 const T* sP1) {
   using C = TransferCfg;
   constexpr int CB = C::CB, CBp = C::CBp, FB = C::FB, CC = C::CC, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t1 = reinterpret_cast<T*>(smem_raw);
-  __shared__ T sP1[2 * K * nl];
-  for (int e = threadIdx.x; e < 2 * K * nl; e += NT) sP1[e] = c_tab<T>.P1[e];
-  const int cx0 = blockIdx.x * CC, cy0 = blockIdx.y * CC;
+  const int cx0 = bx * CC, cy0 = by * CC;
   if constexpr (DIM == 3) {
-    const int cz0 = blockIdx.z * CC;
+    const int cz0 = bz * CC;
     T* t2 = t1 + FB * CB * CBp;
     // along z from global: units (coarse y, coarse x) x coarse cell z
     for (int u = threadIdx.x; u < CB * CB * CC; u += NT) {
@@ -1696,6 +1751,45 @@ prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_
   }
   (void)pzc;
   (void)pzf;
+  (void)bz;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+prolong_add_kernel(const T* __restrict__ xc, T* __restrict__ xf, int n1c, int64_t pxc,
+                   int64_t pzc, int n1f, int64_t pxf, int64_t pzf) {
+  __shared__ T sP1[2 * K * nl];
+  for (int e = threadIdx.x; e < 2 * K * nl; e += TransferCfg::NT) sP1[e] = c_tab<T>.P1[e];
+  __syncthreads();
+  prolong_add_body<T>(xc, xf, n1c, pxc, pzc, n1f, pxf, pzf, blockIdx.x, blockIdx.y, blockIdx.z,
+                      sP1);
+}
+
+// Tile r of a transfer item -> (bx, by, bz) on a t^DIM grid of tiles.
+__device__ __forceinline__ void transfer_tile(int64_t r, int t, int* bx, int* by, int* bz) {
+  *bx = (int)(r % t);
+  *by = (int)((r / t) % t);
+  *bz = DIM == 3 ? (int)(r / ((int64_t)t * t)) : 0;
+}
+
+// Persistent prolongations x_fine += P x_coarse of several levels (queue
+// items: in = x_coarse, out = x_fine; a: coarse layout, b: fine layout).
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+prolong_add_batch_kernel(BatchQueue* __restrict__ q) {
+  __shared__ T sP1[2 * K * nl];
+  for (int e = threadIdx.x; e < 2 * K * nl; e += TransferCfg::NT) sP1[e] = c_tab<T>.P1[e];
+  __syncthreads();
+  int64_t t;
+  int it;
+  while (next_batch_tile(q, &t, &it)) {
+    const BatchItem& I = q->items[it];
+    int bx, by, bz;
+    transfer_tile(t - I.tile0, I.tiles_per_dim, &bx, &by, &bz);
+    prolong_add_body<T>(static_cast<const T*>(I.in), static_cast<T*>(I.out), I.n1a, I.pxa, I.pza,
+                        I.n1b, I.pxb, I.pzb, bx, by, bz, sP1);
+    __syncthreads();
+  }
 }
 
 // Restriction r_c = P^T r_f per direction: coarse node K*C + i gathers the
@@ -1718,17 +1812,17 @@ __device__ __forceinline__ void restrict_1d(const T (&v)[4 * K + 1], T (&out)[K]
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TransferCfg::NT)
-restrict_kernel(const T* __restrict__ rf, T* __restrict__ rc, int n1c, int64_t pxc, int64_t pzc,
-                int n1f, int64_t pxf, int64_t pzf) {
+__device__ __forceinline__ void restrict_body(const T* __restrict__ rf, T* __restrict__ rc,
+                                              int n1c, int64_t pxc, int64_t pzc, int n1f,
+                                              int64_t pxf, int64_t pzf, int bx, int by, int bz) {
   using C = TransferCfg;
   constexpr int RFB = C::RFB, RFBp = C::RFBp, CN = C::CN, CC = C::CC, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t1 = reinterpret_cast<T*>(smem_raw);
-  const int C0x = blockIdx.x * CC, C0y = blockIdx.y * CC;
+  const int C0x = bx * CC, C0y = by * CC;
   const int fx0 = 2 * K * (C0x - 1), fy0 = 2 * K * (C0y - 1);
   if constexpr (DIM == 3) {
-    const int C0z = blockIdx.z * CC;
+    const int C0z = bz * CC;
     T* t2 = t1 + CN * RFB * RFBp;
     // along z from global: units (fine y, fine x) x coarse cell z
     for (int u = threadIdx.x; u < RFB * RFB * CC; u += NT) {
@@ -1808,15 +1902,40 @@ restrict_kernel(const T* __restrict__ rf, T* __restrict__ rc, int n1c, int64_t p
     }
   }
   (void)pzc;
+  (void)bz;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+restrict_kernel(const T* __restrict__ rf, T* __restrict__ rc, int n1c, int64_t pxc, int64_t pzc,
+                int n1f, int64_t pxf, int64_t pzf) {
+  restrict_body<T>(rf, rc, n1c, pxc, pzc, n1f, pxf, pzf, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Persistent restrictions r_coarse = P^T r_fine of several levels (queue
+// items: in = r_fine, out = r_coarse; a: coarse layout, b: fine layout).
+template <typename T>
+__global__ void __launch_bounds__(TransferCfg::NT)
+restrict_batch_kernel(BatchQueue* __restrict__ q) {
+  int64_t t;
+  int it;
+  while (next_batch_tile(q, &t, &it)) {
+    const BatchItem& I = q->items[it];
+    int bx, by, bz;
+    transfer_tile(t - I.tile0, I.tiles_per_dim, &bx, &by, &bz);
+    restrict_body<T>(static_cast<const T*>(I.in), static_cast<T*>(I.out), I.n1a, I.pxa, I.pza,
+                     I.n1b, I.pxb, I.pzb, bx, by, bz);
+    __syncthreads();
+  }
 }
 
 // The upper boundary layer of a coarse vector (index n1c-1 in any
 // direction) is owned by no restriction tile; this zeroes it.
 template <typename T>
-__global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, int64_t pz) {
+__device__ __forceinline__ void zero_upper_faces_body(T* __restrict__ v, int n1, int64_t px,
+                                                      int64_t pz, int64_t first, int64_t step) {
   const int64_t nface = DIM == 3 ? (int64_t)n1 * n1 : n1;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < DIM * nface;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = first; e < DIM * nface; e += step) {
     const int f = (int)(e / nface);
     const int64_t r = e % nface;
     const int a = (int)(r % n1), c = DIM == 3 ? (int)(r / n1) : 0;
@@ -1826,6 +1945,23 @@ __global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, i
     else idx = (int64_t)(n1 - 1) * pz + (int64_t)c * px + a;
     v[idx] = T(0);
   }
+}
+
+template <typename T>
+__global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, int64_t pz) {
+  zero_upper_faces_body<T>(v, n1, px, pz, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                           (int64_t)gridDim.x * blockDim.x);
+}
+
+// The upper faces of the `out` vectors (layout a) of every item of a queue:
+// blockIdx.y selects the item.
+template <typename T>
+__global__ void zero_upper_faces_batch_kernel(const BatchQueue* __restrict__ q) {
+  if ((int)blockIdx.y >= q->nitems) return;
+  const BatchItem& I = q->items[blockIdx.y];
+  zero_upper_faces_body<T>(static_cast<T*>(I.out), I.n1a, I.pxa, I.pza,
+                           blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                           (int64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------ launchers
@@ -1840,6 +1976,89 @@ cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T
   return launch_pdl(smooth_mult_kernel<T, PP, BND, W, false>, dim3((unsigned)grid), dim3(C::NT),
                     BND ? C::smem_bnd : C::smem_mult, s, b, x, inv_lam, (int)g.px, (int)g.pz,
                     cg, bscale, static_cast<T*>(nullptr));
+}
+
+// Multiprocessor count of the current device (first call).
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int d = 0, v = 0;
+    if (cudaGetDevice(&d) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+
+// Grid of a persistent batched launch: every resident block slot of the GPU
+// (occupancy of the kernel at its block size and shared memory), at most
+// one block per tile.
+template <typename KernT>
+cudaError_t persistent_grid(KernT kern, int nt, size_t smem, int64_t ntiles, int* per_sm,
+                            unsigned* grid) {
+  if (*per_sm <= 0) {
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nt, smem);
+    if (e != cudaSuccess) return e;
+    *per_sm = nb > 0 ? nb : 1;
+  }
+  const int64_t cap = (int64_t)(*per_sm) * sm_count();
+  *grid = (unsigned)(ntiles < cap ? ntiles : cap);
+  return cudaSuccess;
+}
+
+template <typename T, int PP, bool BND, int W>
+cudaError_t smooth_mult_batch_launch(BatchQueue* q, int64_t ntiles, const T* inv_lam,
+                                     cudaStream_t s) {
+  using C = SmoothCfg<T, PP, W>;
+  if (ntiles <= 0) return cudaSuccess;
+  static int per_sm = 0;
+  const size_t smem = BND ? C::smem_bnd : C::smem_mult;
+  unsigned grid = 0;
+  cudaError_t e = persistent_grid(smooth_mult_batch_kernel<T, PP, BND, W>, C::NT, smem, ntiles,
+                                  &per_sm, &grid);
+  if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
+  smooth_mult_batch_kernel<T, PP, BND, W><<<grid, C::NT, smem, s>>>(q, inv_lam);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t restrict_batch_launch(BatchQueue* q, int64_t ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  static int per_sm = 0;
+  const size_t smem = TransferCfg::smem_restrict<T>();
+  unsigned grid = 0;
+  cudaError_t e = persistent_grid(restrict_batch_kernel<T>, TransferCfg::NT, smem, ntiles, &per_sm,
+                                  &grid);
+  if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
+  restrict_batch_kernel<T><<<grid, TransferCfg::NT, smem, s>>>(q);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prolong_batch_launch(BatchQueue* q, int64_t ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  static int per_sm = 0;
+  const size_t smem = TransferCfg::smem_prolong<T>();
+  unsigned grid = 0;
+  cudaError_t e = persistent_grid(prolong_add_batch_kernel<T>, TransferCfg::NT, smem, ntiles,
+                                  &per_sm, &grid);
+  if (e != cudaSuccess) return e;
+  VPS_COUNT_LAUNCH();
+  prolong_add_batch_kernel<T><<<grid, TransferCfg::NT, smem, s>>>(q);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t zero_faces_batch_launch(const BatchQueue* q, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  VPS_COUNT_LAUNCH();
+  zero_upper_faces_batch_kernel<T><<<dim3(64, (unsigned)nitems), 256, 0, s>>>(q);
+  return cudaGetLastError();
 }
 
 template <typename T, int PP>
@@ -2006,7 +2225,13 @@ cudaError_t smooth_limits() {
       e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 1>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
       if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, true, 1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+      if (e != cudaSuccess) return e;
     }
+    e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, true, 0>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+    if (e != cudaSuccess) return e;
   }
   if constexpr (!C::fits) {
     return cudaSuccess;
@@ -2016,6 +2241,9 @@ cudaError_t smooth_limits() {
                                          (int)C::smem_mult);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false, 0, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_mult);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, false, 0>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_mult);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(smooth_add_kernel<T, PP>,
@@ -2033,21 +2261,29 @@ void register_variant(KernelFns<T>* f, int v) {
   f->smooth_add_v[v + 2 * kQVariants] = nullptr;
   if constexpr (C::fits_bnd) {
     f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true, 0>;
-    if constexpr (kOneWarpVariants)
+    f->smooth_mult_batch_v[v + kQVariants] = smooth_mult_batch_launch<T, PP, true, 0>;
+    if constexpr (kOneWarpVariants) {
       f->smooth_mult_v[v + 2 * kQVariants] = smooth_mult_launch<T, PP, true, 1>;
-    else
+      f->smooth_mult_batch_v[v + 2 * kQVariants] = smooth_mult_batch_launch<T, PP, true, 1>;
+    } else {
       f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
+      f->smooth_mult_batch_v[v + 2 * kQVariants] = nullptr;
+    }
   } else {
     f->smooth_mult_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
+    f->smooth_mult_batch_v[v + kQVariants] = nullptr;
+    f->smooth_mult_batch_v[v + 2 * kQVariants] = nullptr;
   }
   if constexpr (C::fits) f->resid_v[v] = resid_launch<T, PP>;
   else f->resid_v[v] = nullptr;
   if constexpr (C::fits) {
     f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false, 0>;
+    f->smooth_mult_batch_v[v] = smooth_mult_batch_launch<T, PP, false, 0>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
   } else {
     f->smooth_mult_v[v] = nullptr;
+    f->smooth_mult_batch_v[v] = nullptr;
     f->smooth_add_v[v] = nullptr;
   }
 }
@@ -2062,6 +2298,10 @@ void register_fns(KernelFns<T>* f) {
   f->apply = apply_launch<T>;
   f->prolong_add = prolong_launch<T>;
   f->restrict_ = restrict_launch<T>;
+  f->prolong_batch = prolong_batch_launch<T>;
+  f->restrict_batch = restrict_batch_launch<T>;
+  f->zero_faces_batch = zero_faces_batch_launch<T>;
+  f->transfer_cells = TransferCfg::CC;
   f->inverse_solve = kInvFits ? inverse_launch<T> : nullptr;
 }
 
@@ -2089,6 +2329,12 @@ cudaError_t set_smem_limits() {
   }
   e = cudaFuncSetAttribute(prolong_add_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)TransferCfg::smem_prolong<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(prolong_add_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TransferCfg::smem_prolong<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(restrict_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TransferCfg::smem_restrict<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(restrict_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TransferCfg::smem_restrict<T>());

@@ -2,18 +2,28 @@
 //
 // Requests (dimension, degree, level, sine-mode right-hand side) wait in a
 // queue.  An engine thread admits them as solver slots and device memory
-// (a fixed budget) become free: a slot is a vps handle on a stream of its
-// own whose level hierarchy stays resident and is reused by later requests
-// of the same shape; idle slots are evicted, least recently used first,
-// when memory is needed.  Every admitted request runs the preconditioned CG
-// of the library one iteration at a time: the engine polls each slot's CUDA
-// event and, when an iteration's scalars have arrived, issues the next one.
-// Requests therefore overlap on the GPU, and one that arrives while others
-// run starts as soon as a slot and memory are free.  A request's numbers
-// depend only on its own slot: its result is the same alone and in a mix.
+// (a fixed budget) become free: a slot is a vps handle whose level hierarchy
+// stays resident and is reused by later requests of the same shape; idle
+// slots are evicted, least recently used first, when memory is needed.
+//
+// Admitted requests of the same dimension, degree (and the server's
+// precision) form a cohort that shares one CUDA stream.  Every request runs
+// the preconditioned CG of the library as an asynchronous state machine
+// whose V-cycles are run by the cohort: whenever no work of the cohort is in
+// flight, the engine runs one V-cycle for every member that waits for one
+// (cohort_vcycle: the colour passes, restrictions and prolongations of all
+// members' levels as persistent kernels taking tiles from a device-side
+// queue, one launch per step), then the rest of each member's CG iteration,
+// and polls the members' events.  A request that arrives while others run
+// joins its cohort at the next of these ticks; different cohorts run
+// concurrently on their own streams.  A request's numbers depend only on its
+// own data: every level of it goes through the same operations in the same
+// order as alone, so its result is the same alone and in a mix.
 //
 // The engine never blocks on the GPU (it polls events); waits on the host
-// side take a timeout.
+// side take a timeout.  No kernel waits on work it does not own: a
+// persistent launch's queue is complete before the launch, so there is no
+// device-side spin to bound.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -21,6 +31,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -51,13 +62,28 @@ struct Request {
   double rel = 0;
 };
 
+struct Cohort;
+
 struct Slot {
   vps_context* h = nullptr;
   int d = 0, k = 0, L = 0;
   size_t bytes = 0;
   int64_t req = 0;  // 0: idle
   double last_used = 0;
+  Cohort* cohort = nullptr;
 };
+
+// Requests of one (dimension, degree): one stream, and the staging buffers
+// of the batched V-cycles' queues (pinned host and device).
+struct Cohort {
+  int d = 0, k = 0;
+  cudaStream_t stream = nullptr;
+  void* q_host = nullptr;
+  void* q_dev = nullptr;
+  size_t q_cap = 0;
+};
+
+constexpr size_t kCohortQueueBytes = size_t(4) << 20;
 
 }  // namespace
 
@@ -74,8 +100,12 @@ struct vps_server_ctx {
   std::atomic<bool> stop{false};
   std::map<int64_t, Request> reqs;
   std::deque<int64_t> queue;
-  std::vector<Slot> slots;  // engine thread only
+  std::vector<std::unique_ptr<Slot>> slots;      // engine thread only
+  std::vector<std::unique_ptr<Cohort>> cohorts;  // engine thread only
   size_t used = 0;          // engine thread only
+  // batching statistics (engine thread writes, under mu)
+  int64_t ticks = 0, batched_launches = 0;
+  int max_per_launch = 0, max_per_tick = 0;
   int64_t next_id = 1;
   int64_t n_done = 0;
   int active = 0;
@@ -83,8 +113,69 @@ struct vps_server_ctx {
 
   void run();
   bool admit_one();
+  bool tick(Cohort& c);
+  Cohort* cohort_of(int d, int k, int* rc);
   void finish(Slot& s, int state, int status, int iters, double rel, const double* x);
+  void release();
 };
+
+// The cohort of (d, k), created on first use.
+Cohort* vps_server_ctx::cohort_of(int d, int k, int* rc) {
+  *rc = VPS_OK;
+  for (auto& c : cohorts)
+    if (c->d == d && c->k == k) return c.get();
+  auto c = std::make_unique<Cohort>();
+  c->d = d;
+  c->k = k;
+  c->q_cap = kCohortQueueBytes;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->q_host, c->q_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&c->q_dev, c->q_cap);
+  if (e != cudaSuccess) {
+    if (c->q_dev) cudaFree(c->q_dev);
+    if (c->q_host) cudaFreeHost(c->q_host);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    err = cudaGetErrorString(e);
+    *rc = e == cudaErrorMemoryAllocation ? VPS_ENOMEM : VPS_ECUDA;
+    return nullptr;
+  }
+  cohorts.push_back(std::move(c));
+  return cohorts.back().get();
+}
+
+// Runs one V-cycle for every member of c that waits for one, then the rest
+// of their CG iterations, if no work of the cohort is in flight.
+bool vps_server_ctx::tick(Cohort& c) {
+  std::vector<Slot*> pending;
+  for (auto& sp : slots) {
+    Slot& s = *sp;
+    if (!s.req || s.cohort != &c) continue;
+    if (vps::cg_async_pending_vcycle(s.h)) pending.push_back(&s);
+    else return false;  // a member's work is still in flight
+  }
+  if (pending.empty()) return false;
+  std::vector<vps_context*> hs;
+  for (Slot* s : pending) hs.push_back(s->h);
+  int64_t launches = 0;
+  int per_launch = 0;
+  int rc = vps::cohort_vcycle(hs.data(), (int)hs.size(), c.q_host, c.q_dev, c.q_cap, &launches,
+                              &per_launch);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    ++ticks;
+    batched_launches += launches;
+    max_per_launch = std::max(max_per_launch, per_launch);
+    max_per_tick = std::max(max_per_tick, (int)hs.size());
+  }
+  for (Slot* s : pending) {
+    int r = rc ? rc : vps::cg_async_resume(s->h);
+    if (r) {
+      err = vps::handle_error(rc ? hs[0] : s->h);
+      finish(*s, VPS_REQ_FAILED, r, 0, 0.0, nullptr);
+    }
+  }
+  return true;
+}
 
 void vps_server_ctx::finish(Slot& s, int state, int status, int iters, double rel,
                             const double* x) {
@@ -115,8 +206,8 @@ bool vps_server_ctx::admit_one() {
     bool found = false;
     for (size_t qi = 0; qi < queue.size() && qi < 64 && !found; ++qi) {
       const Request& r = reqs[queue[qi]];
-      for (const Slot& s : slots)
-        if (!s.req && s.d == r.d && s.k == r.k && s.L == r.L) {
+      for (const auto& s : slots)
+        if (!s->req && s->d == r.d && s->k == r.k && s->L == r.L) {
           pick = qi;
           found = true;
           break;
@@ -126,9 +217,9 @@ bool vps_server_ctx::admit_one() {
     snapshot = reqs[id];
   }
   Slot* slot = nullptr;
-  for (Slot& s : slots)
-    if (!s.req && s.d == snapshot.d && s.k == snapshot.k && s.L == snapshot.L) {
-      slot = &s;
+  for (auto& s : slots)
+    if (!s->req && s->d == snapshot.d && s->k == snapshot.k && s->L == snapshot.L) {
+      slot = s.get();
       break;
     }
   if (!slot) {
@@ -149,17 +240,23 @@ bool vps_server_ctx::admit_one() {
     while (used + need > budget) {
       auto victim = slots.end();
       for (auto it = slots.begin(); it != slots.end(); ++it)
-        if (!it->req && (victim == slots.end() || it->last_used < victim->last_used)) victim = it;
+        if (!(*it)->req && (victim == slots.end() || (*it)->last_used < (*victim)->last_used))
+          victim = it;
       if (victim == slots.end()) return false;  // wait for a running request to finish
-      vps_destroy(victim->h);
-      used -= victim->bytes;
+      vps_destroy((*victim)->h);
+      used -= (*victim)->bytes;
       slots.erase(victim);
     }
-    Slot s;
-    s.d = snapshot.d;
-    s.k = snapshot.k;
-    s.L = snapshot.L;
-    int rc = vps::create_own_stream(s.d, s.k, s.L, precision, &s.h);
+    auto s = std::make_unique<Slot>();
+    s->d = snapshot.d;
+    s->k = snapshot.k;
+    s->L = snapshot.L;
+    int rc = VPS_OK;
+    s->cohort = cohort_of(s->d, s->k, &rc);
+    if (!rc)
+      rc = vps_create(s->d, s->k, s->L, precision, VPS_MULTIPLICATIVE, 1.0, 1, 1,
+                      s->cohort->stream, &s->h);
+    if (!rc) vps::set_external_vcycle(s->h, true);
     if (rc) {
       std::lock_guard<std::mutex> lock(mu);
       queue.erase(std::find(queue.begin(), queue.end(), id));
@@ -168,14 +265,14 @@ bool vps_server_ctx::admit_one() {
       r.status = rc;
       r.t_done = now_s();
       ++n_done;
-      err = vps_last_error(nullptr);
+      if (s->cohort) err = vps_last_error(nullptr);  // else cohort_of has set it
       cv.notify_all();
       return true;
     }
-    vps_sizes(s.h, nullptr, nullptr, &s.bytes);
-    used += s.bytes;
-    slots.push_back(s);
-    slot = &slots.back();
+    vps_sizes(s->h, nullptr, nullptr, &s->bytes);
+    used += s->bytes;
+    slots.push_back(std::move(s));
+    slot = slots.back().get();
   }
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -199,8 +296,9 @@ void vps_server_ctx::run() {
   cudaSetDevice(device);
   while (!stop.load()) {
     bool progressed = false;
-    for (Slot& s : slots) {
-      if (!s.req) continue;
+    for (auto& sp : slots) {
+      Slot& s = *sp;
+      if (!s.req || vps::cg_async_pending_vcycle(s.h)) continue;
       int done = 0, status = 0, iters = 0;
       double rel = 0;
       const double* x = nullptr;
@@ -212,9 +310,13 @@ void vps_server_ctx::run() {
       } else if (done) {
         finish(s, status == VPS_OK ? VPS_REQ_DONE : VPS_REQ_FAILED, status, iters, rel, x);
         progressed = true;
+      } else if (vps::cg_async_pending_vcycle(s.h)) {
+        progressed = true;
       }
     }
     while (admit_one()) progressed = true;
+    for (auto& c : cohorts)
+      if (tick(*c)) progressed = true;
     if (!progressed) {
       std::unique_lock<std::mutex> lock(mu);
       if (queue.empty() && active == 0)
@@ -223,6 +325,20 @@ void vps_server_ctx::run() {
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
   }
+}
+
+// Frees the slots and the cohorts (after the engine has stopped).
+void vps_server_ctx::release() {
+  for (auto& c : cohorts)
+    if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& sl : slots) vps_destroy(sl->h);
+  slots.clear();
+  for (auto& c : cohorts) {
+    if (c->q_dev) cudaFree(c->q_dev);
+    if (c->q_host) cudaFreeHost(c->q_host);
+    if (c->stream) cudaStreamDestroy(c->stream);
+  }
+  cohorts.clear();
 }
 
 extern "C" {
@@ -322,12 +438,23 @@ int vps_server_stats(vps_server s, int64_t* submitted, int64_t* done, int* activ
 
 const char* vps_server_last_error(vps_server s) { return s ? s->err.c_str() : ""; }
 
+int vps_server_batch_stats(vps_server s, int64_t* ticks, int64_t* batched_launches,
+                           int* max_requests_per_launch, int* max_requests_per_tick) {
+  if (!s) return VPS_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (ticks) *ticks = s->ticks;
+  if (batched_launches) *batched_launches = s->batched_launches;
+  if (max_requests_per_launch) *max_requests_per_launch = s->max_per_launch;
+  if (max_requests_per_tick) *max_requests_per_tick = s->max_per_tick;
+  return VPS_OK;
+}
+
 int vps_server_destroy(vps_server s) {
   if (!s) return VPS_OK;
   s->stop.store(true);
   s->cv.notify_all();
   if (s->engine.joinable()) s->engine.join();
-  for (Slot& sl : s->slots) vps_destroy(sl.h);
+  s->release();
   delete s;
   return VPS_OK;
 }

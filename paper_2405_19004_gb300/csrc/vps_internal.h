@@ -127,6 +127,32 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// Batched launches (serving): one persistent kernel processes the tiles of
+// several levels -- of different requests -- taken from a queue in device
+// memory.  Item i owns tiles [tile0, next item's tile0); a block takes the
+// next tile with one atomic increment of `head` until head >= ntiles.  The
+// host fills a queue (head = 0) and copies it to the device before the
+// launch, in the launch's stream.
+constexpr int kMaxBatch = 32;   // items per queue
+struct BatchItem {
+  const void* in = nullptr;     // smoother: b; restriction: fine residual; prolongation: coarse x
+  void* out = nullptr;          // smoother: x; restriction: coarse b;      prolongation: fine x
+  int64_t tile0 = 0;            // first tile of the item in the launch's tile space
+  int n1a = 0, n1b = 0;         // nodes per direction: a = the item's level (smoother) or the
+  int64_t pxa = 0, pza = 0;     //   coarse level (transfers); b = the fine level (transfers)
+  int64_t pxb = 0, pzb = 0;
+  ColourGeom cg;                // smoother: the colour's patches
+  double bscale = 1.0;          // smoother: scale of b (1/h in 3D)
+  int tiles_per_dim = 0;        // transfers: tiles per direction (t^dim tiles)
+};
+struct BatchQueue {
+  unsigned long long head;      // next tile (0 when uploaded)
+  int64_t ntiles;
+  int nitems;
+  int pad_;
+  BatchItem items[kMaxBatch];
+};
+
 // Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
 // q = 0, 1, 2 for 1, 2, 4 patches per thread; kind 0 the fused kernel,
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
@@ -156,6 +182,18 @@ struct KernelFns {
                                const T* AinvT, cudaStream_t) = nullptr;
   // y = A x  (b == nullptr)  or  y = b - A x  (residual)
   cudaError_t (*apply)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
+  // batched persistent launches over a device-side queue (q: device copy,
+  // ntiles: its tile count, known on the host): multiplicative colour
+  // passes (variant v), restrictions, prolongations, and the zeroing of the
+  // upper faces of every item's `out` vector (nitems items)
+  cudaError_t (*smooth_mult_batch_v[kSmoothVariants])(BatchQueue* q, int64_t ntiles,
+                                                      const T* inv_lam, cudaStream_t) = {};
+  cudaError_t (*restrict_batch)(BatchQueue* q, int64_t ntiles, cudaStream_t) = nullptr;
+  cudaError_t (*prolong_batch)(BatchQueue* q, int64_t ntiles, cudaStream_t) = nullptr;
+  cudaError_t (*zero_faces_batch)(const BatchQueue* q, int nitems, cudaStream_t) = nullptr;
+  // tiles of one colour pass (patches per block) and of one transfer
+  // (coarse cells per tile and direction)
+  int transfer_cells = 0;
   // x_fine += P x_coarse
   cudaError_t (*prolong_add)(const LevelGeom& fine, const LevelGeom& coarse, const T* xc, T* xf,
                              cudaStream_t) = nullptr;
@@ -273,5 +311,25 @@ int cg_async_begin(vps_context* h, int n_modes, const double* coef, const int* f
 int cg_async_poll(vps_context* h, int* done, int* status, int* iters, double* rel,
                   const double** x_host);
 const char* handle_error(vps_context* h);
+// Asynchronous CG with external V-cycles (serving cohorts): while
+// cg_async_pending_vcycle(h), the caller runs the V-cycle of h (for several
+// handles at once with cohort_vcycle) and then calls cg_async_resume(h).
+void set_external_vcycle(vps_context* h, bool on);
+int cg_async_pending_vcycle(vps_context* h);
+int cg_async_resume(vps_context* h);
+// One V-cycle (Algorithm 1, symmetric colour order, x = 0) for each of n
+// handles with a pending V-cycle that share dimension, degree, precision,
+// smoothing steps and stream: level by level from each handle's top
+// (levels aligned by their distance from the top), the colour passes,
+// restrictions and prolongations of all handles in one persistent batched
+// launch each (queues staged in q_host, pinned, copied to q_dev, both
+// q_cap bytes; neither may be reused before the stream has passed this
+// cycle), the residuals, memsets and coarse solves per handle.  Each
+// handle's levels go through exactly the operations, in the order, of its
+// own V-cycle, so its result equals that of the handle alone.
+// batched_launches / max_items accumulate the launches and the largest
+// number of levels in one launch.
+int cohort_vcycle(vps_context* const* hs, int n, void* q_host, void* q_dev, size_t q_cap,
+                  int64_t* batched_launches, int* max_items);
 
 }  // namespace vps

@@ -1,7 +1,9 @@
 """Continuous-batching server: correctness, isolation between requests, admission.
 
 A request's result must not depend on what else runs: it is compared bit for
-bit between a run alone and a run in a mix of concurrent requests.
+bit between a run alone and a run in a mix of concurrent requests, whose
+V-cycles share batched launches with the other requests of their cohort
+(same dimension and degree).
 """
 
 import numpy as np
@@ -119,4 +121,38 @@ def test_wait_times_out_on_the_host():
     assert e.value.code == vps.VPS_ETIMEOUT
     srv.wait(rid, 120)
     assert srv.query(rid)["state"] == vps.VPS_REQ_DONE
+    srv.close()
+
+
+def test_requests_of_one_cohort_share_batched_launches():
+    """Four 3D Q2 requests of three levels admitted together: their V-cycles
+    run as one cohort, so at least one batched launch processes tiles of
+    several requests; each result still equals the request's result alone."""
+    reqs = [(3, 2, 3), (3, 2, 4), (3, 2, 3), (3, 2, 2)]
+    coefs = [sine_modes(3, 300 + i) for i in range(len(reqs))]
+    srv = vps.Server(4 * GB, max_active=8, precision=vps.VPS_FP32)
+    xs = [srv.submit(d, k, L, *coefs[i])[1] for i, (d, k, L) in enumerate(reqs)]
+    srv.wait(0, 300)
+    st = srv.batch_stats()
+    srv.close()
+    assert st["max_requests_per_launch"] >= 2 and st["max_requests_per_tick"] >= 2, st
+    assert st["batched_launches"] > 0 and st["ticks"] > 0
+    for i, (d, k, L) in enumerate(reqs):
+        alone = vps.Server(GB, max_active=1, precision=vps.VPS_FP32)
+        rid, x = alone.submit(d, k, L, *coefs[i])
+        alone.wait(rid, 120)
+        assert alone.query(rid)["state"] == vps.VPS_REQ_DONE
+        alone.close()
+        assert np.array_equal(x, xs[i])
+
+
+def test_submit_rejects_levels_beyond_the_size_limit():
+    """The size check runs before any size is computed from the level, so
+    levels whose element count would overflow an integer are rejected too."""
+    srv = vps.Server(GB, max_active=1)
+    coef, freq = sine_modes(3, 9)
+    for L in (11, 19, 24):
+        with pytest.raises(vps.VpsError) as e:
+            srv.submit(3, 7, L, coef, freq)
+        assert e.value.code == vps.VPS_EINVAL
     srv.close()
