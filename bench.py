@@ -223,6 +223,8 @@ def run_serving(vps, n_requests, precision, max_active, budget):
     srv.wait(0, 3600)
     t_end = time.perf_counter()
     info = [srv.query(i) for i in ids]
+    batch = srv.batch_stats()
+    host = srv.host_times()
     srv.close()
     lat = sorted(q["latency_s"] for q in info)
     ok = sum(q["state"] == vps.VPS_REQ_DONE for q in info)
@@ -231,7 +233,8 @@ def run_serving(vps, n_requests, precision, max_active, budget):
     return {"requests": len(ids), "completed": ok, "p50_latency_s": pct(50), "p99_latency_s": pct(99),
             "mean_latency_s": sum(lat) / len(lat), "span_s": span,
             "throughput_req_per_s": len(ids) / span, "throughput_dof_per_s": sum(dofs) / span,
-            "max_active": max_active}
+            "offered_req_per_s": len(reqs) / reqs[-1]["t_arrival"],
+            "max_active": max_active, "batching": batch, "host_seconds": host}
 
 
 # ---------------------------------------------------------------- clocks

@@ -397,7 +397,10 @@ int vps_smooth_additive_static(int dim, int degree, int level, int precision, do
  * persistent kernels that take tiles from a device-side queue, one launch
  * per smoothing colour or transfer step -- and then the rest of each
  * member's iteration.  Requests join their cohort between these steps;
- * cohorts run concurrently.  precision: VPS_FP32 (FP32 V-cycle, FP64 CG)
+ * cohorts run concurrently.  The engine thread never waits for the GPU or
+ * for an allocation: hierarchies are built (and evicted ones destroyed) by
+ * a provisioning thread, and results are copied into the callers' buffers
+ * by a completion thread.  precision: VPS_FP32 (FP32 V-cycle, FP64 CG)
  * or VPS_FP64.  A request's result depends only on its own data: every
  * level of it goes through the operations of its own V-cycle in the same
  * order, so it is the same alone and in a mix.  Besides the budget, each
@@ -435,6 +438,12 @@ const char* vps_server_last_error(vps_server s);
  * Errors: VPS_EINVAL (s NULL). */
 int vps_server_batch_stats(vps_server s, int64_t* ticks, int64_t* batched_launches,
                            int* max_requests_per_launch, int* max_requests_per_tick);
+/* vps_server_host_times -- host seconds spent since creation by the engine
+ * thread in admission (seconds[0]), cohort V-cycle steps (seconds[1]) and
+ * polling (seconds[2]), and by the helper threads in building and
+ * destroying hierarchies (seconds[3]) and copying results into the callers'
+ * buffers (seconds[4]).  seconds: host array of 5.  Errors: VPS_EINVAL. */
+int vps_server_host_times(vps_server s, double* seconds);
 /* Stops the engine thread (requests still running are abandoned) and frees
  * every slot. */
 int vps_server_destroy(vps_server s);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "vps_server_stats": (_i, [_p, _i64p, _i64p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_server_last_error": (ctypes.c_char_p, [_p]),
     "vps_server_batch_stats": (_i, [_p, _i64p, _i64p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "vps_server_host_times": (_i, [_p, ctypes.POINTER(_d)]),
     "vps_server_destroy": (_i, [_p]),
     "vps_last_error": (ctypes.c_char_p, [_p]),
     "vps_status_string": (ctypes.c_char_p, [_i]),
@@ -444,6 +445,13 @@ class Server:
                                             ctypes.byref(ml), ctypes.byref(mt)), None)
         return dict(ticks=t.value, batched_launches=bl.value, max_requests_per_launch=ml.value,
                     max_requests_per_tick=mt.value)
+
+    def host_times(self):
+        """Host seconds of the engine's admission, cohort steps and polling,
+        and of the helper threads' hierarchy building and result copies."""
+        t = (ctypes.c_double * 5)()
+        _check(lib().vps_server_host_times(self.s, t), None)
+        return dict(admit_s=t[0], tick_s=t[1], poll_s=t[2], create_s=t[3], copy_s=t[4])
 
     def last_error(self):
         return lib().vps_server_last_error(self.s).decode()

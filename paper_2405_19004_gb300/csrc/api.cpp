@@ -123,6 +123,9 @@ struct vps_context {
   double* comp_x = nullptr;
   double* rhs_buf = nullptr;            // 1D load vectors for vps_assemble_rhs_sines
   size_t rhs_cap = 0;
+  double* rhs_host = nullptr;           // pinned staging of rhs_buf
+  size_t rhs_host_cap = 0;
+  cudaEvent_t rhs_ev = nullptr;         // after the last copy out of rhs_host
   double* l2_tab = nullptr;             // basis table for the L2 error
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -1069,8 +1072,21 @@ int upload_rhs_sines(vps_context* h, int level, int n_modes, const double* coef,
     if (e != cudaSuccess) return fail(h, VPS_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
     h->rhs_cap = need;
   }
-  // pageable source: staged before the call returns
-  VPS_CK(h, cudaMemcpyAsync(h->rhs_buf, b1d.data(), need, cudaMemcpyHostToDevice, h->stream));
+  // through pinned staging, so that the copy is asynchronous (a copy from
+  // pageable memory would first wait for all earlier work of the stream);
+  // the staging is reused once the previous copy out of it has executed
+  if (h->rhs_ev) VPS_CK(h, cudaEventSynchronize(h->rhs_ev));
+  else VPS_CK(h, cudaEventCreateWithFlags(&h->rhs_ev, cudaEventDisableTiming));
+  if (need > h->rhs_host_cap) {
+    if (h->rhs_host) cudaFreeHost(h->rhs_host);
+    h->rhs_host = nullptr;
+    h->rhs_host_cap = 0;
+    VPS_CK(h, cudaMallocHost(reinterpret_cast<void**>(&h->rhs_host), need));
+    h->rhs_host_cap = need;
+  }
+  std::memcpy(h->rhs_host, b1d.data(), need);
+  VPS_CK(h, cudaMemcpyAsync(h->rhs_buf, h->rhs_host, need, cudaMemcpyHostToDevice, h->stream));
+  VPS_CK(h, cudaEventRecord(h->rhs_ev, h->stream));
   VPS_CK(h, launch_rhs_tensor(g, n_modes, h->rhs_buf, b, h->stream));
   return VPS_OK;
 }
@@ -1197,6 +1213,39 @@ int cg_async_resume(vps_handle h) {
 }
 
 int cg_async_pending_vcycle(vps_handle h) { return h->as_external && h->as_need != 0; }
+
+// Allocates what asynchronous solves of up to max_modes sine modes use
+// (event, pinned result staging, the right-hand side's 1D tables), so that
+// cg_async_begin allocates nothing.
+int cg_async_prepare(vps_handle h, int max_modes) {
+  if (int rc = set_device(h)) return rc;
+  const LevelGeom& g = h->geom[h->L];
+  const int64_t ni = g.n1 - 2;
+  if (!h->as_ev) VPS_CK(h, cudaEventCreateWithFlags(&h->as_ev, cudaEventDisableTiming));
+  if (!h->host_x)
+    VPS_CK(h, cudaMallocHost(&h->host_x, (size_t)(h->dim == 3 ? ni * ni * ni : ni * ni) *
+                                              sizeof(double)));
+  const size_t need = (size_t)max_modes * h->dim * ni * sizeof(double);
+  if (need > h->rhs_cap) {
+    if (h->rhs_buf) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->rhs_buf);
+    }
+    h->rhs_buf = nullptr;
+    h->rhs_cap = 0;
+    VPS_CK(h, cudaMalloc(&h->rhs_buf, need));
+    h->rhs_cap = need;
+  }
+  if (!h->rhs_ev) VPS_CK(h, cudaEventCreateWithFlags(&h->rhs_ev, cudaEventDisableTiming));
+  if (need > h->rhs_host_cap) {
+    if (h->rhs_host) cudaFreeHost(h->rhs_host);
+    h->rhs_host = nullptr;
+    h->rhs_host_cap = 0;
+    VPS_CK(h, cudaMallocHost(reinterpret_cast<void**>(&h->rhs_host), need));
+    h->rhs_host_cap = need;
+  }
+  return VPS_OK;
+}
 
 void set_external_vcycle(vps_handle h, bool on) { h->as_external = on; }
 
@@ -1803,6 +1852,8 @@ int vps_destroy(vps_handle h) {
   if (h->host_x) cudaFreeHost(h->host_x);
   if (h->as_ev) cudaEventDestroy(h->as_ev);
   if (h->rhs_buf) cudaFree(h->rhs_buf);
+  if (h->rhs_host) cudaFreeHost(h->rhs_host);
+  if (h->rhs_ev) cudaEventDestroy(h->rhs_ev);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return VPS_OK;

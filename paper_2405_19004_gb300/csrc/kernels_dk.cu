@@ -50,12 +50,34 @@ constexpr int K = VPS_K;
 constexpr int n = 2 * K + 1;   // patch closure nodes per direction
 constexpr int m = 2 * K - 1;   // patch interior nodes per direction
 constexpr int nl = K + 1;      // nodes per cell and direction
+// Even/odd split (reflection about the patch centre): a closure line of n =
+// 2K+1 values has K+1 even parts e_c = x_c + x_{n-1-c} (c < K), e_K = x_K and
+// K odd parts d_c = x_c - x_{n-1-c}; an interior line of m = 2H+1 values has
+// H+1 even and H odd parts (centre H).
+constexpr int H = K - 1;
+constexpr int KE = K + 1;
+constexpr int HE = H + 1;
+constexpr int HO = H > 0 ? H : 1;   // array extent of the odd parts (none for K = 1)
 
 template <typename T>
 struct DevTab {
   T Ap[m * n];
   T Mp[m * n];
   T S[m * m];
+  // Halves of the centrosymmetric interior rows of Mp, Ap (W[m-1-o][n-1-c] =
+  // W[o][c]): WE[o][c] = (W[o][c] + W[o][n-1-c]) / 2 (c < K), WE[o][K] =
+  // W[o][K], o = 0..H; WO[o][c] = (W[o][c] - W[o][n-1-c]) / 2, o < H, c < K.
+  // Then (W x)_o = E_o + O_o, (W x)_{m-1-o} = E_o - O_o with E_o = WE[o] . e,
+  // O_o = WO[o] . d (O_H = 0).
+  T MpE[HE * KE];
+  T MpO[HO * K];
+  T ApE[HE * KE];
+  T ApO[HO * K];
+  // Halves of S, whose first H+1 columns are even and last H odd
+  // eigenvectors: SE[c][a] = S[c][a] (c, a <= H), SO[c][a] = S[c][H+1+a]
+  // (c, a < H).
+  T SE[HE * HE];
+  T SO[HO * HO];
   T Kb[K * n];
   T Mb[K * n];
   T P1[n * nl];
@@ -202,6 +224,127 @@ __device__ __forceinline__ void async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
+// ------------------------------------------------- even/odd contractions
+// Coefficients of the halves of Mp (MAT 0) and Ap (MAT 1).
+template <typename T, int MAT>
+__device__ __forceinline__ T coefE(int i) {
+  if constexpr (MAT == 0) return c_tab<T>.MpE[i];
+  else return c_tab<T>.ApE[i];
+}
+template <typename T, int MAT>
+__device__ __forceinline__ T coefO(int i) {
+  if constexpr (MAT == 0) return c_tab<T>.MpO[i];
+  else return c_tab<T>.ApO[i];
+}
+
+// Even and odd parts of a closure line x[0..n-1].
+template <typename T, int Q>
+__device__ __forceinline__ void split_closure(const T (&x)[n][Q], T (&e)[KE][Q], T (&d)[K][Q]) {
+#pragma unroll
+  for (int c = 0; c < K; ++c)
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      e[c][j] = x[c][j] + x[n - 1 - c][j];
+      d[c][j] = x[c][j] - x[n - 1 - c][j];
+    }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) e[K][j] = x[K][j];
+}
+
+// acc += (interior row o of W's even half) . e   (o <= H)
+template <typename T, int Q, int MAT>
+__device__ __forceinline__ void row_even(int o, const T (&e)[KE][Q], T (&acc)[Q]) {
+#pragma unroll
+  for (int c = 0; c <= K; ++c) {
+    const T w = coefE<T, MAT>(o * KE + c);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) acc[j] = fma(w, e[c][j], acc[j]);
+  }
+}
+// acc += (interior row o of W's odd half) . d   (o < H)
+template <typename T, int Q, int MAT>
+__device__ __forceinline__ void row_odd(int o, const T (&d)[K][Q], T (&acc)[Q]) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const T w = coefO<T, MAT>(o * K + c);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) acc[j] = fma(w, d[c][j], acc[j]);
+  }
+}
+
+// t = S^T x for an interior line: the even eigen-components t[0..H] from the
+// even parts of x, the odd ones t[H+1..m-1] from the odd parts.
+template <typename T, int Q>
+__device__ __forceinline__ void st_line(const T (&x)[m][Q], T (&t)[m][Q]) {
+  T e[HE][Q], d[HO][Q];
+#pragma unroll
+  for (int c = 0; c < H; ++c)
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      e[c][j] = x[c][j] + x[m - 1 - c][j];
+      d[c][j] = x[c][j] - x[m - 1 - c][j];
+    }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) e[H][j] = x[H][j];
+#pragma unroll
+  for (int a = 0; a <= H; ++a) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) t[a][j] = T(0);
+#pragma unroll
+    for (int c = 0; c <= H; ++c) {
+      const T w = c_tab<T>.SE[c * HE + a];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) t[a][j] = fma(w, e[c][j], t[a][j]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) t[HE + a][j] = T(0);
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      const T w = c_tab<T>.SO[c * HO + a];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) t[HE + a][j] = fma(w, d[c][j], t[HE + a][j]);
+    }
+  }
+}
+
+// y = S t for a line in eigen-components: y_o = E_o + O_o and
+// y_{m-1-o} = E_o - O_o (o < H), y_H = E_H, E from the even components,
+// O from the odd ones.
+template <typename T, int Q>
+__device__ __forceinline__ void s_line(const T (&t)[m][Q], T (&y)[m][Q]) {
+#pragma unroll
+  for (int o = 0; o <= H; ++o) {
+    T E[Q], O[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) E[j] = O[j] = T(0);
+#pragma unroll
+    for (int a = 0; a <= H; ++a) {
+      const T w = c_tab<T>.SE[o * HE + a];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) E[j] = fma(w, t[a][j], E[j]);
+    }
+    if (o < H) {
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        const T w = c_tab<T>.SO[o * HO + a];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) O[j] = fma(w, t[HE + a][j], O[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        y[o][j] = E[j] + O[j];
+        y[m - 1 - o][j] = E[j] - O[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) y[o][j] = E[j];
+    }
+  }
+}
+
 // One fast-diagonalisation contraction over interleaved tensors.
 // MODE 0: out = S^T in, MODE 1: out = (S^T in) * il, MODE 2: out = S in.
 template <typename T, int G, int Q, int NT, int MODE>
@@ -220,22 +363,16 @@ __device__ __forceinline__ void fd_stage(const T* __restrict__ in, T* __restrict
 #pragma unroll
       for (int j = 0; j < Q; ++j) v[c][j] = pk.v[j];
     }
+    T u[m][Q];
+    if constexpr (MODE == 2) s_line<T, Q>(v, u);
+    else st_line<T, Q>(v, u);
     PK* dst = reinterpret_cast<PK*>(out + L * m * P + g * Q);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      T acc[Q];
-#pragma unroll
-      for (int j = 0; j < Q; ++j) acc[j] = T(0);
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const T w = MODE == 2 ? c_tab<T>.S[o * m + c] : c_tab<T>.S[c * m + o];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) acc[j] = fma(w, v[c][j], acc[j]);
-      }
       PK r;
       const T sc = MODE == 1 ? il[L * m + o] : T(1);
 #pragma unroll
-      for (int j = 0; j < Q; ++j) r.v[j] = MODE == 1 ? acc[j] * sc : acc[j];
+      for (int j = 0; j < Q; ++j) r.v[j] = MODE == 1 ? u[o][j] * sc : u[o][j];
       dst[o * G] = r;
     }
   });
@@ -264,34 +401,23 @@ __device__ __forceinline__ void fd_pair(const T* __restrict__ in, T* __restrict_
       for (int j = 0; j < Q; ++j) v[c][j] = pk.v[j];
     }
     T tt[m][Q];
+    st_line<T, Q>(v, tt);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-#pragma unroll
-      for (int j = 0; j < Q; ++j) tt[o][j] = T(0);
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const T w = c_tab<T>.S[c * m + o];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) tt[o][j] = fma(w, v[c][j], tt[o][j]);
-      }
       const T sc = il[L * m + o];
 #pragma unroll
       for (int j = 0; j < Q; ++j) tt[o][j] *= sc;
     }
+    T u[m][Q];
+    s_line<T, Q>(tt, u);
     const int Lw = SWAP ? (L % m) * m + L / m : L;
     PK* dst = reinterpret_cast<PK*>(out + Lw * m * P + g * Q);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      PK u;
+      PK r;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) u.v[j] = T(0);
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const T w = c_tab<T>.S[o * m + c];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) u.v[j] = fma(w, tt[c][j], u.v[j]);
-      }
-      dst[o * G] = u;
+      for (int j = 0; j < Q; ++j) r.v[j] = u[o][j];
+      dst[o * G] = r;
     }
   });
 }
@@ -323,17 +449,7 @@ __device__ __forceinline__ void fd_final(const T* __restrict__ in, T* __restrict
       rowoff = (L + 1) * px + 1;
     }
     T u[m][Q];
-#pragma unroll
-    for (int o = 0; o < m; ++o) {
-#pragma unroll
-      for (int j = 0; j < Q; ++j) u[o][j] = T(0);
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const T w = c_tab<T>.S[o * m + c];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) u[o][j] = fma(w, v[c][j], u[o][j]);
-      }
-    }
+    s_line<T, Q>(v, u);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
       const int org = s_org[g * Q + j];
@@ -529,22 +645,34 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
           d[(c - 1) * m * m * G] = pk;
         }
       }
+      // M x and A x on the interior rows, by the even/odd halves
+      T ev[KE][Q], od[K][Q];
+      split_closure<T, Q>(v, ev, od);
 #pragma unroll
-      for (int o = 0; o < m; ++o) {
-        PK am, aa;
+      for (int o = 0; o <= H; ++o) {
+        T em[Q], ea[Q], om[Q], oa[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) am.v[j] = aa.v[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            am.v[j] = fma(wm, v[c][j], am.v[j]);
-            aa.v[j] = fma(wa, v[c][j], aa.v[j]);
-          }
+        for (int j = 0; j < Q; ++j) em[j] = ea[j] = om[j] = oa[j] = T(0);
+        row_even<T, Q, 0>(o, ev, em);
+        row_even<T, Q, 1>(o, ev, ea);
+        if (o < H) {
+          row_odd<T, Q, 0>(o, od, om);
+          row_odd<T, Q, 1>(o, od, oa);
         }
-        dM[o * G] = am;
-        dA[o * G] = aa;
+        PK m0, m1, a0, a1;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          m0.v[j] = em[j] + om[j];
+          m1.v[j] = em[j] - om[j];
+          a0.v[j] = ea[j] + oa[j];
+          a1.v[j] = ea[j] - oa[j];
+        }
+        dM[o * G] = m0;
+        dA[o * G] = a0;
+        if (o < H) {
+          dM[(m - 1 - o) * G] = m1;
+          dA[(m - 1 - o) * G] = a1;
+        }
       }
     });
     __syncthreads();
@@ -567,23 +695,36 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
       }
       PK* dU = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
       PK* dW = reinterpret_cast<PK*>(B1 + L * m * P + g * Q);
+      T em[KE][Q], dm[K][Q], ea[KE][Q], da[K][Q];
+      split_closure<T, Q>(vm, em, dm);
+      split_closure<T, Q>(va, ea, da);
 #pragma unroll
-      for (int o = 0; o < m; ++o) {
-        PK u, w;
+      for (int o = 0; o <= H; ++o) {
+        T eu[Q], ew[Q], ou[Q], ow[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) u.v[j] = w.v[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            u.v[j] = fma(wm, vm[c][j], u.v[j]);
-            w.v[j] = fma(wa, vm[c][j], w.v[j]);
-            w.v[j] = fma(wm, va[c][j], w.v[j]);
-          }
+        for (int j = 0; j < Q; ++j) eu[j] = ew[j] = ou[j] = ow[j] = T(0);
+        row_even<T, Q, 0>(o, em, eu);
+        row_even<T, Q, 1>(o, em, ew);
+        row_even<T, Q, 0>(o, ea, ew);
+        if (o < H) {
+          row_odd<T, Q, 0>(o, dm, ou);
+          row_odd<T, Q, 1>(o, dm, ow);
+          row_odd<T, Q, 0>(o, da, ow);
         }
-        dU[o * G] = u;
-        dW[o * G] = w;
+        PK u0, u1, w0, w1;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          u0.v[j] = eu[j] + ou[j];
+          u1.v[j] = eu[j] - ou[j];
+          w0.v[j] = ew[j] + ow[j];
+          w1.v[j] = ew[j] - ow[j];
+        }
+        dU[o * G] = u0;
+        dW[o * G] = w0;
+        if (o < H) {
+          dU[(m - 1 - o) * G] = u1;
+          dW[(m - 1 - o) * G] = w1;
+        }
       }
     });
     async_wait_all();
@@ -608,29 +749,38 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
       constexpr bool kKeep = !RES && kFuseFD;  // keep the line for S^T along x
       PK* dR = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
       T rr[kKeep ? m : 1][Q];
+      // A vu + M vw on the interior rows, by the even/odd halves
+      T ex[KE][Q], dx[K][Q], ey[KE][Q], dy[K][Q];
+      split_closure<T, Q>(vu, ex, dx);
+      split_closure<T, Q>(vw, ey, dy);
 #pragma unroll
-      for (int o = 0; o < m; ++o) {
-        T acc[Q];
+      for (int o = 0; o <= H; ++o) {
+        T E[Q], O[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) acc[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            acc[j] = fma(wa, vu[c][j], acc[j]);
-            acc[j] = fma(wm, vw[c][j], acc[j]);
-          }
+        for (int j = 0; j < Q; ++j) E[j] = O[j] = T(0);
+        row_even<T, Q, 1>(o, ex, E);
+        row_even<T, Q, 0>(o, ey, E);
+        if (o < H) {
+          row_odd<T, Q, 1>(o, dx, O);
+          row_odd<T, Q, 0>(o, dy, O);
         }
-        const PK bv = sb[o * G];
-        if constexpr (kKeep) {
 #pragma unroll
-          for (int j = 0; j < Q; ++j) rr[o][j] = fma(bscale, bv.v[j], -acc[j]);
-        } else {  // the residual itself, [z][y][x]
-          PK r;
+        for (int side = 0; side < 2; ++side) {
+          if (side == 1 && o == H) continue;
+          const int oo = side == 0 ? o : m - 1 - o;
+          const PK bv = sb[oo * G];
+          T acc[Q];
 #pragma unroll
-          for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
-          dR[o * G] = r;
+          for (int j = 0; j < Q; ++j) acc[j] = side == 0 ? E[j] + O[j] : E[j] - O[j];
+          if constexpr (kKeep) {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) rr[oo][j] = fma(bscale, bv.v[j], -acc[j]);
+          } else {  // the residual itself, [z][y][x]
+            PK r;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+            dR[oo * G] = r;
+          }
         }
       }
       if constexpr (kKeep) {
@@ -638,18 +788,14 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
         // x, written as [y][z][x'] (y contracted next)
         const int Ls = (L % m) * m + L / m;
         PK* dT = reinterpret_cast<PK*>(A0 + Ls * m * P + g * Q);
+        T tt[m][Q];
+        st_line<T, Q>(rr, tt);
 #pragma unroll
         for (int o = 0; o < m; ++o) {
-          PK tt;
+          PK pk;
 #pragma unroll
-          for (int j = 0; j < Q; ++j) tt.v[j] = T(0);
-#pragma unroll
-          for (int c = 0; c < m; ++c) {
-            const T w = c_tab<T>.S[c * m + o];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) tt.v[j] = fma(w, rr[c][j], tt.v[j]);
-          }
-          dT[o * G] = tt;
+          for (int j = 0; j < Q; ++j) pk.v[j] = tt[o][j];
+          dT[o * G] = pk;
         }
       }
     });
@@ -734,22 +880,34 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
       }
       PK* dM = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
       PK* dA = reinterpret_cast<PK*>(A1 + L * m * P + g * Q);
+      // M x and A x on the interior rows, by the even/odd halves
+      T ev[KE][Q], od[K][Q];
+      split_closure<T, Q>(v, ev, od);
 #pragma unroll
-      for (int o = 0; o < m; ++o) {
-        PK am, aa;
+      for (int o = 0; o <= H; ++o) {
+        T em[Q], ea[Q], om[Q], oa[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) am.v[j] = aa.v[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            am.v[j] = fma(wm, v[c][j], am.v[j]);
-            aa.v[j] = fma(wa, v[c][j], aa.v[j]);
-          }
+        for (int j = 0; j < Q; ++j) em[j] = ea[j] = om[j] = oa[j] = T(0);
+        row_even<T, Q, 0>(o, ev, em);
+        row_even<T, Q, 1>(o, ev, ea);
+        if (o < H) {
+          row_odd<T, Q, 0>(o, od, om);
+          row_odd<T, Q, 1>(o, od, oa);
         }
-        dM[o * G] = am;
-        dA[o * G] = aa;
+        PK m0, m1, a0, a1;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          m0.v[j] = em[j] + om[j];
+          m1.v[j] = em[j] - om[j];
+          a0.v[j] = ea[j] + oa[j];
+          a1.v[j] = ea[j] - oa[j];
+        }
+        dM[o * G] = m0;
+        dA[o * G] = a0;
+        if (o < H) {
+          dM[(m - 1 - o) * G] = m1;
+          dA[(m - 1 - o) * G] = a1;
+        }
       }
     });
     async_wait_all();
@@ -773,44 +931,49 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
       PK* dR = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
       constexpr bool kKeep = !RES && kFuseFD;  // keep the line for S^T along x
       T rr[kKeep ? m : 1][Q];
+      // A vm + M va on the interior rows, by the even/odd halves
+      T ex[KE][Q], dx[K][Q], ey[KE][Q], dy[K][Q];
+      split_closure<T, Q>(vm, ex, dx);
+      split_closure<T, Q>(va, ey, dy);
 #pragma unroll
-      for (int o = 0; o < m; ++o) {
-        T acc[Q];
+      for (int o = 0; o <= H; ++o) {
+        T E[Q], O[Q];
 #pragma unroll
-        for (int j = 0; j < Q; ++j) acc[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const T wm = c_tab<T>.Mp[o * n + c], wa = c_tab<T>.Ap[o * n + c];
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            acc[j] = fma(wa, vm[c][j], acc[j]);
-            acc[j] = fma(wm, va[c][j], acc[j]);
-          }
+        for (int j = 0; j < Q; ++j) E[j] = O[j] = T(0);
+        row_even<T, Q, 1>(o, ex, E);
+        row_even<T, Q, 0>(o, ey, E);
+        if (o < H) {
+          row_odd<T, Q, 1>(o, dx, O);
+          row_odd<T, Q, 0>(o, dy, O);
         }
-        const PK bv = sb[o * G];
-        if constexpr (kKeep) {
 #pragma unroll
-          for (int j = 0; j < Q; ++j) rr[o][j] = fma(bscale, bv.v[j], -acc[j]);
-        } else {  // the residual itself, [y][x]
-          PK r;
+        for (int side = 0; side < 2; ++side) {
+          if (side == 1 && o == H) continue;
+          const int oo = side == 0 ? o : m - 1 - o;
+          const PK bv = sb[oo * G];
+          T acc[Q];
 #pragma unroll
-          for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
-          dR[o * G] = r;
+          for (int j = 0; j < Q; ++j) acc[j] = side == 0 ? E[j] + O[j] : E[j] - O[j];
+          if constexpr (kKeep) {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) rr[oo][j] = fma(bscale, bv.v[j], -acc[j]);
+          } else {  // the residual itself, [y][x]
+            PK r;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) r.v[j] = fma(bscale, bv.v[j], -acc[j]);
+            dR[oo * G] = r;
+          }
         }
       }
       if constexpr (kKeep) {  // S^T along x in registers, [y][x']
+        T tt[m][Q];
+        st_line<T, Q>(rr, tt);
 #pragma unroll
         for (int o = 0; o < m; ++o) {
-          PK tt;
+          PK pk;
 #pragma unroll
-          for (int j = 0; j < Q; ++j) tt.v[j] = T(0);
-#pragma unroll
-          for (int c = 0; c < m; ++c) {
-            const T w = c_tab<T>.S[c * m + o];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) tt.v[j] = fma(w, rr[c][j], tt.v[j]);
-          }
-          dR[o * G] = tt;
+          for (int j = 0; j < Q; ++j) pk.v[j] = tt[o][j];
+          dR[o * G] = pk;
         }
       }
     });
@@ -922,18 +1085,14 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
       for (int c = 0; c < m; ++c) v[c][j] = org >= 0 ? src[c * stride] : T(0);
     }
     PK* dst = reinterpret_cast<PK*>(X1 + L * m * P + g * Q);
+    T u[m][Q];
+    st_line<T, Q>(v, u);
 #pragma unroll
     for (int o = 0; o < m; ++o) {
-      PK acc;
+      PK pk;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) acc.v[j] = T(0);
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const T w = c_tab<T>.S[c * m + o];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) acc.v[j] = fma(w, v[c][j], acc.v[j]);
-      }
-      dst[o * G] = acc;
+      for (int j = 0; j < Q; ++j) pk.v[j] = u[o][j];
+      dst[o * G] = pk;
     }
   });
   __syncthreads();
@@ -2347,6 +2506,21 @@ void fill_tab(const HostTables& h, DevTab<T>* d) {
     d->Mp[i] = (T)h.Mp[i];
   }
   for (int i = 0; i < m * m; ++i) d->S[i] = (T)h.S[i];
+  for (int o = 0; o <= H; ++o)
+    for (int c = 0; c <= K; ++c) {
+      const double mr = c < K ? h.Mp[o * n + n - 1 - c] : h.Mp[o * n + c];
+      const double ar = c < K ? h.Ap[o * n + n - 1 - c] : h.Ap[o * n + c];
+      d->MpE[o * KE + c] = (T)(c < K ? 0.5 * (h.Mp[o * n + c] + mr) : h.Mp[o * n + c]);
+      d->ApE[o * KE + c] = (T)(c < K ? 0.5 * (h.Ap[o * n + c] + ar) : h.Ap[o * n + c]);
+      if (o < H && c < K) {
+        d->MpO[o * K + c] = (T)(0.5 * (h.Mp[o * n + c] - mr));
+        d->ApO[o * K + c] = (T)(0.5 * (h.Ap[o * n + c] - ar));
+      }
+    }
+  for (int c = 0; c <= H; ++c)
+    for (int a = 0; a <= H; ++a) d->SE[c * HE + a] = (T)h.S[c * m + a];
+  for (int c = 0; c < H; ++c)
+    for (int a = 0; a < H; ++a) d->SO[c * HO + a] = (T)h.S[c * m + HE + a];
   for (int i = 0; i < K * n; ++i) {
     d->Kb[i] = (T)h.Kb[i];
     d->Mb[i] = (T)h.Mb[i];

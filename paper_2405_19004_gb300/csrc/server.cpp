@@ -35,6 +35,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "vps.h"
@@ -64,11 +65,15 @@ struct Request {
 
 struct Cohort;
 
+enum SlotState { kCreating, kIdle, kActive, kCompleting, kFailed };
+
 struct Slot {
   vps_context* h = nullptr;
   int d = 0, k = 0, L = 0;
   size_t bytes = 0;
-  int64_t req = 0;  // 0: idle
+  std::atomic<int> state{kCreating};  // written under mu; read by the engine without it
+  int create_rc = VPS_OK;
+  int64_t req = 0;  // the request of an active or completing slot
   double last_used = 0;
   Cohort* cohort = nullptr;
 };
@@ -84,9 +89,32 @@ struct Cohort {
 };
 
 constexpr size_t kCohortQueueBytes = size_t(4) << 20;
+constexpr int kMaxModesPrepared = 8;   // sine modes the slots' buffers are sized for
+constexpr int kMaxCreating = 4;        // hierarchies being built at a time
+
+// A job of the provisioning thread: build a slot's hierarchy, or destroy an
+// evicted one.
+struct ProvJob {
+  Slot* create = nullptr;
+  vps_context* destroy = nullptr;
+};
+
+// A job of the completion thread: copy a finished request's result from the
+// slot's pinned staging into the caller's buffer.
+struct DoneJob {
+  Slot* slot = nullptr;
+  int64_t req = 0;
+  const double* x = nullptr;
+  int state = 0, status = 0, iters = 0;
+  double rel = 0.0;
+};
 
 }  // namespace
 
+// Three host threads: the engine (admission, cohort V-cycles, polling; it
+// never waits for the GPU or for an allocation), the provisioner (builds and
+// destroys hierarchies: vps_create allocates and uploads, vps_destroy
+// synchronises) and the completer (copies results into the callers' buffers).
 struct vps_server_ctx {
   size_t budget = 0;
   int max_active = 1;
@@ -95,29 +123,44 @@ struct vps_server_ctx {
   int max_it = 100;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv;
-  std::thread engine;
+  std::condition_variable cv;       // request state changes, slot readiness
+  std::condition_variable prov_cv;  // provisioner jobs
+  std::condition_variable done_cv;  // completer jobs
+  std::thread engine, provisioner, completer;
   std::atomic<bool> stop{false};
   std::map<int64_t, Request> reqs;
   std::deque<int64_t> queue;
-  std::vector<std::unique_ptr<Slot>> slots;      // engine thread only
+  std::vector<std::unique_ptr<Slot>> slots;      // vector: engine thread; Slot fields: under mu
   std::vector<std::unique_ptr<Cohort>> cohorts;  // engine thread only
-  size_t used = 0;          // engine thread only
-  // batching statistics (engine thread writes, under mu)
+  std::deque<ProvJob> prov_jobs;                 // under mu
+  std::deque<DoneJob> done_jobs;                 // under mu
+  size_t used = 0;          // engine thread only (budget accounting)
+  // batching statistics (under mu)
   int64_t ticks = 0, batched_launches = 0;
   int max_per_launch = 0, max_per_tick = 0;
+  // host time of the engine's parts and of the helper threads (under mu)
+  double t_admit = 0, t_tick = 0, t_poll = 0, t_create = 0, t_copy = 0;
   int64_t next_id = 1;
   int64_t n_done = 0;
   int active = 0;
   std::string err;
 
   void run();
-  bool admit_one();
+  void run_provisioner();
+  void run_completer();
+  bool admit();
   bool tick(Cohort& c);
   Cohort* cohort_of(int d, int k, int* rc);
-  void finish(Slot& s, int state, int status, int iters, double rel, const double* x);
+  void fail_request(int64_t id, int status);
+  void finish_error(Slot& s, int status, int iters, double rel);
   void release();
 };
+
+namespace {
+
+double since(double t0) { return now_s() - t0; }
+
+}  // namespace
 
 // The cohort of (d, k), created on first use.
 Cohort* vps_server_ctx::cohort_of(int d, int k, int* rc) {
@@ -135,6 +178,7 @@ Cohort* vps_server_ctx::cohort_of(int d, int k, int* rc) {
     if (c->q_dev) cudaFree(c->q_dev);
     if (c->q_host) cudaFreeHost(c->q_host);
     if (c->stream) cudaStreamDestroy(c->stream);
+    std::lock_guard<std::mutex> lock(mu);
     err = cudaGetErrorString(e);
     *rc = e == cudaErrorMemoryAllocation ? VPS_ENOMEM : VPS_ECUDA;
     return nullptr;
@@ -143,178 +187,340 @@ Cohort* vps_server_ctx::cohort_of(int d, int k, int* rc) {
   return cohorts.back().get();
 }
 
-// Runs one V-cycle for every member of c that waits for one, then the rest
-// of their CG iterations, if no work of the cohort is in flight.
+// Runs one V-cycle for every active member of c that waits for one, then
+// the rest of their CG iterations, if none of the cohort's work is in flight.
 bool vps_server_ctx::tick(Cohort& c) {
   std::vector<Slot*> pending;
   for (auto& sp : slots) {
     Slot& s = *sp;
-    if (!s.req || s.cohort != &c) continue;
+    if (s.state != kActive || s.cohort != &c) continue;
     if (vps::cg_async_pending_vcycle(s.h)) pending.push_back(&s);
     else return false;  // a member's work is still in flight
   }
   if (pending.empty()) return false;
+  const double t0 = now_s();
   std::vector<vps_context*> hs;
   for (Slot* s : pending) hs.push_back(s->h);
   int64_t launches = 0;
   int per_launch = 0;
   int rc = vps::cohort_vcycle(hs.data(), (int)hs.size(), c.q_host, c.q_dev, c.q_cap, &launches,
                               &per_launch);
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    ++ticks;
-    batched_launches += launches;
-    max_per_launch = std::max(max_per_launch, per_launch);
-    max_per_tick = std::max(max_per_tick, (int)hs.size());
-  }
   for (Slot* s : pending) {
     int r = rc ? rc : vps::cg_async_resume(s->h);
     if (r) {
-      err = vps::handle_error(rc ? hs[0] : s->h);
-      finish(*s, VPS_REQ_FAILED, r, 0, 0.0, nullptr);
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        err = vps::handle_error(rc ? hs[0] : s->h);
+      }
+      finish_error(*s, r, 0, 0.0);
     }
   }
+  std::lock_guard<std::mutex> lock(mu);
+  ++ticks;
+  batched_launches += launches;
+  max_per_launch = std::max(max_per_launch, per_launch);
+  max_per_tick = std::max(max_per_tick, (int)hs.size());
+  t_tick += since(t0);
   return true;
 }
 
-void vps_server_ctx::finish(Slot& s, int state, int status, int iters, double rel,
-                            const double* x) {
+// Marks a queued request failed (engine thread, not holding mu).
+void vps_server_ctx::fail_request(int64_t id, int status) {
+  std::lock_guard<std::mutex> lock(mu);
+  auto q = std::find(queue.begin(), queue.end(), id);
+  if (q != queue.end()) queue.erase(q);
+  Request& r = reqs[id];
+  r.state = VPS_REQ_FAILED;
+  r.status = status;
+  r.t_done = now_s();
+  ++n_done;
+  cv.notify_all();
+}
+
+// Ends the request of an active slot with an error (no result to copy).
+void vps_server_ctx::finish_error(Slot& s, int status, int iters, double rel) {
   std::lock_guard<std::mutex> lock(mu);
   Request& r = reqs[s.req];
-  if (x && r.x_out) std::memcpy(r.x_out, x, (size_t)r.n * sizeof(double));
-  r.state = state;
+  r.state = VPS_REQ_FAILED;
   r.status = status;
   r.iters = iters;
   r.rel = rel;
   r.t_done = now_s();
   s.req = 0;
+  s.state = kIdle;
   s.last_used = r.t_done;
   --active;
   ++n_done;
   cv.notify_all();
 }
 
-// Admits the first queued request that fits; returns true if one started.
-bool vps_server_ctx::admit_one() {
-  int64_t id = 0;
-  Request snapshot;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (queue.empty() || active >= max_active) return false;
-    // first queued request with an idle slot of its shape, else the head
-    size_t pick = 0;
-    bool found = false;
-    for (size_t qi = 0; qi < queue.size() && qi < 64 && !found; ++qi) {
-      const Request& r = reqs[queue[qi]];
-      for (const auto& s : slots)
-        if (!s->req && s->d == r.d && s->k == r.k && s->L == r.L) {
-          pick = qi;
-          found = true;
+// Admission: starts queued requests that have an idle slot of their shape
+// (queue order, within the first 64), and orders new hierarchies from the
+// provisioner for shapes with more waiting requests than idle or building
+// slots.  Returns true if anything changed.
+bool vps_server_ctx::admit() {
+  const double t0 = now_s();
+  bool changed = false;
+  // slots whose creation failed: fail one waiting request of their shape
+  for (auto it = slots.begin(); it != slots.end();) {
+    int st, rc;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      st = (*it)->state;
+      rc = (*it)->create_rc;
+    }
+    if (st != kFailed) {
+      ++it;
+      continue;
+    }
+    const Slot& s = **it;
+    int64_t victim = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      for (int64_t id : queue) {
+        const Request& r = reqs[id];
+        if (r.d == s.d && r.k == s.k && r.L == s.L) {
+          victim = id;
           break;
         }
+      }
     }
-    id = queue[pick];
-    snapshot = reqs[id];
+    if (victim) fail_request(victim, rc);
+    used -= s.bytes;
+    it = slots.erase(it);
+    changed = true;
   }
-  Slot* slot = nullptr;
-  for (auto& s : slots)
-    if (!s->req && s->d == snapshot.d && s->k == snapshot.k && s->L == snapshot.L) {
-      slot = s.get();
-      break;
-    }
-  if (!slot) {
-    const size_t need =
-        vps::estimate_device_bytes(snapshot.d, snapshot.k, snapshot.L, precision);
-    if (need > budget) {  // can never fit
-      std::lock_guard<std::mutex> lock(mu);
-      queue.erase(std::find(queue.begin(), queue.end(), id));
-      Request& r = reqs[id];
-      r.state = VPS_REQ_FAILED;
-      r.status = VPS_ENOMEM;
-      r.t_done = now_s();
-      ++n_done;
-      cv.notify_all();
-      return true;
-    }
-    // evict idle slots, least recently used first, until the request fits
-    while (used + need > budget) {
-      auto victim = slots.end();
-      for (auto it = slots.begin(); it != slots.end(); ++it)
-        if (!(*it)->req && (victim == slots.end() || (*it)->last_used < (*victim)->last_used))
-          victim = it;
-      if (victim == slots.end()) return false;  // wait for a running request to finish
-      vps_destroy((*victim)->h);
-      used -= (*victim)->bytes;
-      slots.erase(victim);
-    }
-    auto s = std::make_unique<Slot>();
-    s->d = snapshot.d;
-    s->k = snapshot.k;
-    s->L = snapshot.L;
-    int rc = VPS_OK;
-    s->cohort = cohort_of(s->d, s->k, &rc);
-    if (!rc)
-      rc = vps_create(s->d, s->k, s->L, precision, VPS_MULTIPLICATIVE, 1.0, 1, 1,
-                      s->cohort->stream, &s->h);
-    if (!rc) vps::set_external_vcycle(s->h, true);
-    if (rc) {
-      std::lock_guard<std::mutex> lock(mu);
-      queue.erase(std::find(queue.begin(), queue.end(), id));
-      Request& r = reqs[id];
-      r.state = VPS_REQ_FAILED;
-      r.status = rc;
-      r.t_done = now_s();
-      ++n_done;
-      if (s->cohort) err = vps_last_error(nullptr);  // else cohort_of has set it
-      cv.notify_all();
-      return true;
-    }
-    vps_sizes(s->h, nullptr, nullptr, &s->bytes);
-    used += s->bytes;
-    slots.push_back(std::move(s));
-    slot = slots.back().get();
-  }
+  // start requests with an idle slot
+  std::vector<std::pair<int64_t, Slot*>> starts;
+  std::vector<Request> snaps;
   {
     std::lock_guard<std::mutex> lock(mu);
-    queue.erase(std::find(queue.begin(), queue.end(), id));
-    Request& r = reqs[id];
-    r.state = VPS_REQ_RUNNING;
-    r.t_start = now_s();
-    ++active;
+    for (size_t qi = 0; qi < queue.size() && qi < 64 && active < max_active;) {
+      const Request& r = reqs[queue[qi]];
+      Slot* slot = nullptr;
+      for (auto& s : slots)
+        if (s->state == kIdle && s->d == r.d && s->k == r.k && s->L == r.L) {
+          slot = s.get();
+          break;
+        }
+      if (!slot) {
+        ++qi;
+        continue;
+      }
+      const int64_t id = queue[qi];
+      queue.erase(queue.begin() + qi);
+      Request& rr = reqs[id];
+      rr.state = VPS_REQ_RUNNING;
+      rr.t_start = now_s();
+      ++active;
+      slot->state = kActive;
+      slot->req = id;
+      starts.push_back({id, slot});
+      snaps.push_back(rr);
+    }
   }
-  slot->req = id;
-  const int rc = vps::cg_async_begin(slot->h, (int)snapshot.coef.size(), snapshot.coef.data(),
-                                     snapshot.freq.data(), rtol, max_it);
-  if (rc) {
-    err = vps::handle_error(slot->h);
-    finish(*slot, VPS_REQ_FAILED, rc, 0, 0.0, nullptr);
+  for (size_t i = 0; i < starts.size(); ++i) {
+    Slot* slot = starts[i].second;
+    const Request& r = snaps[i];
+    const int rc = vps::cg_async_begin(slot->h, (int)r.coef.size(), r.coef.data(), r.freq.data(),
+                                       rtol, max_it);
+    if (rc) {
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        err = vps::handle_error(slot->h);
+      }
+      finish_error(*slot, rc, 0, 0.0);
+    }
+    changed = true;
   }
-  return true;
+  // order hierarchies for waiting requests without a slot
+  std::vector<Request> want;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    int creating = 0;
+    for (auto& s : slots) creating += s->state == kCreating;
+    std::map<std::tuple<int, int, int>, int> spare;  // idle or building slots per shape
+    for (auto& s : slots)
+      if (s->state == kIdle || s->state == kCreating) ++spare[std::make_tuple(s->d, s->k, s->L)];
+    for (size_t qi = 0; qi < queue.size() && qi < 64 && creating < kMaxCreating; ++qi) {
+      const Request& r = reqs[queue[qi]];
+      int& sp = spare[std::make_tuple(r.d, r.k, r.L)];
+      if (sp > 0) {
+        --sp;
+        continue;
+      }
+      want.push_back(r);
+      ++creating;
+    }
+  }
+  for (const Request& r : want) {
+    const size_t need = vps::estimate_device_bytes(r.d, r.k, r.L, precision);
+    if (need > budget) {  // can never fit
+      fail_request(r.id, VPS_ENOMEM);
+      changed = true;
+      continue;
+    }
+    // evict idle slots, least recently used first, until the request fits
+    bool fits = true;
+    while (used + need > budget) {
+      auto victim = slots.end();
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto it = slots.begin(); it != slots.end(); ++it)
+          if ((*it)->state == kIdle &&
+              (victim == slots.end() || (*it)->last_used < (*victim)->last_used))
+            victim = it;
+      }
+      if (victim == slots.end()) {
+        fits = false;  // wait for a running request to finish
+        break;
+      }
+      used -= (*victim)->bytes;
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        prov_jobs.push_back({nullptr, (*victim)->h});
+        prov_cv.notify_one();
+      }
+      slots.erase(victim);
+      changed = true;
+    }
+    if (!fits) break;
+    int rc = VPS_OK;
+    Cohort* c = cohort_of(r.d, r.k, &rc);
+    if (rc) {
+      fail_request(r.id, rc);
+      changed = true;
+      continue;
+    }
+    auto s = std::make_unique<Slot>();
+    s->d = r.d;
+    s->k = r.k;
+    s->L = r.L;
+    s->cohort = c;
+    s->bytes = need;
+    used += need;
+    std::lock_guard<std::mutex> lock(mu);
+    prov_jobs.push_back({s.get(), nullptr});
+    prov_cv.notify_one();
+    slots.push_back(std::move(s));
+    changed = true;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  t_admit += since(t0);
+  return changed;
+}
+
+void vps_server_ctx::run_provisioner() {
+  cudaSetDevice(device);
+  while (true) {
+    ProvJob job;
+    {
+      std::unique_lock<std::mutex> lock(mu);
+      prov_cv.wait(lock, [&] { return stop.load() || !prov_jobs.empty(); });
+      if (prov_jobs.empty()) return;  // stopping
+      job = prov_jobs.front();
+      prov_jobs.pop_front();
+    }
+    const double t0 = now_s();
+    if (job.destroy) {
+      vps_destroy(job.destroy);
+    } else if (Slot* s = job.create) {
+      vps_context* h = nullptr;
+      int rc = vps_create(s->d, s->k, s->L, precision, VPS_MULTIPLICATIVE, 1.0, 1, 1,
+                          s->cohort->stream, &h);
+      if (!rc) {
+        vps::set_external_vcycle(h, true);
+        rc = vps::cg_async_prepare(h, kMaxModesPrepared);
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      if (rc) {
+        err = h ? vps::handle_error(h) : vps_last_error(nullptr);
+        if (h) vps_destroy(h);
+        s->create_rc = rc;
+        s->state = kFailed;
+      } else {
+        s->h = h;
+        s->state = kIdle;
+      }
+      cv.notify_all();
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    t_create += since(t0);
+  }
+}
+
+void vps_server_ctx::run_completer() {
+  while (true) {
+    DoneJob job;
+    {
+      std::unique_lock<std::mutex> lock(mu);
+      done_cv.wait(lock, [&] { return stop.load() || !done_jobs.empty(); });
+      if (done_jobs.empty()) return;  // stopping
+      job = done_jobs.front();
+      done_jobs.pop_front();
+    }
+    const double t0 = now_s();
+    double* out = nullptr;
+    int64_t n = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      const Request& r = reqs[job.req];
+      out = r.x_out;
+      n = r.n;
+    }
+    if (out && job.x) std::memcpy(out, job.x, (size_t)n * sizeof(double));
+    std::lock_guard<std::mutex> lock(mu);
+    Request& r = reqs[job.req];
+    r.state = job.state;
+    r.status = job.status;
+    r.iters = job.iters;
+    r.rel = job.rel;
+    r.t_done = now_s();
+    job.slot->req = 0;
+    job.slot->state = kIdle;
+    job.slot->last_used = r.t_done;
+    --active;
+    ++n_done;
+    t_copy += since(t0);
+    cv.notify_all();
+  }
 }
 
 void vps_server_ctx::run() {
   cudaSetDevice(device);
   while (!stop.load()) {
     bool progressed = false;
+    const double t0 = now_s();
     for (auto& sp : slots) {
       Slot& s = *sp;
-      if (!s.req || vps::cg_async_pending_vcycle(s.h)) continue;
+      if (s.state != kActive || vps::cg_async_pending_vcycle(s.h)) continue;
       int done = 0, status = 0, iters = 0;
       double rel = 0;
       const double* x = nullptr;
       const int rc = vps::cg_async_poll(s.h, &done, &status, &iters, &rel, &x);
       if (rc) {
-        err = vps::handle_error(s.h);
-        finish(s, VPS_REQ_FAILED, rc, iters, rel, nullptr);
+        {
+          std::lock_guard<std::mutex> lock(mu);
+          err = vps::handle_error(s.h);
+        }
+        finish_error(s, rc, iters, rel);
         progressed = true;
       } else if (done) {
-        finish(s, status == VPS_OK ? VPS_REQ_DONE : VPS_REQ_FAILED, status, iters, rel, x);
+        std::lock_guard<std::mutex> lock(mu);
+        s.state = kCompleting;
+        done_jobs.push_back({&s, s.req, x, status == VPS_OK ? VPS_REQ_DONE : VPS_REQ_FAILED,
+                             status, iters, rel});
+        done_cv.notify_one();
         progressed = true;
       } else if (vps::cg_async_pending_vcycle(s.h)) {
         progressed = true;
       }
     }
-    while (admit_one()) progressed = true;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      t_poll += since(t0);
+    }
+    if (admit()) progressed = true;
     for (auto& c : cohorts)
       if (tick(*c)) progressed = true;
     if (!progressed) {
@@ -322,16 +528,25 @@ void vps_server_ctx::run() {
       if (queue.empty() && active == 0)
         cv.wait_for(lock, std::chrono::milliseconds(2));
       else
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        cv.wait_for(lock, std::chrono::microseconds(20));
     }
   }
 }
 
-// Frees the slots and the cohorts (after the engine has stopped).
+// Stops the helper threads and frees the slots and the cohorts (after the
+// engine has stopped).
 void vps_server_ctx::release() {
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    prov_cv.notify_all();
+    done_cv.notify_all();
+  }
+  if (provisioner.joinable()) provisioner.join();
+  if (completer.joinable()) completer.join();
   for (auto& c : cohorts)
     if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto& sl : slots) vps_destroy(sl->h);
+  for (auto& sl : slots)
+    if (sl->h) vps_destroy(sl->h);
   slots.clear();
   for (auto& c : cohorts) {
     if (c->q_dev) cudaFree(c->q_dev);
@@ -364,6 +579,8 @@ int vps_server_create(size_t memory_budget, int max_active, int precision, doubl
     return VPS_ECUDA;
   }
   s->engine = std::thread([s] { s->run(); });
+  s->provisioner = std::thread([s] { s->run_provisioner(); });
+  s->completer = std::thread([s] { s->run_completer(); });
   *out = s;
   return VPS_OK;
 }
@@ -446,6 +663,17 @@ int vps_server_batch_stats(vps_server s, int64_t* ticks, int64_t* batched_launch
   if (batched_launches) *batched_launches = s->batched_launches;
   if (max_requests_per_launch) *max_requests_per_launch = s->max_per_launch;
   if (max_requests_per_tick) *max_requests_per_tick = s->max_per_tick;
+  return VPS_OK;
+}
+
+int vps_server_host_times(vps_server s, double* seconds) {
+  if (!s || !seconds) return VPS_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  seconds[0] = s->t_admit;
+  seconds[1] = s->t_tick;
+  seconds[2] = s->t_poll;
+  seconds[3] = s->t_create;
+  seconds[4] = s->t_copy;
   return VPS_OK;
 }
 

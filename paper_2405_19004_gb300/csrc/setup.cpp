@@ -116,6 +116,38 @@ void jacobi_eigen(int m, double* C, double* Q, double* w) {
   for (int i = 0; i < m; ++i) w[i] = C[i * m + i];
 }
 
+// Generalised symmetric eigenproblem A S = M S diag(w), S^T M S = I
+// (M SPD; m <= 13): Cholesky M = L L^T, C = L^-1 A L^-T, Jacobi on C,
+// S = L^-T Q.  Returns false if M is not positive definite.
+bool generalised_eigen(int m, const double* A, const double* M, double* S, double* w) {
+  double L[13 * 13], C[13 * 13], Q[13 * 13], tmp[13 * 13];
+  if (!cholesky(m, M, L)) return false;
+  // tmp = L^-1 A  (forward substitution per column), C = tmp L^-T
+  for (int col = 0; col < m; ++col)
+    for (int i = 0; i < m; ++i) {
+      double s = A[i * m + col];
+      for (int p = 0; p < i; ++p) s -= L[i * m + p] * tmp[p * m + col];
+      tmp[i * m + col] = s / L[i * m + i];
+    }
+  for (int row = 0; row < m; ++row)
+    for (int i = 0; i < m; ++i) {
+      double s = tmp[row * m + i];
+      for (int p = 0; p < i; ++p) s -= L[i * m + p] * C[row * m + p];
+      C[row * m + i] = s / L[i * m + i];
+    }
+  for (int i = 0; i < m; ++i)  // symmetrise against rounding
+    for (int j = i + 1; j < m; ++j) C[i * m + j] = C[j * m + i] = 0.5 * (C[i * m + j] + C[j * m + i]);
+  jacobi_eigen(m, C, Q, w);
+  // S = L^-T Q: back substitution L^T S = Q per column
+  for (int col = 0; col < m; ++col)
+    for (int i = m - 1; i >= 0; --i) {
+      double s = Q[i * m + col];
+      for (int p = i + 1; p < m; ++p) s -= L[p * m + i] * S[p * m + col];
+      S[i * m + col] = s / L[i * m + i];
+    }
+  return true;
+}
+
 }  // namespace
 
 void gauss_rule(int q, double* x, double* w) {
@@ -180,40 +212,69 @@ bool build_tables(int k, HostTables* T, char* err, size_t errlen) {
       T->Mp[i * n + j] = Mf[(i + 1) * n + j];
     }
 
-  // Generalised eigenproblem of the interior blocks.
-  double AI[13 * 13], MI[13 * 13], L[13 * 13], C[13 * 13], Q[13 * 13], tmp[13 * 13];
+  // Generalised eigenproblem of the interior blocks.  The two-cell patch is
+  // symmetric about its centre node k, so A_I and M_I commute with the
+  // reversal J of the m interior nodes: every eigenvector can be taken even
+  // (J s = s) or odd (J s = -s).  The problem is solved separately on the
+  // even subspace (basis (e_i + e_{m-1-i})/sqrt2, i < h, and e_h; h = k-1)
+  // and the odd one ((e_i - e_{m-1-i})/sqrt2), so that the columns of S have
+  // exact parity: the h+1 even eigenvectors first, then the h odd ones.  The
+  // kernels use this to apply S and S^T with half the multiply-adds.
+  double AI[13 * 13], MI[13 * 13];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) {
       AI[i * m + j] = T->Ap[i * n + j + 1];
       MI[i * m + j] = T->Mp[i * n + j + 1];
     }
-  if (!cholesky(m, MI, L)) {
-    std::snprintf(err, errlen, "mass matrix not positive definite (k=%d)", k);
-    return false;
+  const int h = k - 1, ne = h + 1, no = h;
+  const double r2 = std::sqrt(0.5);
+  // basis vectors of the even (j < ne) and odd (j >= ne) subspaces, columns of B
+  double B[13 * 13] = {0};
+  for (int j = 0; j < ne; ++j) {
+    if (j < h) {
+      B[j * m + j] = r2;
+      B[(m - 1 - j) * m + j] = r2;
+    } else {
+      B[h * m + j] = 1.0;
+    }
   }
-  // tmp = L^-1 A  (forward substitution per column), C = tmp L^-T
-  for (int col = 0; col < m; ++col)
-    for (int i = 0; i < m; ++i) {
-      double s = AI[i * m + col];
-      for (int p = 0; p < i; ++p) s -= L[i * m + p] * tmp[p * m + col];
-      tmp[i * m + col] = s / L[i * m + i];
+  for (int j = 0; j < no; ++j) {
+    B[j * m + ne + j] = r2;
+    B[(m - 1 - j) * m + ne + j] = -r2;
+  }
+  for (int part = 0; part < 2; ++part) {
+    const int off = part == 0 ? 0 : ne, sz = part == 0 ? ne : no;
+    if (sz == 0) continue;
+    double Ab[13 * 13], Mb[13 * 13], Sb[13 * 13], lb[13];
+    for (int a = 0; a < sz; ++a)
+      for (int b = 0; b < sz; ++b) {
+        double sa = 0.0, sm = 0.0;
+        for (int p = 0; p < m; ++p)
+          for (int q = 0; q < m; ++q) {
+            const double w = B[p * m + off + a] * B[q * m + off + b];
+            sa += w * AI[p * m + q];
+            sm += w * MI[p * m + q];
+          }
+        Ab[a * sz + b] = sa;
+        Mb[a * sz + b] = sm;
+      }
+    if (!generalised_eigen(sz, Ab, Mb, Sb, lb)) {
+      std::snprintf(err, errlen, "mass matrix not positive definite (k=%d)", k);
+      return false;
     }
-  for (int row = 0; row < m; ++row)
-    for (int i = 0; i < m; ++i) {
-      double s = tmp[row * m + i];
-      for (int p = 0; p < i; ++p) s -= L[i * m + p] * C[row * m + p];
-      C[row * m + i] = s / L[i * m + i];
-    }
-  for (int i = 0; i < m; ++i)  // symmetrise against rounding
-    for (int j = i + 1; j < m; ++j) C[i * m + j] = C[j * m + i] = 0.5 * (C[i * m + j] + C[j * m + i]);
-  jacobi_eigen(m, C, Q, T->lam);
-  // S = L^-T Q: back substitution L^T S = Q per column
-  for (int col = 0; col < m; ++col)
-    for (int i = m - 1; i >= 0; --i) {
-      double s = Q[i * m + col];
-      for (int p = i + 1; p < m; ++p) s -= L[p * m + i] * T->S[p * m + col];
-      T->S[i * m + col] = s / L[i * m + i];
-    }
+    for (int a = 0; a < sz; ++a) T->lam[off + a] = lb[a];
+    // S column off+a = B_part Sb column a
+    for (int i = 0; i < m; ++i)
+      for (int a = 0; a < sz; ++a) {
+        double v = 0.0;
+        for (int b = 0; b < sz; ++b) v += B[i * m + off + b] * Sb[b * sz + a];
+        T->S[i * m + off + a] = v;
+      }
+  }
+  // exact parity (the products above give it up to rounding only)
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < h; ++i) T->S[(m - 1 - i) * m + j] = (j < ne ? 1.0 : -1.0) * T->S[i * m + j];
+  for (int j = ne; j < m; ++j) T->S[h * m + j] = 0.0;
   // self-check: S^T M S = I and S^T A S = diag(lam)
   double worst = 0.0, scale = 0.0;
   for (int i = 0; i < m; ++i) scale = std::fmax(scale, std::fabs(T->lam[i]));
@@ -228,7 +289,9 @@ bool build_tables(int k, HostTables* T, char* err, size_t errlen) {
       worst = std::fmax(worst, std::fabs(sm - (i == j)));
       worst = std::fmax(worst, std::fabs(sa - (i == j ? T->lam[i] : 0.0)) / scale);
     }
-  if (!(worst < 1e-10) || !(T->lam[0] > 0)) {
+  double lmin = T->lam[0];
+  for (int i = 1; i < m; ++i) lmin = std::fmin(lmin, T->lam[i]);
+  if (!(worst < 1e-10) || !(lmin > 0)) {
     std::snprintf(err, errlen, "fast-diagonalisation self-check failed (k=%d, err %.3g)", k, worst);
     return false;
   }

@@ -315,6 +315,7 @@ const char* handle_error(vps_context* h);
 // cg_async_pending_vcycle(h), the caller runs the V-cycle of h (for several
 // handles at once with cohort_vcycle) and then calls cg_async_resume(h).
 void set_external_vcycle(vps_context* h, bool on);
+int cg_async_prepare(vps_context* h, int max_modes);
 int cg_async_pending_vcycle(vps_context* h);
 int cg_async_resume(vps_context* h);
 // One V-cycle (Algorithm 1, symmetric colour order, x = 0) for each of n
