@@ -2372,41 +2372,43 @@ cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf,
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of a smoother kernel, and the largest shared-memory
+// carveout of the SM's unified L1/shared storage: the number of patches in
+// flight per SM is bounded by shared memory (registers allow more), and the
+// default carveout leaves part of the 228 KB unused.
+template <typename KernT>
+cudaError_t smoother_smem(KernT kern, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
 template <typename T, int PP>
 cudaError_t smooth_limits() {
   using C = SmoothCfg<T, PP>;
   if constexpr (C::fits_bnd) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::smem_bnd);
+    cudaError_t e = smoother_smem(smooth_mult_kernel<T, PP, true, 0>, C::smem_bnd);
     if (e != cudaSuccess) return e;
     if constexpr (kOneWarpVariants) {
-      e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, true, 1>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+      e = smoother_smem(smooth_mult_kernel<T, PP, true, 1>, C::smem_bnd);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, true, 1>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+      e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 1>, C::smem_bnd);
       if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, true, 0>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bnd);
+    e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 0>, C::smem_bnd);
     if (e != cudaSuccess) return e;
   }
   if constexpr (!C::fits) {
     return cudaSuccess;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::smem_mult);
+    cudaError_t e = smoother_smem(smooth_mult_kernel<T, PP, false, 0>, C::smem_mult);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(smooth_mult_kernel<T, PP, false, 0, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_mult);
+    e = smoother_smem(smooth_mult_kernel<T, PP, false, 0, true>, C::smem_mult);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(smooth_mult_batch_kernel<T, PP, false, 0>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_mult);
+    e = smoother_smem(smooth_mult_batch_kernel<T, PP, false, 0>, C::smem_mult);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(smooth_add_kernel<T, PP>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_add);
+    return smoother_smem(smooth_add_kernel<T, PP>, C::smem_add);
   }
 }
 

@@ -84,6 +84,43 @@ def smoother_flops_per_patch(d, k, boundary=False):
     return s0 + 4 * m * m * n + 8 * m ** 3 + upd
 
 
+def smoother_flops_executed_per_patch(d, k, boundary=False):
+    """Floating-point operations the kernels execute per patch (FMA = 2,
+    multiply or add = 1) with the even/odd halves of the 1D matrices.
+
+    A closure line (n = 2k+1 values) against one centrosymmetric patch matrix
+    takes 2k^2 multiply-adds on its k+1 even and k odd parts (the dense
+    product takes m n = 4k^2 - 1); the parts cost 2k additions, the interior
+    outputs 2(k-1) more.  A fast-diagonalisation line (m = 2k-1 values) takes
+    k^2 + (k-1)^2 multiply-adds (dense m^2) and 2(k-1) additions.  Stages as
+    in the kernels: the first and middle fast-diagonalisation directions in
+    registers for k <= 5.  The Boundary kernel's interior lines of the first
+    contraction use their two end nodes only (one multiply and one
+    multiply-add per output and matrix)."""
+    n, m, h = 2 * k + 1, 2 * k - 1, k - 1
+    close1 = 4 * k * k + 2 * h                      # one matrix on a split closure line, + combine
+    split_n = 2 * k
+    fd_line = 2 * (k * k + h * h) + 2 * h           # S or S^T on one interior line
+    fuse = k <= 5
+    if d == 3:
+        full0 = split_n + 2 * close1
+        s0 = (8 * k * full0 + m * m * 2 * 3 * m) if boundary else n * n * full0
+        s1 = n * m * (2 * split_n + 3 * 4 * k * k + 2 * 2 * h)
+        s2 = m * m * (2 * split_n + 2 * 4 * k * k + 2 * h + 2 * m + (fd_line if fuse else 0))
+        if fuse:
+            fd = m * m * (fd_line + (2 * fd_line + m) + fd_line)
+        else:
+            fd = m * m * (3 * fd_line + m + 2 * fd_line)
+        final = m * m * (fd_line + (1 if boundary else 2) * m)
+        return s0 + s1 + s2 + fd + final
+    full0 = split_n + 2 * close1
+    s0 = (2 * full0 + m * 2 * 3 * m) if boundary else n * full0
+    s1 = m * (2 * split_n + 2 * 4 * k * k + 2 * h + 2 * m + (fd_line if fuse else 0))
+    fd = m * ((2 * fd_line + m) if fuse else (3 * fd_line + m))
+    final = m * (fd_line + (1 if boundary else 2) * m)
+    return s0 + s1 + fd + final
+
+
 def smoother_smem_words_per_patch(d, k, boundary=False):
     """Shared-memory words read + written per patch by the fused kernel (the
     Boundary kernel neither stages nor reads back the interior of x)."""
@@ -138,9 +175,12 @@ def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cach
     fp32 = prec == vps.VPS_FP32
     derived = fp32_peak(peaks["sm_count"], peaks["sm_max_mhz"]) if fp32 else None
     measured = peaks["fp32_fma_measured_flops" if fp32 else "fp64_fma_measured_flops"]
+    executed = smoother_flops_executed_per_patch(d, k, bnd) * patches
     row = {"dim": d, "degree": k, "level": L, "precision": "fp32" if fp32 else "fp64",
            "dofs": N, "ms_per_step": 1e3 * t, "dof_per_s": N / t, "gflops": flops / t / 1e9,
+           "gflops_executed": executed / t / 1e9,
            "frac_of_measured_fma_peak": flops / t / measured,
+           "frac_of_measured_fma_peak_executed": executed / t / measured,
            "frac_smem_roofline": flops / t / roof_smem, "smem_roofline_tflops": roof_smem / 1e12,
            "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb}
     if derived:
