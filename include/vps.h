@@ -257,7 +257,9 @@ int vps_get_coarse_level(vps_handle h, int* level);
  * smoother variant of every level (patches per thread block, the tuning
  * axis of Section 3.1.2) and the coarsest level (vps_set_coarse_level) that
  * give the fastest CG solve.  cache_path (may be NULL): a JSON file keyed by
- * (dim, degree, precision, smoother, level, smoothing steps); an entry found
+ * (dim, degree, precision, smoother, level, smoothing steps) with the
+ * smoother variant and operator tile structure of every level, the colour
+ * schedule and the coarsest level; an entry found
  * there is applied without timing (*from_cache = 1), otherwise the result is
  * written to it.  Synchronous; runs solves on the handle's stream.
  */
@@ -277,6 +279,25 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);
 int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_per_block);
+
+/* vps_set_operator_variant / vps_get_operator_variant -- tile structure of
+ * the level's operator A_l x (Section 2.3's Kronecker sum on the Cartesian
+ * mesh) in the V-cycle's residuals: 0 the default; 1 the alternative where
+ * one exists (*n_variants = 2: 3D FP32 handles of degree <= 4, whose default
+ * takes the z contraction one cell of planes at a time; the alternative
+ * takes it plane by plane).  Both compute the same operator.  Chosen per
+ * level by vps_autotune.  Errors: VPS_EINVAL (level, unavailable variant). */
+int vps_set_operator_variant(vps_handle h, int level, int variant);
+int vps_get_operator_variant(vps_handle h, int level, int* variant, int* n_variants);
+
+/* vps_set_colour_pdl / vps_get_colour_pdl -- colour schedule of the
+ * multiplicative smoother: enable = 1 (default) launches the colour passes
+ * of a step as programmatic dependent launches (a pass is scheduled while
+ * the previous one drains and waits for it before reading b or x), 0 as
+ * ordinary launches.  The same arithmetic either way; chosen by
+ * vps_autotune.  Errors: VPS_EINVAL (h NULL). */
+int vps_set_colour_pdl(vps_handle h, int enable);
+int vps_get_colour_pdl(vps_handle h, int* enable);
 
 /* vps_kernel_launches -- number of kernels the handle has launched since
  * creation (direct launches plus, for every replay of a captured graph, the

@@ -66,6 +66,10 @@ SIGNATURES = {
     "vps_autotune": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i)]),
     "vps_set_smooth_variant": (_i, [_p, _i, _i]),
     "vps_get_smooth_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "vps_set_operator_variant": (_i, [_p, _i, _i]),
+    "vps_get_operator_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "vps_set_colour_pdl": (_i, [_p, _i]),
+    "vps_get_colour_pdl": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
     "vps_server_create": (_i, [ctypes.c_size_t, _i, _i, _d, _i, ctypes.POINTER(_p)]),
@@ -321,6 +325,23 @@ class Poisson:
         _check(lib().vps_get_smooth_variant(self.h, int(level), ctypes.byref(v), ctypes.byref(p)),
                self.h)
         return v.value, p.value
+
+    def vps_set_operator_variant(self, level, variant):
+        self._call(lib().vps_set_operator_variant, int(level), int(variant))
+
+    def vps_get_operator_variant(self, level):
+        v, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().vps_get_operator_variant(self.h, int(level), ctypes.byref(v), ctypes.byref(n)),
+               self.h)
+        return v.value, n.value
+
+    def vps_set_colour_pdl(self, enable):
+        self._call(lib().vps_set_colour_pdl, 1 if enable else 0)
+
+    def vps_get_colour_pdl(self):
+        e = ctypes.c_int()
+        _check(lib().vps_get_colour_pdl(self.h, ctypes.byref(e)), self.h)
+        return bool(e.value)
 
     def vps_set_coarse_level(self, level):
         self._call(lib().vps_set_coarse_level, int(level))

@@ -142,6 +142,8 @@ struct vps_context {
   int64_t graph_kernels = 0;            // kernel nodes in prec_graph
   int64_t kernels = 0;                  // kernels launched by this handle
   int smooth_var[kMaxLevels + 1] = {};  // smoother variant per level (index into the table)
+  int op_var[kMaxLevels + 1] = {};      // operator tile structure per level (1: apply_alt)
+  bool pdl = true;                      // colour passes as programmatic dependent launches
   // kernel structure of the multiplicative smoother (Section 3.1's
   // Fused / Separate / Global, and Global with the dense inverse)
   int kernel_kind = VPS_KERNEL_FUSED;
@@ -246,6 +248,14 @@ const KernelFns<float>& fns<float>(vps_context* h) { return h->ks->f; }
 template <>
 const KernelFns<double>& fns<double>(vps_context* h) { return h->ks->d; }
 
+// y = A_l x, or y = b - A_l x, with the level's operator tile structure.
+template <typename T>
+cudaError_t level_apply(vps_context* h, int l, const T* x, const T* b, T* y) {
+  const KernelFns<T>& F = fns<T>(h);
+  if (h->op_var[l] && F.apply_alt) return F.apply_alt(h->geom[l], x, b, y, h->stream);
+  return F.apply(h->geom[l], x, b, y, h->stream);
+}
+
 // One colour pass of the multiplicative smoother with the handle's kernel
 // structure (Section 3.1): Fused (one kernel), Separate (local residual
 // kernel, then the local solve), Global (global residual by the operator,
@@ -267,16 +277,17 @@ int colour_pass(vps_context* h, int l, int c, const T* b, T* x) {
       VPS_CK(h, F.smooth_add_v[q](g, cg, r, x, il, T(1), h->stream));
       return VPS_OK;
     case VPS_KERNEL_GLOBAL:
-      VPS_CK(h, F.apply(g, x, b, r, h->stream));
+      VPS_CK(h, level_apply<T>(h, l, x, b, r));
       VPS_CK(h, F.smooth_add_v[q](g, cg, r, x, il, T(1), h->stream));
       return VPS_OK;
     case VPS_KERNEL_GLOBAL_INVERSE:
       if (!F.inverse_solve || !h->ainv) return fail(h, VPS_EINVAL, "dense inverse unavailable");
-      VPS_CK(h, F.apply(g, x, b, r, h->stream));
+      VPS_CK(h, level_apply<T>(h, l, x, b, r));
       VPS_CK(h, F.inverse_solve(g, cg, r, x, static_cast<const T*>(h->ainv), h->stream));
       return VPS_OK;
     default:
-      VPS_CK(h, F.smooth_mult_v[v](g, cg, b, x, il, h->stream));
+      if (h->pdl || !F.smooth_mult_plain_v[v]) VPS_CK(h, F.smooth_mult_v[v](g, cg, b, x, il, h->stream));
+      else VPS_CK(h, F.smooth_mult_plain_v[v](g, cg, b, x, il, h->stream));
       return VPS_OK;
   }
 }
@@ -293,7 +304,7 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
     return fail(h, VPS_EINVAL, "smoother variant %d unavailable", v);
   if (h->smoother == VPS_ADDITIVE) {
     T* r = static_cast<T*>(h->rv[l]);
-    VPS_CK(h, fns<T>(h).apply(g, x, b, r, h->stream));
+    VPS_CK(h, level_apply<T>(h, l, x, b, r));
     for (int c = 0; c < nc; ++c)
       VPS_CK(h, fns<T>(h).smooth_add_v[v](g, make_colour(g, c), r, x, il, (T)h->damping,
                                           h->stream));
@@ -422,7 +433,7 @@ int vcycle_core(vps_context* h, const T* bL, T* xL, int top = 0, bool symmetric 
       if (rc) return rc;
     }
     T* r = static_cast<T*>(h->rv[l]);
-    VPS_CK(h, F.apply(g, x[l], b[l], r, h->stream));
+    VPS_CK(h, level_apply<T>(h, l, x[l], b[l], r));
     VPS_CK(h, F.restrict_(g, h->geom[l - 1], r, static_cast<T*>(h->bv[l - 1]), h->stream));
   }
   // coarsest level: exact solve (Algorithm 1's coarse grid solver)
@@ -1527,8 +1538,8 @@ int cohort_vcycle_t(vps_context* const* hs, int n, QueueWriter* qw, cudaStream_t
         break;
       case 4: {
         vps_context* h = hs[op.m];
-        VPS_CK(h0, F.apply(h->geom[op.l], xptr(op.m, op.l), bptr(op.m, op.l),
-                           static_cast<T*>(h->rv[op.l]), st));
+        VPS_CK(h0, level_apply<T>(h, op.l, xptr(op.m, op.l), bptr(op.m, op.l),
+                                  static_cast<T*>(h->rv[op.l])));
         break;
       }
       case 5:
@@ -1606,38 +1617,49 @@ std::string tune_key(vps_context* h) {
 }
 
 // Cache file: one JSON object, one entry per line:
-//   "d3_k4_fp32_mult_L5_pre1_post1": {"coarse": 3, "variants": [1, 1, 2, 0, 1]},
-bool cache_lookup(const char* path, const std::string& key, int* coarse, int* var, int nvar) {
+//   "d3_k4_fp32_mult_L5_pre1_post1": {"coarse": 3, "variants": [1, 1, 2, 0, 1],
+//                                     "ops": [0, 0, 1, 1, 0], "pdl": 1},
+// (one line each).  Entries without every field are tuned again.
+bool parse_list(const char* p, const char* name, int* out, int nvar) {
+  const char* v = std::strstr(p, name);
+  if (!v) return false;
+  v += std::strlen(name);
+  int i = 0;
+  while (i < nvar && *v && *v != ']') {
+    while (*v == ' ' || *v == ',') ++v;
+    if (*v == ']' || !*v) break;
+    out[i++] = std::atoi(v);
+    while (*v && *v != ',' && *v != ']') ++v;
+  }
+  return i == nvar;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int* coarse, int* var, int* ops,
+                  int* pdl, int nvar) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
-  char line[1024];
+  char line[2048];
   bool found = false;
   const std::string pat = "\"" + key + "\"";
   while (std::fgets(line, sizeof(line), f)) {
     const char* p = std::strstr(line, pat.c_str());
     if (!p) continue;
     const char* c = std::strstr(p, "\"coarse\":");
-    const char* v = std::strstr(p, "\"variants\": [");
-    if (!c || !v) continue;
+    const char* d = std::strstr(p, "\"pdl\":");
+    if (!c || !d) continue;
     *coarse = std::atoi(c + 9);
-    v += 13;
-    int i = 0;
-    while (i < nvar && *v && *v != ']') {
-      while (*v == ' ' || *v == ',') ++v;
-      if (*v == ']' || !*v) break;
-      var[i++] = std::atoi(v);
-      while (*v && *v != ',' && *v != ']') ++v;
-    }
-    found = i == nvar;
+    *pdl = std::atoi(d + 6);
+    found = parse_list(p, "\"variants\": [", var, nvar) && parse_list(p, "\"ops\": [", ops, nvar);
   }
   std::fclose(f);
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, int coarse, const int* var, int nvar) {
+void cache_store(const char* path, const std::string& key, int coarse, const int* var,
+                 const int* ops, int pdl, int nvar) {
   std::vector<std::string> keep;
   if (FILE* f = std::fopen(path, "r")) {
-    char line[1024];
+    char line[2048];
     const std::string pat = "\"" + key + "\"";
     while (std::fgets(line, sizeof(line), f)) {
       std::string sline(line);
@@ -1650,7 +1672,9 @@ void cache_store(const char* path, const std::string& key, int coarse, const int
   }
   std::string entry = "\"" + key + "\": {\"coarse\": " + std::to_string(coarse) + ", \"variants\": [";
   for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(var[i]);
-  entry += "]}";
+  entry += "], \"ops\": [";
+  for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(ops[i]);
+  entry += "], \"pdl\": " + std::to_string(pdl) + "}";
   keep.push_back(entry);
   if (FILE* f = std::fopen(path, "w")) {
     std::fputs("{\n", f);
@@ -2134,13 +2158,21 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
   LaunchTally tally(h);
   const std::string key = tune_key(h);
   int var[kMaxLevels + 1] = {};
-  int coarse = 0;
+  int ops[kMaxLevels + 1] = {};
+  int coarse = 0, pdl = 1;
   if (from_cache) *from_cache = 0;
-  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, h->L)) {
-    bool ok = coarse >= 1 && coarse <= h->L;
-    for (int l = 1; l <= h->L; ++l) ok = ok && variant_ok(h, var[l]);
+  const bool has_alt = h->prec == VPS_FP64 ? h->ks->d.apply_alt != nullptr
+                                           : h->ks->f.apply_alt != nullptr;
+  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, ops + 1, &pdl, h->L)) {
+    bool ok = coarse >= 1 && coarse <= h->L && (pdl == 0 || pdl == 1);
+    for (int l = 1; l <= h->L; ++l)
+      ok = ok && variant_ok(h, var[l]) && (ops[l] == 0 || (ops[l] == 1 && has_alt));
     if (ok) {
-      for (int l = 1; l <= h->L; ++l) h->smooth_var[l] = var[l];
+      for (int l = 1; l <= h->L; ++l) {
+        h->smooth_var[l] = var[l];
+        h->op_var[l] = ops[l];
+      }
+      h->pdl = pdl != 0;
       if (coarse != h->coarse)
         if (int rc = setup_coarse(h, coarse)) return rc;
       drop_graphs(h);
@@ -2169,7 +2201,51 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     }
     h->smooth_var[l] = bestv;
   }
-  // 2) coarsest level: fastest full CG solve of a smooth right-hand side
+  // 2) operator tile structure per level where two exist: the faster
+  //    residual b - A x on the level's buffers
+  for (int l = 1; l <= h->L; ++l) {
+    h->op_var[l] = 0;
+    if (!has_alt || l < 2) continue;
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < 2; ++v) {
+      h->op_var[l] = v;
+      float ms = 0.f;
+      int rc = h->prec == VPS_FP64
+                   ? time_ms(h, 5, [&] { return level_apply<double>(h, l, (const double*)h->xv[l],
+                                                                    (const double*)h->bv[l],
+                                                                    (double*)h->rv[l]) == cudaSuccess
+                                                ? VPS_OK : VPS_ECUDA; }, &ms)
+                   : time_ms(h, 5, [&] { return level_apply<float>(h, l, (const float*)h->xv[l],
+                                                                   (const float*)h->bv[l],
+                                                                   (float*)h->rv[l]) == cudaSuccess
+                                                ? VPS_OK : VPS_ECUDA; }, &ms);
+      if (rc) return rc;
+      if (ms < best * 0.98f) {
+        best = ms;
+        bestv = v;
+      }
+    }
+    h->op_var[l] = bestv;
+  }
+  // 3) colour schedule: the passes of a smoothing step on the finest level as
+  //    programmatic dependent launches (the next pass is scheduled while the
+  //    previous one drains) or as ordinary launches
+  if (h->smoother == VPS_MULTIPLICATIVE && h->L >= 2) {
+    float t[2] = {0.f, 0.f};
+    for (int on = 0; on < 2; ++on) {
+      h->pdl = on != 0;
+      const int l = h->L;
+      int rc = h->prec == VPS_FP64
+                   ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
+                                                                    (double*)h->xv[l], true); }, &t[on])
+                   : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
+                                                                   (float*)h->xv[l], true); }, &t[on]);
+      if (rc) return rc;
+    }
+    h->pdl = t[1] <= t[0] * 1.02f;  // programmatic launches on near ties
+  }
+  // 4) coarsest level: fastest full CG solve of a smooth right-hand side
   {
     const LevelGeom& g = h->geom[h->L];
     const int ni = g.n1 - 2;
@@ -2204,9 +2280,48 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     if (int rc = setup_coarse(h, bestc)) return rc;
   }
   if (cache_path) {
-    for (int l = 1; l <= h->L; ++l) var[l] = h->smooth_var[l];
-    cache_store(cache_path, key, h->coarse, var + 1, h->L);
+    for (int l = 1; l <= h->L; ++l) {
+      var[l] = h->smooth_var[l];
+      ops[l] = h->op_var[l];
+    }
+    cache_store(cache_path, key, h->coarse, var + 1, ops + 1, h->pdl ? 1 : 0, h->L);
   }
+  drop_graphs(h);
+  return VPS_OK;
+}
+
+int vps_set_operator_variant(vps_handle h, int level, int variant) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  const bool has_alt = h->prec == VPS_FP64 ? h->ks->d.apply_alt != nullptr
+                                           : h->ks->f.apply_alt != nullptr;
+  if (variant != 0 && !(variant == 1 && has_alt))
+    return fail(h, VPS_EINVAL, "operator variant %d unavailable", variant);
+  h->op_var[level] = variant;
+  drop_graphs(h);
+  return VPS_OK;
+}
+
+int vps_get_operator_variant(vps_handle h, int level, int* variant, int* n_variants) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (variant) *variant = h->op_var[level];
+  if (n_variants)
+    *n_variants = (h->prec == VPS_FP64 ? h->ks->d.apply_alt != nullptr
+                                       : h->ks->f.apply_alt != nullptr) ? 2 : 1;
+  return VPS_OK;
+}
+
+int vps_set_colour_pdl(vps_handle h, int enable) {
+  if (!h) return VPS_EINVAL;
+  h->pdl = enable != 0;
+  drop_graphs(h);
+  return VPS_OK;
+}
+
+int vps_get_colour_pdl(vps_handle h, int* enable) {
+  if (!h || !enable) return VPS_EINVAL;
+  *enable = h->pdl ? 1 : 0;
   return VPS_OK;
 }
 

@@ -2220,6 +2220,22 @@ cudaError_t zero_faces_batch_launch(const BatchQueue* q, int nitems, cudaStream_
   return cudaGetLastError();
 }
 
+// The colour pass as an ordinary launch (no programmatic dependent launch;
+// griddepcontrol.wait is then a no-op).
+template <typename T, int PP, bool BND, int W>
+cudaError_t smooth_mult_plain_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
+                                     const T* inv_lam, cudaStream_t s) {
+  using C = SmoothCfg<T, PP, W>;
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + C::P - 1) / C::P;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
+  smooth_mult_kernel<T, PP, BND, W, false><<<(unsigned)grid, C::NT, BND ? C::smem_bnd : C::smem_mult,
+                                             s>>>(b, x, inv_lam, (int)g.px, (int)g.pz, cg, bscale,
+                                                  static_cast<T*>(nullptr));
+  return cudaGetLastError();
+}
+
 template <typename T, int PP>
 cudaError_t resid_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, const T* x, T* r,
                          cudaStream_t s) {
@@ -2263,6 +2279,28 @@ cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T*
 
 // Tiles cover the nodes 0 .. n1-2 of every direction; the upper boundary
 // layer (index n1-1) is zeroed by a second, small kernel.
+// The per-plane 3D operator where the default is the cell-batched one.
+template <typename T>
+cudaError_t apply_alt_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
+  if constexpr (DIM == 3 && kApply3C<T>) {
+    using C3 = Apply3Cfg;
+    const int span = g.n1 - 1;
+    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
+    const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
+    VPS_COUNT_LAUNCH();
+    apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
+                                                                   (int)g.pz, T(g.h));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    VPS_COUNT_LAUNCH();
+    zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
+    return cudaGetLastError();
+  } else {
+    (void)g; (void)x; (void)b; (void)y; (void)s;
+    return cudaErrorNotSupported;
+  }
+}
+
 template <typename T>
 cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
   const int span = g.n1 - 1;
@@ -2422,17 +2460,22 @@ void register_variant(KernelFns<T>* f, int v) {
   f->smooth_add_v[v + 2 * kQVariants] = nullptr;
   if constexpr (C::fits_bnd) {
     f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true, 0>;
+    f->smooth_mult_plain_v[v + kQVariants] = smooth_mult_plain_launch<T, PP, true, 0>;
     f->smooth_mult_batch_v[v + kQVariants] = smooth_mult_batch_launch<T, PP, true, 0>;
     if constexpr (kOneWarpVariants) {
       f->smooth_mult_v[v + 2 * kQVariants] = smooth_mult_launch<T, PP, true, 1>;
+      f->smooth_mult_plain_v[v + 2 * kQVariants] = smooth_mult_plain_launch<T, PP, true, 1>;
       f->smooth_mult_batch_v[v + 2 * kQVariants] = smooth_mult_batch_launch<T, PP, true, 1>;
     } else {
       f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
+      f->smooth_mult_plain_v[v + 2 * kQVariants] = nullptr;
       f->smooth_mult_batch_v[v + 2 * kQVariants] = nullptr;
     }
   } else {
     f->smooth_mult_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
+    f->smooth_mult_plain_v[v + kQVariants] = nullptr;
+    f->smooth_mult_plain_v[v + 2 * kQVariants] = nullptr;
     f->smooth_mult_batch_v[v + kQVariants] = nullptr;
     f->smooth_mult_batch_v[v + 2 * kQVariants] = nullptr;
   }
@@ -2440,10 +2483,12 @@ void register_variant(KernelFns<T>* f, int v) {
   else f->resid_v[v] = nullptr;
   if constexpr (C::fits) {
     f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false, 0>;
+    f->smooth_mult_plain_v[v] = smooth_mult_plain_launch<T, PP, false, 0>;
     f->smooth_mult_batch_v[v] = smooth_mult_batch_launch<T, PP, false, 0>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
   } else {
     f->smooth_mult_v[v] = nullptr;
+    f->smooth_mult_plain_v[v] = nullptr;
     f->smooth_mult_batch_v[v] = nullptr;
     f->smooth_add_v[v] = nullptr;
   }
@@ -2457,6 +2502,8 @@ void register_fns(KernelFns<T>* f) {
   // default additive variant: the middle one, or the smallest where it does not fit
   f->smooth_add = f->smooth_add_v[1] ? f->smooth_add_v[1] : f->smooth_add_v[0];
   f->apply = apply_launch<T>;
+  if constexpr (DIM == 3 && kApply3C<T>) f->apply_alt = apply_alt_launch<T>;
+  else f->apply_alt = nullptr;
   f->prolong_add = prolong_launch<T>;
   f->restrict_ = restrict_launch<T>;
   f->prolong_batch = prolong_batch_launch<T>;

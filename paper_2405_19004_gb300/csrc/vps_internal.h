@@ -182,6 +182,12 @@ struct KernelFns {
                                const T* AinvT, cudaStream_t) = nullptr;
   // y = A x  (b == nullptr)  or  y = b - A x  (residual)
   cudaError_t (*apply)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
+  // the same operator with the other tile structure where two exist (3D
+  // FP32, k <= 4: per-plane tiles instead of the cell-batched z windows of
+  // `apply`); nullptr elsewhere
+  cudaError_t (*apply_alt)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
+  // colour passes launched without programmatic dependent launch
+  SmoothMultFn smooth_mult_plain_v[kSmoothVariants] = {};
   // batched persistent launches over a device-side queue (q: device copy,
   // ntiles: its tile count, known on the host): multiplicative colour
   // passes (variant v), restrictions, prolongations, and the zeroing of the
