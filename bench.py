@@ -491,6 +491,40 @@ def main():
         extras["smoother_3d_q4_l7"] = [
             smoother_point(vps, torch, 3, 4, 7, prec, 20, peaks, True, args.tune_cache)
             for prec in (vps.VPS_FP32, vps.VPS_FP64)]
+        # the small 2D workload: Q2 on 16 x 16 cells, f from u = sin(pi x) sin(pi y);
+        # one FP64 multiplicative smoothing step on a seeded N(0,1) vector, then the
+        # FP64 V-cycle-preconditioned CG to 1e-10
+        from synthetic import manufactured_sine, normal_vector
+        P2 = vps.Poisson(2, 2, 4, precision=vps.VPS_FP64)
+        N2 = P2.n_interior()
+        coef2, freq2 = manufactured_sine(2)
+        b2 = torch.zeros(N2, dtype=torch.float64, device="cuda")
+        P2.vps_assemble_rhs_sines(coef2, freq2, b2)
+        xs2 = P2.to_level(torch.as_tensor(normal_vector(N2, 0), device="cuda"))
+        bs2 = P2.to_level(b2)
+        P2.vps_smooth(4, bs2, xs2, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(P2.stream)
+        for _ in range(20):
+            vps._check(lib.vps_smooth(P2.h, 4, ptr(bs2), ptr(xs2), 1), P2.h)
+        e1.record(P2.stream)
+        torch.cuda.synchronize()
+        t2s = e0.elapsed_time(e1) / 20e3
+        x2 = torch.zeros_like(b2)
+        P2.vps_solve(b2, x2, RTOL, 100)
+        t2 = []
+        for _ in range(5):
+            x2.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it2, rel2 = P2.vps_solve(b2, x2, RTOL, 100)
+            t2.append(time.perf_counter() - t0)
+        extras["poisson_2d_q2_l4_fp64"] = {
+            "dofs": N2, "smoother_step_s": t2s, "smoother_dof_per_s": N2 / t2s,
+            "cg_time_to_1e-10_s": min(t2), "iterations": it2, "rel_residual": rel2,
+            "l2_error": P2.vps_l2_error_sine(x2)}
+        P2.close()
         # the mixed-precision setting: 3D Q3 on 2^7 cells, manufactured sine, 2/2
         # smoothing, FP32 V-cycle in FP64 CG against the FP64 V-cycle, to 1e-10
         extras["mixed_precision_3d_q3_l7"] = mixed_precision_solve(vps, torch, 7, 3,

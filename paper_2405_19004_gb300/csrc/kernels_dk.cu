@@ -157,14 +157,23 @@ struct SmoothCfg {
   static constexpr int NT = W_ > 0 ? 32 * W_ : (NT0 > 1024 ? 1024 : NT0);
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
   // interleaved buffers [..][p] (elements):
-  //   3D: A0, A1 = n n m P (stage-0 outputs, later FD ping-pong),
-  //       B0, B1 = n m m P (stage-1 outputs), bI, xI = md P, il = md
+  //   3D: A0, A1 = n n m P (stage-0 outputs), B0, B1 = n m m P (stage-1
+  //       outputs), F0, F1 (stage-2 output and the fast-diagonalisation
+  //       ping-pong, md P each), bI, xI = md P, il = md.
+  //       With `alias` (blocks that run every stage in one round of lines)
+  //       stage 1 reads its lines into registers and crosses a barrier
+  //       before it writes, so B0, B1 overlay A0, A1; F0 follows them and F1
+  //       overlays B0: one region of max(2 n n m, 2 n m m + md) P elements
+  //       (3D Q4: 6.3 KB per patch in FP32 instead of 10.8 KB).  Otherwise
+  //       F0 = A0, F1 = A1.
   //   2D: A0, A1 = n m P, B0 = m m P (residual), bI, xI = md P, il = md
   static constexpr int sizeA = DIM == 3 ? n * n * m : n * m;
   static constexpr int sizeB = DIM == 3 ? n * m * m : m * m;
   static constexpr int nB = DIM == 3 ? 2 : 1;
-  static constexpr size_t elems_mult =
-      (size_t)P * (2 * sizeA + nB * sizeB + 2 * md) + md;
+  static constexpr bool alias = DIM == 3 && W_ == 0;
+  static constexpr int region =
+      alias ? (2 * sizeA > 2 * sizeB + md ? 2 * sizeA : 2 * sizeB + md) : 2 * sizeA + nB * sizeB;
+  static constexpr size_t elems_mult = (size_t)P * (region + 2 * md) + md;
   static constexpr size_t smem_mult = sizeof(T) * elems_mult + sizeof(int) * P;
   // Boundary kernel: no staged copy of the interior of x
   static constexpr size_t smem_bnd = smem_mult - sizeof(T) * (size_t)P * md;
@@ -576,10 +585,14 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
   constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
   using PK = Pack<T, Q>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* A0 = reinterpret_cast<T*>(smem_raw);
+  constexpr bool kAlias = C::alias;
+  T* const base = reinterpret_cast<T*>(smem_raw);
+  T* A0 = base;
   T* A1 = A0 + P * C::sizeA;
-  T* B0 = A1 + P * C::sizeA;
-  T* bI = B0 + C::nB * P * C::sizeB;
+  T* B0 = kAlias ? base : A1 + P * C::sizeA;
+  T* F0 = kAlias ? base + 2 * P * C::sizeB : A0;
+  T* F1 = kAlias ? base : A1;
+  T* bI = base + (size_t)P * C::region;
   T* xI = BND ? nullptr : bI + P * MD;
   T* il = bI + (BND ? 1 : 2) * P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
@@ -679,11 +692,15 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
     // Stage 1: along y.  U = M (M x), W = A (M x) + M (A x)  (the inner sum
     // M x along z is shared by two terms, Section 3.1.1).
     constexpr int NL1 = n * m;
-    for_lines<G * NL1, NT>([&](const int t) {
+    // with kAlias, B0/B1 overlay A0/A1: every line is read into registers
+    // before the barrier, written after it (one round: NT >= G n m)
+    static_assert(!kAlias || NT >= G * NL1, "aliased stage 1 needs one round of lines");
+    const bool act1 = !kAlias || (int)threadIdx.x < G * NL1;
+    T vm[n][Q], va[n][Q];
+    auto load1 = [&](const int t) {
       const int L = t / G, g = t % G;
       const PK* sM = reinterpret_cast<const PK*>(A0 + L * P + g * Q);
       const PK* sA = reinterpret_cast<const PK*>(A1 + L * P + g * Q);
-      T vm[n][Q], va[n][Q];
 #pragma unroll
       for (int c = 0; c < n; ++c) {
         const PK a = sM[c * NL1 * G], bb = sA[c * NL1 * G];
@@ -693,6 +710,14 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
           va[c][j] = bb.v[j];
         }
       }
+    };
+    if constexpr (kAlias) {
+      if (act1) load1(threadIdx.x);
+      __syncthreads();
+    }
+    for_lines<G * NL1, NT>([&](const int t) {
+      const int L = t / G, g = t % G;
+      if constexpr (!kAlias) load1(t);
       PK* dU = reinterpret_cast<PK*>(B0 + L * m * P + g * Q);
       PK* dW = reinterpret_cast<PK*>(B1 + L * m * P + g * Q);
       T em[KE][Q], dm[K][Q], ea[KE][Q], da[K][Q];
@@ -747,7 +772,7 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
       }
       const PK* sb = reinterpret_cast<const PK*>(bI + L * m * P + g * Q);
       constexpr bool kKeep = !RES && kFuseFD;  // keep the line for S^T along x
-      PK* dR = reinterpret_cast<PK*>(A0 + L * m * P + g * Q);
+      PK* dR = reinterpret_cast<PK*>(F0 + L * m * P + g * Q);
       T rr[kKeep ? m : 1][Q];
       // A vu + M vw on the interior rows, by the even/odd halves
       T ex[KE][Q], dx[K][Q], ey[KE][Q], dy[K][Q];
@@ -787,7 +812,7 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
         // first direction of the fast diagonalisation in registers: S^T along
         // x, written as [y][z][x'] (y contracted next)
         const int Ls = (L % m) * m + L / m;
-        PK* dT = reinterpret_cast<PK*>(A0 + Ls * m * P + g * Q);
+        PK* dT = reinterpret_cast<PK*>(F0 + Ls * m * P + g * Q);
         T tt[m][Q];
         st_line<T, Q>(rr, tt);
 #pragma unroll
@@ -801,33 +826,33 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
     });
     __syncthreads();
     if constexpr (RES) {
-      store_lines<T, G, Q, NT>(A0, rout, s_org, px, pz, T(1) / bscale);
+      store_lines<T, G, Q, NT>(F0, rout, s_org, px, pz, T(1) / bscale);
       return;
     }
     if constexpr (kFuseFD) {
       // Rest of the fast diagonalisation (Eq. 2.14): S^T along y; S^T along z,
       // the eigenvalue scaling and S along z in one stage; S along y; S along x
       // with the update of the interior.
-      fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);  // [y][z][x'] -> [z][x'][y']
+      fd_stage<T, G, Q, NT, 0>(F0, F1, nullptr);  // [y][z][x'] -> [z][x'][y']
       __syncthreads();
-      fd_pair<T, G, Q, NT, true>(A1, A0, il);     // [z][x'][y'] -> [y'][x'][z'']
+      fd_pair<T, G, Q, NT, true>(F1, F0, il);     // [z][x'][y'] -> [y'][x'][z'']
       __syncthreads();
-      fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);  // [y'][x'][z''] -> [x'][z''][y'']
+      fd_stage<T, G, Q, NT, 2>(F0, F1, nullptr);  // [y'][x'][z''] -> [x'][z''][y'']
       __syncthreads();
     } else {
       // S^T along z, y, x (scaled), then S along z, y; S along x below
-      fd_stage<T, G, Q, NT, 0>(A0, A1, nullptr);
+      fd_stage<T, G, Q, NT, 0>(F0, F1, nullptr);
       __syncthreads();
-      fd_stage<T, G, Q, NT, 0>(A1, A0, nullptr);
+      fd_stage<T, G, Q, NT, 0>(F1, F0, nullptr);
       __syncthreads();
-      fd_stage<T, G, Q, NT, 1>(A0, A1, il);
+      fd_stage<T, G, Q, NT, 1>(F0, F1, il);
       __syncthreads();
-      fd_stage<T, G, Q, NT, 2>(A1, A0, nullptr);
+      fd_stage<T, G, Q, NT, 2>(F1, F0, nullptr);
       __syncthreads();
-      fd_stage<T, G, Q, NT, 2>(A0, A1, nullptr);
+      fd_stage<T, G, Q, NT, 2>(F0, F1, nullptr);
       __syncthreads();
     }
-    fd_final<T, G, Q, NT, BND>(A1, x, xI, s_org, px, pz, T(1));
+    fd_final<T, G, Q, NT, BND>(F1, x, xI, s_org, px, pz, T(1));
   } else {
     // 2D.  Stage 0: lines along y from global; M x and A x along y into [x][oy].
     for_lines<G * n, NT>([&](const int t) {
@@ -2429,9 +2454,12 @@ cudaError_t smooth_limits() {
     cudaError_t e = smoother_smem(smooth_mult_kernel<T, PP, true, 0>, C::smem_bnd);
     if (e != cudaSuccess) return e;
     if constexpr (kOneWarpVariants) {
-      e = smoother_smem(smooth_mult_kernel<T, PP, true, 1>, C::smem_bnd);
+      // the one-warp blocks run their stages in several rounds: no buffer
+      // overlay, so their own (larger) shared-memory size
+      using C1 = SmoothCfg<T, PP, 1>;
+      e = smoother_smem(smooth_mult_kernel<T, PP, true, 1>, C1::smem_bnd);
       if (e != cudaSuccess) return e;
-      e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 1>, C::smem_bnd);
+      e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 1>, C1::smem_bnd);
       if (e != cudaSuccess) return e;
     }
     e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 0>, C::smem_bnd);
