@@ -205,6 +205,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(value, dist):
+    """The largest of a rank-local number over all ranks (the number itself
+    without a process group): the step time every rank waits for."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, t_step, world):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank per step, the step taking t_step (the maximum over ranks)."""
+    return world * units_per_rank / t_step
+
+
 # ---------------------------------------------------------------- serving
 def run_serving(vps, n_requests, precision, max_active, budget):
     """Replays a seeded Poisson-arrival stream of solve requests in real time."""
@@ -379,12 +398,8 @@ def main():
     barrier()
     launches = P.vps_kernel_launches() - launches0
     clocks = sampler.stop()
-    t_step = statistics.mean(times)
-    if dist is not None:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = world * N / t_step
+    t_step = max_over_ranks(statistics.mean(times), dist)
+    value = job_throughput(N, t_step, world)
 
     # end to end through the host-buffer entry point (copies inside)
     bh = torch.as_tensor(uniform_vector(N, 1 + rank)).pin_memory()
@@ -397,11 +412,7 @@ def main():
         t0 = time.perf_counter()
         P.vps_solve_host(bh, xh, RTOL, 100)
         e2e_t.append(time.perf_counter() - t0)
-    t_e2e = statistics.mean(e2e_t)
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(statistics.mean(e2e_t), dist)
 
     # dominant kernel: finest-level FP32 smoother colour passes (same kernel and data
     # sizes as in the solve), CUDA events on the library's stream around each run of the
@@ -654,7 +665,7 @@ def main():
                      "avg_launch_us": 1e6 * t_launch, "flops_per_launch": flops_per_launch,
                      "executed_flops_per_launch": executed_per_launch,
                      "frac_executed": executed_per_launch / t_launch / 1e12 / fp32_peak_tflops},
-        "e2e": {"value": world * N / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,
+        "e2e": {"value": job_throughput(N, t_e2e, world), "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N},
         "gpu_launches": launches,
         "clocks": clocks,
