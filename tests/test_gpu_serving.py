@@ -125,18 +125,24 @@ def test_wait_times_out_on_the_host():
 
 
 def test_requests_of_one_cohort_share_batched_launches():
-    """Four 3D Q2 requests of three levels admitted together: their V-cycles
-    run as one cohort, so at least one batched launch processes tiles of
-    several requests; each result still equals the request's result alone."""
+    """Four 3D Q2 requests of three levels: a first round builds their
+    hierarchies; in the second round all four have a resident slot, are
+    admitted together and run as one cohort, so batched launches process
+    tiles of several requests.  Each result still equals the request's result
+    alone."""
     reqs = [(3, 2, 3), (3, 2, 4), (3, 2, 3), (3, 2, 2)]
     coefs = [sine_modes(3, 300 + i) for i in range(len(reqs))]
     srv = vps.Server(4 * GB, max_active=8, precision=vps.VPS_FP32)
+    for i, (d, k, L) in enumerate(reqs):
+        srv.submit(d, k, L, *coefs[i])
+    srv.wait(0, 300)
+    before = srv.batch_stats()
     xs = [srv.submit(d, k, L, *coefs[i])[1] for i, (d, k, L) in enumerate(reqs)]
     srv.wait(0, 300)
     st = srv.batch_stats()
     srv.close()
-    assert st["max_requests_per_launch"] >= 2 and st["max_requests_per_tick"] >= 2, st
-    assert st["batched_launches"] > 0 and st["ticks"] > 0
+    assert st["max_requests_per_launch"] >= 2 and st["max_requests_per_tick"] >= 2, (before, st)
+    assert st["batched_launches"] > before["batched_launches"] and st["ticks"] > before["ticks"]
     for i, (d, k, L) in enumerate(reqs):
         alone = vps.Server(GB, max_active=1, precision=vps.VPS_FP32)
         rid, x = alone.submit(d, k, L, *coefs[i])
