@@ -308,3 +308,28 @@ def test_operator_structure_and_colour_schedule_keep_parity(op, pdl):
     x = P.empty_level(L)
     P.vps_vcycle(to_dev(P, b, L), x)
     assert rel_err(to_host(P, x, L), H.vcycle(L, b)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_zero_right_hand_side_gives_zero_without_iterations(prec):
+    """b = 0: x = 0 is the solution; the solve takes no iteration."""
+    import torch
+    P = _poisson(3, 2, 3, prec)
+    b = torch.zeros(P.n_interior(), dtype=torch.float64, device="cuda")
+    x = torch.full_like(b, 7.0)
+    it, rel = P.vps_solve(b, x, 1e-10, 50)
+    assert it == 0 and rel == 0.0
+    assert torch.count_nonzero(x).item() == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_non_finite_right_hand_side_is_a_breakdown(prec):
+    """A NaN in b is reported as VPS_EBREAKDOWN, not as a result."""
+    import torch
+    P = _poisson(2, 2, 3, prec)
+    b = torch.ones(P.n_interior(), dtype=torch.float64, device="cuda")
+    b[5] = float("nan")
+    x = torch.zeros_like(b)
+    with pytest.raises(vps.VpsError) as e:
+        P.vps_solve(b, x, 1e-10, 50)
+    assert e.value.code == vps.VPS_EBREAKDOWN
