@@ -267,14 +267,18 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
 
 /* vps_set_smooth_variant / vps_get_smooth_variant -- the smoother kernel
  * variant of `level` (0: every level), and its patches per thread block.
- *   0, 1, 2: the fused kernel (Algorithm 3) with 1, 2, 4 patches per thread;
- *   3, 4, 5: the Boundary kernel of Section 3.2 with 1, 2, 4 patches per
- *            thread: x_I = A_j^-1 (b_I - A^IB x_B), which equals the fused
- *            update for the exact local solver without reading x_I
+ * Variant 3 * kind + shape, shape 0, 1, 2 the block shape: shape 0 has G1
+ * groups of 1 patch per thread, shape 1 G1 groups of 2 patches per thread,
+ * shape 2 G2 groups of 1 (G1, G2 per dimension and degree, chosen so that
+ * the lines of every contraction stage nearly fill whole warps; the patches
+ * per block are returned in *patches_per_block);
+ *   kind 0 (variants 0-2): the fused kernel (Algorithm 3);
+ *   kind 1 (3-5): the Boundary kernel of Section 3.2:
+ *            x_I = A_j^-1 (b_I - A^IB x_B), which equals the fused update
+ *            for the exact local solver without reading x_I
  *            (VPS_MULTIPLICATIVE handles only);
- *   6, 7, 8: the Boundary kernel in blocks of one warp (1, 2, 4 patches
- *            per thread), each stage in several rounds of 32 lines
- *            (degrees 1..3 only).
+ *   kind 2 (6-8): the Boundary kernel in blocks of one warp, each stage in
+ *            several rounds of 32 lines (degrees 1..3 only).
  * A variant whose shared memory exceeds the GPU's limit for the handle's
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);
@@ -338,7 +342,7 @@ int vps_get_outer_operator(vps_handle h, int* mode);
  *     precomputed A_j^-1 instead of fast diagonalisation (the "inverse
  *     matrix" local solver; m^d <= 1024 rows, i.e. k <= 5 in 3D; built on
  *     the host in FP64 on first selection).
- * Kinds 1-3 take the patches per thread of the level's variant.  Errors:
+ * Kinds 1-3 take the block shape of the level's variant.  Errors:
  * VPS_EINVAL (unknown kind, additive handle, inverse too large). */
 #define VPS_KERNEL_FUSED 0
 #define VPS_KERNEL_SEPARATE 1

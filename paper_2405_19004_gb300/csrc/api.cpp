@@ -1783,9 +1783,9 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     }
   }
   int rc;
-  // default variant before tuning: the Boundary kernel with 2 (else 1) patches
-  // per thread for the multiplicative smoother; 2 (else 1) for the additive
-  const int prefer[2][4] = {{4, 3, 1, 0}, {1, 0, 1, 0}};
+  // default variant before tuning: the Boundary kernel of block shape 0 for
+  // the multiplicative smoother, else the fused one; shape 0 for the additive
+  const int prefer[2][4] = {{3, 4, 0, 1}, {0, 1, 0, 1}};
   int def_var = 0;
   for (int v : prefer[smoother == VPS_ADDITIVE ? 1 : 0])
     if (variant_ok(h, v)) {

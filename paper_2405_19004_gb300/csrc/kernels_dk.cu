@@ -127,12 +127,20 @@ __device__ __forceinline__ void grid_dependency_wait() {
 // the Q values of a tensor entry are adjacent in shared memory (patch index
 // fastest), so they move as one vector access.  With G and Q powers of two
 // and the odd extents 2k+-1, every warp access is free of bank conflicts.
-// The autotuner chooses Q among kVarQ; G is fixed per (dim, degree) so that
-// a block has enough lines to fill its warps.
+// Block shapes (the autotuner picks one per level): shape s has kShapeG[s]
+// patch groups of kShapeQ[s] patches per thread.  G is chosen so that the
+// G n^2, G n m and G m^2 lines of the 3D stages (G n and G m in 2D) nearly
+// fill whole warps -- a stage whose lines leave most of a warp idle costs
+// the same issue slots and shared-memory wavefronts as a full one -- within
+// 1024 threads: 3D k = 4 fills 88-98 % of the lanes with G = 4 against
+// 77-98 % with one patch per block.
 constexpr int kLinesMax = DIM == 3 ? n * n : n;
-constexpr int kG = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 4 : K == 3 ? 2 : 1)
-                            : (K <= 2 ? 32 : (K <= 4 ? 16 : 8));
-constexpr int kVarQ[kQVariants] = {1, 2, 4};
+constexpr int kG1 = DIM == 3 ? (K == 1 ? 32 : K == 2 ? 16 : K == 3 ? 8 : K <= 5 ? 4 : 2)
+                             : (K <= 6 ? 32 : 16);
+constexpr int kG2 = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 32 : K == 3 ? 16 : K <= 5 ? 8 : 4)
+                             : (K <= 6 ? 16 : 32);
+constexpr int kShapeG[kQVariants] = {kG1, kG1, kG2};
+constexpr int kShapeQ[kQVariants] = {1, 2, 1};
 // Contract the first and the middle direction of the fast diagonalisation in
 // registers (two stages and two barriers fewer); above k = 5 the extra live
 // values cost more resident blocks than the barriers save.
@@ -150,9 +158,9 @@ struct alignas(sizeof(T) * Q) Pack {
 // W_ = 0: enough warps for every line of the first stage in one round
 // (at most 1024 threads); W_ > 0: W_ warps, each stage in several rounds
 // (one-warp blocks wait at their barriers for no other warp).
-template <typename T, int Q_, int W_ = 0>
+template <typename T, int S_, int W_ = 0>
 struct SmoothCfg {
-  static constexpr int G = kG, Q = Q_, P = G * Q;
+  static constexpr int G = kShapeG[S_], Q = kShapeQ[S_], P = G * Q;
   static constexpr int NT0 = ((G * kLinesMax + 31) / 32) * 32;
   static constexpr int NT = W_ > 0 ? 32 * W_ : (NT0 > 1024 ? 1024 : NT0);
   static constexpr int md = DIM == 3 ? m * m * m : m * m;
@@ -208,7 +216,7 @@ __device__ __forceinline__ int closure_origin(int gp, const ColourGeom& cg, int 
 }
 
 // Origins of the block's P patches (-1: beyond the colour), computed once;
-// P may exceed the block's NT threads (2D, k = 1, 4 patches per thread).
+// P may exceed the block's NT threads (2D, k = 1, 2 patches per thread).
 template <int P, int NT>
 __device__ __forceinline__ void load_origins(int* s_org, const ColourGeom& cg, int px, int pz,
                                              int64_t tile) {
@@ -2152,7 +2160,7 @@ __global__ void zero_upper_faces_batch_kernel(const BatchQueue* __restrict__ q) 
 template <typename T, int PP, bool BND, int W>
 cudaError_t smooth_mult_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                                const T* inv_lam, cudaStream_t s) {
-  using C = SmoothCfg<T, PP, W>;  // PP: patches per thread (Q), W: warps (0: automatic)
+  using C = SmoothCfg<T, PP, W>;  // PP: block shape, W: warps (0: automatic)
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
@@ -2292,7 +2300,7 @@ cudaError_t inverse_launch(const LevelGeom& g, const ColourGeom& cg, const T* r,
 template <typename T, int PP>
 cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T* r, T* x,
                               const T* inv_lam, T scale, cudaStream_t s) {
-  using C = SmoothCfg<T, PP>;  // PP: patches per thread (Q)
+  using C = SmoothCfg<T, PP>;  // PP: block shape
   if (cg.npatch == 0) return cudaSuccess;
   const int64_t grid = (cg.npatch + C::P - 1) / C::P;
   const T sc = DIM == 3 ? T(scale / g.h) : scale;
@@ -2524,11 +2532,11 @@ void register_variant(KernelFns<T>* f, int v) {
 
 template <typename T>
 void register_fns(KernelFns<T>* f) {
-  register_variant<T, kVarQ[0]>(f, 0);
-  register_variant<T, kVarQ[1]>(f, 1);
-  register_variant<T, kVarQ[2]>(f, 2);
-  // default additive variant: the middle one, or the smallest where it does not fit
-  f->smooth_add = f->smooth_add_v[1] ? f->smooth_add_v[1] : f->smooth_add_v[0];
+  register_variant<T, 0>(f, 0);
+  register_variant<T, 1>(f, 1);
+  register_variant<T, 2>(f, 2);
+  // default additive variant (the allocation-free entry point): shape 0
+  f->smooth_add = f->smooth_add_v[0] ? f->smooth_add_v[0] : f->smooth_add_v[1];
   f->apply = apply_launch<T>;
   if constexpr (DIM == 3 && kApply3C<T>) f->apply_alt = apply_alt_launch<T>;
   else f->apply_alt = nullptr;
@@ -2544,11 +2552,11 @@ void register_fns(KernelFns<T>* f) {
 template <typename T>
 cudaError_t set_smem_limits() {
   cudaError_t e;
-  e = smooth_limits<T, kVarQ[0]>();
+  e = smooth_limits<T, 0>();
   if (e != cudaSuccess) return e;
-  e = smooth_limits<T, kVarQ[1]>();
+  e = smooth_limits<T, 1>();
   if (e != cudaSuccess) return e;
-  e = smooth_limits<T, kVarQ[2]>();
+  e = smooth_limits<T, 2>();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ApplyCfg::smem<T>());

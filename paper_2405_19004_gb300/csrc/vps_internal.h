@@ -154,7 +154,9 @@ struct BatchQueue {
 };
 
 // Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
-// q = 0, 1, 2 for 1, 2, 4 patches per thread; kind 0 the fused kernel,
+// q = 0, 1, 2 the block shape (q = 0: G1 patch groups of 1 patch per thread,
+// q = 1: G1 groups of 2, q = 2: G2 groups of 1, with G1 and G2 per (dim,
+// degree) so that the stages' lines fill whole warps; kind 0 the fused kernel,
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
 // kind 2 the Boundary kernel in one-warp blocks.  Kinds 1 and 2 serve the
 // multiplicative smoother only (smooth_add_v[3..8] stay null).
@@ -174,7 +176,7 @@ struct KernelFns {
   SmoothAddFn smooth_add_v[kSmoothVariants] = {};
   int variant_p[kSmoothVariants] = {};           // patches per block of each variant
   // ablation kernels of Section 3.1: the local residual of every patch of a
-  // colour written to r (Separate; 1, 2, 4 patches per thread), and the
+  // colour written to r (Separate; the three block shapes), and the
   // local solve with the dense inverse (AinvT: A_j^-1 transposed, m^d x m^d)
   cudaError_t (*resid_v[kQVariants])(const LevelGeom&, const ColourGeom&, const T* b,
                                      const T* x, T* r, cudaStream_t) = {};

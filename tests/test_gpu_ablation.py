@@ -29,7 +29,7 @@ def test_kernel_structures_match_the_oracle(d, k, l, prec, kind):
     P = vps.Poisson(d, k, l, precision=prec)
     P.vps_set_smoother_kernel(kind)
     assert P.vps_get_smoother_kernel() == kind
-    for v in (0, 1, 3, 4):  # patches per thread of the solve kernels follow the level's variant
+    for v in (0, 1, 3, 4):  # the block shape of the solve kernels follows the level's variant
         try:
             P.vps_set_smooth_variant(0, v)
         except vps.VpsError:
