@@ -36,17 +36,21 @@ METRIC = "smoother DoF/s & % FP32/FP64 peak; time-to-1e-10 residual FP32-MG vs F
 D, K, L = 3, 4, 5
 RTOL = 1e-10
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (Blackwell)
+SCHEDULE_NAMES = {0: "colour passes, ordinary launches",
+                  1: "colour passes, programmatic dependent launches",
+                  2: "dataflow sweep (one launch per smoothing step)"}
 CPU_SAMPLE_LEVEL = 4           # oracle sample: the same problem at level 4 (250,047 DoFs)
 CPU_SAMPLE_REPEATS = 3         # best of 3 solves
 REF_STEP_BUDGET_S = 240.0      # reference arm: whole run within about four minutes
 REF_STEP_S_LEVEL4 = 4.0        # one oracle solve at level 4 on the GPU machine's host (3.05 s measured)
 
 
-def smoother_traffic(variant):
-    """DRAM bytes per finest-level colour pass of the timed smoother kernel
-    from the committed ncu record (dram__bytes_read.sum + dram__bytes_write.sum
-    of the kernel, summarised in profiles/smoother_traffic_3d_q4_l5.md), or
-    None if the record is for another variant or was taken before the kernel
+def smoother_traffic(variant, schedule):
+    """DRAM bytes per launch of the timed smoother kernel on the finest level
+    (a colour pass, or a whole step for the dataflow sweep) from the committed
+    ncu record (dram__bytes_read.sum + dram__bytes_write.sum of the kernel,
+    summarised in profiles/smoother_traffic_3d_q4_l5.md), or None if the
+    record is for another variant or schedule or was taken before the kernel
     source last changed."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "smoother_traffic_3d_q4_l5.json")
@@ -58,7 +62,8 @@ def smoother_traffic(variant):
         return None
     if rec.get("kernels_dk.cu sha256") != sha:
         return None
-    v = rec.get("traffic_bytes_per_launch", {}).get(str(variant))
+    key = f"{'sweep' if schedule == 2 else 'pass'}:{variant}"
+    v = rec.get("traffic_bytes_per_launch", {}).get(key)
     return float(v) if v is not None else None
 
 
@@ -96,6 +101,10 @@ def parse():
     p.add_argument("--smoother-variant", type=int, default=None,
                    help="pin the finest level's smoother variant after tuning (profiling runs; "
                         "default: the autotuner's choice)")
+    p.add_argument("--colour-schedule", type=int, default=None, choices=[0, 1, 2],
+                   help="pin the colour schedule after tuning: 0 ordinary launches, 1 programmatic "
+                        "dependent launches, 2 one dataflow sweep per smoothing step (profiling "
+                        "runs; default: the autotuner's choice)")
     p.add_argument("--no-graphs", action="store_true",
                    help="launch every kernel directly (no CUDA graphs, host-driven CG iterations): "
                         "the same kernels, for profilers that do not follow graph conditional nodes")
@@ -343,12 +352,17 @@ def main():
     P.vps_autotune(args.tune_cache)  # timed trials on this GPU, before the timed region
     if args.smoother_variant is not None:
         P.vps_set_smooth_variant(L, args.smoother_variant)
+    if args.colour_schedule is not None:
+        P.vps_set_colour_schedule(args.colour_schedule)
+    schedule = P.vps_get_colour_schedule()
     if args.no_graphs:
         P.vps_set_graphs(False)
     tuned = {"coarse_level": P.vps_get_coarse_level(),
              "smoother_variants": [P.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
              "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)],
              "finest_variant_pinned": args.smoother_variant is not None,
+             "colour_schedule": SCHEDULE_NAMES[schedule],
+             "colour_schedule_pinned": args.colour_schedule is not None,
              "cuda_graphs": not args.no_graphs}
     N = P.n_interior()
     b = torch.as_tensor(uniform_vector(N, 1 + rank), device="cuda")
@@ -414,12 +428,13 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     t_e2e = max_over_ranks(statistics.mean(e2e_t), dist)
 
-    # dominant kernel: finest-level FP32 smoother colour passes (same kernel and data
-    # sizes as in the solve), CUDA events on the library's stream around each run of the
-    # 8 passes of a smoothing step, launched back to back as in the V-cycle (the passes
-    # are programmatic dependent launches: a pass is scheduled while the previous one
-    # drains, which an event between two passes would prevent); the average launch
-    # duration is the run's time / 8
+    # dominant kernel: the finest-level FP32 smoother (same kernel and data sizes
+    # as in the solve), CUDA events on the library's stream.  Dataflow sweep: one
+    # launch per smoothing step, timed launch by launch.  Colour passes: around
+    # each run of the 8 passes of a step, launched back to back as in the V-cycle
+    # (programmatic dependent launches: a pass is scheduled while the previous one
+    # drains, which an event between two passes would prevent); the average
+    # launch duration is the run's time / 8
     lib = vps.lib()
     import ctypes
     bs = P.to_level(b.float())
@@ -429,22 +444,31 @@ def main():
     n_rep = 20
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(n_rep)]
-    for c in range(8):  # warm-up
-        vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+    sweep = schedule == vps.VPS_SCHEDULE_SWEEP
+
+    def smoother_launches():
+        if sweep:
+            vps._check(lib.vps_smooth(P.h, L, ptr(bs), ptr(xs), 1), P.h)
+        else:
+            for c in range(8):
+                vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+
+    smoother_launches()  # warm-up
     with nvtx("smoother_colour_passes"):
         for r in range(n_rep):
             a, z = evs[r]
             a.record(stream)
-            for c in range(8):
-                vps._check(lib.vps_smooth_colour(P.h, L, c, ptr(bs), ptr(xs)), P.h)
+            smoother_launches()
             z.record(stream)
         torch.cuda.synchronize()
-    launch_ms = [a.elapsed_time(z) / 8.0 for a, z in evs]
+    P.vps_check_waits()
+    per_run = 1 if sweep else 8
+    launch_ms = [a.elapsed_time(z) / per_run for a, z in evs]
     t_launch = statistics.mean(launch_ms) / 1e3
     n_patches = (2 ** L - 1) ** 3
     var_L = P.vps_get_smooth_variant(L)[0]
     bnd_L = var_L // 3 >= 1
-    flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / 8.0
+    flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / per_run
     # FP32 peak from the unit counts and the device's maximum SM clock; the
     # shared-memory roofline of Section 4.3 at the SM clock sampled under load
     fp32_peak_tflops = fp32_peak(peaks["sm_count"], peaks["sm_max_mhz"]) / 1e12
@@ -453,8 +477,8 @@ def main():
     smem_roof_tflops = smem_bandwidth(peaks["sm_count"], smem_mhz) * smoother_flops_per_patch(
         D, K, bnd_L) / (4.0 * smem_words) / 1e12
     achieved = flops_per_launch / t_launch / 1e12
-    executed_per_launch = smoother_flops_executed_per_patch(D, K, bnd_L) * n_patches / 8.0
-    t_smooth_step = 8 * t_launch
+    executed_per_launch = smoother_flops_executed_per_patch(D, K, bnd_L) * n_patches / per_run
+    t_smooth_step = per_run * t_launch
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -654,11 +678,14 @@ def main():
                           "smem_roofline_tflops": smem_roof_tflops,
                           "smem_roofline_clock_mhz": smem_mhz,
                           "smem_words_per_patch_model": smem_words},
-        "roofline": {"kernel": "smooth_mult_kernel<float> (3D, k=4), finest level, "
+        "roofline": {"kernel": ("smooth_sweep_kernel<float> (3D, k=4), finest level, one launch "
+                                "per smoothing step (all 8 colours), " if sweep else
+                                "smooth_mult_kernel<float> (3D, k=4), finest level, one launch "
+                                "per colour pass, ")
                                + ("Boundary" if bnd_L else "fused") + f" variant {var_L}",
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                     "traffic": smoother_traffic(var_L),
+                     "traffic": smoother_traffic(var_L, schedule),
                      "peak_source": f"{peaks['sm_count']} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                     f"flop x {peaks['sm_max_mhz']:g} MHz ({peaks['sm_max_mhz_source']})"
                                     "; measured FMA throughput in peaks.fp32_fma_measured_flops",

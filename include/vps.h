@@ -255,8 +255,12 @@ int vps_get_coarse_level(vps_handle h, int* level);
 /*
  * vps_autotune -- choose, by timed trials on this handle's own buffers, the
  * smoother variant of every level (patches per thread block, the tuning
- * axis of Section 3.1.2) and the coarsest level (vps_set_coarse_level) that
- * give the fastest CG solve.  cache_path (may be NULL): a JSON file keyed by
+ * axis of Section 3.1.2) together with the colour schedule
+ * (vps_set_colour_schedule: for each schedule the fastest variant of every
+ * level, and the schedule whose fastest steps add up to the least time),
+ * the operator tile structure of every level (vps_set_operator_variant),
+ * and the coarsest level (vps_set_coarse_level) that gives the fastest CG
+ * solve.  cache_path (may be NULL): a JSON file keyed by
  * (dim, degree, precision, smoother, level, smoothing steps) with the
  * smoother variant and operator tile structure of every level, the colour
  * schedule and the coarsest level; an entry found
@@ -294,14 +298,44 @@ int vps_get_smooth_variant(vps_handle h, int level, int* variant, int* patches_p
 int vps_set_operator_variant(vps_handle h, int level, int variant);
 int vps_get_operator_variant(vps_handle h, int level, int* variant, int* n_variants);
 
-/* vps_set_colour_pdl / vps_get_colour_pdl -- colour schedule of the
- * multiplicative smoother: enable = 1 (default) launches the colour passes
- * of a step as programmatic dependent launches (a pass is scheduled while
- * the previous one drains and waits for it before reading b or x), 0 as
- * ordinary launches.  The same arithmetic either way; chosen by
- * vps_autotune.  Errors: VPS_EINVAL (h NULL). */
-int vps_set_colour_pdl(vps_handle h, int enable);
-int vps_get_colour_pdl(vps_handle h, int* enable);
+/* vps_set_colour_schedule / vps_get_colour_schedule -- how the colour
+ * passes of a multiplicative smoothing step (Algorithm 3, colour by colour)
+ * are scheduled on the GPU; chosen by vps_autotune:
+ *   VPS_SCHEDULE_PLAIN: one ordinary launch per colour;
+ *   VPS_SCHEDULE_PDL (default): one programmatic dependent launch per
+ *     colour (a pass is scheduled while the previous one drains and waits
+ *     for it before reading b or x);
+ *   VPS_SCHEDULE_SWEEP: the whole step as one dataflow launch of one block
+ *     per tile of every colour.  Blocks take tiles in the colours' order,
+ *     and a tile starts once the patches of earlier colours that overlap
+ *     its patches (vertices at most one apart in every direction) are done,
+ *     so the passes overlap where the patches do not.  The result equals the
+ *     colour-by-colour passes bit for bit.  Each dependency wait polls a
+ *     flag a bounded number of times (about a second at the least); on
+ *     expiry the sweep records it and finishes without waiting (its values
+ *     are then undefined), and the next vps_solve (at its FP64 residual
+ *     check), vps_gmres, vps_fmg or vps_check_waits returns VPS_ETIMEOUT.
+ *     Fused kernel structure only (VPS_KERNEL_FUSED, smoother variants
+ *     0-5); otherwise, and for vps_smooth_colour, the passes are launched
+ *     as with VPS_SCHEDULE_PDL.
+ * The same arithmetic in every schedule.  Errors: VPS_EINVAL. */
+#define VPS_SCHEDULE_PLAIN 0
+#define VPS_SCHEDULE_PDL   1
+#define VPS_SCHEDULE_SWEEP 2
+int vps_set_colour_schedule(vps_handle h, int schedule);
+int vps_get_colour_schedule(vps_handle h, int* schedule);
+
+/* vps_check_waits -- synchronises the handle's stream; VPS_ETIMEOUT if a
+ * dependency wait of a VPS_SCHEDULE_SWEEP smoothing step of this handle
+ * expired since the last check (the record is then cleared), else VPS_OK. */
+int vps_check_waits(vps_handle h);
+
+/* vps_skip_sweep_tiles -- fault injection for tests: the next dataflow
+ * sweep on `level` starts taking tiles at index `tiles` (in the order of the
+ * sweep), so the first `tiles` tiles are never run and the tiles that depend
+ * on them wait until their poll limit (VPS_ETIMEOUT afterwards).  The sweep
+ * after that one runs normally.  Synchronous.  Errors: VPS_EINVAL. */
+int vps_skip_sweep_tiles(vps_handle h, int level, int64_t tiles);
 
 /* vps_kernel_launches -- number of kernels the handle has launched since
  * creation (direct launches plus, for every replay of a captured graph, the

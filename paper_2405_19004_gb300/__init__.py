@@ -31,6 +31,7 @@ VPS_MAX_DEGREE = 7
 VPS_KERNEL_FUSED, VPS_KERNEL_SEPARATE, VPS_KERNEL_GLOBAL, VPS_KERNEL_GLOBAL_INVERSE = 0, 1, 2, 3
 VPS_OUTER_FP64 = 0
 VPS_OUTER_DOUBLE_FLOAT = 1
+VPS_SCHEDULE_PLAIN, VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP = 0, 1, 2
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
 
 # C signatures: name -> (restype, argtypes)
@@ -68,8 +69,10 @@ SIGNATURES = {
     "vps_get_smooth_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "vps_set_operator_variant": (_i, [_p, _i, _i]),
     "vps_get_operator_variant": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
-    "vps_set_colour_pdl": (_i, [_p, _i]),
-    "vps_get_colour_pdl": (_i, [_p, ctypes.POINTER(_i)]),
+    "vps_set_colour_schedule": (_i, [_p, _i]),
+    "vps_get_colour_schedule": (_i, [_p, ctypes.POINTER(_i)]),
+    "vps_check_waits": (_i, [_p]),
+    "vps_skip_sweep_tiles": (_i, [_p, _i, ctypes.c_int64]),
     "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
     "vps_server_create": (_i, [ctypes.c_size_t, _i, _i, _d, _i, ctypes.POINTER(_p)]),
@@ -335,13 +338,19 @@ class Poisson:
                self.h)
         return v.value, n.value
 
-    def vps_set_colour_pdl(self, enable):
-        self._call(lib().vps_set_colour_pdl, 1 if enable else 0)
+    def vps_set_colour_schedule(self, schedule):
+        self._call(lib().vps_set_colour_schedule, int(schedule))
 
-    def vps_get_colour_pdl(self):
+    def vps_get_colour_schedule(self):
         e = ctypes.c_int()
-        _check(lib().vps_get_colour_pdl(self.h, ctypes.byref(e)), self.h)
-        return bool(e.value)
+        _check(lib().vps_get_colour_schedule(self.h, ctypes.byref(e)), self.h)
+        return e.value
+
+    def vps_check_waits(self):
+        self._call(lib().vps_check_waits)
+
+    def vps_skip_sweep_tiles(self, level, tiles):
+        self._call(lib().vps_skip_sweep_tiles, int(level), int(tiles))
 
     def vps_set_coarse_level(self, level):
         self._call(lib().vps_set_coarse_level, int(level))

@@ -143,7 +143,19 @@ struct vps_context {
   int64_t kernels = 0;                  // kernels launched by this handle
   int smooth_var[kMaxLevels + 1] = {};  // smoother variant per level (index into the table)
   int op_var[kMaxLevels + 1] = {};      // operator tile structure per level (1: apply_alt)
-  bool pdl = true;                      // colour passes as programmatic dependent launches
+  // colour schedule of the multiplicative smoothing step: ordinary launches
+  // of the colour passes, programmatic dependent launches, or one dataflow
+  // sweep kernel per step (VPS_SCHEDULE_*)
+  int schedule = VPS_SCHEDULE_PDL;
+  // dataflow sweeps: per level one flag per patch and the sweep counters;
+  // the wait-expiry word of every sweep of the handle, and whether a sweep
+  // ran since it was last read
+  unsigned int* sweep_flags[kMaxLevels + 1] = {};
+  SweepCounters* sweep_ctr = nullptr;   // kMaxLevels + 1
+  int* wait_err = nullptr;
+  bool sweep_ran = false;
+  unsigned int spin_limit = 1u << 21;   // polls of one flag (at least 128 ns each)
+  int* host_err = nullptr;              // pinned copy of *wait_err
   // kernel structure of the multiplicative smoother (Section 3.1's
   // Fused / Separate / Global, and Global with the dense inverse)
   int kernel_kind = VPS_KERNEL_FUSED;
@@ -286,10 +298,42 @@ int colour_pass(vps_context* h, int l, int c, const T* b, T* x) {
       VPS_CK(h, F.inverse_solve(g, cg, r, x, static_cast<const T*>(h->ainv), h->stream));
       return VPS_OK;
     default:
-      if (h->pdl || !F.smooth_mult_plain_v[v]) VPS_CK(h, F.smooth_mult_v[v](g, cg, b, x, il, h->stream));
+      if (h->schedule != VPS_SCHEDULE_PLAIN || !F.smooth_mult_plain_v[v])
+        VPS_CK(h, F.smooth_mult_v[v](g, cg, b, x, il, h->stream));
       else VPS_CK(h, F.smooth_mult_plain_v[v](g, cg, b, x, il, h->stream));
       return VPS_OK;
   }
+}
+
+// The dataflow sweep of level l over the colours in forward (0 .. 2^d-1)
+// or backward order, for the variant's patches per block.
+SweepGeom sweep_geom(vps_context* h, int l, bool forward, int patches_per_block) {
+  SweepGeom sg;
+  const LevelGeom& g = h->geom[l];
+  const int nc = 1 << h->dim;
+  sg.ncol = nc;
+  sg.ncell = (int)g.ncell;
+  ColourGeom byc[8];
+  int64_t off = 0;
+  for (int c = 0; c < nc; ++c) {
+    byc[c] = make_colour(g, c);
+    sg.flag_off[c] = off;
+    off += byc[c].npatch;
+  }
+  int64_t tiles = 0;
+  for (int s = 0; s < nc; ++s) {
+    const int c = forward ? s : nc - 1 - s;
+    sg.colour[s] = c;
+    sg.pos_of[c] = s;
+    sg.cg[s] = byc[c];
+    tiles += (byc[c].npatch + patches_per_block - 1) / patches_per_block;
+    sg.tile_end[s] = tiles;
+  }
+  sg.flags = h->sweep_flags[l];
+  sg.ctr = h->sweep_ctr + l;
+  sg.err = h->wait_err;
+  sg.spin_limit = h->spin_limit;
+  return sg;
 }
 
 template <typename T>
@@ -308,6 +352,11 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
     for (int c = 0; c < nc; ++c)
       VPS_CK(h, fns<T>(h).smooth_add_v[v](g, make_colour(g, c), r, x, il, (T)h->damping,
                                           h->stream));
+  } else if (h->schedule == VPS_SCHEDULE_SWEEP && h->kernel_kind == VPS_KERNEL_FUSED &&
+             fns<T>(h).smooth_sweep_v[v]) {
+    const SweepGeom sg = sweep_geom(h, l, forward, fns<T>(h).variant_p[v]);
+    h->sweep_ran = true;
+    VPS_CK(h, fns<T>(h).smooth_sweep_v[v](g, sg, b, x, il, h->stream));
   } else {
     for (int i = 0; i < nc; ++i) {
       const int c = forward ? i : nc - 1 - i;
@@ -315,6 +364,19 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
     }
   }
   return VPS_OK;
+}
+
+// VPS_ETIMEOUT if a wait of a dataflow sweep of this handle expired since
+// the last check (synchronises the stream), else VPS_OK; clears the record.
+int check_waits(vps_context* h) {
+  if (!h->sweep_ran || !h->wait_err) return VPS_OK;
+  int err = 0;
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  VPS_CK(h, cudaMemcpy(&err, h->wait_err, sizeof(int), cudaMemcpyDeviceToHost));
+  h->sweep_ran = false;
+  if (!err) return VPS_OK;
+  VPS_CK(h, cudaMemset(h->wait_err, 0, sizeof(int)));
+  return fail(h, VPS_ETIMEOUT, "a dependency wait of a smoothing sweep reached its limit");
 }
 
 // x = A_l^{-1} b on the coarse level by global fast diagonalisation: S^T
@@ -701,7 +763,18 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       if ((rc = cg_true_residual(h))) return rc;
       VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                 h->stream));
+      const bool read_waits = h->sweep_ran;  // the wait-expiry word, in the same synchronisation
+      if (read_waits)
+        VPS_CK(h, cudaMemcpyAsync(h->host_err, h->wait_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                  h->stream));
       VPS_CK(h, cudaStreamSynchronize(h->stream));
+      if (read_waits) {
+        h->sweep_ran = false;
+        if (*h->host_err) {
+          VPS_CK(h, cudaMemset(h->wait_err, 0, sizeof(int)));
+          return fail(h, VPS_ETIMEOUT, "a dependency wait of a smoothing sweep reached its limit");
+        }
+      }
       rel = std::sqrt(h->host_sc->rr) / nb;
       if (rel_res) *rel_res = rel;
       if (!std::isfinite(rel))
@@ -1166,6 +1239,8 @@ size_t estimate_device_bytes(int dim, int degree, int level, int precision) {
   const double ni = (double)degree * std::ldexp(1.0, level) - 1.0;
   total += 7 * elems * 8 + 2 * (dim == 3 ? ni * ni * ni : ni * ni) * 8;
   if (precision == VPS_FP32) total += 2 * elems * 4;  // double-float split of p
+  for (int l = 1; l <= level; ++l)                     // flags of the dataflow sweep
+    total += std::pow(std::ldexp(1.0, l) - 1.0, dim) * 4;
   total += (double)(4 << 20);                         // tables, coarse-level data, scalars
   return total < 1.8e19 ? (size_t)total : SIZE_MAX;
 }
@@ -1618,7 +1693,7 @@ std::string tune_key(vps_context* h) {
 
 // Cache file: one JSON object, one entry per line:
 //   "d3_k4_fp32_mult_L5_pre1_post1": {"coarse": 3, "variants": [1, 1, 2, 0, 1],
-//                                     "ops": [0, 0, 1, 1, 0], "pdl": 1},
+//                                     "ops": [0, 0, 1, 1, 0], "schedule": 1},
 // (one line each).  Entries without every field are tuned again.
 bool parse_list(const char* p, const char* name, int* out, int nvar) {
   const char* v = std::strstr(p, name);
@@ -1635,7 +1710,7 @@ bool parse_list(const char* p, const char* name, int* out, int nvar) {
 }
 
 bool cache_lookup(const char* path, const std::string& key, int* coarse, int* var, int* ops,
-                  int* pdl, int nvar) {
+                  int* schedule, int nvar) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
   char line[2048];
@@ -1645,10 +1720,10 @@ bool cache_lookup(const char* path, const std::string& key, int* coarse, int* va
     const char* p = std::strstr(line, pat.c_str());
     if (!p) continue;
     const char* c = std::strstr(p, "\"coarse\":");
-    const char* d = std::strstr(p, "\"pdl\":");
+    const char* d = std::strstr(p, "\"schedule\":");
     if (!c || !d) continue;
     *coarse = std::atoi(c + 9);
-    *pdl = std::atoi(d + 6);
+    *schedule = std::atoi(d + 11);
     found = parse_list(p, "\"variants\": [", var, nvar) && parse_list(p, "\"ops\": [", ops, nvar);
   }
   std::fclose(f);
@@ -1656,7 +1731,7 @@ bool cache_lookup(const char* path, const std::string& key, int* coarse, int* va
 }
 
 void cache_store(const char* path, const std::string& key, int coarse, const int* var,
-                 const int* ops, int pdl, int nvar) {
+                 const int* ops, int schedule, int nvar) {
   std::vector<std::string> keep;
   if (FILE* f = std::fopen(path, "r")) {
     char line[2048];
@@ -1674,7 +1749,7 @@ void cache_store(const char* path, const std::string& key, int coarse, const int
   for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(var[i]);
   entry += "], \"ops\": [";
   for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(ops[i]);
-  entry += "], \"pdl\": " + std::to_string(pdl) + "}";
+  entry += "], \"schedule\": " + std::to_string(schedule) + "}";
   keep.push_back(entry);
   if (FILE* f = std::fopen(path, "w")) {
     std::fputs("{\n", f);
@@ -1799,6 +1874,19 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     if ((rc = dalloc(h, &h->bv[l], vb)) || (rc = dalloc(h, &h->xv[l], vb)) ||
         (rc = dalloc(h, &h->rv[l], vb)))
       return bail(rc);
+    // one flag per vertex patch of the level for the dataflow sweep
+    const int64_t nv = h->geom[l].ncell - 1;
+    void* fl = nullptr;
+    if ((rc = dalloc(h, &fl, (size_t)(dim == 3 ? nv * nv * nv : nv * nv) * sizeof(unsigned))))
+      return bail(rc);
+    h->sweep_flags[l] = static_cast<unsigned int*>(fl);
+  }
+  {
+    void* q = nullptr;
+    if ((rc = dalloc(h, &q, (kMaxLevels + 1) * sizeof(SweepCounters)))) return bail(rc);
+    h->sweep_ctr = static_cast<SweepCounters*>(q);
+    if ((rc = dalloc(h, &q, sizeof(int)))) return bail(rc);
+    h->wait_err = static_cast<int*>(q);
   }
   // 1/(lambda_i + lambda_j [+ lambda_l]) in reference units
   {
@@ -1854,6 +1942,9 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
   e = cudaMallocHost(&p, 8 * sizeof(double));
   if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
   h->host_dots = (double*)p;
+  e = cudaMallocHost(&p, sizeof(int));
+  if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return bail(VPS_ENOMEM); }
+  h->host_err = (int*)p;
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->err = std::string("create: ") + cudaGetErrorString(e);
@@ -1873,6 +1964,7 @@ int vps_destroy(vps_handle h) {
   if (h->gm_host) cudaFreeHost(h->gm_host);
   if (h->host_sc) cudaFreeHost(h->host_sc);
   if (h->host_dots) cudaFreeHost(h->host_dots);
+  if (h->host_err) cudaFreeHost(h->host_err);
   if (h->host_x) cudaFreeHost(h->host_x);
   if (h->as_ev) cudaEventDestroy(h->as_ev);
   if (h->rhs_buf) cudaFree(h->rhs_buf);
@@ -2053,7 +2145,7 @@ int vps_gmres(vps_handle h, const double* b, double* x, double rtol, int restart
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (rc) return rc;
   if (e != cudaSuccess) return fail(h, VPS_ECUDA, "unpack: %s", cudaGetErrorString(e));
-  return VPS_OK;
+  return check_waits(h);
 }
 
 int vps_solve_host(vps_handle h, const double* b_host, double* x_host, double rtol, int max_it,
@@ -2099,6 +2191,7 @@ int vps_fmg(vps_handle h, int n_modes, const double* coef, const int* freq, doub
   cudaError_t e = launch_unpack<double>(g, h->cx, x, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess && rc == VPS_OK) return fail(h, VPS_ECUDA, "fmg: %s", cudaGetErrorString(e));
+  if (rc == VPS_OK) rc = check_waits(h);
   return rc;
 }
 
@@ -2159,12 +2252,13 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
   const std::string key = tune_key(h);
   int var[kMaxLevels + 1] = {};
   int ops[kMaxLevels + 1] = {};
-  int coarse = 0, pdl = 1;
+  int coarse = 0, schedule = VPS_SCHEDULE_PDL;
   if (from_cache) *from_cache = 0;
   const bool has_alt = h->prec == VPS_FP64 ? h->ks->d.apply_alt != nullptr
                                            : h->ks->f.apply_alt != nullptr;
-  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, ops + 1, &pdl, h->L)) {
-    bool ok = coarse >= 1 && coarse <= h->L && (pdl == 0 || pdl == 1);
+  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, ops + 1, &schedule, h->L)) {
+    bool ok = coarse >= 1 && coarse <= h->L && schedule >= VPS_SCHEDULE_PLAIN &&
+              schedule <= VPS_SCHEDULE_SWEEP;
     for (int l = 1; l <= h->L; ++l)
       ok = ok && variant_ok(h, var[l]) && (ops[l] == 0 || (ops[l] == 1 && has_alt));
     if (ok) {
@@ -2172,7 +2266,7 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
         h->smooth_var[l] = var[l];
         h->op_var[l] = ops[l];
       }
-      h->pdl = pdl != 0;
+      h->schedule = schedule;
       if (coarse != h->coarse)
         if (int rc = setup_coarse(h, coarse)) return rc;
       drop_graphs(h);
@@ -2180,26 +2274,55 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
       return VPS_OK;
     }
   }
-  // 1) smoother variant per level: fastest smoothing step on the level's buffers
-  for (int l = 2; l <= h->L; ++l) {
-    float best = 1e30f;
-    int bestv = h->smooth_var[l];
-    for (int v = 0; v < kSmoothVariants; ++v) {
-      if (!variant_ok(h, v)) continue;
-      h->smooth_var[l] = v;
-      float ms = 0.f;
-      int rc = h->prec == VPS_FP64
-                   ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
-                                                                    (double*)h->xv[l], true); }, &ms)
-                   : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
-                                                                   (float*)h->xv[l], true); }, &ms);
-      if (rc) return rc;
-      if (ms < best * 0.98f) {  // prefer the earlier (smaller) variant on near ties
-        best = ms;
-        bestv = v;
+  // 1) smoother variant per level and colour schedule: for each schedule
+  //    (multiplicative smoother: programmatic dependent launches, the
+  //    dataflow sweep, ordinary launches; additive: the handle's), the
+  //    fastest smoothing step of every level on the level's buffers; the
+  //    schedule whose levels' fastest steps add up to the least time wins
+  {
+    const bool mult = h->smoother == VPS_MULTIPLICATIVE;
+    const int scheds[3] = {VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP, VPS_SCHEDULE_PLAIN};
+    const int nsched = mult ? 3 : 1;
+    float best_total = 1e30f;
+    int best_sched = h->schedule;
+    int best_var[kMaxLevels + 1] = {};
+    for (int l = 1; l <= h->L; ++l) best_var[l] = h->smooth_var[l];
+    for (int si = 0; si < nsched; ++si) {
+      if (mult) h->schedule = scheds[si];
+      float total = 0.f;
+      int var_s[kMaxLevels + 1] = {};
+      for (int l = 1; l <= h->L; ++l) var_s[l] = h->smooth_var[l];
+      for (int l = 2; l <= h->L; ++l) {
+        float best = 1e30f;
+        int bestv = h->smooth_var[l];
+        for (int v = 0; v < kSmoothVariants; ++v) {
+          if (!variant_ok(h, v)) continue;
+          h->smooth_var[l] = v;
+          float ms = 0.f;
+          int rc = h->prec == VPS_FP64
+                       ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
+                                                                        (double*)h->xv[l], true); }, &ms)
+                       : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
+                                                                       (float*)h->xv[l], true); }, &ms);
+          if (rc) return rc;
+          if (ms < best * 0.98f) {  // prefer the earlier (smaller) variant on near ties
+            best = ms;
+            bestv = v;
+          }
+        }
+        var_s[l] = bestv;
+        h->smooth_var[l] = bestv;
+        total += best;
+      }
+      if (total < best_total * 0.99f) {  // prefer the earlier schedule on near ties
+        best_total = total;
+        best_sched = h->schedule;
+        for (int l = 1; l <= h->L; ++l) best_var[l] = var_s[l];
       }
     }
-    h->smooth_var[l] = bestv;
+    if (int rc = check_waits(h)) return rc;
+    h->schedule = best_sched;
+    for (int l = 1; l <= h->L; ++l) h->smooth_var[l] = best_var[l];
   }
   // 2) operator tile structure per level where two exist: the faster
   //    residual b - A x on the level's buffers
@@ -2228,24 +2351,7 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     }
     h->op_var[l] = bestv;
   }
-  // 3) colour schedule: the passes of a smoothing step on the finest level as
-  //    programmatic dependent launches (the next pass is scheduled while the
-  //    previous one drains) or as ordinary launches
-  if (h->smoother == VPS_MULTIPLICATIVE && h->L >= 2) {
-    float t[2] = {0.f, 0.f};
-    for (int on = 0; on < 2; ++on) {
-      h->pdl = on != 0;
-      const int l = h->L;
-      int rc = h->prec == VPS_FP64
-                   ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
-                                                                    (double*)h->xv[l], true); }, &t[on])
-                   : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
-                                                                   (float*)h->xv[l], true); }, &t[on]);
-      if (rc) return rc;
-    }
-    h->pdl = t[1] <= t[0] * 1.02f;  // programmatic launches on near ties
-  }
-  // 4) coarsest level: fastest full CG solve of a smooth right-hand side
+  // 3) coarsest level: fastest full CG solve of a smooth right-hand side
   {
     const LevelGeom& g = h->geom[h->L];
     const int ni = g.n1 - 2;
@@ -2284,7 +2390,7 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
       var[l] = h->smooth_var[l];
       ops[l] = h->op_var[l];
     }
-    cache_store(cache_path, key, h->coarse, var + 1, ops + 1, h->pdl ? 1 : 0, h->L);
+    cache_store(cache_path, key, h->coarse, var + 1, ops + 1, h->schedule, h->L);
   }
   drop_graphs(h);
   return VPS_OK;
@@ -2312,16 +2418,35 @@ int vps_get_operator_variant(vps_handle h, int level, int* variant, int* n_varia
   return VPS_OK;
 }
 
-int vps_set_colour_pdl(vps_handle h, int enable) {
+int vps_set_colour_schedule(vps_handle h, int schedule) {
   if (!h) return VPS_EINVAL;
-  h->pdl = enable != 0;
+  if (schedule < VPS_SCHEDULE_PLAIN || schedule > VPS_SCHEDULE_SWEEP)
+    return fail(h, VPS_EINVAL, "colour schedule %d unknown", schedule);
+  h->schedule = schedule;
   drop_graphs(h);
   return VPS_OK;
 }
 
-int vps_get_colour_pdl(vps_handle h, int* enable) {
-  if (!h || !enable) return VPS_EINVAL;
-  *enable = h->pdl ? 1 : 0;
+int vps_get_colour_schedule(vps_handle h, int* schedule) {
+  if (!h || !schedule) return VPS_EINVAL;
+  *schedule = h->schedule;
+  return VPS_OK;
+}
+
+int vps_check_waits(vps_handle h) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = set_device(h)) return rc;
+  return check_waits(h);
+}
+
+int vps_skip_sweep_tiles(vps_handle h, int level, int64_t tiles) {
+  if (!h) return VPS_EINVAL;
+  if (int rc = check_level(h, level, 1)) return rc;
+  if (tiles < 0) return fail(h, VPS_EINVAL, "tiles < 0");
+  if (int rc = set_device(h)) return rc;
+  const unsigned long long head = (unsigned long long)tiles;
+  VPS_CK(h, cudaStreamSynchronize(h->stream));
+  VPS_CK(h, cudaMemcpy(&h->sweep_ctr[level].head, &head, sizeof(head), cudaMemcpyHostToDevice));
   return VPS_OK;
 }
 

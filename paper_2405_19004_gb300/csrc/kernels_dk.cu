@@ -241,6 +241,10 @@ __device__ __forceinline__ void async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
+struct NoWait {
+  __device__ void operator()() const {}
+};
+
 // ------------------------------------------------- even/odd contractions
 // Coefficients of the halves of Mp (MAT 0) and Ap (MAT 1).
 template <typename T, int MAT>
@@ -583,11 +587,20 @@ __device__ __forceinline__ int boundary_first_line(int L, bool* full) {
 // The body processes tile `tile` of the colour (patches tile*P .. tile*P+P-1);
 // smooth_mult_kernel runs tile blockIdx.x, smooth_mult_batch_kernel the
 // tiles it takes from a queue of several levels' colour passes.
-template <typename T, int QQ, bool BND, int W, bool RES = false>
+//
+// SW = true (the dataflow sweep): x changes under the kernel (other blocks
+// update it).  `wait`, the tile's dependency wait, runs first; its acquire
+// loads and the barrier after the prologue order every thread's loads of x
+// after the release of the patches it waited for, so they observe those
+// updates (the memory model's acquire, which also covers data the SM's L1
+// cached earlier).
+template <typename T, int QQ, bool BND, int W, bool RES = false, bool SW = false,
+          class WaitF = NoWait>
 __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __restrict__ x,
                                                  const T* __restrict__ inv_lam, int px, int pz,
                                                  const ColourGeom& cg, T bscale,
-                                                 T* __restrict__ rout, int64_t tile) {
+                                                 T* __restrict__ rout, int64_t tile,
+                                                 const WaitF& wait = WaitF()) {
   static_assert(!(RES && BND), "the residual-only kernel reads the whole closure");
   using C = SmoothCfg<T, QQ, W>;
   constexpr int G = C::G, Q = C::Q, P = C::P, NT = C::NT, MD = C::md;
@@ -604,6 +617,7 @@ __device__ __forceinline__ void smooth_mult_body(const T* __restrict__ b, T* __r
   T* xI = BND ? nullptr : bI + P * MD;
   T* il = bI + (BND ? 1 : 2) * P * MD;
   int* s_org = reinterpret_cast<int*>(il + MD);
+  if constexpr (SW) wait();
   // the origins and the eigenvalue table (written at setup) do not depend
   // on the previous kernel: read them before waiting for it to complete
   load_origins<P, NT>(s_org, cg, px, pz, tile);
@@ -1077,6 +1091,122 @@ smooth_mult_batch_kernel(BatchQueue* __restrict__ q, const T* __restrict__ inv_l
                                            inv_lam, (int)I.pxa, (int)I.pza, I.cg, (T)I.bscale,
                                            nullptr, t - I.tile0);
     __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
+// ------------------------------------------------------- dataflow sweep
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// The dependency wait of a tile of the sweep: until every patch of an
+// earlier colour that overlaps a patch of the tile is done (its flag holds
+// this sweep's epoch ep).  Two vertex patches overlap -- the interior of one
+// meets the closure of the other -- exactly when their vertices differ by
+// at most one in every direction, so each patch checks its 3^d - 1
+// neighbouring vertices (one thread per neighbour).  A wait polls at most
+// spin_limit times; on expiry it sets *err and returns (the step's values
+// are then undefined, its memory accesses are not), and once *err is set
+// every later wait returns at once.
+template <int P, int NT>
+__device__ __forceinline__ void sweep_wait(const SweepGeom& sg, int pos, int64_t tile,
+                                           unsigned ep) {
+  constexpr int NNB = DIM == 3 ? 26 : 8;
+  const ColourGeom& cg = sg.cg[pos];
+  for (int u = threadIdx.x; u < P * NNB; u += NT) {
+    const int64_t gp = tile * P + u / NNB;
+    if (gp >= cg.npatch) continue;
+    int code = u % NNB;
+    code += code >= NNB / 2 ? 1 : 0;  // offsets in {-1,0,1}^d without the centre
+    int iv[3];
+    iv[0] = (int)(gp % cg.cnt[0]);
+    const int r = (int)(gp / cg.cnt[0]);
+    iv[1] = r % cg.cnt[1];
+    iv[2] = r / cg.cnt[1];
+    int w[3], cn = 0;
+    bool inside = true;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      const int d = (t == 0 ? code : t == 1 ? code / 3 : code / 9) % 3 - 1;
+      w[t] = cg.par[t] + 2 * iv[t] + 1 + d;  // vertex of the neighbour
+      inside = inside && w[t] >= 1 && w[t] <= sg.ncell - 1;
+      cn |= ((w[t] - 1) & 1) << t;
+    }
+    if (!inside) continue;
+    const int pn = sg.pos_of[cn];
+    if (pn >= pos) continue;  // a later colour of the sweep
+    const ColourGeom& cc = sg.cg[pn];
+    int64_t gq = 0;
+#pragma unroll
+    for (int t = DIM - 1; t >= 0; --t) gq = gq * cc.cnt[t] + (w[t] - 1 - cc.par[t]) / 2;
+    const unsigned* f = sg.flags + sg.flag_off[cn] + gq;
+    unsigned polls = 0;
+    while (ld_acquire(f) != ep) {
+      if ((polls & 31u) == 31u && *reinterpret_cast<volatile const int*>(sg.err)) break;
+      if (++polls >= sg.spin_limit) {
+        atomicOr(sg.err, 1);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+}
+
+// A multiplicative smoothing step of one level in one launch of one block
+// per tile: each block takes the next tile of the sweep (one atomic
+// increment, so tiles are taken in the order blocks start), waits for the
+// tile's dependencies, runs the colour-pass body on it and marks its patches
+// done.  A block waits only for tiles taken before its own, each by a block
+// that is running or has finished, so the waits end.  (One block per tile
+// rather than a loop over tiles in resident blocks: the loop kept values
+// live across tiles and needed twice the registers.)  The last block to
+// finish resets the counters for the next sweep and advances the epoch.
+template <typename T, int QQ, bool BND>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ, 0>::NT)
+smooth_sweep_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
+                    int px, int pz, const __grid_constant__ SweepGeom sg, T bscale) {
+  using C = SmoothCfg<T, QQ, 0>;
+  constexpr int P = C::P, NT = C::NT;
+  __shared__ int64_t s_tile;
+  __shared__ unsigned s_ep;
+  grid_dependency_wait();  // the counters and x are written by earlier kernels
+  if (threadIdx.x == 0) {
+    s_ep = *reinterpret_cast<volatile const unsigned*>(&sg.ctr->epoch) + 1u;
+    s_tile = (int64_t)atomicAdd(&sg.ctr->head, 1ull);
+  }
+  __syncthreads();
+  const int64_t t = s_tile;
+  const unsigned ep = s_ep;
+  if (t < sg.tile_end[sg.ncol - 1]) {
+    int pos = 0;
+    while (t >= sg.tile_end[pos]) ++pos;
+    const int64_t tile = t - (pos > 0 ? sg.tile_end[pos - 1] : 0);
+    const ColourGeom& cg = sg.cg[pos];
+    smooth_mult_body<T, QQ, BND, 0, false, true>(
+        b, x, inv_lam, px, pz, cg, bscale, nullptr, tile,
+        [&] { sweep_wait<P, NT>(sg, pos, tile, ep); });
+    __syncthreads();  // every store of the tile is issued
+    if (threadIdx.x < P) {
+      const int64_t gp = tile * P + threadIdx.x;
+      if (gp < cg.npatch) {
+        __threadfence();
+        st_release(sg.flags + sg.flag_off[sg.colour[pos]] + gp, ep);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&sg.ctr->done, 1u) == gridDim.x - 1) {
+      sg.ctr->head = 0ull;
+      sg.ctr->done = 0u;
+      __threadfence();
+      *reinterpret_cast<volatile unsigned*>(&sg.ctr->epoch) = ep;
+    }
   }
 }
 
@@ -2217,6 +2347,23 @@ cudaError_t smooth_mult_batch_launch(BatchQueue* q, int64_t ntiles, const T* inv
   return cudaGetLastError();
 }
 
+// A smoothing step as one dataflow sweep (smooth_sweep_kernel, one block per
+// tile of every colour), launched as a programmatic dependent launch (the
+// kernel waits for the previous one before it reads the counters or x).
+template <typename T, int PP, bool BND>
+cudaError_t smooth_sweep_launch(const LevelGeom& g, const SweepGeom& sg, const T* b, T* x,
+                                const T* inv_lam, cudaStream_t s) {
+  using C = SmoothCfg<T, PP>;
+  const int64_t ntiles = sg.ncol > 0 ? sg.tile_end[sg.ncol - 1] : 0;
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const size_t smem = BND ? C::smem_bnd : C::smem_mult;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
+  return launch_pdl(smooth_sweep_kernel<T, PP, BND>, dim3((unsigned)ntiles), dim3(C::NT), smem, s,
+                    b, x, inv_lam, (int)g.px, (int)g.pz, sg, bscale);
+}
+
 template <typename T>
 cudaError_t restrict_batch_launch(BatchQueue* q, int64_t ntiles, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
@@ -2472,6 +2619,8 @@ cudaError_t smooth_limits() {
     }
     e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, 0>, C::smem_bnd);
     if (e != cudaSuccess) return e;
+    e = smoother_smem(smooth_sweep_kernel<T, PP, true>, C::smem_bnd);
+    if (e != cudaSuccess) return e;
   }
   if constexpr (!C::fits) {
     return cudaSuccess;
@@ -2481,6 +2630,8 @@ cudaError_t smooth_limits() {
     e = smoother_smem(smooth_mult_kernel<T, PP, false, 0, true>, C::smem_mult);
     if (e != cudaSuccess) return e;
     e = smoother_smem(smooth_mult_batch_kernel<T, PP, false, 0>, C::smem_mult);
+    if (e != cudaSuccess) return e;
+    e = smoother_smem(smooth_sweep_kernel<T, PP, false>, C::smem_mult);
     if (e != cudaSuccess) return e;
     return smoother_smem(smooth_add_kernel<T, PP>, C::smem_add);
   }
@@ -2494,7 +2645,9 @@ void register_variant(KernelFns<T>* f, int v) {
   f->variant_p[v + 2 * kQVariants] = C::P;
   f->smooth_add_v[v + kQVariants] = nullptr;
   f->smooth_add_v[v + 2 * kQVariants] = nullptr;
+  f->smooth_sweep_v[v + 2 * kQVariants] = nullptr;
   if constexpr (C::fits_bnd) {
+    f->smooth_sweep_v[v + kQVariants] = smooth_sweep_launch<T, PP, true>;
     f->smooth_mult_v[v + kQVariants] = smooth_mult_launch<T, PP, true, 0>;
     f->smooth_mult_plain_v[v + kQVariants] = smooth_mult_plain_launch<T, PP, true, 0>;
     f->smooth_mult_batch_v[v + kQVariants] = smooth_mult_batch_launch<T, PP, true, 0>;
@@ -2508,6 +2661,7 @@ void register_variant(KernelFns<T>* f, int v) {
       f->smooth_mult_batch_v[v + 2 * kQVariants] = nullptr;
     }
   } else {
+    f->smooth_sweep_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + kQVariants] = nullptr;
     f->smooth_mult_v[v + 2 * kQVariants] = nullptr;
     f->smooth_mult_plain_v[v + kQVariants] = nullptr;
@@ -2518,11 +2672,13 @@ void register_variant(KernelFns<T>* f, int v) {
   if constexpr (C::fits) f->resid_v[v] = resid_launch<T, PP>;
   else f->resid_v[v] = nullptr;
   if constexpr (C::fits) {
+    f->smooth_sweep_v[v] = smooth_sweep_launch<T, PP, false>;
     f->smooth_mult_v[v] = smooth_mult_launch<T, PP, false, 0>;
     f->smooth_mult_plain_v[v] = smooth_mult_plain_launch<T, PP, false, 0>;
     f->smooth_mult_batch_v[v] = smooth_mult_batch_launch<T, PP, false, 0>;
     f->smooth_add_v[v] = smooth_add_launch<T, PP>;
   } else {
+    f->smooth_sweep_v[v] = nullptr;
     f->smooth_mult_v[v] = nullptr;
     f->smooth_mult_plain_v[v] = nullptr;
     f->smooth_mult_batch_v[v] = nullptr;

@@ -153,6 +153,34 @@ struct BatchQueue {
   BatchItem items[kMaxBatch];
 };
 
+// Dataflow schedule of a multiplicative smoothing step: one persistent
+// kernel runs every colour.  Blocks claim tiles in the order of the sweep
+// (all tiles of the first colour, then of the second, ...), and a tile
+// starts once every patch of an earlier colour that overlaps one of its
+// patches is done; the result equals the colour-by-colour passes bit for
+// bit.  Per level, in device memory, zero-initialised:
+struct SweepCounters {
+  unsigned long long head;      // next tile of the running sweep (0 between sweeps)
+  unsigned int done;            // blocks of the running sweep that have finished
+  unsigned int epoch;           // sweeps completed on the level
+};
+// flags: one per patch of the level, colour by colour (colour c from
+// flag_off[c], in the colour's patch order); a patch's flag holds the epoch
+// of the sweep that finished it last.
+struct SweepGeom {
+  ColourGeom cg[8];             // colour geometry by position in the sweep order
+  int colour[8] = {};           // colour at each position
+  int pos_of[8] = {};           // position of each colour
+  int64_t flag_off[8] = {};     // first flag of each colour
+  int64_t tile_end[8] = {};     // tiles of positions 0..s together
+  int ncol = 0;                 // 2^dim
+  int ncell = 0;                // cells per direction
+  unsigned int* flags = nullptr;
+  SweepCounters* ctr = nullptr;
+  int* err = nullptr;           // set to 1 by a wait that reached its poll limit
+  unsigned int spin_limit = 0;  // polls of one flag before the wait gives up
+};
+
 // Smoother kernel variants the autotuner chooses from: v = 3 * kind + q,
 // q = 0, 1, 2 the block shape (q = 0: G1 patch groups of 1 patch per thread,
 // q = 1: G1 groups of 2, q = 2: G2 groups of 1, with G1 and G2 per (dim,
@@ -190,6 +218,11 @@ struct KernelFns {
   cudaError_t (*apply_alt)(const LevelGeom&, const T* x, const T* b, T* y, cudaStream_t) = nullptr;
   // colour passes launched without programmatic dependent launch
   SmoothMultFn smooth_mult_plain_v[kSmoothVariants] = {};
+  // a whole multiplicative smoothing step (every colour, in the order of
+  // the SweepGeom) as one persistent dataflow kernel; null for the
+  // one-warp variants
+  cudaError_t (*smooth_sweep_v[kSmoothVariants])(const LevelGeom&, const SweepGeom&, const T* b,
+                                                 T* x, const T* inv_lam, cudaStream_t) = {};
   // batched persistent launches over a device-side queue (q: device copy,
   // ntiles: its tile count, known on the host): multiplicative colour
   // passes (variant v), restrictions, prolongations, and the zeroing of the

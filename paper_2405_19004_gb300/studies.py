@@ -143,12 +143,15 @@ def level_for(d, k, target):
 
 
 def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cache=None,
-                   seed=None):
+                   seed=None, schedule=None):
     """Times `apps` multiplicative smoothing steps of Q_k on level L (after two
-    warm-up steps) and returns the measurement row."""
+    warm-up steps) and returns the measurement row; `schedule` pins the
+    colour schedule (default: the handle's, autotuned with `tune`)."""
     P = vps.Poisson(d, k, L, precision=prec)
     if tune:
         P.vps_autotune(tune_cache)
+    if schedule is not None:
+        P.vps_set_colour_schedule(schedule)
     N = P.n_interior()
     gen = torch.Generator(device="cuda").manual_seed(2 + k if seed is None else seed)
     b = P.empty_level()
@@ -163,6 +166,7 @@ def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cach
     P.vps_smooth(L, b, x, apps)
     e1.record(P.stream)
     torch.cuda.synchronize()
+    P.vps_check_waits()
     t = e0.elapsed_time(e1) / 1e3 / apps
     patches = (2 ** L - 1) ** d
     var, ppb = P.vps_get_smooth_variant(L)
@@ -182,7 +186,8 @@ def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cach
            "frac_of_measured_fma_peak": flops / t / measured,
            "frac_of_measured_fma_peak_executed": executed / t / measured,
            "frac_smem_roofline": flops / t / roof_smem, "smem_roofline_tflops": roof_smem / 1e12,
-           "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb}
+           "kernel": "boundary" if bnd else "fused", "patches_per_block": ppb,
+           "colour_schedule": P.vps_get_colour_schedule()}
     if derived:
         row["frac_of_fp32_peak"] = flops / t / derived
     P.close()

@@ -272,7 +272,7 @@ def test_autotune_caches_and_keeps_parity(tmp_path):
     def choice(H):
         return ([H.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
                 [H.vps_get_operator_variant(l)[0] for l in range(1, L + 1)],
-                H.vps_get_colour_pdl(), H.vps_get_coarse_level())
+                H.vps_get_colour_schedule(), H.vps_get_coarse_level())
     chosen = choice(P)
     assert [P.vps_get_operator_variant(l)[1] for l in range(1, L + 1)] == [2] * L  # 3D FP32 k <= 4
     Q = _poisson(d, k, L, 1)
@@ -282,7 +282,7 @@ def test_autotune_caches_and_keeps_parity(tmp_path):
     entry = json.load(open(cache))
     assert len(entry) == 1
     (rec,) = entry.values()
-    assert {"coarse", "variants", "ops", "pdl"} <= set(rec)
+    assert {"coarse", "variants", "ops", "schedule"} <= set(rec)
     H = multigrid.Hierarchy(d, k, L, coarse_level=Q.vps_get_coarse_level())
     b = uniform_vector(H.levels[L].N, 33)
     bt = torch.as_tensor(b, device="cuda")
@@ -293,16 +293,17 @@ def test_autotune_caches_and_keeps_parity(tmp_path):
     assert rel_err(xt.cpu().numpy(), xo) <= 1e-8
 
 
-@pytest.mark.parametrize("op,pdl", [(1, 1), (0, 0), (1, 0)])
-def test_operator_structure_and_colour_schedule_keep_parity(op, pdl):
+@pytest.mark.parametrize("op,schedule", [(1, 1), (0, 0), (1, 0), (1, 2), (0, 2)])
+def test_operator_structure_and_colour_schedule_keep_parity(op, schedule):
     """Every tuning choice computes the same V-cycle: the alternative operator
-    tile structure on every level and ordinary launches of the colour passes
-    against the oracle's V-cycle."""
+    tile structure on every level and each colour schedule (ordinary,
+    programmatic dependent launches, the dataflow sweep) against the
+    oracle's V-cycle."""
     d, k, L = 3, 3, 4
     P = _poisson(d, k, L, 1)
     for l in range(2, L + 1):
         P.vps_set_operator_variant(l, op)
-    P.vps_set_colour_pdl(pdl)
+    P.vps_set_colour_schedule(schedule)
     H = multigrid.Hierarchy(d, k, L, coarse_level=P.vps_get_coarse_level())
     b = as_prec(uniform_vector(H.levels[L].N, 34), 1)
     x = P.empty_level(L)
