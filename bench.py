@@ -337,6 +337,7 @@ def main():
 
     import paper_2405_19004_gb300 as vps
     from paper_2405_19004_gb300.studies import (device_peaks, fp32_peak, mixed_precision_solve,
+                                                paper_flops_per_patch,
                                                 smem_bandwidth, smoother_flops_executed_per_patch,
                                                 smoother_flops_per_patch, smoother_point,
                                                 smoother_smem_words_per_patch)
@@ -358,6 +359,10 @@ def main():
     if args.no_graphs:
         P.vps_set_graphs(False)
     tuned = {"coarse_level": P.vps_get_coarse_level(),
+             "coarse_solver": (("one cooperative launch" if P.vps_get_coarse_solver() &
+                                vps.VPS_COARSE_COOPERATIVE else "one launch per pass") +
+                               (", 64-output tiles" if P.vps_get_coarse_solver() &
+                                vps.VPS_COARSE_WIDE_TILES else ", 32-output tiles")),
              "smoother_variants": [P.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
              "patches_per_block": [P.vps_get_smooth_variant(l)[1] for l in range(1, L + 1)],
              "finest_variant_pinned": args.smoother_variant is not None,
@@ -468,7 +473,11 @@ def main():
     n_patches = (2 ** L - 1) ** 3
     var_L = P.vps_get_smooth_variant(L)[0]
     bnd_L = var_L // 3 >= 1
-    flops_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / per_run
+    # algorithmic work per launch: the method's plain sum-factorisation count
+    # per patch x the patches of the launch (the kernels' own dense and
+    # executed counts are reported beside it)
+    flops_per_launch = paper_flops_per_patch(D, K) * n_patches / per_run
+    dense_per_launch = smoother_flops_per_patch(D, K, bnd_L) * n_patches / per_run
     # FP32 peak from the unit counts and the device's maximum SM clock; the
     # shared-memory roofline of Section 4.3 at the SM clock sampled under load
     fp32_peak_tflops = fp32_peak(peaks["sm_count"], peaks["sm_max_mhz"]) / 1e12
@@ -477,6 +486,7 @@ def main():
     smem_roof_tflops = smem_bandwidth(peaks["sm_count"], smem_mhz) * smoother_flops_per_patch(
         D, K, bnd_L) / (4.0 * smem_words) / 1e12
     achieved = flops_per_launch / t_launch / 1e12
+    achieved_dense = dense_per_launch / t_launch / 1e12
     executed_per_launch = smoother_flops_executed_per_patch(D, K, bnd_L) * n_patches / per_run
     t_smooth_step = per_run * t_launch
 
@@ -671,10 +681,15 @@ def main():
                           "frac_of_fp32_peak": achieved / fp32_peak_tflops,
                           "frac_of_measured_fma_peak":
                               achieved / (peaks["fp32_fma_measured_flops"] / 1e12),
+                          # the kernel's own dense count (the inner mass contraction
+                          # shared by two terms, Section 3.1.1)
+                          "tflops_kernel_dense_count": achieved_dense,
+                          "frac_of_fp32_peak_kernel_dense_count": achieved_dense / fp32_peak_tflops,
                           # shared-memory roofline R = B F / (d_r + d_w) (Section 4.3),
                           # B = SMs x 32 banks x 4 B x the SM clock sampled under load,
-                          # d_r + d_w = the kernel's modelled shared-memory words per patch
-                          "frac_of_smem_roofline": achieved / smem_roof_tflops,
+                          # F and d_r + d_w = the kernel's dense flops and modelled
+                          # shared-memory words per patch
+                          "frac_of_smem_roofline": achieved_dense / smem_roof_tflops,
                           "smem_roofline_tflops": smem_roof_tflops,
                           "smem_roofline_clock_mhz": smem_mhz,
                           "smem_words_per_patch_model": smem_words},
@@ -690,6 +705,12 @@ def main():
                                     f"flop x {peaks['sm_max_mhz']:g} MHz ({peaks['sm_max_mhz_source']})"
                                     "; measured FMA throughput in peaks.fp32_fma_measured_flops",
                      "avg_launch_us": 1e6 * t_launch, "flops_per_launch": flops_per_launch,
+                     "flops_count": "sum-factorisation count of the patch update, "
+                                    f"{paper_flops_per_patch(D, K)} flop per patch x "
+                                    f"{n_patches / per_run:g} "
+                                    "patches per launch",
+                     "kernel_dense_flops_per_launch": dense_per_launch,
+                     "frac_kernel_dense_count": achieved_dense / fp32_peak_tflops,
                      "executed_flops_per_launch": executed_per_launch,
                      "frac_executed": executed_per_launch / t_launch / 1e12 / fp32_peak_tflops},
         "e2e": {"value": job_throughput(N, t_e2e, world), "unit": "DoF/s", "h2d_bytes_per_step": 8 * N,

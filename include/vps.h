@@ -253,6 +253,30 @@ int vps_set_coarse_level(vps_handle h, int level);
 int vps_get_coarse_level(vps_handle h, int* level);
 
 /*
+ * vps_set_coarse_solver / vps_get_coarse_solver -- how the exact coarse
+ * solve (the 2d passes of the global fast diagonalisation: S^T along each
+ * direction, the last of them scaled by 1/(sum of eigenvalues), then S along
+ * each) is launched; solver is a combination of
+ *   VPS_COARSE_COOPERATIVE: one cooperative launch, every block resident,
+ *     with a grid barrier between the passes (without: one kernel per pass,
+ *     VPS_COARSE_PASSES).  Each barrier wait polls a bounded number of times
+ *     (about a second at the least); an expiry is reported like a sweep's
+ *     (VPS_ETIMEOUT, see vps_set_colour_schedule);
+ *   VPS_COARSE_WIDE_TILES: thread blocks of 16 lines x 64 outputs (4 outputs
+ *     per thread) instead of 16 x 32 (2 per thread, twice the blocks).
+ * Every output is the same dot product in the same order in every form
+ * (bit-identical results); chosen per coarse level by vps_autotune, the
+ * default is VPS_COARSE_COOPERATIVE where the device supports cooperative
+ * launches.  Errors: VPS_EINVAL (unknown value, or cooperative launches
+ * unsupported).
+ */
+#define VPS_COARSE_PASSES      0
+#define VPS_COARSE_COOPERATIVE 1
+#define VPS_COARSE_WIDE_TILES  2
+int vps_set_coarse_solver(vps_handle h, int solver);
+int vps_get_coarse_solver(vps_handle h, int* solver);
+
+/*
  * vps_autotune -- choose, by timed trials on this handle's own buffers, the
  * smoother variant of every level (patches per thread block, the tuning
  * axis of Section 3.1.2) together with the colour schedule
@@ -260,7 +284,8 @@ int vps_get_coarse_level(vps_handle h, int* level);
  * level, and the schedule whose fastest steps add up to the least time),
  * the operator tile structure of every level (vps_set_operator_variant),
  * and the coarsest level (vps_set_coarse_level) that gives the fastest CG
- * solve.  cache_path (may be NULL): a JSON file keyed by
+ * solve, each candidate with its faster coarse solver form
+ * (vps_set_coarse_solver).  cache_path (may be NULL): a JSON file keyed by
  * (dim, degree, precision, smoother, level, smoothing steps) with the
  * smoother variant and operator tile structure of every level, the colour
  * schedule and the coarsest level; an entry found
@@ -326,8 +351,9 @@ int vps_set_colour_schedule(vps_handle h, int schedule);
 int vps_get_colour_schedule(vps_handle h, int* schedule);
 
 /* vps_check_waits -- synchronises the handle's stream; VPS_ETIMEOUT if a
- * dependency wait of a VPS_SCHEDULE_SWEEP smoothing step of this handle
- * expired since the last check (the record is then cleared), else VPS_OK. */
+ * dependency wait of a VPS_SCHEDULE_SWEEP smoothing step or a grid barrier
+ * of a VPS_COARSE_COOPERATIVE coarse solve of this handle expired since the
+ * last check (the record is then cleared), else VPS_OK. */
 int vps_check_waits(vps_handle h);
 
 /* vps_skip_sweep_tiles -- fault injection for tests: the next dataflow

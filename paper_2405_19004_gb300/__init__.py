@@ -32,6 +32,7 @@ VPS_KERNEL_FUSED, VPS_KERNEL_SEPARATE, VPS_KERNEL_GLOBAL, VPS_KERNEL_GLOBAL_INVE
 VPS_OUTER_FP64 = 0
 VPS_OUTER_DOUBLE_FLOAT = 1
 VPS_SCHEDULE_PLAIN, VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP = 0, 1, 2
+VPS_COARSE_PASSES, VPS_COARSE_COOPERATIVE, VPS_COARSE_WIDE_TILES = 0, 1, 2
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
 
 # C signatures: name -> (restype, argtypes)
@@ -72,6 +73,8 @@ SIGNATURES = {
     "vps_set_colour_schedule": (_i, [_p, _i]),
     "vps_get_colour_schedule": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_check_waits": (_i, [_p]),
+    "vps_set_coarse_solver": (_i, [_p, _i]),
+    "vps_get_coarse_solver": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_skip_sweep_tiles": (_i, [_p, _i, ctypes.c_int64]),
     "vps_get_coarse_level": (_i, [_p, ctypes.POINTER(_i)]),
     "vps_smooth_additive_static": (_i, [_i, _i, _i, _i, _d, _p, _p, _p]),
@@ -348,6 +351,14 @@ class Poisson:
 
     def vps_check_waits(self):
         self._call(lib().vps_check_waits)
+
+    def vps_set_coarse_solver(self, solver):
+        self._call(lib().vps_set_coarse_solver, int(solver))
+
+    def vps_get_coarse_solver(self):
+        e = ctypes.c_int()
+        _check(lib().vps_get_coarse_solver(self.h, ctypes.byref(e)), self.h)
+        return e.value
 
     def vps_skip_sweep_tiles(self, level, tiles):
         self._call(lib().vps_skip_sweep_tiles, int(level), int(tiles))

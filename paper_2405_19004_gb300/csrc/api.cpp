@@ -153,7 +153,13 @@ struct vps_context {
   unsigned int* sweep_flags[kMaxLevels + 1] = {};
   SweepCounters* sweep_ctr = nullptr;   // kMaxLevels + 1
   int* wait_err = nullptr;
-  bool sweep_ran = false;
+  bool waits_ran = false;
+  // exact coarse solve as one cooperative launch (grid barriers between its
+  // passes; barrier words in gsync) or as one launch per pass
+  bool coarse_coop = false;
+  bool coarse_wide = false;             // tiles of 64 outputs instead of 32
+  bool coop_ok = false;                 // the device supports cooperative launches
+  unsigned int* gsync = nullptr;        // count, generation
   unsigned int spin_limit = 1u << 21;   // polls of one flag (at least 128 ns each)
   int* host_err = nullptr;              // pinned copy of *wait_err
   // kernel structure of the multiplicative smoother (Section 3.1's
@@ -355,7 +361,7 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
   } else if (h->schedule == VPS_SCHEDULE_SWEEP && h->kernel_kind == VPS_KERNEL_FUSED &&
              fns<T>(h).smooth_sweep_v[v]) {
     const SweepGeom sg = sweep_geom(h, l, forward, fns<T>(h).variant_p[v]);
-    h->sweep_ran = true;
+    h->waits_ran = true;
     VPS_CK(h, fns<T>(h).smooth_sweep_v[v](g, sg, b, x, il, h->stream));
   } else {
     for (int i = 0; i < nc; ++i) {
@@ -369,11 +375,11 @@ int smooth_step(vps_context* h, int l, const T* b, T* x, bool forward) {
 // VPS_ETIMEOUT if a wait of a dataflow sweep of this handle expired since
 // the last check (synchronises the stream), else VPS_OK; clears the record.
 int check_waits(vps_context* h) {
-  if (!h->sweep_ran || !h->wait_err) return VPS_OK;
+  if (!h->waits_ran || !h->wait_err) return VPS_OK;
   int err = 0;
   VPS_CK(h, cudaStreamSynchronize(h->stream));
   VPS_CK(h, cudaMemcpy(&err, h->wait_err, sizeof(int), cudaMemcpyDeviceToHost));
-  h->sweep_ran = false;
+  h->waits_ran = false;
   if (!err) return VPS_OK;
   VPS_CK(h, cudaMemset(h->wait_err, 0, sizeof(int)));
   return fail(h, VPS_ETIMEOUT, "a dependency wait of a smoothing sweep reached its limit");
@@ -386,24 +392,36 @@ int coarse_solve(vps_context* h, const T* b, T* x) {
   const LevelGeom& g = h->geom[h->coarse];
   const int ni = h->gni, d = h->dim, px = (int)g.px, pz = (int)g.pz;
   const T* S = static_cast<const T*>(h->gS);      // W of the S^T passes
-  const T* St = S + (size_t)ni * ni;               // W of the S passes
+  const T* St = S + (size_t)ni * fd_pad(ni);       // W of the S passes
   const T* inv = static_cast<const T*>(h->ginv);
   T* t1 = static_cast<T*>(h->gt1);
   T* t2 = static_cast<T*>(h->gt2);
   cudaStream_t st = h->stream;
+  const bool wide = h->coarse_wide;
+  if (h->coarse_coop) {
+    GridSync gs;
+    gs.count = h->gsync;
+    gs.gen = h->gsync + 1;
+    gs.err = h->wait_err;
+    gs.limit = h->spin_limit;
+    h->waits_ran = true;
+    VPS_CK(h, launch_fd_global_solve<T>(b, x, S, St, inv, t1, t2, ni, d, px, pz, g.total, gs, wide,
+                                        st));
+    return VPS_OK;
+  }
   VPS_CK(h, cudaMemsetAsync(x, 0, g.total * sizeof(T), st));
   if (d == 3) {
-    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(0, t1, t2, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(1, t2, t1, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, t2, St, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(0, t1, t2, S, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(1, t2, t1, S, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, t2, St, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, wide, st));
   } else {
-    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(1, t1, t2, S, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, st));
-    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, st));
+    VPS_CK(h, launch_fd_global_pass<T>(0, b, t1, S, inv, ni, d, true, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(1, t1, t2, S, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t2, t1, St, inv, ni, d, false, false, px, pz, wide, st));
+    VPS_CK(h, launch_fd_global_pass<T>(2, t1, x, St, inv, ni, d, false, true, px, pz, wide, st));
   }
   return VPS_OK;
 }
@@ -439,12 +457,19 @@ int setup_coarse(vps_context* h, int lc) {
     }
   h->gS = h->ginv = h->gt1 = h->gt2 = nullptr;
   int rc;
-  // gS: S followed by S^T (both row-major)
-  S.reserve(2 * (size_t)ni * ni);
+  // gS: S followed by S^T (both row-major, rows of fd_pad(ni) with zeros
+  // past ni); work tensors: ni rows of fd_pad(ni^(d-1))
+  const int nip = fd_pad(ni);
+  const size_t nt = (size_t)ni * fd_pad(d == 3 ? ni * ni : ni);
+  std::vector<double> Sp(2 * (size_t)ni * nip, 0.0);
   for (int i = 0; i < ni; ++i)
-    for (int j = 0; j < ni; ++j) S.push_back(S[(size_t)j * ni + i]);
-  if ((rc = dalloc(h, &h->gS, 2 * (size_t)ni * ni * h->esz)) || (rc = dalloc(h, &h->ginv, nd * h->esz)) ||
-      (rc = dalloc(h, &h->gt1, nd * h->esz)) || (rc = dalloc(h, &h->gt2, nd * h->esz)))
+    for (int j = 0; j < ni; ++j) {
+      Sp[(size_t)i * nip + j] = S[(size_t)i * ni + j];
+      Sp[(size_t)(ni + i) * nip + j] = S[(size_t)j * ni + i];
+    }
+  S.swap(Sp);
+  if ((rc = dalloc(h, &h->gS, S.size() * h->esz)) || (rc = dalloc(h, &h->ginv, nd * h->esz)) ||
+      (rc = dalloc(h, &h->gt1, nt * h->esz)) || (rc = dalloc(h, &h->gt2, nt * h->esz)))
     return rc;
   cudaError_t e;
   // pageable source: the copies are staged before the calls return
@@ -763,13 +788,13 @@ int cg_solve(vps_context* h, double rtol, int max_it, int* iters, double* rel_re
       if ((rc = cg_true_residual(h))) return rc;
       VPS_CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                 h->stream));
-      const bool read_waits = h->sweep_ran;  // the wait-expiry word, in the same synchronisation
+      const bool read_waits = h->waits_ran;  // the wait-expiry word, in the same synchronisation
       if (read_waits)
         VPS_CK(h, cudaMemcpyAsync(h->host_err, h->wait_err, sizeof(int), cudaMemcpyDeviceToHost,
                                   h->stream));
       VPS_CK(h, cudaStreamSynchronize(h->stream));
       if (read_waits) {
-        h->sweep_ran = false;
+        h->waits_ran = false;
         if (*h->host_err) {
           VPS_CK(h, cudaMemset(h->wait_err, 0, sizeof(int)));
           return fail(h, VPS_ETIMEOUT, "a dependency wait of a smoothing sweep reached its limit");
@@ -1693,7 +1718,8 @@ std::string tune_key(vps_context* h) {
 
 // Cache file: one JSON object, one entry per line:
 //   "d3_k4_fp32_mult_L5_pre1_post1": {"coarse": 3, "variants": [1, 1, 2, 0, 1],
-//                                     "ops": [0, 0, 1, 1, 0], "schedule": 1},
+//                                     "ops": [0, 0, 1, 1, 0], "schedule": 1,
+//                                     "coarse_solver": 1},
 // (one line each).  Entries without every field are tuned again.
 bool parse_list(const char* p, const char* name, int* out, int nvar) {
   const char* v = std::strstr(p, name);
@@ -1710,7 +1736,7 @@ bool parse_list(const char* p, const char* name, int* out, int nvar) {
 }
 
 bool cache_lookup(const char* path, const std::string& key, int* coarse, int* var, int* ops,
-                  int* schedule, int nvar) {
+                  int* schedule, int* coarse_solver, int nvar) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
   char line[2048];
@@ -1721,7 +1747,9 @@ bool cache_lookup(const char* path, const std::string& key, int* coarse, int* va
     if (!p) continue;
     const char* c = std::strstr(p, "\"coarse\":");
     const char* d = std::strstr(p, "\"schedule\":");
-    if (!c || !d) continue;
+    const char* cs = std::strstr(p, "\"coarse_solver\":");
+    if (!c || !d || !cs) continue;
+    *coarse_solver = std::atoi(cs + 16);
     *coarse = std::atoi(c + 9);
     *schedule = std::atoi(d + 11);
     found = parse_list(p, "\"variants\": [", var, nvar) && parse_list(p, "\"ops\": [", ops, nvar);
@@ -1731,7 +1759,7 @@ bool cache_lookup(const char* path, const std::string& key, int* coarse, int* va
 }
 
 void cache_store(const char* path, const std::string& key, int coarse, const int* var,
-                 const int* ops, int schedule, int nvar) {
+                 const int* ops, int schedule, int coarse_solver, int nvar) {
   std::vector<std::string> keep;
   if (FILE* f = std::fopen(path, "r")) {
     char line[2048];
@@ -1749,7 +1777,8 @@ void cache_store(const char* path, const std::string& key, int coarse, const int
   for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(var[i]);
   entry += "], \"ops\": [";
   for (int i = 0; i < nvar; ++i) entry += (i ? ", " : "") + std::to_string(ops[i]);
-  entry += "], \"schedule\": " + std::to_string(schedule) + "}";
+  entry += "], \"schedule\": " + std::to_string(schedule) +
+           ", \"coarse_solver\": " + std::to_string(coarse_solver) + "}";
   keep.push_back(entry);
   if (FILE* f = std::fopen(path, "w")) {
     std::fputs("{\n", f);
@@ -1887,6 +1916,11 @@ int vps_create(int dim, int degree, int level, int precision, int smoother, doub
     h->sweep_ctr = static_cast<SweepCounters*>(q);
     if ((rc = dalloc(h, &q, sizeof(int)))) return bail(rc);
     h->wait_err = static_cast<int*>(q);
+    if ((rc = dalloc(h, &q, 2 * sizeof(unsigned)))) return bail(rc);
+    h->gsync = static_cast<unsigned*>(q);
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) == cudaSuccess)
+      h->coop_ok = h->coarse_coop = coop != 0;
   }
   // 1/(lambda_i + lambda_j [+ lambda_l]) in reference units
   {
@@ -2252,13 +2286,16 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
   const std::string key = tune_key(h);
   int var[kMaxLevels + 1] = {};
   int ops[kMaxLevels + 1] = {};
-  int coarse = 0, schedule = VPS_SCHEDULE_PDL;
+  int coarse = 0, schedule = VPS_SCHEDULE_PDL, coarse_solver = 0;
   if (from_cache) *from_cache = 0;
   const bool has_alt = h->prec == VPS_FP64 ? h->ks->d.apply_alt != nullptr
                                            : h->ks->f.apply_alt != nullptr;
-  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, ops + 1, &schedule, h->L)) {
+  if (cache_path && cache_lookup(cache_path, key, &coarse, var + 1, ops + 1, &schedule,
+                                 &coarse_solver, h->L)) {
     bool ok = coarse >= 1 && coarse <= h->L && schedule >= VPS_SCHEDULE_PLAIN &&
-              schedule <= VPS_SCHEDULE_SWEEP;
+              schedule <= VPS_SCHEDULE_SWEEP &&
+              coarse_solver >= 0 && coarse_solver <= 3 &&
+              (!(coarse_solver & VPS_COARSE_COOPERATIVE) || h->coop_ok);
     for (int l = 1; l <= h->L; ++l)
       ok = ok && variant_ok(h, var[l]) && (ops[l] == 0 || (ops[l] == 1 && has_alt));
     if (ok) {
@@ -2269,6 +2306,8 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
       h->schedule = schedule;
       if (coarse != h->coarse)
         if (int rc = setup_coarse(h, coarse)) return rc;
+      h->coarse_coop = (coarse_solver & VPS_COARSE_COOPERATIVE) != 0;
+      h->coarse_wide = (coarse_solver & VPS_COARSE_WIDE_TILES) != 0;
       drop_graphs(h);
       if (from_cache) *from_cache = 1;
       return VPS_OK;
@@ -2370,9 +2409,36 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     VPS_CK(h, launch_rhs_tensor(g, 1, h->rhs_buf, h->comp_b, h->stream));
     float best = 1e30f;
     int bestc = h->coarse;
+    bool bestcoop = h->coarse_coop, bestwide = h->coarse_wide;
+    const bool can_coop = h->coop_ok;
     for (int c = 1; c <= h->L - 1 || c == 1; ++c) {
       if (h->k * (1 << c) - 1 > 64) break;  // the global solve grows as ni^(d+1)
       if (int rc = setup_coarse(h, c)) return rc;
+      // the coarse solver's form on this level (one cooperative launch or
+      // one launch per pass; tiles of 32 or 64 outputs), whichever solves
+      // the level's system fastest
+      {
+        float tbest = 1e30f;
+        int sbest = 0;
+        for (int sv = 0; sv < 4; ++sv) {
+          if ((sv & VPS_COARSE_COOPERATIVE) && !can_coop) continue;
+          h->coarse_coop = (sv & VPS_COARSE_COOPERATIVE) != 0;
+          h->coarse_wide = (sv & VPS_COARSE_WIDE_TILES) != 0;
+          float t = 0.f;
+          int rc = h->prec == VPS_FP64
+                       ? time_ms(h, 5, [&] { return coarse_solve<double>(h, (const double*)h->bv[c],
+                                                                         (double*)h->xv[c]); }, &t)
+                       : time_ms(h, 5, [&] { return coarse_solve<float>(h, (const float*)h->bv[c],
+                                                                        (float*)h->xv[c]); }, &t);
+          if (rc) return rc;
+          if (t < tbest * 0.98f) {
+            tbest = t;
+            sbest = sv;
+          }
+        }
+        h->coarse_coop = (sbest & VPS_COARSE_COOPERATIVE) != 0;
+        h->coarse_wide = (sbest & VPS_COARSE_WIDE_TILES) != 0;
+      }
       float ms = 0.f;
       int rc = time_ms(h, 2, [&] { return trial_solve(h); }, &ms);
       if (rc == VPS_ENOCONV || rc == VPS_EBREAKDOWN) ms = 1e30f;  // not a usable candidate
@@ -2380,17 +2446,24 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
       if (ms < best * 0.98f) {
         best = ms;
         bestc = c;
+        bestcoop = h->coarse_coop;
+        bestwide = h->coarse_wide;
       }
       if (c >= h->L) break;
     }
+    if (int rc = check_waits(h)) return rc;
     if (int rc = setup_coarse(h, bestc)) return rc;
+    h->coarse_coop = bestcoop;
+    h->coarse_wide = bestwide;
   }
   if (cache_path) {
     for (int l = 1; l <= h->L; ++l) {
       var[l] = h->smooth_var[l];
       ops[l] = h->op_var[l];
     }
-    cache_store(cache_path, key, h->coarse, var + 1, ops + 1, h->schedule, h->L);
+    cache_store(cache_path, key, h->coarse, var + 1, ops + 1, h->schedule,
+                (h->coarse_coop ? VPS_COARSE_COOPERATIVE : 0) |
+                    (h->coarse_wide ? VPS_COARSE_WIDE_TILES : 0), h->L);
   }
   drop_graphs(h);
   return VPS_OK;
@@ -2430,6 +2503,24 @@ int vps_set_colour_schedule(vps_handle h, int schedule) {
 int vps_get_colour_schedule(vps_handle h, int* schedule) {
   if (!h || !schedule) return VPS_EINVAL;
   *schedule = h->schedule;
+  return VPS_OK;
+}
+
+int vps_set_coarse_solver(vps_handle h, int solver) {
+  if (!h) return VPS_EINVAL;
+  if (solver < 0 || solver > (VPS_COARSE_COOPERATIVE | VPS_COARSE_WIDE_TILES))
+    return fail(h, VPS_EINVAL, "coarse solver %d unknown", solver);
+  if ((solver & VPS_COARSE_COOPERATIVE) && !h->coop_ok)
+    return fail(h, VPS_EINVAL, "the device does not support cooperative launches");
+  h->coarse_coop = (solver & VPS_COARSE_COOPERATIVE) != 0;
+  h->coarse_wide = (solver & VPS_COARSE_WIDE_TILES) != 0;
+  drop_graphs(h);
+  return VPS_OK;
+}
+
+int vps_get_coarse_solver(vps_handle h, int* solver) {
+  if (!h || !solver) return VPS_EINVAL;
+  *solver = (h->coarse_coop ? VPS_COARSE_COOPERATIVE : 0) | (h->coarse_wide ? VPS_COARSE_WIDE_TILES : 0);
   return VPS_OK;
 }
 

@@ -5,6 +5,7 @@
 // (Section 3, building blocks); here they are plain kernels.  Reductions use
 // a fixed grid and fixed trees, so a result does not depend on scheduling:
 // the same inputs give bit-identical scalars on every run.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -559,19 +560,20 @@ l2_partial_kernel(const double* __restrict__ x, const double* __restrict__ tab, 
 
 // One pass of the global fast diagonalisation: for every line L of the
 // ni^(d-1) lines along the slowest index c,
-//   out[L][o] = sum_c in[c][L] W[c][o]   (MODE 1: times inv[L][o]),
+//   out[L][o] = sum_c in[c][L] W[c][o]   (scaled: times inv[L][o]),
 // i.e. the product In^T W of an (ni x NL) and an (ni x ni) matrix, written
-// with o fastest (the next pass contracts the next direction).  A block
-// computes FD_TL lines x FD_TO outputs; the whole contraction length fits
-// in shared memory (ni <= 255), so the input and weight tiles are loaded in
-// one stage, by asynchronous copies that are all in flight at once (the
-// tiles come from L2; copied one element per thread and round trip, the
-// load stage took most of a pass).  Each thread owns a 2 x 2 register
-// tile: per c, one pair of the input tile (lines) and one of the weight
-// tile (outputs), 4 FMAs.  Small register tiles give the small coarse
-// problems enough warps to hide latency (4 x 4 tiles left about three
-// warps per SM on 63^3 unknowns).
-constexpr int FD_TL = 16, FD_TO = 32, FD_R = 2, FD_THREADS = (FD_TL / FD_R) * (FD_TO / FD_R);
+// with o fastest (the next pass contracts the next direction).  The work
+// tensors between passes hold rows of NLp = fd_pad(NL) elements (in[c][L] at
+// c NLp + L) and the weights rows of fd_pad(ni) (zero past ni), so a block
+// stages its tiles with 16-byte asynchronous copies (the first pass reads the
+// level layout element by element).  A block computes FD_TL lines x TO
+// outputs with the whole contraction length in shared memory (ni <= 255);
+// each of its 128 threads owns 2 lines x TO/16 outputs.  Two tile widths,
+// chosen per coarse level by the autotuner: TO = 32 (2 x 2 per thread, twice
+// the blocks: small or FP64 problems) and TO = 64 (2 x 4, 8 FMAs per pair of
+// shared loads; all outputs of a line for ni <= 64).
+constexpr int FD_TL = 16, FD_RL = 2, FD_THREADS = 128;
+
 
 // One element global -> shared without staging in registers; with valid
 // false the element is filled with zeros and nothing is read (src is then
@@ -588,18 +590,103 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) 
                  : "memory");
 }
 
-template <typename T>
-__device__ __forceinline__ void ld2s(const T* p, T (&v)[2]) {
-  if constexpr (sizeof(T) == 4) {
+// 16 bytes global -> shared (both 16-byte aligned), zero-filled when !valid.
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(sz)
+               : "memory");
+}
+
+// N consecutive elements from shared memory, p aligned to N elements
+// (16 bytes at most per access).
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N == 2) {
     const float2 q = *reinterpret_cast<const float2*>(p);
     v[0] = q.x; v[1] = q.y;
+  } else if constexpr (sizeof(T) == 4 && N == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   } else {
-    const double2 q = *reinterpret_cast<const double2*>(p);
-    v[0] = q.x; v[1] = q.y;
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(p + i);
+      v[i] = q.x; v[i + 1] = q.y;
+    }
   }
 }
 
-template <typename T, int MODE>
+// One FD_TL x FD_TO tile (lines L0.., outputs o0..) of a pass.
+template <typename T, int FD_TO>
+__device__ __forceinline__ void fd_pass_tile(const T* __restrict__ in, T* __restrict__ out,
+                                             const T* __restrict__ W, const T* __restrict__ inv,
+                                             bool scale, int ni, int dim, int in_lev, int out_lev,
+                                             int px, int pz, int L0, int o0, T* As, T* Bs) {
+  constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  const int NL = dim == 3 ? ni * ni : ni, NLp = fd_pad(NL), nip = fd_pad(ni);
+  for (int u = threadIdx.x; u < ni * (FD_TO / V); u += FD_THREADS) {
+    const int c = u / (FD_TO / V), o = o0 + (u % (FD_TO / V)) * V;
+    cp_async_16(Bs + c * FD_TO + (o - o0), o < nip ? W + ((size_t)c * nip + o) : W, o < nip);
+  }
+  if (in_lev) {
+    for (int u = threadIdx.x; u < ni * FD_TL; u += FD_THREADS) {
+      const int l = u % FD_TL, c = u / FD_TL, L = L0 + l;
+      const T* src = in;
+      if (L < NL) {
+        const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
+        src = dim == 3 ? in + ((c + 1) * pz + (a + 1) * px + bb + 1) : in + ((c + 1) * px + bb + 1);
+      }
+      cp_async_elem(As + u, src, L < NL);
+    }
+  } else {
+    for (int u = threadIdx.x; u < ni * (FD_TL / V); u += FD_THREADS) {
+      const int c = u / (FD_TL / V), L = L0 + (u % (FD_TL / V)) * V;
+      cp_async_16(As + c * FD_TL + (L - L0), L < NLp ? in + ((size_t)c * NLp + L) : in, L < NLp);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  constexpr int FD_RO = FD_TO / 16;
+  static_assert((FD_TL / FD_RL) * (FD_TO / FD_RO) == FD_THREADS, "one output tile per thread");
+  const int tl = threadIdx.x % (FD_TL / FD_RL), to = threadIdx.x / (FD_TL / FD_RL);
+  T acc[FD_RL][FD_RO];
+#pragma unroll
+  for (int i = 0; i < FD_RL; ++i)
+#pragma unroll
+    for (int j = 0; j < FD_RO; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+  for (int c = 0; c < ni; ++c) {
+    T av[FD_RL], bv[FD_RO];
+    lds_vec(As + c * FD_TL + FD_RL * tl, av);
+    lds_vec(Bs + c * FD_TO + FD_RO * to, bv);
+#pragma unroll
+    for (int i = 0; i < FD_RL; ++i)
+#pragma unroll
+      for (int j = 0; j < FD_RO; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < FD_RL; ++i) {
+    const int L = L0 + FD_RL * tl + i;
+    if (L >= NL) continue;
+    const int a = dim == 3 ? L / ni : L, bb = dim == 3 ? L % ni : 0;
+#pragma unroll
+    for (int j = 0; j < FD_RO; ++j) {
+      const int o = o0 + FD_RO * to + j;
+      if (o >= ni) continue;
+      T r = acc[i][j];
+      if (scale) r *= inv[(size_t)L * ni + o];
+      if (out_lev) {
+        if (dim == 3) out[(a + 1) * pz + (bb + 1) * px + o + 1] = r;
+        else out[(L + 1) * px + o + 1] = r;
+      } else {
+        out[(size_t)a * NLp + bb * ni + o] = r;
+      }
+    }
+  }
+}
+
+template <typename T, int MODE, int FD_TO>
 __global__ void __launch_bounds__(FD_THREADS, 8)
 fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ W,
                       const T* __restrict__ inv, int ni, int dim, int in_lev, int out_lev, int px,
@@ -607,75 +694,94 @@ fd_global_pass_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);  // [ni][FD_TL]
   T* Bs = As + (size_t)ni * FD_TL;         // [ni][FD_TO]
-  const int NL = dim == 3 ? ni * ni : ni;
-  const int L0 = blockIdx.x * FD_TL, o0 = blockIdx.y * FD_TO;
-  for (int u = threadIdx.x; u < ni * FD_TL; u += FD_THREADS) {
-    const int l = u % FD_TL, c = u / FD_TL, L = L0 + l;
-    const T* src = in;
-    if (L < NL) {
-      if (in_lev) {
-        const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
-        src = dim == 3 ? in + ((c + 1) * pz + (a + 1) * px + bb + 1) : in + ((c + 1) * px + bb + 1);
-      } else {
-        src = in + ((size_t)c * NL + L);
-      }
-    }
-    cp_async_elem(As + u, src, L < NL);
-  }
-  for (int u = threadIdx.x; u < ni * FD_TO; u += FD_THREADS) {
-    const int oo = u % FD_TO, c = u / FD_TO, o = o0 + oo;
-    cp_async_elem(Bs + u, o < ni ? W + (c * ni + o) : W, o < ni);
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  fd_pass_tile<T, FD_TO>(in, out, W, inv, MODE == 1, ni, dim, in_lev, out_lev, px, pz,
+                         blockIdx.x * FD_TL, blockIdx.y * FD_TO, As, Bs);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): the last
+// block to arrive resets the count and advances the generation; the others
+// poll the generation at most `limit` times, then record the expiry in *err
+// and go on (the result is then undefined, the memory accesses are not).
+__device__ __forceinline__ void grid_barrier(const GridSync& gs) {
   __syncthreads();
-  const int tl = threadIdx.x % (FD_TL / FD_R), to = threadIdx.x / (FD_TL / FD_R);
-  T acc[FD_R][FD_R];
-#pragma unroll
-  for (int i = 0; i < FD_R; ++i)
-#pragma unroll
-    for (int j = 0; j < FD_R; ++j) acc[i][j] = T(0);
-#pragma unroll 8
-  for (int c = 0; c < ni; ++c) {
-    T av[FD_R], bv[FD_R];
-    ld2s(As + c * FD_TL + FD_R * tl, av);
-    ld2s(Bs + c * FD_TO + FD_R * to, bv);
-#pragma unroll
-    for (int i = 0; i < FD_R; ++i)
-#pragma unroll
-      for (int j = 0; j < FD_R; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < FD_R; ++i) {
-    const int L = L0 + FD_R * tl + i;
-    if (L >= NL) continue;
-    const int a = dim == 3 ? L / ni : 0, bb = dim == 3 ? L % ni : L;
-#pragma unroll
-    for (int j = 0; j < FD_R; ++j) {
-      const int o = o0 + FD_R * to + j;
-      if (o >= ni) continue;
-      T r = acc[i][j];
-      if (MODE == 1) r *= inv[(size_t)L * ni + o];
-      if (out_lev) {
-        if (dim == 3) out[(a + 1) * pz + (bb + 1) * px + o + 1] = r;
-        else out[(L + 1) * px + o + 1] = r;
-      } else {
-        out[(size_t)L * ni + o] = r;
+  if (threadIdx.x == 0) {
+    unsigned g;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(g) : "l"(gs.gen) : "memory");
+    __threadfence();
+    if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
+      *gs.count = 0u;
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(gs.gen), "r"(g + 1u) : "memory");
+    } else {
+      unsigned polls = 0, cur;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(cur) : "l"(gs.gen) : "memory");
+        if (cur != g) break;
+        if ((polls & 31u) == 31u && *reinterpret_cast<volatile const int*>(gs.err)) break;
+        if (++polls >= gs.limit) {
+          atomicOr(gs.err, 1);
+          break;
+        }
+        __nanosleep(64);
       }
     }
+  }
+  __syncthreads();
+}
+
+// The whole exact coarse solve x = A^-1 b by global fast diagonalisation in
+// one cooperative launch: the passes of launch_fd_global_pass (S^T along
+// each direction, the last of them scaled by 1/(sum of eigenvalues), then S
+// along each), separated by grid barriers instead of kernel boundaries;
+// every block takes the pass's tiles in a grid-stride loop.  x is zeroed
+// (boundary and padding) during the first pass; its interior is written by
+// the last.
+template <typename T, int FD_TO>
+__global__ void __launch_bounds__(FD_THREADS, 8)
+fd_global_solve_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ S,
+                       const T* __restrict__ St, const T* __restrict__ inv, T* __restrict__ t1,
+                       T* __restrict__ t2, int ni, int dim, int px, int pz, int64_t xtotal,
+                       GridSync gs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);
+  T* Bs = As + (size_t)ni * FD_TL;
+  const int NL = dim == 3 ? ni * ni : ni;
+  const int gx = (NL + FD_TL - 1) / FD_TL, gy = (ni + FD_TO - 1) / FD_TO;
+  const int ntiles = gx * gy;
+  const int npass = dim == 3 ? 6 : 4;
+  for (int64_t e = blockIdx.x * (int64_t)FD_THREADS + threadIdx.x; e < xtotal;
+       e += (int64_t)gridDim.x * FD_THREADS)
+    x[e] = T(0);
+  for (int p = 0; p < npass; ++p) {
+    // 3D: b->t1 (S^T), t1->t2 (S^T), t2->t1 (S^T, scaled), t1->t2 (S), t2->t1 (S), t1->x (S)
+    // 2D: b->t1 (S^T), t1->t2 (S^T, scaled), t2->t1 (S), t1->x (S)
+    const int half = npass / 2;
+    const T* in = p == 0 ? b : ((p & 1) ? t1 : t2);
+    T* out = p == npass - 1 ? x : ((p & 1) ? t2 : t1);
+    const T* W = p < half ? S : St;
+    const bool scale = p == half - 1;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      fd_pass_tile<T, FD_TO>(in, out, W, inv, scale, ni, dim, p == 0, p == npass - 1, px, pz,
+                             (tile % gx) * FD_TL, (tile / gx) * FD_TO, As, Bs);
+      __syncthreads();  // the next tile reloads As and Bs
+    }
+    if (p < npass - 1) grid_barrier(gs);
   }
 }
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
+template <typename T, int FD_TO>
+cudaError_t fd_global_pass_launch(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
                                   int dim, bool in_lev, bool out_lev, int px, int pz,
                                   cudaStream_t s) {
   const int NL = dim == 3 ? ni * ni : ni;
   const dim3 grid((unsigned)((NL + FD_TL - 1) / FD_TL), (unsigned)((ni + FD_TO - 1) / FD_TO));
   const size_t smem = (size_t)ni * (FD_TL + FD_TO) * sizeof(T);
-  auto kern = mode == 0 ? fd_global_pass_kernel<T, 0>
-                        : (mode == 1 ? fd_global_pass_kernel<T, 1> : fd_global_pass_kernel<T, 2>);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = mode == 0 ? fd_global_pass_kernel<T, 0, FD_TO>
+                        : (mode == 1 ? fd_global_pass_kernel<T, 1, FD_TO>
+                                     : fd_global_pass_kernel<T, 2, FD_TO>);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -685,12 +791,74 @@ cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, con
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
+                                  int dim, bool in_lev, bool out_lev, int px, int pz, bool wide,
+                                  cudaStream_t s) {
+  return wide ? fd_global_pass_launch<T, 64>(mode, in, out, W, inv, ni, dim, in_lev, out_lev, px,
+                                             pz, s)
+              : fd_global_pass_launch<T, 32>(mode, in, out, W, inv, ni, dim, in_lev, out_lev, px,
+                                             pz, s);
+}
+
+template <typename T, int FD_TO>
+cudaError_t fd_global_solve_launch(const T* b, T* x, const T* S, const T* St, const T* inv, T* t1,
+                                   T* t2, int ni, int dim, int px, int pz, int64_t xtotal,
+                                   const GridSync& gs, cudaStream_t s) {
+  const int NL = dim == 3 ? ni * ni : ni;
+  const int ntiles = ((NL + FD_TL - 1) / FD_TL) * ((ni + FD_TO - 1) / FD_TO);
+  const size_t smem = (size_t)ni * (FD_TL + FD_TO) * sizeof(T);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = fd_global_solve_kernel<T, FD_TO>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FD_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(ntiles, per_sm * nsm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(FD_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  VPS_COUNT_LAUNCH();
+  return cudaLaunchKernelEx(&cfg, kern, b, x, S, St, inv, t1, t2, ni, dim, px, pz, xtotal, gs);
+}
+
+template <typename T>
+cudaError_t launch_fd_global_solve(const T* b, T* x, const T* S, const T* St, const T* inv, T* t1,
+                                   T* t2, int ni, int dim, int px, int pz, int64_t xtotal,
+                                   const GridSync& gs, bool wide, cudaStream_t s) {
+  return wide ? fd_global_solve_launch<T, 64>(b, x, S, St, inv, t1, t2, ni, dim, px, pz, xtotal,
+                                              gs, s)
+              : fd_global_solve_launch<T, 32>(b, x, S, St, inv, t1, t2, ni, dim, px, pz, xtotal,
+                                              gs, s);
+}
+
+template cudaError_t launch_fd_global_solve<float>(const float*, float*, const float*, const float*,
+                                                   const float*, float*, float*, int, int, int, int,
+                                                   int64_t, const GridSync&, bool, cudaStream_t);
+template cudaError_t launch_fd_global_solve<double>(const double*, double*, const double*,
+                                                    const double*, const double*, double*, double*,
+                                                    int, int, int, int, int64_t, const GridSync&,
+                                                    bool, cudaStream_t);
+
 template cudaError_t launch_fd_global_pass<float>(int, const float*, float*, const float*,
                                                   const float*, int, int, bool, bool, int, int,
-                                                  cudaStream_t);
+                                                  bool, cudaStream_t);
 template cudaError_t launch_fd_global_pass<double>(int, const double*, double*, const double*,
                                                    const double*, int, int, bool, bool, int, int,
-                                                   cudaStream_t);
+                                                   bool, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_pack(const LevelGeom& g, const T* compact, T* lev, cudaStream_t s) {

@@ -153,8 +153,8 @@ struct BatchQueue {
   BatchItem items[kMaxBatch];
 };
 
-// Dataflow schedule of a multiplicative smoothing step: one persistent
-// kernel runs every colour.  Blocks claim tiles in the order of the sweep
+// Dataflow schedule of a multiplicative smoothing step: one launch of one
+// block per tile runs every colour.  Blocks claim tiles in the order of the sweep
 // (all tiles of the first colour, then of the second, ...), and a tile
 // starts once every patch of an earlier colour that overlaps one of its
 // patches is done; the result equals the colour-by-colour passes bit for
@@ -331,9 +331,34 @@ cudaError_t launch_axpy_inplace(T* y, const T* x, T a, int64_t n, cudaStream_t s
 // (W = S applies S^T to each line; W = S^T stored row-major applies S).
 // in_lev / out_lev: read / write the interior of a level-layout vector
 // instead of a compact tensor.
+// Row length of the global fast diagonalisation's work tensors and weight
+// matrices: n rounded up to a multiple of 4 elements, so that rows start on
+// 16-byte boundaries (the padding holds zeros).
+__host__ __device__ inline int fd_pad(int n) { return (n + 3) & ~3; }
+
+// Grid-wide barrier state of a cooperative launch (device words, zero at
+// rest) and its bounded wait.
+struct GridSync {
+  unsigned int* count = nullptr;  // blocks arrived at the current barrier
+  unsigned int* gen = nullptr;    // barriers completed
+  int* err = nullptr;             // set to 1 by a wait that reached its poll limit
+  unsigned int limit = 0;         // polls before a wait gives up
+};
+// The whole exact coarse solve (the passes of launch_fd_global_pass) in one
+// cooperative launch with grid barriers between the passes; x of total
+// elements xtotal is zeroed outside the interior.
+template <typename T>
+cudaError_t launch_fd_global_solve(const T* b, T* x, const T* S, const T* St, const T* inv, T* t1,
+                                   T* t2, int ni, int dim, int px, int pz, int64_t xtotal,
+                                   const GridSync& gs, bool wide, cudaStream_t s);
+
+// One pass (mode 0: S^T, 1: S^T scaled by inv, 2: S) of the global fast
+// diagonalisation, W with rows of fd_pad(ni), work tensors with rows of
+// fd_pad(ni^(d-1)); in_lev / out_lev: the input / output in the level layout;
+// wide: tiles of 64 outputs instead of 32.
 template <typename T>
 cudaError_t launch_fd_global_pass(int mode, const T* in, T* out, const T* W, const T* inv, int ni,
-                                  int dim, bool in_lev, bool out_lev, int px, int pz,
+                                  int dim, bool in_lev, bool out_lev, int px, int pz, bool wide,
                                   cudaStream_t s);
 
 // b (compact, double) = sum_m coef_m prod_t b1d[m][t][node_t]  with b1d on device

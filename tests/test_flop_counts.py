@@ -350,3 +350,22 @@ def test_even_odd_update_matches_dense_and_executed_count(d, k, boundary):
     ref = x[inner] + np.linalg.solve(AbarI, rd)
     assert np.allclose(got.ravel(), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
     assert c.flops == smoother_flops_executed_per_patch(d, k, boundary)
+
+
+def test_paper_count_per_dof_at_the_degree_sweep_sizes():
+    """The plain sum-factorisation count per patch (the roofline's algorithmic
+    work) per DoF at the sweep's sizes: 3D on 2^7 cells (2^8 for k = 2, 2^6 for
+    k = 6, 7), 2D on 2^12, as tabulated for the degree sweep."""
+    from paper_2405_19004_gb300.studies import paper_flops_per_patch
+    want = {3: [513, 788, 1140, 1521, 1911, 2262, 2651], 2: [155, 261, 381, 505, 630, 756, 883]}
+    lev3 = [7, 8, 7, 7, 7, 6, 6]
+    for d in (2, 3):
+        for k in range(1, 8):
+            L = lev3[k - 1] if d == 3 else 12
+            per_dof = paper_flops_per_patch(d, k) * (2 ** L - 1) ** d / (k * 2 ** L - 1) ** d
+            assert round(per_dof) == want[d][k - 1], (d, k)
+    # and it counts more than the kernels' dense count (the shared mass contraction)
+    from paper_2405_19004_gb300.studies import smoother_flops_per_patch
+    for d in (2, 3):
+        for k in range(1, 8):
+            assert paper_flops_per_patch(d, k) > smoother_flops_per_patch(d, k)

@@ -272,7 +272,7 @@ def test_autotune_caches_and_keeps_parity(tmp_path):
     def choice(H):
         return ([H.vps_get_smooth_variant(l)[0] for l in range(1, L + 1)],
                 [H.vps_get_operator_variant(l)[0] for l in range(1, L + 1)],
-                H.vps_get_colour_schedule(), H.vps_get_coarse_level())
+                H.vps_get_colour_schedule(), H.vps_get_coarse_level(), H.vps_get_coarse_solver())
     chosen = choice(P)
     assert [P.vps_get_operator_variant(l)[1] for l in range(1, L + 1)] == [2] * L  # 3D FP32 k <= 4
     Q = _poisson(d, k, L, 1)
@@ -282,7 +282,7 @@ def test_autotune_caches_and_keeps_parity(tmp_path):
     entry = json.load(open(cache))
     assert len(entry) == 1
     (rec,) = entry.values()
-    assert {"coarse", "variants", "ops", "schedule"} <= set(rec)
+    assert {"coarse", "variants", "ops", "schedule", "coarse_solver"} <= set(rec)
     H = multigrid.Hierarchy(d, k, L, coarse_level=Q.vps_get_coarse_level())
     b = uniform_vector(H.levels[L].N, 33)
     bt = torch.as_tensor(b, device="cuda")
