@@ -1343,6 +1343,37 @@ struct ApplyCfg {
 #define VPS_BAND_LOOP(q, j) \
   _Pragma("unroll") for (int j = 0; j <= 2 * K; ++j) if (q == 0 || (j >= K - q && j <= 2 * K - q))
 
+// The upper boundary layer of a level vector (index n1-1 in any direction)
+// is owned by no operator or restriction tile; this zeroes the elements
+// first, first + step, ... of it (faces x, y, z in turn).
+template <typename T>
+__device__ __forceinline__ void zero_upper_faces_body(T* __restrict__ v, int n1, int64_t px,
+                                                      int64_t pz, int64_t first, int64_t step) {
+  const int64_t nface = DIM == 3 ? (int64_t)n1 * n1 : n1;
+  for (int64_t e = first; e < DIM * nface; e += step) {
+    const int f = (int)(e / nface);
+    const int64_t r = e % nface;
+    const int a = (int)(r % n1), c = DIM == 3 ? (int)(r / n1) : 0;
+    int64_t idx;
+    if (f == 0) idx = (int64_t)c * pz + (int64_t)a * px + (n1 - 1);
+    else if (f == 1) idx = (int64_t)c * pz + (int64_t)(n1 - 1) * px + a;
+    else idx = (int64_t)(n1 - 1) * pz + (int64_t)c * px + a;
+    v[idx] = T(0);
+  }
+}
+
+// This block's share of the upper faces of y (every block of the grid takes
+// a stride of them): the operator and transfer kernels write every node
+// 0..n1-2 of each direction and zero the layer n1-1 this way, so no separate
+// launch is needed.  The face nodes are disjoint from the nodes the tiles
+// write.
+template <typename T>
+__device__ __forceinline__ void block_zero_faces(T* __restrict__ y, int n1, int64_t px, int64_t pz) {
+  const int64_t nb = (int64_t)gridDim.x * gridDim.y * gridDim.z;
+  const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+  zero_upper_faces_body<T>(y, n1, px, pz, bid * blockDim.x + threadIdx.x, nb * blockDim.x);
+}
+
 template <typename T, bool ABS = false>
 __global__ void __launch_bounds__(ApplyCfg::NT)
 apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
@@ -1353,6 +1384,7 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
   T* tm = reinterpret_cast<T*>(smem_raw);
   T* tk = tm + C::a_sz;
   const int x0 = blockIdx.x * TN, y0 = blockIdx.y * TN;
+  block_zero_faces<T>(y, n1, px, pz);
   if constexpr (DIM == 3) {
     const int z0 = blockIdx.z * TN;
     T* mm = tk + C::a_sz;
@@ -1542,6 +1574,7 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
   T* MM = zbuf + 4 * BX * RB;                // [TX][RB]
   T* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  block_zero_faces<T>(y, n1, px, pz);
   const int z0 = blockIdx.z * (kApplyZC<T> * K);  // a multiple of K
   int buf = 0;
   for (int cz = 0; cz < kApplyZC<T>; ++cz) {
@@ -1647,6 +1680,7 @@ apply3c_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restric
   T* zb = reinterpret_cast<T*>(smem_raw);  // [K][M, K rows][BX][RB]
   T* mw = zb + 2 * K * BX * RB;            // [2 buffers][MM, WW][TX][RB]
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  block_zero_faces<T>(y, n1, px, pz);
   for (int cz = 0; cz < kApply3CZ; ++cz) {
     const int z0 = (blockIdx.z * kApply3CZ + cz) * K;
     if (z0 >= n1 - 1) break;  // uniform in the block; plane n1-1 is zeroed elsewhere
@@ -1821,6 +1855,7 @@ apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
   DF* MM = zbuf + 4 * BX * RB;
   DF* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
+  block_zero_faces<double>(y, n1, px, pz);
   const int z0 = blockIdx.z * (kApplyZC<double> * K);
   int buf = 0;
   for (int cz = 0; cz < kApplyZC<double>; ++cz) {
@@ -1898,6 +1933,7 @@ apply2_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl, dou
   DF* tm = reinterpret_cast<DF*>(smem_raw);
   DF* tk = tm + C::a_sz;
   const int x0 = blockIdx.x * TN, y0 = blockIdx.y * TN;
+  block_zero_faces<double>(y, n1, px, 0);
   for (int u = threadIdx.x; u < BN * CT; u += NT) {
     const int xx = u % BN, cy = u / BN;
     const int gx = x0 - K + xx, gy0 = y0 + cy * K - K;
@@ -2231,6 +2267,7 @@ template <typename T>
 __global__ void __launch_bounds__(TransferCfg::NT)
 restrict_kernel(const T* __restrict__ rf, T* __restrict__ rc, int n1c, int64_t pxc, int64_t pzc,
                 int n1f, int64_t pxf, int64_t pzf) {
+  block_zero_faces<T>(rc, n1c, pxc, pzc);
   restrict_body<T>(rf, rc, n1c, pxc, pzc, n1f, pxf, pzf, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -2251,29 +2288,6 @@ restrict_batch_kernel(BatchQueue* __restrict__ q) {
   }
 }
 
-// The upper boundary layer of a coarse vector (index n1c-1 in any
-// direction) is owned by no restriction tile; this zeroes it.
-template <typename T>
-__device__ __forceinline__ void zero_upper_faces_body(T* __restrict__ v, int n1, int64_t px,
-                                                      int64_t pz, int64_t first, int64_t step) {
-  const int64_t nface = DIM == 3 ? (int64_t)n1 * n1 : n1;
-  for (int64_t e = first; e < DIM * nface; e += step) {
-    const int f = (int)(e / nface);
-    const int64_t r = e % nface;
-    const int a = (int)(r % n1), c = DIM == 3 ? (int)(r / n1) : 0;
-    int64_t idx;
-    if (f == 0) idx = (int64_t)c * pz + (int64_t)a * px + (n1 - 1);
-    else if (f == 1) idx = (int64_t)c * pz + (int64_t)(n1 - 1) * px + a;
-    else idx = (int64_t)(n1 - 1) * pz + (int64_t)c * px + a;
-    v[idx] = T(0);
-  }
-}
-
-template <typename T>
-__global__ void zero_upper_faces_kernel(T* __restrict__ v, int n1, int64_t px, int64_t pz) {
-  zero_upper_faces_body<T>(v, n1, px, pz, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                           (int64_t)gridDim.x * blockDim.x);
-}
 
 // The upper faces of the `out` vectors (layout a) of every item of a queue:
 // blockIdx.y selects the item.
@@ -2458,7 +2472,7 @@ cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T*
 }
 
 // Tiles cover the nodes 0 .. n1-2 of every direction; the upper boundary
-// layer (index n1-1) is zeroed by a second, small kernel.
+// layer (index n1-1) is zeroed by the kernel's blocks (block_zero_faces).
 // The per-plane 3D operator where the default is the cell-batched one.
 template <typename T>
 cudaError_t apply_alt_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
@@ -2470,10 +2484,6 @@ cudaError_t apply_alt_launch(const LevelGeom& g, const T* x, const T* b, T* y, c
     VPS_COUNT_LAUNCH();
     apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
                                                                    (int)g.pz, T(g.h));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    VPS_COUNT_LAUNCH();
-    zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
     return cudaGetLastError();
   } else {
     (void)g; (void)x; (void)b; (void)y; (void)s;
@@ -2503,10 +2513,6 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
     VPS_COUNT_LAUNCH();
     apply_kernel<T><<<dim3(t, t, 1), C::NT, C::smem<T>(), s>>>(x, b, y, g.n1, g.px, g.pz, T(1));
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  VPS_COUNT_LAUNCH();
-  zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
   return cudaGetLastError();
 }
 
@@ -2529,10 +2535,6 @@ cudaError_t apply_abs_launch(const LevelGeom& g, const double* x, double* y, cud
     apply_kernel<double, true><<<dim3(t, t, 1), C::NT, C::smem<double>(), s>>>(
         x, nullptr, y, g.n1, g.px, g.pz, 1.0);
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  VPS_COUNT_LAUNCH();
-  zero_upper_faces_kernel<double><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
   return cudaGetLastError();
 }
 
@@ -2555,10 +2557,6 @@ cudaError_t apply_df_launch(const LevelGeom& g, const float* xh, const float* xl
     apply2_df_kernel<0><<<dim3(t, t, 1), C::NT, C::smem<double>(), s>>>(xh, xl, y, g.n1,
                                                                        (int)g.px);
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  VPS_COUNT_LAUNCH();
-  zero_upper_faces_kernel<double><<<64, 256, 0, s>>>(y, g.n1, g.px, g.pz);
   return cudaGetLastError();
 }
 
@@ -2583,10 +2581,6 @@ cudaError_t restrict_launch(const LevelGeom& f, const LevelGeom& c, const T* rf,
   VPS_COUNT_LAUNCH();
   restrict_kernel<T><<<grid, C::NT, C::smem_restrict<T>(), s>>>(rf, rc, c.n1, c.px, c.pz, f.n1,
                                                                  f.px, f.pz);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  VPS_COUNT_LAUNCH();
-  zero_upper_faces_kernel<T><<<64, 256, 0, s>>>(rc, c.n1, c.px, c.pz);
   return cudaGetLastError();
 }
 
