@@ -234,8 +234,11 @@ def job_throughput(units_per_rank, t_step, world):
 
 
 # ---------------------------------------------------------------- serving
-def run_serving(vps, n_requests, precision, max_active, budget):
-    """Replays a seeded Poisson-arrival stream of solve requests in real time."""
+def run_serving(vps, n_requests, precision, max_active, budget, closed_loop=False):
+    """Replays a seeded Poisson-arrival stream of solve requests in real time;
+    closed_loop: submits the same requests all at once, so that the span
+    measures the server's capacity (the rate at which it drains a full
+    queue) rather than the offered rate."""
     from synthetic import request_stream
     reqs = request_stream(n_requests, 200.0, seed=5)
     srv = vps.Server(budget, max_active=max_active, precision=precision, rtol=RTOL, max_it=200)
@@ -243,7 +246,7 @@ def run_serving(vps, n_requests, precision, max_active, budget):
     t0 = time.perf_counter()
     for r in reqs:
         delay = t0 + r["t_arrival"] - time.perf_counter()
-        if delay > 0:
+        if delay > 0 and not closed_loop:
             time.sleep(delay)
         rid, x = srv.submit(r["d"], r["k"], r["level"], r["coef"], r["freq"])
         ids.append(rid)
@@ -258,6 +261,10 @@ def run_serving(vps, n_requests, precision, max_active, budget):
     ok = sum(q["state"] == vps.VPS_REQ_DONE for q in info)
     pct = lambda p: lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
     span = t_end - t0
+    if closed_loop:
+        return {"requests": len(ids), "completed": ok, "span_s": span,
+                "capacity_req_per_s": len(ids) / span, "capacity_dof_per_s": sum(dofs) / span,
+                "max_active": max_active, "batching": batch}
     return {"requests": len(ids), "completed": ok, "p50_latency_s": pct(50), "p99_latency_s": pct(99),
             "mean_latency_s": sum(lat) / len(lat), "span_s": span,
             "throughput_req_per_s": len(ids) / span, "throughput_dof_per_s": sum(dofs) / span,
@@ -472,7 +479,7 @@ def main():
     t_launch = statistics.mean(launch_ms) / 1e3
     n_patches = (2 ** L - 1) ** 3
     var_L = P.vps_get_smooth_variant(L)[0]
-    bnd_L = var_L // 3 >= 1
+    bnd_L = var_L // 3 in vps.BOUNDARY_KINDS
     # algorithmic work per launch: the method's plain sum-factorisation count
     # per patch x the patches of the launch (the kernels' own dense and
     # executed counts are reported beside it)
@@ -515,7 +522,7 @@ def main():
         e1.record(P64.stream)
         torch.cuda.synchronize()
         t64_step = e0.elapsed_time(e1) / 3e3
-        bnd64 = P64.vps_get_smooth_variant(L)[0] // 3 >= 1
+        bnd64 = P64.vps_get_smooth_variant(L)[0] // 3 in vps.BOUNDARY_KINDS
         f64 = smoother_flops_per_patch(D, K, bnd64) * n_patches / t64_step / 1e12
         f64x = smoother_flops_executed_per_patch(D, K, bnd64) * n_patches / t64_step / 1e12
         dx = (x64 - x).abs().max().item() / x64.abs().max().item()
@@ -661,6 +668,10 @@ def main():
             "workload": f"{args.serving_requests} requests, Poisson arrivals 200/s, d in {{2,3}}, "
                         "k in 2..6, levels with 1e4..2e7 DoFs, 4 sine modes, seed 5, CG to 1e-10",
             "fp32_mg_batched": run_serving(vps, args.serving_requests, vps.VPS_FP32, 16, budget),
+            # the same requests queued at once: the rate the server sustains
+            # (an open-loop stream cannot complete faster than it arrives)
+            "fp32_mg_batched_capacity": run_serving(vps, args.serving_requests, vps.VPS_FP32, 16,
+                                                    budget, closed_loop=True),
             "fp64_one_at_a_time": run_serving(vps, args.serving_requests, vps.VPS_FP64, 1, budget),
         }
 

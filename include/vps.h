@@ -307,7 +307,13 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
  *            for the exact local solver without reading x_I
  *            (VPS_MULTIPLICATIVE handles only);
  *   kind 2 (6-8): the Boundary kernel in blocks of one warp, each stage in
- *            several rounds of 32 lines (degrees 1..3 only).
+ *            several rounds of 32 lines (degrees 1..3 only);
+ *   kind 3 (9-11) / kind 4 (12-14): the fused / the Boundary kernel in
+ *            blocks of the fewest warps that take every stage after the
+ *            first in one round (the first, whose lines are the most, in
+ *            two): fewer threads per block, so more resident blocks and
+ *            patches per SM (VPS_MULTIPLICATIVE handles only; a shape whose
+ *            automatic block is already that small has no kind 3 or 4).
  * A variant whose shared memory exceeds the GPU's limit for the handle's
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);

@@ -34,6 +34,9 @@ VPS_OUTER_DOUBLE_FLOAT = 1
 VPS_SCHEDULE_PLAIN, VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP = 0, 1, 2
 VPS_COARSE_PASSES, VPS_COARSE_COOPERATIVE, VPS_COARSE_WIDE_TILES = 0, 1, 2
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
+# smoother variants (vps_set_smooth_variant): variant = 3 * kind + block shape
+VPS_SMOOTH_VARIANTS = 15
+BOUNDARY_KINDS = (1, 2, 4)   # kinds whose kernel is the Boundary kernel of Section 3.2
 
 # C signatures: name -> (restype, argtypes)
 _i, _d, _p, _i64p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)

@@ -141,6 +141,16 @@ constexpr int kG2 = DIM == 3 ? (K == 1 ? 16 : K == 2 ? 32 : K == 3 ? 16 : K <= 5
                              : (K <= 6 ? 16 : 32);
 constexpr int kShapeG[kQVariants] = {kG1, kG1, kG2};
 constexpr int kShapeQ[kQVariants] = {1, 2, 1};
+// Fewest warps of a block of shape s that still covers the lines of the
+// residual stage after the first (3D: G n m, 2D: G m) in one round (kinds 3
+// and 4): the first stage, whose G n^2 (2D: G n) lines are the most, takes
+// two rounds, and the threads that every later stage leaves idle are not
+// launched.  A block then holds fewer registers (3D Q4 FP32: 256 threads
+// instead of 352 at 32 registers), so more blocks -- and patches -- are
+// resident on an SM.
+constexpr int warps_min(int s) {
+  return (kShapeG[s] * (DIM == 3 ? n * m : m) + 31) / 32;
+}
 // Contract the first and the middle direction of the fast diagonalisation in
 // registers (two stages and two barriers fewer); above k = 5 the extra live
 // values cost more resident blocks than the barriers save.
@@ -178,7 +188,8 @@ struct SmoothCfg {
   static constexpr int sizeA = DIM == 3 ? n * n * m : n * m;
   static constexpr int sizeB = DIM == 3 ? n * m * m : m * m;
   static constexpr int nB = DIM == 3 ? 2 : 1;
-  static constexpr bool alias = DIM == 3 && W_ == 0;
+  // (stage 1 reads its line into registers before a barrier: one round)
+  static constexpr bool alias = DIM == 3 && (W_ == 0 || 32 * W_ >= G * n * m);
   static constexpr int region =
       alias ? (2 * sizeA > 2 * sizeB + md ? 2 * sizeA : 2 * sizeB + md) : 2 * sizeA + nB * sizeB;
   static constexpr size_t elems_mult = (size_t)P * (region + 2 * md) + md;
@@ -1166,11 +1177,11 @@ __device__ __forceinline__ void sweep_wait(const SweepGeom& sg, int pos, int64_t
 // rather than a loop over tiles in resident blocks: the loop kept values
 // live across tiles and needed twice the registers.)  The last block to
 // finish resets the counters for the next sweep and advances the epoch.
-template <typename T, int QQ, bool BND>
-__global__ void __launch_bounds__(SmoothCfg<T, QQ, 0>::NT)
+template <typename T, int QQ, bool BND, int W = 0>
+__global__ void __launch_bounds__(SmoothCfg<T, QQ, W>::NT)
 smooth_sweep_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
                     int px, int pz, const __grid_constant__ SweepGeom sg, T bscale) {
-  using C = SmoothCfg<T, QQ, 0>;
+  using C = SmoothCfg<T, QQ, W>;
   constexpr int P = C::P, NT = C::NT;
   __shared__ int64_t s_tile;
   __shared__ unsigned s_ep;
@@ -1187,12 +1198,13 @@ smooth_sweep_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restr
     while (t >= sg.tile_end[pos]) ++pos;
     const int64_t tile = t - (pos > 0 ? sg.tile_end[pos - 1] : 0);
     const ColourGeom& cg = sg.cg[pos];
-    smooth_mult_body<T, QQ, BND, 0, false, true>(
+    smooth_mult_body<T, QQ, BND, W, false, true>(
         b, x, inv_lam, px, pz, cg, bscale, nullptr, tile,
         [&] { sweep_wait<P, NT>(sg, pos, tile, ep); });
     __syncthreads();  // every store of the tile is issued
-    if (threadIdx.x < P) {
-      const int64_t gp = tile * P + threadIdx.x;
+    // (a block of few warps may hold more patches than threads)
+    for (int i = threadIdx.x; i < P; i += NT) {
+      const int64_t gp = tile * P + i;
       if (gp < cg.npatch) {
         __threadfence();
         st_release(sg.flags + sg.flag_off[sg.colour[pos]] + gp, ep);
@@ -2364,17 +2376,17 @@ cudaError_t smooth_mult_batch_launch(BatchQueue* q, int64_t ntiles, const T* inv
 // A smoothing step as one dataflow sweep (smooth_sweep_kernel, one block per
 // tile of every colour), launched as a programmatic dependent launch (the
 // kernel waits for the previous one before it reads the counters or x).
-template <typename T, int PP, bool BND>
+template <typename T, int PP, bool BND, int W = 0>
 cudaError_t smooth_sweep_launch(const LevelGeom& g, const SweepGeom& sg, const T* b, T* x,
                                 const T* inv_lam, cudaStream_t s) {
-  using C = SmoothCfg<T, PP>;
+  using C = SmoothCfg<T, PP, W>;
   const int64_t ntiles = sg.ncol > 0 ? sg.tile_end[sg.ncol - 1] : 0;
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const size_t smem = BND ? C::smem_bnd : C::smem_mult;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  return launch_pdl(smooth_sweep_kernel<T, PP, BND>, dim3((unsigned)ntiles), dim3(C::NT), smem, s,
+  return launch_pdl(smooth_sweep_kernel<T, PP, BND, W>, dim3((unsigned)ntiles), dim3(C::NT), smem, s,
                     b, x, inv_lam, (int)g.px, (int)g.pz, sg, bscale);
 }
 
@@ -2596,9 +2608,37 @@ cudaError_t smoother_smem(KernT kern, size_t bytes) {
                               (int)cudaSharedmemCarveoutMaxShared);
 }
 
+// The fewer-warps kinds 3 and 4 exist for a block shape where they launch
+// fewer threads than the automatic block of kinds 0 and 1.
+template <typename T, int PP>
+constexpr bool kFewWarps = 32 * warps_min(PP) < SmoothCfg<T, PP>::NT;
+
+template <typename T, int PP>
+cudaError_t smooth_few_warps_limits() {
+  if constexpr (kFewWarps<T, PP>) {
+    constexpr int Wm = warps_min(PP);
+    using CW = SmoothCfg<T, PP, Wm>;
+    cudaError_t e = cudaSuccess;
+    if constexpr (CW::fits_bnd) {
+      if ((e = smoother_smem(smooth_mult_kernel<T, PP, true, Wm>, CW::smem_bnd)) ||
+          (e = smoother_smem(smooth_mult_batch_kernel<T, PP, true, Wm>, CW::smem_bnd)) ||
+          (e = smoother_smem(smooth_sweep_kernel<T, PP, true, Wm>, CW::smem_bnd)))
+        return e;
+    }
+    if constexpr (CW::fits) {
+      if ((e = smoother_smem(smooth_mult_kernel<T, PP, false, Wm>, CW::smem_mult)) ||
+          (e = smoother_smem(smooth_mult_batch_kernel<T, PP, false, Wm>, CW::smem_mult)) ||
+          (e = smoother_smem(smooth_sweep_kernel<T, PP, false, Wm>, CW::smem_mult)))
+        return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 template <typename T, int PP>
 cudaError_t smooth_limits() {
   using C = SmoothCfg<T, PP>;
+  if (cudaError_t e = smooth_few_warps_limits<T, PP>(); e != cudaSuccess) return e;
   if constexpr (C::fits_bnd) {
     cudaError_t e = smoother_smem(smooth_mult_kernel<T, PP, true, 0>, C::smem_bnd);
     if (e != cudaSuccess) return e;
@@ -2631,9 +2671,41 @@ cudaError_t smooth_limits() {
   }
 }
 
+// Kinds 3 (fused) and 4 (Boundary) of block shape PP: the blocks of
+// warps_min(PP) warps; multiplicative smoother only.
+template <typename T, int PP>
+void register_few_warps(KernelFns<T>* f, int v) {
+  constexpr int vf = v0_kind(3), vb = v0_kind(4);
+  f->variant_p[vf + v] = f->variant_p[vb + v] = SmoothCfg<T, PP>::P;
+  f->smooth_add_v[vf + v] = f->smooth_add_v[vb + v] = nullptr;
+  f->smooth_mult_v[vf + v] = f->smooth_mult_plain_v[vf + v] = nullptr;
+  f->smooth_mult_batch_v[vf + v] = nullptr;
+  f->smooth_sweep_v[vf + v] = nullptr;
+  f->smooth_mult_v[vb + v] = f->smooth_mult_plain_v[vb + v] = nullptr;
+  f->smooth_mult_batch_v[vb + v] = nullptr;
+  f->smooth_sweep_v[vb + v] = nullptr;
+  if constexpr (kFewWarps<T, PP>) {
+    constexpr int Wm = warps_min(PP);
+    using CW = SmoothCfg<T, PP, Wm>;
+    if constexpr (CW::fits) {
+      f->smooth_mult_v[vf + v] = smooth_mult_launch<T, PP, false, Wm>;
+      f->smooth_mult_plain_v[vf + v] = smooth_mult_plain_launch<T, PP, false, Wm>;
+      f->smooth_mult_batch_v[vf + v] = smooth_mult_batch_launch<T, PP, false, Wm>;
+      f->smooth_sweep_v[vf + v] = smooth_sweep_launch<T, PP, false, Wm>;
+    }
+    if constexpr (CW::fits_bnd) {
+      f->smooth_mult_v[vb + v] = smooth_mult_launch<T, PP, true, Wm>;
+      f->smooth_mult_plain_v[vb + v] = smooth_mult_plain_launch<T, PP, true, Wm>;
+      f->smooth_mult_batch_v[vb + v] = smooth_mult_batch_launch<T, PP, true, Wm>;
+      f->smooth_sweep_v[vb + v] = smooth_sweep_launch<T, PP, true, Wm>;
+    }
+  }
+}
+
 template <typename T, int PP>
 void register_variant(KernelFns<T>* f, int v) {
   using C = SmoothCfg<T, PP>;
+  register_few_warps<T, PP>(f, v);
   f->variant_p[v] = C::P;
   f->variant_p[v + kQVariants] = C::P;
   f->variant_p[v + 2 * kQVariants] = C::P;

@@ -186,10 +186,14 @@ struct SweepGeom {
 // q = 1: G1 groups of 2, q = 2: G2 groups of 1, with G1 and G2 per (dim,
 // degree) so that the stages' lines fill whole warps; kind 0 the fused kernel,
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
-// kind 2 the Boundary kernel in one-warp blocks.  Kinds 1 and 2 serve the
-// multiplicative smoother only (smooth_add_v[3..8] stay null).
+// kind 2 the Boundary kernel in one-warp blocks, kinds 3 and 4 the fused and
+// the Boundary kernel in blocks of the fewest warps that run every stage
+// after the first in one round.  Kinds 1 to 4 serve the multiplicative
+// smoother only (smooth_add_v[3..14] stay null).
 constexpr int kQVariants = 3;
-constexpr int kSmoothVariants = 3 * kQVariants;
+constexpr int kSmoothKinds = 5;
+constexpr int kSmoothVariants = kSmoothKinds * kQVariants;
+constexpr int v0_kind(int kind) { return kind * kQVariants; }
 
 template <typename T>
 struct KernelFns {

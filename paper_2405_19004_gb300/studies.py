@@ -188,7 +188,7 @@ def smoother_point(vps, torch, d, k, L, prec, apps, peaks, tune=False, tune_cach
     t = e0.elapsed_time(e1) / 1e3 / apps
     patches = (2 ** L - 1) ** d
     var, ppb = P.vps_get_smooth_variant(L)
-    bnd = var // 3 >= 1
+    bnd = var // 3 in vps.BOUNDARY_KINDS
     fpp = smoother_flops_per_patch(d, k, bnd)
     flops = fpp * patches
     esz = 4 if prec == vps.VPS_FP32 else 8
