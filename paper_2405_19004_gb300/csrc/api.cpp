@@ -2316,53 +2316,61 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
   // 1) smoother variant per level and colour schedule: for each schedule
   //    (multiplicative smoother: programmatic dependent launches, the
   //    dataflow sweep, ordinary launches; additive: the handle's), the
-  //    fastest smoothing step of every level on the level's buffers; the
-  //    schedule whose levels' fastest steps add up to the least time wins
-  {
-    const bool mult = h->smoother == VPS_MULTIPLICATIVE;
-    const int scheds[3] = {VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP, VPS_SCHEDULE_PLAIN};
-    const int nsched = mult ? 3 : 1;
-    float best_total = 1e30f;
-    int best_sched = h->schedule;
-    int best_var[kMaxLevels + 1] = {};
-    for (int l = 1; l <= h->L; ++l) best_var[l] = h->smooth_var[l];
-    for (int si = 0; si < nsched; ++si) {
-      if (mult) h->schedule = scheds[si];
-      float total = 0.f;
-      int var_s[kMaxLevels + 1] = {};
-      for (int l = 1; l <= h->L; ++l) var_s[l] = h->smooth_var[l];
-      for (int l = 2; l <= h->L; ++l) {
-        float best = 1e30f;
-        int bestv = h->smooth_var[l];
-        for (int v = 0; v < kSmoothVariants; ++v) {
-          if (!variant_ok(h, v)) continue;
-          h->smooth_var[l] = v;
-          float ms = 0.f;
-          int rc = h->prec == VPS_FP64
-                       ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
-                                                                        (double*)h->xv[l], true); }, &ms)
-                       : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
-                                                                       (float*)h->xv[l], true); }, &ms);
-          if (rc) return rc;
-          if (ms < best * 0.98f) {  // prefer the earlier (smaller) variant on near ties
-            best = ms;
-            bestv = v;
-          }
+  //    fastest smoothing step of every level on the level's buffers.  The
+  //    schedule is chosen once the coarsest level is known (step 3): the one
+  //    whose fastest steps on the levels above the coarsest -- the levels a
+  //    V-cycle smooths -- add up to the least time.
+  const bool mult = h->smoother == VPS_MULTIPLICATIVE;
+  const int scheds[3] = {VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP, VPS_SCHEDULE_PLAIN};
+  const int nsched = mult ? 3 : 1;
+  float t_s[3][kMaxLevels + 1] = {};
+  int v_s[3][kMaxLevels + 1] = {};
+  for (int si = 0; si < nsched; ++si) {
+    if (mult) h->schedule = scheds[si];
+    for (int l = 1; l <= h->L; ++l) v_s[si][l] = h->smooth_var[l];
+    for (int l = 2; l <= h->L; ++l) {
+      float best = 1e30f;
+      int bestv = h->smooth_var[l];
+      for (int v = 0; v < kSmoothVariants; ++v) {
+        if (!variant_ok(h, v)) continue;
+        h->smooth_var[l] = v;
+        float ms = 0.f;
+        int rc = h->prec == VPS_FP64
+                     ? time_ms(h, 3, [&] { return smooth_step<double>(h, l, (const double*)h->bv[l],
+                                                                      (double*)h->xv[l], true); }, &ms)
+                     : time_ms(h, 3, [&] { return smooth_step<float>(h, l, (const float*)h->bv[l],
+                                                                     (float*)h->xv[l], true); }, &ms);
+        if (rc) return rc;
+        if (ms < best * 0.98f) {  // prefer the earlier (smaller) variant on near ties
+          best = ms;
+          bestv = v;
         }
-        var_s[l] = bestv;
-        h->smooth_var[l] = bestv;
-        total += best;
       }
+      v_s[si][l] = bestv;
+      t_s[si][l] = best;
+      h->smooth_var[l] = bestv;
+    }
+  }
+  if (int rc = check_waits(h)) return rc;
+  // the schedule for levels lc+1 .. L smoothed, with each level's fastest
+  // variant under it; returns its index in scheds
+  auto choose_schedule = [&](int lc) {
+    float best_total = 1e30f;
+    int best_si = 0;
+    for (int si = 0; si < nsched; ++si) {
+      float total = 0.f;
+      for (int l = std::max(2, lc + 1); l <= h->L; ++l) total += t_s[si][l];
       if (total < best_total * 0.99f) {  // prefer the earlier schedule on near ties
         best_total = total;
-        best_sched = h->schedule;
-        for (int l = 1; l <= h->L; ++l) best_var[l] = var_s[l];
+        best_si = si;
       }
     }
-    if (int rc = check_waits(h)) return rc;
-    h->schedule = best_sched;
-    for (int l = 1; l <= h->L; ++l) h->smooth_var[l] = best_var[l];
-  }
+    if (mult) h->schedule = scheds[best_si];
+    for (int l = 2; l <= h->L; ++l) h->smooth_var[l] = v_s[best_si][l];
+    drop_graphs(h);  // graphs captured under another schedule or variant
+    return best_si;
+  };
+  int sched_now = choose_schedule(1);
   // 2) operator tile structure per level where two exist: the faster
   //    residual b - A x on the level's buffers
   for (int l = 1; l <= h->L; ++l) {
@@ -2390,8 +2398,10 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     }
     h->op_var[l] = bestv;
   }
-  // 3) coarsest level: fastest full CG solve of a smooth right-hand side
-  {
+  // 3) coarsest level: fastest full CG solve of a smooth right-hand side;
+  //    then the colour schedule for the levels above it (step 1), and, if
+  //    that changed the schedule, the coarsest level once more under it
+  auto tune_coarse = [&]() -> int {
     const LevelGeom& g = h->geom[h->L];
     const int ni = g.n1 - 2;
     std::vector<double> b1d((size_t)h->dim * ni);
@@ -2455,6 +2465,12 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache) {
     if (int rc = setup_coarse(h, bestc)) return rc;
     h->coarse_coop = bestcoop;
     h->coarse_wide = bestwide;
+    return VPS_OK;
+  };
+  if (int rc = tune_coarse()) return rc;
+  if (choose_schedule(h->coarse) != sched_now) {
+    if (int rc = tune_coarse()) return rc;
+    choose_schedule(h->coarse);
   }
   if (cache_path) {
     for (int l = 1; l <= h->L; ++l) {
