@@ -1537,14 +1537,6 @@ apply_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict_
 // costs two barriers.  Halo recomputation: ((T+2K)/T)^2 in the z stage and
 // (T+2K)/T in the y stage, against ((T+2K)/T)^2 and (T+2K)/T with T = K*CT
 // small for cubic tiles.
-// Cells per block in z of the 3D operator (planes per block: kApplyZC * K).
-// For k >= 4 the FP64 and double-float operators (8-byte type) take one
-// cell of planes per block: twice the blocks spread more evenly over the
-// 152 SMs (4 % faster at 2^5 and 2^6 cells); the FP32 operator was measured
-// slower that way and keeps two.
-template <typename T>
-constexpr int kApplyZC = K >= 4 ? (sizeof(T) == 8 ? 1 : 2) : (K == 1 ? 8 : 4);
-
 struct Apply3Cfg {
   // cells per tile in x and y: a power of two, so that tiles of TX nodes
   // cover the nodes 0 .. n1-2 = k 2^l - 1 exactly (no ragged tiles)
@@ -1575,10 +1567,50 @@ constexpr bool kApply3C = sizeof(T) == 4 && K <= 4;
 // cells of planes per block of apply3c_kernel
 constexpr int kApply3CZ = K == 1 ? 8 : (K <= 3 ? 4 : 2);
 
+// z contraction of plane z (Q: the plane's position in its cell, which
+// selects the band) over the halo'd tile of apply3_kernel.
+template <typename T, bool ABS, int Q>
+__device__ __forceinline__ void apply3_zstage(const T* __restrict__ x, T* mZ, T* kZ, int x0, int y0,
+                                              int z, int n1, int px, int pz) {
+  using C = Apply3Cfg;
+  constexpr int BX = C::BX, RB = C::RB, NT = C::NT;
+  for (int u = threadIdx.x; u < BX * BX; u += NT) {
+    const int xx = u % BX, yy = u / BX;
+    const int gx = x0 - K + xx, gy = y0 - K + yy;
+    T am = T(0), ak = T(0);
+    if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
+      const T* col = x + gy * px + gx;
+      VPS_BAND_LOOP(Q, j) {
+        const int gz = z - K + j;
+        T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
+        if constexpr (ABS) v = fabs(v);
+        am = fma(coefM<T, ABS>(Q * n + j), v, am);
+        ak = fma(coefK<T, ABS>(Q * n + j), v, ak);
+      }
+    }
+    mZ[yy * RB + xx] = am;
+    kZ[yy * RB + xx] = ak;
+  }
+}
+
+// apply3_zstage<Qc> for a run-time plane position q < K.
+template <typename T, bool ABS, int Qc>
+__device__ __forceinline__ void apply3_zstage_at(int q, const T* __restrict__ x, T* mZ, T* kZ,
+                                                 int x0, int y0, int z, int n1, int px, int pz) {
+  if constexpr (Qc < K) {
+    if (q == Qc) apply3_zstage<T, ABS, Qc>(x, mZ, kZ, x0, y0, z, n1, px, pz);
+    else apply3_zstage_at<T, ABS, Qc + 1>(q, x, mZ, kZ, x0, y0, z, n1, px, pz);
+  }
+}
+
+// The per-plane 3D operator: a block takes the planes zpb * blockIdx.z ..
+// of its x-y tile (any run of planes: the launcher chooses zpb so that the
+// grid fills the resident block slots of the GPU in few rounds), the z
+// contraction of each plane dispatched by the plane's position in its cell.
 template <typename T, bool ABS = false>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
 apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict__ y, int n1,
-              int px, int pz, T scale) {
+              int px, int pz, T scale, int zpb) {
   using C = Apply3Cfg;
   constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1587,33 +1619,15 @@ apply3_kernel(const T* __restrict__ x, const T* __restrict__ bvec, T* __restrict
   T* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
   block_zero_faces<T>(y, n1, px, pz);
-  const int z0 = blockIdx.z * (kApplyZC<T> * K);  // a multiple of K
+  const int zb = blockIdx.z * zpb;
+  const int ze = min(zb + zpb, n1 - 1);  // plane n1-1 is zeroed by block_zero_faces
   int buf = 0;
-  for (int cz = 0; cz < kApplyZC<T>; ++cz) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const int z = z0 + cz * K + q;
-      if (z >= n1 - 1) break;  // uniform in the block; plane n1-1 is zeroed elsewhere
+  {
+#pragma unroll 1
+    for (int z = zb; z < ze; ++z) {
       T* mZ = zbuf + (2 * buf) * BX * RB;
       T* kZ = mZ + BX * RB;
-      // z contraction of plane z over the halo'd tile
-      for (int u = threadIdx.x; u < BX * BX; u += NT) {
-        const int xx = u % BX, yy = u / BX;
-        const int gx = x0 - K + xx, gy = y0 - K + yy;
-        T am = T(0), ak = T(0);
-        if (gx >= 0 && gx < n1 && gy >= 0 && gy < n1) {
-          const T* col = x + gy * px + gx;
-          VPS_BAND_LOOP(q, j) {
-            const int gz = z - K + j;
-            T v = (gz >= 0 && gz < n1) ? __ldg(col + gz * pz) : T(0);
-            if constexpr (ABS) v = fabs(v);
-            am = fma(coefM<T, ABS>(q * n + j), v, am);
-            ak = fma(coefK<T, ABS>(q * n + j), v, ak);
-          }
-        }
-        mZ[yy * RB + xx] = am;
-        kZ[yy * RB + xx] = ak;
-      }
+      apply3_zstage_at<T, ABS, 0>(z % K, x, mZ, kZ, x0, y0, z, n1, px, pz);
       __syncthreads();
       // y contraction: units (x over the halo, cell segment in y)
       for (int u = threadIdx.x; u < BX * CX; u += NT) {
@@ -1859,7 +1873,7 @@ __device__ __forceinline__ void df_zstage_at(int q, const float* __restrict__ xh
 template <int DUMMY>
 __global__ void __launch_bounds__(Apply3Cfg::NT, Apply3Cfg::MINB)
 apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
-                 double* __restrict__ y, int n1, int px, int pz, float scale) {
+                 double* __restrict__ y, int n1, int px, int pz, float scale, int zpb) {
   using C = Apply3Cfg;
   constexpr int TX = C::TX, BX = C::BX, RB = C::RB, CX = C::CX, NT = C::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1868,16 +1882,16 @@ apply3_df_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
   DF* WW = MM + TX * RB;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TX;
   block_zero_faces<double>(y, n1, px, pz);
-  const int z0 = blockIdx.z * (kApplyZC<double> * K);
+  // planes zpb * blockIdx.z .. (as in apply3_kernel)
+  const int zb = blockIdx.z * zpb;
+  const int ze = min(zb + zpb, n1 - 1);
   int buf = 0;
-  for (int cz = 0; cz < kApplyZC<double>; ++cz) {
+  {
 #pragma unroll 1
-    for (int q = 0; q < K; ++q) {
-      const int z = z0 + cz * K + q;
-      if (z >= n1 - 1) break;
+    for (int z = zb; z < ze; ++z) {
       DF* mZ = zbuf + (2 * buf) * BX * RB;
       DF* kZ = mZ + BX * RB;
-      df_zstage_at<0>(q, xh, xl, mZ, kZ, x0, y0, z, n1, px, pz);
+      df_zstage_at<0>(z % K, xh, xl, mZ, kZ, x0, y0, z, n1, px, pz);
       __syncthreads();
       for (int u = threadIdx.x; u < BX * CX; u += NT) {
         const int xx = u % BX, cy = u / BX;
@@ -2483,20 +2497,63 @@ cudaError_t smooth_add_launch(const LevelGeom& g, const ColourGeom& cg, const T*
   return cudaGetLastError();
 }
 
+// Planes per block of the per-plane 3D operators (apply3_kernel,
+// apply3_df_kernel) for `planes` planes and tiles_xy tiles per plane: a
+// launch takes about (rounds of resident blocks) x (planes per block), so
+// the zpb that minimises ceil(tiles_xy ceil(planes / zpb) / slots) zpb,
+// slots = the kernel's resident blocks per SM x SMs; on ties the most
+// planes per block (fewest blocks).  A fixed cell of planes per block left
+// the last round two-thirds full on 2^5 cells at k = 4 (512 blocks for 304
+// slots); 7 planes per block fill one round.
+template <typename KernT>
+int planes_per_block(KernT kern, size_t smem, int planes, int64_t tiles_xy, int* per_sm) {
+  if (*per_sm <= 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Apply3Cfg::NT, smem) !=
+            cudaSuccess ||
+        nb <= 0)
+      nb = 1;
+    *per_sm = nb;
+  }
+  const int64_t slots = (int64_t)(*per_sm) * sm_count();
+  int best = planes;
+  int64_t best_cost = INT64_MAX;
+  for (int zp = planes; zp >= 1; --zp) {
+    const int64_t blocks = tiles_xy * ((planes + zp - 1) / zp);
+    const int64_t cost = ((blocks + slots - 1) / slots) * zp;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = zp;
+    }
+  }
+  return best;
+}
+
+// Launch of apply3_kernel<T, ABS> over a level (tiles of TX x TX nodes in x
+// and y, runs of planes in z).
+template <typename T, bool ABS>
+cudaError_t apply3_launch(const LevelGeom& g, const T* x, const T* b, T* y, T scale,
+                          cudaStream_t s) {
+  using C3 = Apply3Cfg;
+  static int per_sm = 0;
+  const int span = g.n1 - 1;
+  const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
+  const int zpb = planes_per_block(apply3_kernel<T, ABS>, C3::smem<T>(), span, (int64_t)t * t,
+                                   &per_sm);
+  const unsigned tz = (unsigned)((span + zpb - 1) / zpb);
+  VPS_COUNT_LAUNCH();
+  apply3_kernel<T, ABS><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
+                                                                      (int)g.pz, scale, zpb);
+  return cudaGetLastError();
+}
+
 // Tiles cover the nodes 0 .. n1-2 of every direction; the upper boundary
 // layer (index n1-1) is zeroed by the kernel's blocks (block_zero_faces).
 // The per-plane 3D operator where the default is the cell-batched one.
 template <typename T>
 cudaError_t apply_alt_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
   if constexpr (DIM == 3 && kApply3C<T>) {
-    using C3 = Apply3Cfg;
-    const int span = g.n1 - 1;
-    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
-    VPS_COUNT_LAUNCH();
-    apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
-                                                                   (int)g.pz, T(g.h));
-    return cudaGetLastError();
+    return apply3_launch<T, false>(g, x, b, y, T(g.h), s);
   } else {
     (void)g; (void)x; (void)b; (void)y; (void)s;
     return cudaErrorNotSupported;
@@ -2507,17 +2564,15 @@ template <typename T>
 cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaStream_t s) {
   const int span = g.n1 - 1;
   if constexpr (DIM == 3) {
-    using C3 = Apply3Cfg;
-    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    VPS_COUNT_LAUNCH();
     if constexpr (kApply3C<T>) {
+      using C3 = Apply3Cfg;
+      const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
       const unsigned tz = (unsigned)((span + kApply3CZ * K - 1) / (kApply3CZ * K));
+      VPS_COUNT_LAUNCH();
       apply3c_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem_c<T>(), s>>>(x, b, y, g.n1, (int)g.px,
                                                                         (int)g.pz, T(g.h));
     } else {
-      const unsigned tz = (unsigned)((span + (kApplyZC<T> * K) - 1) / (kApplyZC<T> * K));
-      apply3_kernel<T><<<dim3(t, t, tz), C3::NT, C3::smem<T>(), s>>>(x, b, y, g.n1, (int)g.px,
-                                                                     (int)g.pz, T(g.h));
+      return apply3_launch<T, false>(g, x, b, y, T(g.h), s);
     }
   } else {
     using C = ApplyCfg;
@@ -2534,12 +2589,7 @@ cudaError_t apply_launch(const LevelGeom& g, const T* x, const T* b, T* y, cudaS
 cudaError_t apply_abs_launch(const LevelGeom& g, const double* x, double* y, cudaStream_t s) {
   const int span = g.n1 - 1;
   if constexpr (DIM == 3) {
-    using C3 = Apply3Cfg;
-    const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + (kApplyZC<double> * K) - 1) / (kApplyZC<double> * K));
-    VPS_COUNT_LAUNCH();
-    apply3_kernel<double, true><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(
-        x, nullptr, y, g.n1, (int)g.px, (int)g.pz, g.h);
+    return apply3_launch<double, true>(g, x, static_cast<const double*>(nullptr), y, g.h, s);
   } else {
     using C = ApplyCfg;
     const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
@@ -2555,13 +2605,16 @@ cudaError_t apply_df_launch(const LevelGeom& g, const float* xh, const float* xl
   const int span = g.n1 - 1;
   if constexpr (DIM == 3) {
     using C3 = Apply3Cfg;
+    static int per_sm = 0;
     const unsigned t = (unsigned)((span + C3::TX - 1) / C3::TX);
-    const unsigned tz = (unsigned)((span + (kApplyZC<double> * K) - 1) / (kApplyZC<double> * K));
+    const int zpb = planes_per_block(apply3_df_kernel<0>, C3::smem<double>(), span,
+                                     (int64_t)t * t, &per_sm);
+    const unsigned tz = (unsigned)((span + zpb - 1) / zpb);
     VPS_COUNT_LAUNCH();
     // g.h = 1 / 2^level: exact as a float
     apply3_df_kernel<0><<<dim3(t, t, tz), C3::NT, C3::smem<double>(), s>>>(xh, xl, y, g.n1,
                                                                           (int)g.px, (int)g.pz,
-                                                                          (float)g.h);
+                                                                          (float)g.h, zpb);
   } else {
     using C = ApplyCfg;
     const unsigned t = (unsigned)((span + C::TN - 1) / C::TN);
