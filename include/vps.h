@@ -313,7 +313,10 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
  *            first in one round (the first, whose lines are the most, in
  *            two): fewer threads per block, so more resident blocks and
  *            patches per SM (VPS_MULTIPLICATIVE handles only; a shape whose
- *            automatic block is already that small has no kind 3 or 4).
+ *            automatic block is already that small has no kind 3 or 4);
+ *   kind 5 (variant 15, degree 1 only): the colour pass as point
+ *            Gauss-Seidel (a Q1 patch has one interior DoF), one thread per
+ *            patch, 256 patches per block (VPS_MULTIPLICATIVE handles only).
  * A variant whose shared memory exceeds the GPU's limit for the handle's
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);

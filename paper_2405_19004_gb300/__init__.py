@@ -35,7 +35,7 @@ VPS_SCHEDULE_PLAIN, VPS_SCHEDULE_PDL, VPS_SCHEDULE_SWEEP = 0, 1, 2
 VPS_COARSE_PASSES, VPS_COARSE_COOPERATIVE, VPS_COARSE_WIDE_TILES = 0, 1, 2
 VPS_REQ_QUEUED, VPS_REQ_RUNNING, VPS_REQ_DONE, VPS_REQ_FAILED = 0, 1, 2, 3
 # smoother variants (vps_set_smooth_variant): variant = 3 * kind + block shape
-VPS_SMOOTH_VARIANTS = 15
+VPS_SMOOTH_VARIANTS = 18
 BOUNDARY_KINDS = (1, 2, 4)   # kinds whose kernel is the Boundary kernel of Section 3.2
 
 # C signatures: name -> (restype, argtypes)

@@ -1290,6 +1290,59 @@ smooth_add_kernel(const T* __restrict__ r, T* __restrict__ x, const T* __restric
   }
 }
 
+// ------------------------------------------------------ degree 1 (Q1)
+// For k = 1 a vertex patch has a single interior DoF, its vertex (m = 1):
+// the colour pass of the multiplicative smoother (Algorithm 3) is a
+// 2^d-colour point Gauss-Seidel pass, x_v += A_vv^-1 (b - A x)_v.  A block
+// first forms the 3^d stencil of the patch's interior row, the Kronecker
+// sum of the interior rows of the patch matrices (Ap, Mp: 1 x 3), in
+// shared memory; then one thread per patch of the colour evaluates the
+// local residual over its 3^d closure (3^d multiply-adds) and applies the
+// local solve of Eq. 2.14 with 1 x 1 factors, u = S^(2d) (d lambda)^-1 r.
+// Without the stages, barriers and staging of the general kernel the FP32
+// pass is bound by memory and the FP64 pass by its 3^d multiply-adds.
+constexpr int kQ1Threads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kQ1Threads)
+smooth_q1_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
+                 int px, int pz, ColourGeom cg, T bscale) {
+  constexpr int NS = DIM == 3 ? 27 : 9;
+  __shared__ T st[NS];  // st[(cz * 3 + cy) * 3 + cx] (2D: st[cy * 3 + cx])
+  if (threadIdx.x < NS) {
+    const int t = threadIdx.x;
+    const int cx = t % 3, cy = (t / 3) % 3, cz = t / 9;
+    const T ax = c_tab<T>.Ap[cx], mx = c_tab<T>.Mp[cx];
+    const T ay = c_tab<T>.Ap[cy], my = c_tab<T>.Mp[cy];
+    if constexpr (DIM == 3) {
+      const T az = c_tab<T>.Ap[cz], mz = c_tab<T>.Mp[cz];
+      st[t] = az * my * mx + mz * ay * mx + mz * my * ax;
+    } else {
+      st[t] = ay * mx + my * ax;
+    }
+  }
+  __syncthreads();
+  grid_dependency_wait();  // x and b are written by earlier kernels
+  const int64_t gp = blockIdx.x * (int64_t)kQ1Threads + threadIdx.x;
+  if (gp >= cg.npatch) return;
+  const T s2 = c_tab<T>.S[0] * c_tab<T>.S[0];
+  const T scale = DIM == 3 ? s2 * s2 * s2 * __ldg(inv_lam) : s2 * s2 * __ldg(inv_lam);
+  const int org = closure_origin((int)gp, cg, px, pz);
+  T acc = T(0);
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 3 : 1); ++cz) {
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      const T* row = x + org + cz * pz + cy * px;
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) acc = fma(st[(cz * 3 + cy) * 3 + cx], row[cx], acc);
+    }
+  }
+  const int c = org + (DIM == 3 ? pz : 0) + px + 1;  // the patch's vertex
+  const T r = fma(bscale, b[c], -acc);
+  x[c] = fma(scale, r, x[c]);
+}
+
 // -------------------------------------------------- inverse-matrix solve
 // x_I += scale * A_j^-1 r_I for every patch of one colour with the dense
 // precomputed inverse (one copy: the coefficients are constant), the
@@ -2456,6 +2509,29 @@ cudaError_t smooth_mult_plain_launch(const LevelGeom& g, const ColourGeom& cg, c
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t smooth_q1_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
+                             const T* inv_lam, cudaStream_t s) {
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + kQ1Threads - 1) / kQ1Threads;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
+  return launch_pdl(smooth_q1_kernel<T>, dim3((unsigned)grid), dim3(kQ1Threads), 0, s, b, x,
+                    inv_lam, (int)g.px, (int)g.pz, cg, bscale);
+}
+
+template <typename T>
+cudaError_t smooth_q1_plain_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
+                                   const T* inv_lam, cudaStream_t s) {
+  if (cg.npatch == 0) return cudaSuccess;
+  const int64_t grid = (cg.npatch + kQ1Threads - 1) / kQ1Threads;
+  const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
+  VPS_COUNT_LAUNCH();
+  smooth_q1_kernel<T><<<(unsigned)grid, kQ1Threads, 0, s>>>(b, x, inv_lam, (int)g.px, (int)g.pz,
+                                                            cg, bscale);
+  return cudaGetLastError();
+}
+
 template <typename T, int PP>
 cudaError_t resid_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, const T* x, T* r,
                          cudaStream_t s) {
@@ -2755,10 +2831,30 @@ void register_few_warps(KernelFns<T>* f, int v) {
   }
 }
 
+// Kind 5 (variant 15, degree 1 only): the point Gauss-Seidel form of the
+// multiplicative colour pass; multiplicative smoother only.
+template <typename T>
+void register_q1(KernelFns<T>* f, int v) {
+  const int vq = v0_kind(5) + v;
+  f->variant_p[vq] = 0;
+  f->smooth_add_v[vq] = nullptr;
+  f->smooth_mult_v[vq] = f->smooth_mult_plain_v[vq] = nullptr;
+  f->smooth_mult_batch_v[vq] = nullptr;
+  f->smooth_sweep_v[vq] = nullptr;
+  if constexpr (K == 1) {
+    if (v == 0) {
+      f->variant_p[vq] = kQ1Threads;
+      f->smooth_mult_v[vq] = smooth_q1_launch<T>;
+      f->smooth_mult_plain_v[vq] = smooth_q1_plain_launch<T>;
+    }
+  }
+}
+
 template <typename T, int PP>
 void register_variant(KernelFns<T>* f, int v) {
   using C = SmoothCfg<T, PP>;
   register_few_warps<T, PP>(f, v);
+  register_q1<T>(f, v);
   f->variant_p[v] = C::P;
   f->variant_p[v + kQVariants] = C::P;
   f->variant_p[v + 2 * kQVariants] = C::P;

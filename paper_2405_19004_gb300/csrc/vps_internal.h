@@ -188,10 +188,11 @@ struct SweepGeom {
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
 // kind 2 the Boundary kernel in one-warp blocks, kinds 3 and 4 the fused and
 // the Boundary kernel in blocks of the fewest warps that run every stage
-// after the first in one round.  Kinds 1 to 4 serve the multiplicative
-// smoother only (smooth_add_v[3..14] stay null).
+// after the first in one round, kind 5 (variant 15, degree 1 only) the
+// colour pass as point Gauss-Seidel, one thread per patch.  Kinds 1 to 5
+// serve the multiplicative smoother only (smooth_add_v[3..17] stay null).
 constexpr int kQVariants = 3;
-constexpr int kSmoothKinds = 5;
+constexpr int kSmoothKinds = 6;
 constexpr int kSmoothVariants = kSmoothKinds * kQVariants;
 constexpr int v0_kind(int kind) { return kind * kQVariants; }
 

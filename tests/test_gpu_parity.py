@@ -251,7 +251,7 @@ def test_every_smoother_variant_matches_oracle(d, k, l, prec):
         for c in range(2 ** d):
             P.vps_smooth_colour(l, c, bg, xg)
         assert rel_err(to_host(P, xg, l), ref) <= TOL[prec], v
-    assert kinds == ({0, 1, 2, 3, 4} if k <= 3 else {0, 1, 3, 4})
+    assert kinds == ({0, 1, 2, 3, 4, 5} if k == 1 else {0, 1, 2, 3, 4} if k <= 3 else {0, 1, 3, 4})
 
 
 def test_boundary_variants_are_multiplicative_only():

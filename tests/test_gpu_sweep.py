@@ -37,7 +37,7 @@ def _smooth(P, level, x0, b, schedule, steps=2):
 def _variants(P, level):
     """The smoother variants of `level` that have a sweep kernel (0-5, 9-14) and fit."""
     out = []
-    for v in list(range(6)) + list(range(9, vps.VPS_SMOOTH_VARIANTS)):
+    for v in list(range(6)) + list(range(9, 15)):
         try:
             P.vps_set_smooth_variant(level, v)
         except vps.VpsError:
