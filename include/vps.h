@@ -314,9 +314,10 @@ int vps_autotune(vps_handle h, const char* cache_path, int* from_cache);
  *            two): fewer threads per block, so more resident blocks and
  *            patches per SM (VPS_MULTIPLICATIVE handles only; a shape whose
  *            automatic block is already that small has no kind 3 or 4);
- *   kind 5 (variant 15, degree 1 only): the colour pass as point
- *            Gauss-Seidel (a Q1 patch has one interior DoF), one thread per
- *            patch, 256 patches per block (VPS_MULTIPLICATIVE handles only).
+ *   kind 5 (variant 15): the colour pass with one thread per patch, 256
+ *            patches per block -- degree 1 as point Gauss-Seidel (a Q1 patch
+ *            has one interior DoF); 2D degrees 2 and 3 (3: FP32 only) with
+ *            the whole patch in registers (VPS_MULTIPLICATIVE handles only).
  * A variant whose shared memory exceeds the GPU's limit for the handle's
  * (dim, degree, precision) is unavailable.  Errors: VPS_EINVAL. */
 int vps_set_smooth_variant(vps_handle h, int level, int variant);

@@ -1343,6 +1343,106 @@ smooth_q1_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict
   x[c] = fma(scale, r, x[c]);
 }
 
+// 2D, k = 2, 3: one thread per patch, the whole patch in registers (closure
+// n^2 = 25 or 49 values, interior m^2 = 9 or 25).  The same contractions as
+// smooth_mult_body in the same even/odd form -- M and A along y on the
+// interior rows, A_x (M_y x) + M_x (A_y x) along x, then S^T along x and
+// y, the eigenvalue scaling, S along y and x (Eq. 2.13/2.14) -- on register
+// arrays, with no shared memory and no barriers; lines that the block
+// kernel spreads over threads are here loops of one thread.
+template <typename T>
+__global__ void __launch_bounds__(kQ1Threads)
+smooth_patch2d_kernel(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv_lam,
+                      int px, int pz, ColourGeom cg, T bscale) {
+  static_assert(DIM == 2 && sizeof(T) > 0, "2D only");
+  grid_dependency_wait();  // x and b are written by earlier kernels
+  const int64_t gp = blockIdx.x * (int64_t)kQ1Threads + threadIdx.x;
+  if (gp >= cg.npatch) return;
+  const int org = closure_origin((int)gp, cg, px, pz);
+  // along y, column by column: my[o][c] = (M_y x)(o, c), ay[o][c] = (A_y x)(o, c)
+  T my[m][n], ay[m][n];
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    T v[n][1];
+#pragma unroll
+    for (int r = 0; r < n; ++r) v[r][0] = x[org + r * px + c];
+    T ev[KE][1], od[K][1];
+    split_closure<T, 1>(v, ev, od);
+#pragma unroll
+    for (int o = 0; o <= H; ++o) {
+      T em[1] = {T(0)}, ea[1] = {T(0)}, om[1] = {T(0)}, oa[1] = {T(0)};
+      row_even<T, 1, 0>(o, ev, em);
+      row_even<T, 1, 1>(o, ev, ea);
+      if (o < H) {
+        row_odd<T, 1, 0>(o, od, om);
+        row_odd<T, 1, 1>(o, od, oa);
+      }
+      my[o][c] = em[0] + om[0];
+      ay[o][c] = ea[0] + oa[0];
+      if (o < H) {
+        my[m - 1 - o][c] = em[0] - om[0];
+        ay[m - 1 - o][c] = ea[0] - oa[0];
+      }
+    }
+  }
+  // along x on each interior row: r = bscale b - (A_x my + M_x ay), then S^T along x
+  T w[m][m];  // w[oy][a]
+#pragma unroll
+  for (int oy = 0; oy < m; ++oy) {
+    T vm[n][1], va[n][1];
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+      vm[c][0] = my[oy][c];
+      va[c][0] = ay[oy][c];
+    }
+    T ex[KE][1], dx[K][1], ey[KE][1], dy[K][1];
+    split_closure<T, 1>(vm, ex, dx);
+    split_closure<T, 1>(va, ey, dy);
+    const T* brow = b + org + (oy + 1) * px + 1;
+    T rr[m][1];
+#pragma unroll
+    for (int o = 0; o <= H; ++o) {
+      T E[1] = {T(0)}, O[1] = {T(0)};
+      row_even<T, 1, 1>(o, ex, E);
+      row_even<T, 1, 0>(o, ey, E);
+      if (o < H) {
+        row_odd<T, 1, 1>(o, dx, O);
+        row_odd<T, 1, 0>(o, dy, O);
+      }
+      rr[o][0] = fma(bscale, brow[o], -(E[0] + O[0]));
+      if (o < H) rr[m - 1 - o][0] = fma(bscale, brow[m - 1 - o], -(E[0] - O[0]));
+    }
+    T tt[m][1];
+    st_line<T, 1>(rr, tt);
+#pragma unroll
+    for (int a = 0; a < m; ++a) w[oy][a] = tt[a][0];
+  }
+  // S^T along y, the scaling by 1/(lambda_a + lambda_b), S along y
+#pragma unroll
+  for (int a = 0; a < m; ++a) {
+    T col[m][1], ty[m][1], u[m][1];
+#pragma unroll
+    for (int oy = 0; oy < m; ++oy) col[oy][0] = w[oy][a];
+    st_line<T, 1>(col, ty);
+#pragma unroll
+    for (int be = 0; be < m; ++be) ty[be][0] *= __ldg(inv_lam + be * m + a);
+    s_line<T, 1>(ty, u);
+#pragma unroll
+    for (int oy = 0; oy < m; ++oy) w[oy][a] = u[oy][0];
+  }
+  // S along x and the update of the interior
+#pragma unroll
+  for (int oy = 0; oy < m; ++oy) {
+    T row[m][1], u[m][1];
+#pragma unroll
+    for (int a = 0; a < m; ++a) row[a][0] = w[oy][a];
+    s_line<T, 1>(row, u);
+    T* dst = x + org + (oy + 1) * px + 1;
+#pragma unroll
+    for (int o = 0; o < m; ++o) dst[o] = fma(T(1), u[o][0], dst[o]);
+  }
+}
+
 // -------------------------------------------------- inverse-matrix solve
 // x_I += scale * A_j^-1 r_I for every patch of one colour with the dense
 // precomputed inverse (one copy: the coefficients are constant), the
@@ -2509,6 +2609,14 @@ cudaError_t smooth_mult_plain_launch(const LevelGeom& g, const ColourGeom& cg, c
   return cudaGetLastError();
 }
 
+// The colour pass with one thread per patch (kind 5): smooth_q1_kernel for
+// k = 1, smooth_patch2d_kernel for 2D k = 2, 3.
+template <typename T>
+constexpr auto patch_thread_kernel() {
+  if constexpr (K == 1) return smooth_q1_kernel<T>;
+  else return smooth_patch2d_kernel<T>;
+}
+
 template <typename T>
 cudaError_t smooth_q1_launch(const LevelGeom& g, const ColourGeom& cg, const T* b, T* x,
                              const T* inv_lam, cudaStream_t s) {
@@ -2516,7 +2624,7 @@ cudaError_t smooth_q1_launch(const LevelGeom& g, const ColourGeom& cg, const T* 
   const int64_t grid = (cg.npatch + kQ1Threads - 1) / kQ1Threads;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  return launch_pdl(smooth_q1_kernel<T>, dim3((unsigned)grid), dim3(kQ1Threads), 0, s, b, x,
+  return launch_pdl(patch_thread_kernel<T>(), dim3((unsigned)grid), dim3(kQ1Threads), 0, s, b, x,
                     inv_lam, (int)g.px, (int)g.pz, cg, bscale);
 }
 
@@ -2527,8 +2635,8 @@ cudaError_t smooth_q1_plain_launch(const LevelGeom& g, const ColourGeom& cg, con
   const int64_t grid = (cg.npatch + kQ1Threads - 1) / kQ1Threads;
   const T bscale = DIM == 3 ? T(1.0 / g.h) : T(1);
   VPS_COUNT_LAUNCH();
-  smooth_q1_kernel<T><<<(unsigned)grid, kQ1Threads, 0, s>>>(b, x, inv_lam, (int)g.px, (int)g.pz,
-                                                            cg, bscale);
+  patch_thread_kernel<T>()<<<(unsigned)grid, kQ1Threads, 0, s>>>(b, x, inv_lam, (int)g.px,
+                                                                 (int)g.pz, cg, bscale);
   return cudaGetLastError();
 }
 
@@ -2831,8 +2939,13 @@ void register_few_warps(KernelFns<T>* f, int v) {
   }
 }
 
-// Kind 5 (variant 15, degree 1 only): the point Gauss-Seidel form of the
-// multiplicative colour pass; multiplicative smoother only.
+// Kind 5 (variant 15): the colour pass with one thread per patch -- the
+// point Gauss-Seidel form for k = 1, the patch in registers for 2D k = 2, 3
+// (FP32 only at k = 3, whose FP64 patch would not fit the registers);
+// multiplicative smoother only.
+template <typename T>
+constexpr bool kPatchThread = K == 1 || (DIM == 2 && (K == 2 || (K == 3 && sizeof(T) == 4)));
+
 template <typename T>
 void register_q1(KernelFns<T>* f, int v) {
   const int vq = v0_kind(5) + v;
@@ -2841,7 +2954,7 @@ void register_q1(KernelFns<T>* f, int v) {
   f->smooth_mult_v[vq] = f->smooth_mult_plain_v[vq] = nullptr;
   f->smooth_mult_batch_v[vq] = nullptr;
   f->smooth_sweep_v[vq] = nullptr;
-  if constexpr (K == 1) {
+  if constexpr (kPatchThread<T>) {
     if (v == 0) {
       f->variant_p[vq] = kQ1Threads;
       f->smooth_mult_v[vq] = smooth_q1_launch<T>;

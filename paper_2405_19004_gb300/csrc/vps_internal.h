@@ -188,8 +188,9 @@ struct SweepGeom {
 // kind 1 the Boundary kernel (x_I = A_j^-1 (b_I - A^IB x_B), Section 3.2),
 // kind 2 the Boundary kernel in one-warp blocks, kinds 3 and 4 the fused and
 // the Boundary kernel in blocks of the fewest warps that run every stage
-// after the first in one round, kind 5 (variant 15, degree 1 only) the
-// colour pass as point Gauss-Seidel, one thread per patch.  Kinds 1 to 5
+// after the first in one round, kind 5 (variant 15) the colour pass with
+// one thread per patch (degree 1: point Gauss-Seidel; 2D degrees 2, 3: the
+// patch in registers).  Kinds 1 to 5
 // serve the multiplicative smoother only (smooth_add_v[3..17] stay null).
 constexpr int kQVariants = 3;
 constexpr int kSmoothKinds = 6;
