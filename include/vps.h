@@ -281,11 +281,12 @@ int vps_get_coarse_solver(vps_handle h, int* solver);
  * smoother variant of every level (patches per thread block, the tuning
  * axis of Section 3.1.2) together with the colour schedule
  * (vps_set_colour_schedule: for each schedule the fastest variant of every
- * level, and the schedule whose fastest steps add up to the least time),
- * the operator tile structure of every level (vps_set_operator_variant),
- * and the coarsest level (vps_set_coarse_level) that gives the fastest CG
- * solve, each candidate with its faster coarse solver form
- * (vps_set_coarse_solver).  cache_path (may be NULL): a JSON file keyed by
+ * level; then the schedule whose fastest steps on the levels above the
+ * chosen coarsest level add up to the least time, the coarsest level being
+ * timed once more if that changes the schedule), the operator tile
+ * structure of every level (vps_set_operator_variant), and the coarsest
+ * level (vps_set_coarse_level) that gives the fastest CG solve, each
+ * candidate with its faster coarse solver form (vps_set_coarse_solver).  cache_path (may be NULL): a JSON file keyed by
  * (dim, degree, precision, smoother, level, smoothing steps) with the
  * smoother variant and operator tile structure of every level, the colour
  * schedule and the coarsest level; an entry found
